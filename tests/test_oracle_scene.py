@@ -1,0 +1,145 @@
+"""Scene-level pins of the oracle: convergence to the surface, agreement with a dense tessellation, and
+watertightness at shared patch edges (Sec. 3.4: only false positives).  CPU only."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_03510_gb300 import scenegen as sg
+
+RNG = np.random.default_rng(99)
+
+
+@pytest.fixture(scope="module")
+def scene2():
+    return sg.config_scene(2)
+
+
+def _hits_surface_point(s, out, rays, i):
+    pid = int(out["pid"][i])
+    f, _, _ = oracle.patch_frame(s.P[pid].astype(float), bool(s.types[pid]), float(out["u"][i]), float(out["v"][i]))
+    p = rays.o[i].astype(float) + out["t"][i] * rays.d[i].astype(float)
+    return np.linalg.norm(f - p), np.ptp(s.P[pid].astype(float), axis=0).max()
+
+
+def test_deep_leaves_converge_to_the_surface(scene2):
+    """At leaf depth 20 the leaf cell's surface point lies on the ray to within a few leaf sizes."""
+    L = 20
+    r = sg.random_rays(400, seed=3)
+    out = oracle.intersect(scene2.P, scene2.types, r.soa(), L=L)
+    hit = np.nonzero(out["pid"] != 0xFFFFFFFF)[0]
+    assert len(hit) > 200
+    for i in hit:
+        dist, ext = _hits_surface_point(scene2, out, r, i)
+        assert dist <= 8 * ext * 2.0 ** -L, (i, dist)
+
+
+def _mt(o, d, A, B, C):
+    """Moller-Trumbore, vectorised over triangles; returns t (inf where missed)."""
+    e1, e2 = B - A, C - A
+    pv = np.cross(d, e2)
+    det = np.einsum("ij,ij->i", e1, pv)
+    ok = np.abs(det) > 1e-300
+    inv = np.where(ok, 1.0 / np.where(ok, det, 1.0), 0.0)
+    tv = o - A
+    u = np.einsum("ij,ij->i", tv, pv) * inv
+    qv = np.cross(tv, e1)
+    v = (qv @ d) * inv
+    t = np.einsum("ij,ij->i", e2, qv) * inv
+    good = ok & (u >= 0) & (v >= 0) & (u + v <= 1) & (t > 0)
+    return np.where(good, t, np.inf)
+
+
+def _tessellate(g, greg, N):
+    us = np.linspace(0, 1, N + 1)
+    pts = np.array([[oracle.patch_frame(g, greg, u, v)[0] for u in us] for v in us])  # [v, u]
+    A = pts[:-1, :-1].reshape(-1, 3)
+    B = pts[:-1, 1:].reshape(-1, 3)
+    C = pts[1:, 1:].reshape(-1, 3)
+    D = pts[1:, :-1].reshape(-1, 3)
+    return A, B, C, D
+
+
+def test_agrees_with_dense_tessellation(scene2):
+    """Closest hit of a dense tessellation (256 x 256 quads per candidate patch, FP64 Moller-Trumbore)
+    agrees with the oracle's leaf at depth 12 within the chordal error plus the leaf size."""
+    L, N = 12, 256
+    cam = sg.pinhole_rays(48, 27)
+    out = oracle.intersect(scene2.P, scene2.types, cam.soa(), L=L, flags=True, delta=1e-3)
+    hit = np.nonzero((out["pid"] != 0xFFFFFFFF) & (out["flags"] == 0))[0]
+    pick = RNG.choice(hit, size=12, replace=False)
+    P = scene2.P.astype(float)
+    lo = np.where(scene2.types[:, None] == 1, P.min(1), P[:, :16].min(1))
+    hi = np.where(scene2.types[:, None] == 1, P.max(1), P[:, :16].max(1))
+    for i in pick:
+        o, d = cam.o[i].astype(float), cam.d[i].astype(float)
+        with np.errstate(divide="ignore"):
+            inv = 1.0 / d
+        ta, tb = (lo - o) * inv, (hi - o) * inv
+        t0 = np.minimum(ta, tb).max(1)
+        t1 = np.maximum(ta, tb).min(1)
+        cand = np.nonzero(t0 <= t1)[0]
+        best = np.inf
+        for c in cand:
+            A, B, C, D = _tessellate(P[c], bool(scene2.types[c]), N)
+            best = min(best, _mt(o, d, A, B, C).min(), _mt(o, d, A, C, D).min())
+        assert np.isfinite(best)
+        ext = np.ptp(P[out["pid"][i]], axis=0).max()
+        # chordal error of a 1/N grid on these gently curved patches, plus one leaf box
+        tol = ext * (4.0 / N ** 2 * 8 + 4 * 2.0 ** -L)
+        assert abs(out["t"][i] - best) <= tol, (i, out["t"][i], best, tol)
+        assert out["t"][i] <= best + 1e-12 + ext * 4.0 / N ** 2 * 8
+
+
+def test_rays_through_shared_edges_and_corners_never_miss():
+    """Sec. 3.4: the method only produces false positives, so rays through points on shared patch
+    boundaries of the closed cube-sphere always hit (watertightness)."""
+    s = sg.config_scene(1)
+    P = s.P.astype(float)
+    targets = []
+    for f in range(s.n):
+        for slots in [(0, 1, 2, 3), (3, 7, 11, 15), (15, 14, 13, 12), (12, 8, 4, 0)]:
+            b = P[f, list(slots)]
+            for t in (0.0, 0.25, 0.5, 0.75):
+                w = np.array([(1 - t) ** 3, 3 * t * (1 - t) ** 2, 3 * t * t * (1 - t), t ** 3])
+                targets.append(w @ b)
+    targets = np.array(targets)
+    o = RNG.normal(size=targets.shape)
+    o *= 3.0 / np.linalg.norm(o, axis=1, keepdims=True)
+    # keep origins on the outer side of the target so the ray enters the closed surface there
+    flip = np.einsum("ij,ij->i", o, targets) < 0
+    o[flip] *= -1
+    d = targets - o
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    n = len(targets)
+    rays = [o[:, 0], o[:, 1], o[:, 2], d[:, 0], d[:, 1], d[:, 2], np.zeros(n), np.full(n, np.inf)]
+    rays = [np.ascontiguousarray(a, dtype=np.float32) for a in rays]
+    out = oracle.intersect(s.P, s.types, rays, L=8)
+    assert (out["pid"] != 0xFFFFFFFF).all()
+
+
+def test_silhouette_flag_marks_rays_at_the_outline(scene2):
+    """Rays found by bisection at the hit/miss boundary are flagged as silhouette; rays far inside the
+    outline are not."""
+    o = np.array([0.0, 0.0, 3.0])
+    rays, inner = [], []
+    for ang in np.linspace(0, 2 * np.pi, 24, endpoint=False):
+        a, b = 0.0, 0.6   # image-plane radius: a hits, b misses
+        for _ in range(40):
+            m = 0.5 * (a + b)
+            d = np.array([m * np.cos(ang), m * np.sin(ang), -1.0])
+            d /= np.linalg.norm(d)
+            ray = [np.array([x], np.float32) for x in (*o, *d, 0.0, np.inf)]
+            hit = oracle.intersect(scene2.P, scene2.types, ray, L=8)["pid"][0] != 0xFFFFFFFF
+            a, b = (m, b) if hit else (a, m)
+        for rr in (a, 0.5 * a):
+            d = np.array([rr * np.cos(ang), rr * np.sin(ang), -1.0])
+            (rays if rr == a else inner).append(d / np.linalg.norm(d))
+    for group, expect in ((rays, True), (inner, False)):
+        d = np.array(group)
+        n = len(d)
+        soa = [np.full(n, o[0]), np.full(n, o[1]), np.full(n, o[2]), d[:, 0], d[:, 1], d[:, 2], np.zeros(n),
+               np.full(n, np.inf)]
+        out = oracle.intersect(scene2.P, scene2.types, [np.asarray(x, np.float32) for x in soa], L=8, flags=True,
+                               delta=1e-4)
+        sil = (out["flags"] & 4) != 0
+        assert sil.all() if expect else not sil.any()
