@@ -1,0 +1,310 @@
+"""Benchmark: closest-hit MRays/s of the 1536-patch cube-sphere workload (8x8 quads per face, radial noise
+amplitude 0.05 with 3 octaves, one Catmull-Clark refinement; 1920x1080 pinhole primary rays plus one
+generation of cosine-weighted diffuse rays from their hits; leaf depth 8; FP32).
+
+One step = one closest-hit launch over the primary batch plus one over the diffuse batch, inputs resident
+on the device, L2 flushed (256 MB write) before every timed step.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ccs|reference] [--variant plain]
+Under torchrun every rank runs its own copy of the workload (rays are independent; no collective on the
+data path) and rank 0 reports the whole-job rate over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import signal
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "closest-hit MRays/s (primary, diffuse) & % FP32 roofline, learned/batched vs plain"
+UNIT = "MRays/s"
+WORKLOAD = "cfg2: 1536-patch cube-sphere (8x8/face, noise 0.05, 3 oct, seed 1), 1920x1080 primary + diffuse, L=8"
+
+# FP32 operations per unit of work that the method itself performs (roofline):
+OPS_BVH_NODE = 34        # two slab tests
+OPS_SPLIT_BEZIER = 360   # de Casteljau split 144 + two 16-point boxes 180 + two slabs 34 + order 2
+OPS_SPLIT_GREGORY = 360 + 1130   # + Algorithm 2 bounds and Algorithm 1 crop of the lower patch
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
+    ap.add_argument("--variant", default="plain", choices=["plain"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--width", type=int, default=1920)
+    ap.add_argument("--height", type=int, default=1080)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.send_signal(signal.SIGTERM)
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        out.update(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+def build_workload(width, height, seed=1):
+    from paper_1811_03510_gb300 import scenegen as sg
+    s = sg.config_scene(2, seed=seed)
+    r = sg.pinhole_rays(width, height)
+    return s, r
+
+
+def fp32_peak_ops(n_sm: int, mhz: float) -> float:
+    """FP32 issue peak: SMs x 128 FP32 lanes x SM clock (one FMA, add, mul or min/max = one op)."""
+    return n_sm * 128 * mhz * 1e6
+
+
+def run_reference(args, rank, world):
+    """The oracle (FP64 C, explicit stack, all host cores) timed on bounded samples of the workload."""
+    import oracle
+    out = {"impl": "reference", "metric": METRIC, "unit": UNIT, "higher_is_better": True}
+    if rank != 0:
+        return None
+    s, r = build_workload(args.width, args.height)
+    # diffuse rays of the reference arm come from the oracle's own primary hits
+    from oracle.raygen import diffuse_rays
+    stride = 8
+    sub = r.subset(np.arange(0, r.n, stride))
+    o = oracle.intersect(s.P, s.types, sub.soa(), L=8)
+    d = diffuse_rays(s.P, s.types, sub.soa(), o, seed=1)
+    act = d[7] >= d[6]
+    dsub = [a[act] for a in d]
+    n_step = sub.n + int(act.sum())
+    times = []
+    threads = 0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        a = oracle.intersect(s.P, s.types, sub.soa(), L=8)
+        b = oracle.intersect(s.P, s.types, dsub, L=8)
+        dt = time.perf_counter() - t0
+        threads = a["threads"]
+        if k >= args.warmup:
+            times.append(dt)
+    T = float(np.sum(times))
+    value = n_step * args.steps / T / 1e6
+    out.update(value=value, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+               ms_per_step=1e3 * T / args.steps, scaling="weak", vs_baseline=None, dtype="f64",
+               data="synthetic", config={"workload": WORKLOAD, "sample": f"every {stride}th primary ray "
+                                         f"({sub.n}) + its {int(act.sum())} diffuse rays per step"},
+               cpu_baseline={"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"every {stride}th primary ray + its diffuse rays, {n_step} rays per step"},
+               e2e={"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+    return out
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ccs" else "gloo"
+        dist.init_process_group(backend)
+    if args.impl == "reference":
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    import torch
+    from paper_1811_03510_gb300 import build_ext, ccs
+
+    torch.cuda.set_device(local)
+    build_ext.build()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    s, r = build_workload(args.width, args.height)
+    scene = ccs.Scene(s.P, s.types)
+    prim = ccs.rays_to_device(r.soa(), dev)
+    n_prim = r.n
+    opts = ccs.make_opts(leaf_depth=8)
+    hits_p = ccs.alloc_hits(n_prim, dev)
+    ccs.ccs_intersect(scene.handle, prim, n_prim, hits_p, opts, stream)
+    # diffuse generation on the device from the primary hits, compacted to the active slots (setup)
+    dplanes = ccs.gen_diffuse(scene, prim, hits_p, seed=1, leaf_depth=8, offset_abs=1e-4, stream=stream)
+    torch.cuda.synchronize()
+    active = (dplanes[7] >= dplanes[6]).nonzero().squeeze(1)
+    diff = [p.index_select(0, active).contiguous() for p in dplanes]
+    n_diff = int(active.numel())
+    hits_d = ccs.alloc_hits(n_diff, dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        ccs.ccs_intersect(scene.handle, prim, n_prim, hits_p, opts, stream)
+        ccs.ccs_intersect(scene.handle, diff, n_diff, hits_d, opts, stream)
+
+    # algorithmic work per launch from the traversal counters (separate, untimed launches)
+    counts = {}
+    for name, rays, n, h in (("primary", prim, n_prim, hits_p), ("diffuse", diff, n_diff, hits_d)):
+        c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        ccs.ccs_intersect(scene.handle, rays, n, h, ccs.make_opts(leaf_depth=8, counters=c), stream)
+        torch.cuda.synchronize()
+        counts[name] = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
+    alg_ops = {k: v["bvh_nodes"] * OPS_BVH_NODE + v["bezier_splits"] * OPS_SPLIT_BEZIER
+               + v["gregory_splits"] * OPS_SPLIT_GREGORY for k, v in counts.items()}
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        ev[k][0].record(stream)
+        ccs.ccs_intersect(scene.handle, prim, n_prim, hits_p, opts, stream)
+        ev[k][1].record(stream)
+        ccs.ccs_intersect(scene.handle, diff, n_diff, hits_d, opts, stream)
+        ev[k][2].record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    t_prim = sum(a.elapsed_time(b) for a, b, _ in ev) / 1e3
+    t_diff = sum(b.elapsed_time(c) for _, b, c in ev) / 1e3
+    T = t_prim + t_diff
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([T], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        T = float(t.item())
+        dist.barrier()
+    st = ccs.ccs_scene_sync_status(scene.handle, stream)
+    assert st == ccs.CCS_OK, "traversal limit reached"
+
+    rays_per_step = n_prim + n_diff
+    value = rays_per_step * world * args.steps / T / 1e6
+
+    # end to end through the host-buffer entry point: pinned host rays in, hits out, every step
+    host_p = [p.cpu().pin_memory() for p in prim]
+    host_d = [p.cpu().pin_memory() for p in diff]
+    out_p = [torch.empty(n_prim, dtype=torch.float32).pin_memory() for _ in range(4)]
+    out_d = [torch.empty(n_diff, dtype=torch.float32).pin_memory() for _ in range(4)]
+    for _ in range(2):
+        ccs.ccs_intersect_host(scene.handle, host_p, n_prim, out_p, opts, stream)
+    te = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ccs.ccs_intersect_host(scene.handle, host_p, n_prim, out_p, opts, stream)
+        ccs.ccs_intersect_host(scene.handle, host_d, n_diff, out_d, opts, stream)
+        te.append(time.perf_counter() - t0)
+    e2e_value = rays_per_step * world * args.steps / sum(te) / 1e6
+
+    peak_max = fp32_peak_ops(n_sm, 2070.0)
+    ops_step = alg_ops["primary"] + alg_ops["diffuse"]
+    achieved = ops_step * args.steps / T
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "primary_rays": n_prim, "diffuse_rays": n_diff, "leaf_depth": 8,
+                   "variant": args.variant, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "primary_mrays_s": n_prim * args.steps / t_prim / 1e6,
+        "diffuse_mrays_s": n_diff * args.steps / t_diff / 1e6,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_max / 1e12, "unit": "Top/s (FP32)",
+                     "frac": achieved / peak_max, "traffic": None,
+                     "note": "algorithmic FP32 ops (BVH node 34, Bezier split 360, Gregory split 1490) from the "
+                             "kernel's traversal counters / event-timed launch time; peak = SMs x 128 lanes x 2070 MHz",
+                     "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None},
+        "counters": counts,
+        "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
+                   "samples": ck["samples"]},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * rays_per_step,
+                "d2h_bytes_per_step": 16 * rays_per_step},
+        "gpu_launches": 2 * args.steps,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        o = oracle.intersect(s.P, s.types, r.soa(), L=8)
+        dh = [p.cpu().numpy() for p in diff]
+        o2 = oracle.intersect(s.P, s.types, dh, L=8)
+        dt = time.perf_counter() - t0
+        res["cpu_baseline"] = {"value": rays_per_step / dt / 1e6, "unit": UNIT, "cores": o["threads"],
+                               "kind": "oracle", "sample": f"the full step: {n_prim} primary + {n_diff} diffuse rays, "
+                               f"FP64 oracle, {dt:.1f} s"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    scene.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,149 @@
+/*
+ * ccs.h -- C ABI of the GB300 (sm_103a) library for closest-hit ray intersection with Catmull-Clark
+ * subdivision surfaces given as bicubic Bezier (16 control points) and Gregory (20 control points)
+ * patches, after Binder & Keller, "Massively Parallel Stackless Ray Tracing of Catmull-Clark
+ * Subdivision Surfaces" (arXiv 1811.03510).
+ *
+ * Conventions shared by every entry point
+ *  - All pointers are plain host or device addresses; no framework types cross this boundary.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is enqueued
+ *    asynchronously on it unless the entry point says otherwise; caller-owned device buffers must stay
+ *    valid until that work completes.
+ *  - Every call returns a ccs_status.  On failure, ccs_last_error() returns a message for the calling
+ *    thread.  Errors detected on the device (traversal iteration cap reached) are latched in a status
+ *    word of the scene and returned by ccs_scene_sync_status().
+ *  - Rays and hits are structure-of-arrays float32 / uint32 planes with one element per ray.
+ *  - A miss is patch_id = 0xFFFFFFFF, t = +INF, u = v = 0.  Rays with NaN components or tmin > tmax
+ *    are misses, not errors.
+ *
+ * What a hit is (Sec. 3 and Algorithm 3 of the paper): the (u,v) domain of each patch is split
+ * alternately along u and v, starting with u, down to leaf cells of 2^-L x 2^-L; a node's box is the
+ * AABB of its control points (de Casteljau halves for Bezier patches, Sec. 3.1; the lower bounding
+ * patch raised by the displacement d of Algorithm 2 for Gregory patches, Sec. 3.2); a node's ray
+ * interval is its box's slab interval intersected with its parent's.  The hit is the leaf with the
+ * smallest key (entry distance t, patch id, cell index); u, v are the centre of that leaf cell.
+ */
+#ifndef CCS_H
+#define CCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CCS_OK = 0,
+    CCS_ERR_INVALID_ARG = 1,     /* null pointer, size out of range, bad option value */
+    CCS_ERR_CUDA = 2,            /* a CUDA runtime call failed; message in ccs_last_error() */
+    CCS_ERR_OOM = 3,             /* device or host allocation failed */
+    CCS_ERR_TRAVERSAL_LIMIT = 4, /* a ray hit the iteration cap; that ray was written as a miss */
+    CCS_ERR_NOT_BUILT = 5        /* intersect called before ccs_bvh_build */
+} ccs_status;
+
+typedef enum { CCS_BEZIER = 0, CCS_GREGORY = 1 } ccs_patch_type;
+
+typedef struct ccs_scene ccs_scene;   /* opaque; created and freed by the library */
+
+/* Ray batch: eight caller-owned float32 planes of n elements (device addresses for ccs_intersect,
+ * host addresses for ccs_intersect_host).  Directions need not be normalised; t is in units of d. */
+typedef struct {
+    const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+} ccs_rays;
+
+/* Hit output: caller-owned planes of n elements. */
+typedef struct {
+    float *t, *u, *v;
+    uint32_t *patch_id;
+} ccs_hits;
+
+/* Launch and method options.  Zero-initialised fields take the defaults given in brackets. */
+typedef struct {
+    uint32_t leaf_depth;      /* L, splits per axis of the (u,v) domain, 1..15 [8] */
+    uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
+    uint32_t blocks_per_sm;   /* resident blocks per SM of the persistent launch [4] */
+    uint32_t chunk;           /* rays taken per warp from the global work queue, multiple of 32 [32] */
+    uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
+    uint32_t flags;           /* CCS_TRACE_* bits */
+    uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
+} ccs_trace_opts;
+
+#define CCS_TRACE_COUNT 1u          /* accumulate traversal counters into opts->counters */
+#define CCS_NUM_COUNTERS 8          /* bvh nodes, bezier splits, gregory splits, leaves, backtracks,
+                                       re-descent levels, pruned siblings, pairs */
+
+typedef struct {
+    uint32_t bins;            /* SAH bins per axis, 4..64 [16] */
+} ccs_bvh_params;
+
+/* Create a scene from n_patches patches.
+ * x, y, z: control points, 20 float32 slots per patch, patch-major: x[20*p + s].  Slots 0..15 are the
+ *   4x4 grid, slot 4*j + i with i along u and j along v (corner p_00 at (u,v) = (0,0)).  For Gregory
+ *   patches (Sec. 3.2) slots 5, 6, 9, 10 (inner points (1,1), (2,1), (1,2), (2,2)) hold p^u and slots
+ *   16..19 hold p^v in the same order; p^u is the point that the v = 0 / v = 1 edges use, i.e. the inner
+ *   point is p^v + h (p^u - p^v) with h_11 = u/(u+v), h_21 = (1-u)/((1-u)+v), h_12 = u/(u+1-v),
+ *   h_22 = (1-u)/((1-u)+(1-v)) (the convention of Algorithm 2).  Bezier patches ignore slots 16..19.
+ * types: n_patches bytes, CCS_BEZIER or CCS_GREGORY.
+ * device_ptrs: 0 if x, y, z, types are host addresses, 1 if device addresses.
+ * The library copies the data into its own device store (patch records anchored at their box centre,
+ * Sec. 3.4); the caller keeps ownership of its arrays.  n_patches may be 0 (every ray misses).
+ * Blocks until the copy has finished.  Errors: INVALID_ARG (null pointers, n_patches > 2^26),
+ * OOM, CUDA. */
+ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, const float *z, const uint8_t *types,
+                            uint32_t n_patches, int device_ptrs, void *stream);
+
+/* Replace the control points (same layout, same patch count and types) from device addresses,
+ * asynchronously on `stream`; a following ccs_bvh_refit updates the hierarchy.  Graph-capturable. */
+ccs_status ccs_scene_update_points(ccs_scene *scene, const float *x, const float *y, const float *z, void *stream);
+
+ccs_status ccs_scene_destroy(ccs_scene *scene);
+
+/* Binary BVH over whole-patch boxes (AABB of the 16 or 20 control points; convex hull property,
+ * Sec. 3.1), built on the host with binned SAH (Sec. 4), one patch per leaf, and uploaded.  Uses the
+ * points given at creation (or copied back after an update).  Blocks.  params may be NULL. */
+ccs_status ccs_bvh_build(ccs_scene *scene, const ccs_bvh_params *params);
+
+/* Recompute every box of the hierarchy bottom-up from the current control points, keeping its
+ * topology.  Asynchronous on `stream`, graph-capturable. */
+ccs_status ccs_bvh_refit(ccs_scene *scene, void *stream);
+
+/* Closest hit of n rays (Algorithm 3 per candidate patch of a BVH traversal; see the file comment for
+ * the exact answer).  rays, hits: device addresses, caller-owned.  opts may be NULL (defaults).
+ * Asynchronous on `stream`.  n may be 0.  Errors: INVALID_ARG, NOT_BUILT, CUDA. */
+ccs_status ccs_intersect(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                         const ccs_trace_opts *opts, void *stream);
+
+/* Same answer as ccs_intersect, for rays and hits in host memory (pinned memory gives full copy
+ * bandwidth): copies the rays to a device staging buffer owned by the scene, intersects, copies the
+ * hits back, and synchronises `stream` before returning. */
+ccs_status ccs_intersect_host(ccs_scene *scene, const ccs_rays *host_rays, uint32_t n, ccs_hits *host_hits,
+                              const ccs_trace_opts *opts, void *stream);
+
+/* Wait for `stream`, then return and clear the scene's latched device status (CCS_OK or
+ * CCS_ERR_TRAVERSAL_LIMIT). */
+ccs_status ccs_scene_sync_status(ccs_scene *scene, void *stream);
+
+/* Number of patches and of BVH nodes of a scene (host-side values). */
+ccs_status ccs_scene_info(const ccs_scene *scene, uint32_t *n_patches, uint32_t *n_nodes);
+
+/* Secondary rays of a wavefront tracer (input generation, not part of the intersection): for every
+ * slot i with a hit, a cosine-weighted diffuse ray leaves the surface point f(u_i, v_i) of the hit
+ * patch (Gregory patches reduced at (u, v)), offset along the normal (flipped against the incoming
+ * direction) by offset_abs + 2 * 2^-L * L1(diagonal of the patch box), which stays outside the hit
+ * leaf box (Sec. 3.3 offsets by the L1 size of the last box).  Direction from two PCG32 draws
+ * (pcg32_srandom_r(seed, i)), orthonormal basis of Duff et al. 2017.  Slots without a hit get the
+ * empty interval tmin = 1, tmax = 0 (they miss).  in_rays (for the incoming direction), hits and
+ * out_rays are device planes of n elements; out_rays planes are written (const is cast away).
+ * Asynchronous on `stream`. */
+ccs_status ccs_gen_diffuse(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
+                           uint64_t seed, uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *ccs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CCS_H */

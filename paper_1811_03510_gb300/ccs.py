@@ -1,0 +1,284 @@
+"""Python binding of libccs (include/ccs.h): argument marshalling only, every step runs in the CUDA
+library.  Device buffers are passed as torch tensors (their data_ptr()) or raw integer addresses;
+streams as torch.cuda.Stream or raw handles.  There is no fallback: if libccs.so is missing, every
+call raises."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build_ext
+
+CCS_OK = 0
+CCS_ERR_INVALID_ARG = 1
+CCS_ERR_CUDA = 2
+CCS_ERR_OOM = 3
+CCS_ERR_TRAVERSAL_LIMIT = 4
+CCS_ERR_NOT_BUILT = 5
+CCS_BEZIER = 0
+CCS_GREGORY = 1
+CCS_TRACE_COUNT = 1
+CCS_NUM_COUNTERS = 8
+COUNTER_NAMES = ("bvh_nodes", "bezier_splits", "gregory_splits", "leaves", "backtracks", "redescent_levels",
+                 "pruned_siblings", "pairs")
+MISS = 0xFFFFFFFF
+
+_STATUS = {0: "CCS_OK", 1: "CCS_ERR_INVALID_ARG", 2: "CCS_ERR_CUDA", 3: "CCS_ERR_OOM",
+           4: "CCS_ERR_TRAVERSAL_LIMIT", 5: "CCS_ERR_NOT_BUILT"}
+
+
+class CcsError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ccs_rays(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("ox", "oy", "oz", "dx", "dy", "dz", "tmin", "tmax")]
+
+
+class ccs_hits(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("t", "u", "v", "patch_id")]
+
+
+class ccs_trace_opts(ctypes.Structure):
+    _fields_ = [("leaf_depth", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
+
+
+class ccs_bvh_params(ctypes.Structure):
+    _fields_ = [("bins", ctypes.c_uint32)]
+
+
+_lib = None
+
+# name -> argtypes; every function returns ccs_status (int) except ccs_last_error
+_SIGS = {
+    "ccs_scene_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_void_p, ctypes.c_uint32, ctypes.c_int, ctypes.c_void_p],
+    "ccs_scene_update_points": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_scene_destroy": [ctypes.c_void_p],
+    "ccs_bvh_build": [ctypes.c_void_p, ctypes.POINTER(ccs_bvh_params)],
+    "ccs_bvh_refit": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_intersect": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.POINTER(ccs_hits),
+                      ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_intersect_host": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.POINTER(ccs_hits),
+                           ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_scene_sync_status": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_gen_diffuse": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
+                        ctypes.c_uint64, ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays), ctypes.c_void_p],
+    "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
+}
+
+
+def lib_path() -> str:
+    return build_ext.LIB
+
+
+def lib():
+    """Load libccs.so (built by build_ext.build()); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = build_ext.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libccs.so not built ({path}); run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        L.ccs_last_error.argtypes = []
+        L.ccs_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def declared_symbols():
+    """Names of the functions declared in include/*.h."""
+    import glob
+    import re
+    names = []
+    for h in sorted(glob.glob(os.path.join(build_ext.INCLUDE, "*.h"))):
+        src = open(h).read()
+        names += re.findall(r"^\s*(?:ccs_status|const char \*)\s*(ccs_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def _check(status: int):
+    if status != CCS_OK:
+        raise CcsError(status, lib().ccs_last_error().decode())
+
+
+def _ptr(x) -> int:
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)
+
+
+def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, chunk=0, iter_cap=0, counters=None) -> ccs_trace_opts:
+    o = ccs_trace_opts()
+    o.leaf_depth = leaf_depth
+    o.block_threads = block_threads
+    o.blocks_per_sm = blocks_per_sm
+    o.chunk = chunk
+    o.iter_cap = iter_cap
+    o.flags = CCS_TRACE_COUNT if counters is not None else 0
+    o.counters = _ptr(counters) if counters is not None else None
+    return o
+
+
+def rays_struct(planes) -> ccs_rays:
+    return ccs_rays(*[_ptr(p) for p in planes])
+
+
+def hits_struct(planes) -> ccs_hits:
+    return ccs_hits(*[_ptr(p) for p in planes])
+
+
+# ------------------------------------------------------------------ entry points (same names as the C ABI)
+
+def ccs_scene_create(x, y, z, types, n_patches: int, device_ptrs: bool, stream=None) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ccs_scene_create(ctypes.byref(h), _ptr(x), _ptr(y), _ptr(z), _ptr(types), n_patches,
+                                  1 if device_ptrs else 0, _stream(stream)))
+    return h.value
+
+
+def ccs_scene_update_points(scene: int, x, y, z, stream=None):
+    _check(lib().ccs_scene_update_points(scene, _ptr(x), _ptr(y), _ptr(z), _stream(stream)))
+
+
+def ccs_scene_destroy(scene: int):
+    _check(lib().ccs_scene_destroy(scene))
+
+
+def ccs_bvh_build(scene: int, bins: int = 16):
+    p = ccs_bvh_params(bins)
+    _check(lib().ccs_bvh_build(scene, ctypes.byref(p)))
+
+
+def ccs_bvh_refit(scene: int, stream=None):
+    _check(lib().ccs_bvh_refit(scene, _stream(stream)))
+
+
+def ccs_intersect(scene: int, rays, n: int, hits, opts: ccs_trace_opts | None = None, stream=None):
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    _check(lib().ccs_intersect(scene, ctypes.byref(r), n, ctypes.byref(h), ctypes.byref(opts) if opts else None,
+                               _stream(stream)))
+
+
+def ccs_intersect_host(scene: int, rays, n: int, hits, opts: ccs_trace_opts | None = None, stream=None):
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    _check(lib().ccs_intersect_host(scene, ctypes.byref(r), n, ctypes.byref(h),
+                                    ctypes.byref(opts) if opts else None, _stream(stream)))
+
+
+def ccs_gen_diffuse(scene: int, in_rays, hits, n: int, seed: int, leaf_depth: int, offset_abs: float, out_rays,
+                    stream=None):
+    r = in_rays if isinstance(in_rays, ccs_rays) else rays_struct(in_rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    o = out_rays if isinstance(out_rays, ccs_rays) else rays_struct(out_rays)
+    _check(lib().ccs_gen_diffuse(scene, ctypes.byref(r), ctypes.byref(h), n, seed, leaf_depth, offset_abs,
+                                 ctypes.byref(o), _stream(stream)))
+
+
+def gen_diffuse(scene: "Scene", rays_dev, hits, seed: int, leaf_depth: int = 8, offset_abs: float = 1e-4,
+                stream=None):
+    """Diffuse rays for every slot (inactive slots have tmin > tmax); returns eight device planes."""
+    import torch
+    n = int(rays_dev[0].numel())
+    o = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    d = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    tmin = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    tmax = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    planes = [o[:n], o[n:2 * n], o[2 * n:], d[:n], d[n:2 * n], d[2 * n:], tmin, tmax]
+    ccs_gen_diffuse(scene.handle, rays_dev, hits, n, seed, leaf_depth, offset_abs, planes, stream)
+    return planes
+
+
+def ccs_scene_sync_status(scene: int, stream=None) -> int:
+    """Returns CCS_OK or CCS_ERR_TRAVERSAL_LIMIT (does not raise for the latter)."""
+    st = lib().ccs_scene_sync_status(scene, _stream(stream))
+    if st not in (CCS_OK, CCS_ERR_TRAVERSAL_LIMIT):
+        _check(st)
+    return st
+
+
+def ccs_scene_info(scene: int):
+    a, b = ctypes.c_uint32(), ctypes.c_uint32()
+    _check(lib().ccs_scene_info(scene, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def ccs_last_error() -> str:
+    return lib().ccs_last_error().decode()
+
+
+# ------------------------------------------------------------------ small conveniences over the entry points
+
+class Scene:
+    """Owns a ccs_scene handle built from host arrays P [n, 20, 3] float32 and types [n] uint8."""
+
+    def __init__(self, P, types, bins: int = 16, stream=None):
+        import numpy as np
+        P = np.ascontiguousarray(P, dtype=np.float32)
+        self.n = int(P.shape[0])
+        x = np.ascontiguousarray(P[..., 0]).reshape(-1)
+        y = np.ascontiguousarray(P[..., 1]).reshape(-1)
+        z = np.ascontiguousarray(P[..., 2]).reshape(-1)
+        t = np.ascontiguousarray(types, dtype=np.uint8)
+        self.handle = ccs_scene_create(x.ctypes.data, y.ctypes.data, z.ctypes.data, t.ctypes.data, self.n, False,
+                                       stream)
+        ccs_bvh_build(self.handle, bins)
+
+    def close(self):
+        if self.handle:
+            ccs_scene_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rays_to_device(rays_soa, device="cuda"):
+    """Eight host float32 planes -> list of contiguous device tensors."""
+    import numpy as np
+    import torch
+    return [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device) for a in rays_soa]
+
+
+def alloc_hits(n: int, device="cuda"):
+    import torch
+    return [torch.empty(n, dtype=torch.float32, device=device), torch.empty(n, dtype=torch.float32, device=device),
+            torch.empty(n, dtype=torch.float32, device=device), torch.empty(n, dtype=torch.int32, device=device)]
+
+
+def hits_to_numpy(hits):
+    import numpy as np
+    t, u, v, p = [h.cpu().numpy() for h in hits]
+    return dict(t=t, u=u, v=v, pid=p.view(np.uint32))
+
+
+def intersect(scene: Scene, rays_dev, opts: ccs_trace_opts | None = None, stream=None):
+    """Allocate hit planes and intersect device rays; returns the four hit tensors (pid as int32 bits)."""
+    n = int(rays_dev[0].numel())
+    hits = alloc_hits(n, rays_dev[0].device)
+    ccs_intersect(scene.handle, rays_dev, n, hits, opts, stream)
+    return hits

@@ -1,0 +1,312 @@
+// C ABI of libccs (declared in include/ccs.h): scene store, BVH build/refit, intersect launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "bvh_build.h"
+#include "ccs_internal.h"
+
+namespace ccs {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+}  // namespace ccs
+
+using namespace ccs;
+
+#define CCS_CUDA(call)                                                                 \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));             \
+            return e_ == cudaErrorMemoryAllocation ? CCS_ERR_OOM : CCS_ERR_CUDA;       \
+        }                                                                              \
+    } while (0)
+
+#define CCS_ARG(cond, msg)                  \
+    do {                                    \
+        if (!(cond)) {                      \
+            set_error(msg);                 \
+            return CCS_ERR_INVALID_ARG;     \
+        }                                   \
+    } while (0)
+
+static const uint32_t kMaxPatches = 1u << 26;
+
+namespace {
+
+void free_scene(ccs_scene *s)
+{
+    if (!s) return;
+    cudaFree(s->d_rec);
+    cudaFree(s->d_leaf_box);
+    cudaFree(s->d_types);
+    cudaFree(s->d_nodes);
+    cudaFree(s->d_leaf_parent);
+    cudaFree(s->d_refit_flags);
+    cudaFree(s->d_work);
+    cudaFree(s->d_stage);
+    delete s;
+}
+
+ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
+{
+    c.leaf_depth = o && o->leaf_depth ? o->leaf_depth : 8;
+    c.block_threads = o && o->block_threads ? o->block_threads : 128;
+    c.blocks_per_sm = o && o->blocks_per_sm ? o->blocks_per_sm : 4;
+    c.chunk = o && o->chunk ? o->chunk : 32;
+    c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
+    c.flags = o ? o->flags : 0;
+    c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
+    CCS_ARG(c.leaf_depth >= 1 && c.leaf_depth <= (uint32_t)kMaxLeafDepth, "leaf_depth must be in 1..15");
+    CCS_ARG(c.block_threads % 32 == 0 && c.block_threads >= 32 && c.block_threads <= 128,
+            "block_threads must be a multiple of 32 in 32..128");
+    CCS_ARG(c.blocks_per_sm >= 1 && c.blocks_per_sm <= 64, "blocks_per_sm must be in 1..64");
+    CCS_ARG(c.chunk % 32 == 0 && c.chunk >= 32 && c.chunk <= 4096, "chunk must be a multiple of 32 in 32..4096");
+    CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
+    return CCS_OK;
+}
+
+ccs_status check_rays(const ccs_rays *r, const ccs_hits *h)
+{
+    CCS_ARG(r && h, "rays and hits must not be NULL");
+    CCS_ARG(r->ox && r->oy && r->oz && r->dx && r->dy && r->dz && r->tmin && r->tmax, "a ray plane is NULL");
+    CCS_ARG(h->t && h->u && h->v && h->patch_id, "a hit plane is NULL");
+    return CCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ccs_last_error(void) { return g_err.c_str(); }
+
+ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, const float *z, const uint8_t *types,
+                            uint32_t n_patches, int device_ptrs, void *stream)
+{
+    CCS_ARG(out, "out must not be NULL");
+    *out = nullptr;
+    CCS_ARG(n_patches <= kMaxPatches, "n_patches above 2^26");
+    CCS_ARG(n_patches == 0 || (x && y && z && types), "point or type array is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    ccs_scene *sc = new (std::nothrow) ccs_scene();
+    if (!sc) {
+        set_error("host allocation failed");
+        return CCS_ERR_OOM;
+    }
+    sc->n = n_patches;
+    ccs_status st = CCS_OK;
+    do {
+        cudaError_t e;
+        if ((e = cudaGetDevice(&sc->device)) != cudaSuccess) break;
+        if ((e = cudaDeviceGetAttribute(&sc->num_sms, cudaDevAttrMultiProcessorCount, sc->device)) != cudaSuccess) break;
+        const size_t np = (size_t)n_patches * 20;
+        sc->hx.resize(np);
+        sc->hy.resize(np);
+        sc->hz.resize(np);
+        sc->htypes.resize(n_patches);
+        if ((e = cudaMalloc(&sc->d_work, 64)) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(sc->d_work, 0, 64, s)) != cudaSuccess) break;
+        if (n_patches) {
+            const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+            if ((e = cudaMemcpy(sc->hx.data(), x, np * 4, k)) != cudaSuccess) break;
+            if ((e = cudaMemcpy(sc->hy.data(), y, np * 4, k)) != cudaSuccess) break;
+            if ((e = cudaMemcpy(sc->hz.data(), z, np * 4, k)) != cudaSuccess) break;
+            if ((e = cudaMemcpy(sc->htypes.data(), types, n_patches, k)) != cudaSuccess) break;
+            for (uint32_t i = 0; i < n_patches; ++i) sc->htypes[i] = sc->htypes[i] ? 1 : 0;
+            if ((e = cudaMalloc(&sc->d_rec, (size_t)n_patches * kRecF4 * sizeof(float4))) != cudaSuccess) break;
+            if ((e = cudaMalloc(&sc->d_leaf_box, (size_t)n_patches * 2 * sizeof(float4))) != cudaSuccess) break;
+            if ((e = cudaMalloc(&sc->d_types, n_patches)) != cudaSuccess) break;
+            float *tmp = nullptr;
+            if ((e = cudaMalloc(&tmp, np * 3 * 4)) != cudaSuccess) break;
+            cudaMemcpyAsync(tmp, sc->hx.data(), np * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(tmp + np, sc->hy.data(), np * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(tmp + 2 * np, sc->hz.data(), np * 4, cudaMemcpyHostToDevice, s);
+            cudaMemcpyAsync(sc->d_types, sc->htypes.data(), n_patches, cudaMemcpyHostToDevice, s);
+            e = launch_repack(tmp, tmp + np, tmp + 2 * np, sc->d_types, n_patches, sc->d_rec, sc->d_leaf_box, s);
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            cudaFree(tmp);
+            if (e == cudaSuccess) e = e2;
+            if (e != cudaSuccess) break;
+        }
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) break;
+        *out = sc;
+        return CCS_OK;
+    } while (0);
+    cudaError_t e = cudaGetLastError();
+    set_error(std::string("scene creation failed: ") + cudaGetErrorString(e));
+    st = e == cudaErrorMemoryAllocation ? CCS_ERR_OOM : CCS_ERR_CUDA;
+    free_scene(sc);
+    return st;
+}
+
+ccs_status ccs_scene_destroy(ccs_scene *scene)
+{
+    if (!scene) return CCS_OK;
+    free_scene(scene);
+    return CCS_OK;
+}
+
+ccs_status ccs_scene_info(const ccs_scene *scene, uint32_t *n_patches, uint32_t *n_nodes)
+{
+    CCS_ARG(scene, "scene is NULL");
+    if (n_patches) *n_patches = scene->n;
+    if (n_nodes) *n_nodes = scene->n_nodes;
+    return CCS_OK;
+}
+
+ccs_status ccs_bvh_build(ccs_scene *sc, const ccs_bvh_params *params)
+{
+    CCS_ARG(sc, "scene is NULL");
+    int bins = params && params->bins ? (int)params->bins : 16;
+    CCS_ARG(bins >= 4 && bins <= 64, "bins must be in 4..64");
+    const uint32_t n = sc->n;
+    std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n);
+    for (uint32_t p = 0; p < n; ++p) {
+        const int np = sc->htypes[p] ? 20 : 16;
+        const float *pl[3] = {&sc->hx[20 * (size_t)p], &sc->hy[20 * (size_t)p], &sc->hz[20 * (size_t)p]};
+        for (int c = 0; c < 3; ++c) {
+            float a = pl[c][0], b = pl[c][0];
+            for (int k = 1; k < np; ++k) {
+                a = std::min(a, pl[c][k]);
+                b = std::max(b, pl[c][k]);
+            }
+            lo[3 * (size_t)p + c] = a;
+            hi[3 * (size_t)p + c] = b;
+        }
+    }
+    BvhHost bvh;
+    std::string err;
+    if (!build_bvh(lo, hi, n, bins, bvh, err)) {
+        set_error(err);
+        return CCS_ERR_INVALID_ARG;
+    }
+    cudaFree(sc->d_nodes);
+    cudaFree(sc->d_leaf_parent);
+    cudaFree(sc->d_refit_flags);
+    sc->d_nodes = nullptr;
+    sc->d_leaf_parent = nullptr;
+    sc->d_refit_flags = nullptr;
+    sc->n_nodes = (uint32_t)(bvh.nodes.size() / 16);
+    sc->built = false;
+    if (sc->n_nodes) {
+        CCS_CUDA(cudaMalloc(&sc->d_nodes, bvh.nodes.size() * sizeof(float)));
+        CCS_CUDA(cudaMemcpy(sc->d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float), cudaMemcpyHostToDevice));
+        CCS_CUDA(cudaMalloc(&sc->d_leaf_parent, (size_t)n * sizeof(int)));
+        CCS_CUDA(cudaMemcpy(sc->d_leaf_parent, bvh.leaf_parent.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
+        CCS_CUDA(cudaMalloc(&sc->d_refit_flags, (size_t)sc->n_nodes * sizeof(uint32_t)));
+    }
+    sc->built = true;
+    return CCS_OK;
+}
+
+ccs_status ccs_scene_update_points(ccs_scene *sc, const float *x, const float *y, const float *z, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    CCS_ARG(sc->n == 0 || (x && y && z), "point array is NULL");
+    CCS_CUDA(launch_repack(x, y, z, sc->d_types, sc->n, sc->d_rec, sc->d_leaf_box, (cudaStream_t)stream));
+    return CCS_OK;
+}
+
+ccs_status ccs_bvh_refit(ccs_scene *sc, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    if (!sc->built) {
+        set_error("ccs_bvh_refit before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    CCS_CUDA(launch_refit(sc->d_nodes, sc->d_leaf_parent, sc->d_leaf_box, sc->d_refit_flags, sc->n, sc->n_nodes,
+                          (cudaStream_t)stream));
+    return CCS_OK;
+}
+
+ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                         const ccs_trace_opts *opts, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    ccs_status st = check_rays(rays, hits);
+    if (st != CCS_OK) return st;
+    if (!sc->built) {
+        set_error("ccs_intersect before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    LaunchCfg cfg;
+    if ((st = fill_cfg(opts, cfg)) != CCS_OK) return st;
+    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
+    DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    return CCS_OK;
+}
+
+ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs_hits *hh, const ccs_trace_opts *opts,
+                              void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    ccs_status st = check_rays(hr, hh);
+    if (st != CCS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t need = (size_t)n * 12 * sizeof(float);
+    if (need > sc->stage_bytes) {
+        CCS_CUDA(cudaStreamSynchronize(s));
+        cudaFree(sc->d_stage);
+        sc->d_stage = nullptr;
+        sc->stage_bytes = 0;
+        CCS_CUDA(cudaMalloc(&sc->d_stage, need));
+        sc->stage_bytes = need;
+    }
+    float *b = static_cast<float *>(sc->d_stage);
+    const float *src[8] = {hr->ox, hr->oy, hr->oz, hr->dx, hr->dy, hr->dz, hr->tmin, hr->tmax};
+    for (int k = 0; k < 8; ++k) CCS_CUDA(cudaMemcpyAsync(b + (size_t)k * n, src[k], (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    ccs_rays dr = {b, b + n, b + 2 * (size_t)n, b + 3 * (size_t)n, b + 4 * (size_t)n, b + 5 * (size_t)n,
+                   b + 6 * (size_t)n, b + 7 * (size_t)n};
+    ccs_hits dh = {b + 8 * (size_t)n, b + 9 * (size_t)n, b + 10 * (size_t)n,
+                   reinterpret_cast<uint32_t *>(b + 11 * (size_t)n)};
+    if ((st = ccs_intersect(sc, &dr, n, &dh, opts, stream)) != CCS_OK) return st;
+    void *dst[4] = {hh->t, hh->u, hh->v, hh->patch_id};
+    for (int k = 0; k < 4; ++k)
+        CCS_CUDA(cudaMemcpyAsync(dst[k], b + (size_t)(8 + k) * n, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    CCS_CUDA(cudaStreamSynchronize(s));
+    return CCS_OK;
+}
+
+ccs_status ccs_gen_diffuse(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
+                           uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
+{
+    CCS_ARG(sc && out, "scene and out_rays must not be NULL");
+    ccs_status st = check_rays(in, hits);
+    if (st != CCS_OK) return st;
+    CCS_ARG(out->ox && out->dx && out->tmin && out->tmax, "an output plane is NULL");
+    CCS_ARG(out->oy == out->ox + n && out->oz == out->ox + 2 * (size_t)n && out->dy == out->dx + n &&
+                out->dz == out->dx + 2 * (size_t)n,
+            "output origin and direction planes must each be one contiguous block of 3n floats");
+    CCS_ARG(leaf_depth >= 1 && leaf_depth <= (uint32_t)kMaxLeafDepth, "leaf_depth must be in 1..15");
+    if (n == 0) return CCS_OK;
+    DevRays dr{in->ox, in->oy, in->oz, in->dx, in->dy, in->dz, in->tmin, in->tmax};
+    DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
+    CCS_CUDA(launch_gen_diffuse(sc->d_rec, sc->d_leaf_box, sc->n, dr, dh, n, seed, (int)leaf_depth, offset_abs,
+                                const_cast<float *>(out->ox), const_cast<float *>(out->dx),
+                                const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), (cudaStream_t)stream));
+    return CCS_OK;
+}
+
+ccs_status ccs_scene_sync_status(ccs_scene *sc, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    CCS_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t w = 0;
+    CCS_CUDA(cudaMemcpy(&w, sc->d_work + 1, 4, cudaMemcpyDeviceToHost));
+    if (w) {
+        CCS_CUDA(cudaMemset(sc->d_work + 1, 0, 4));
+        set_error("a ray reached the traversal iteration cap and was written as a miss");
+        return CCS_ERR_TRAVERSAL_LIMIT;
+    }
+    return CCS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// Internal declarations shared by the host API and the kernels of libccs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ccs.h"
+
+namespace ccs {
+
+// One patch record = 16 float4 = 256 bytes, control points relative to the record's anchor:
+//   [0..3] x of the 16 grid slots (slot 4*j + i), [4..7] y, [8..11] z,
+//   [12] x of p^v (inner slots (1,1),(2,1),(1,2),(2,2)), [13] y, [14] z,
+//   [15] anchor xyz (box centre), w = 1 for Gregory, 0 for Bezier.
+constexpr int kRecF4 = 16;
+
+// BVH node = 4 float4 = 64 bytes (both children's boxes stored in the parent):
+//   [0] (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
+//   [1] (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+//   [2] (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
+//   [3] (child0, child1, parent, slot in parent) as int bits; child >= 0 is a node index,
+//       child < 0 is the leaf of patch ~child.  Node 0 is the root (parent -1).
+constexpr int kNodeF4 = 4;
+
+constexpr int kMaxLeafDepth = 15;
+constexpr int kNumCounters = CCS_NUM_COUNTERS;
+
+struct LaunchCfg {
+    uint32_t leaf_depth, block_threads, blocks_per_sm, chunk, iter_cap, flags;
+    unsigned long long *counters;
+};
+
+struct DevScene {
+    const float4 *rec;       // n_patches records
+    const float4 *nodes;     // n_nodes nodes
+    uint32_t n_patches, n_nodes;
+};
+
+struct DevRays {
+    const float *ox, *oy, *oz, *dx, *dy, *dz, *tmin, *tmax;
+};
+
+struct DevHits {
+    float *t, *u, *v;
+    uint32_t *pid;
+};
+
+// kernels (intersect.cu, scene.cu)
+cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
+                          float4 *rec, float4 *leaf_box, cudaStream_t s);
+cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,
+                         uint32_t n_patches, uint32_t n_nodes, cudaStream_t s);
+cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
+                             const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s);
+
+cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
+                               const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
+                               float *tmin, float *tmax, cudaStream_t s);
+
+void set_error(const std::string &msg);
+
+}  // namespace ccs
+
+struct ccs_scene {
+    uint32_t n = 0;
+    int device = 0;
+    int num_sms = 0;
+    std::vector<float> hx, hy, hz;     // host copy of the input points (BVH build)
+    std::vector<uint8_t> htypes;
+    float4 *d_rec = nullptr;           // patch records
+    float4 *d_leaf_box = nullptr;      // 2 float4 per patch: (lo.xyz, 0), (hi.xyz, 0)
+    uint8_t *d_types = nullptr;
+    float4 *d_nodes = nullptr;
+    int *d_leaf_parent = nullptr;      // per patch: (node << 1) | slot
+    uint32_t *d_refit_flags = nullptr; // per node arrival counters of the refit
+    uint32_t n_nodes = 0;
+    bool built = false;
+    uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word
+    // host-buffer path staging
+    void *d_stage = nullptr;
+    size_t stage_bytes = 0;
+};

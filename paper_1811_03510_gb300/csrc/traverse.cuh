@@ -1,0 +1,542 @@
+// Device routines of the closest-hit path: ray/box slab test, de Casteljau split with child boxes,
+// Gregory lower patch and displacement (Algorithm 2 with the crop of Algorithm 1), the per-patch
+// stackless bit-trail traversal (Algorithm 3) and the BVH traversal.  Shared by every kernel that
+// intersects, so plain, learned and batched launches compute bit-identical answers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ccs_internal.h"
+
+namespace ccs {
+
+#define CCS_DEV __device__ __forceinline__
+
+constexpr uint32_t kMissId = 0xFFFFFFFFu;
+
+CCS_DEV float min3f(float a, float b, float c)
+{
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+CCS_DEV float max3f(float a, float b, float c)
+{
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
+}
+
+// de Casteljau midpoint: rounding of a + b, then an exact halving.  The explicit intrinsics keep the
+// compiler from contracting or reassociating, so every path that computes a node computes it the same way.
+CCS_DEV float mid(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
+
+// Robustness factor on the far slab distance (Ize 2013, 1 + 2 gamma_3 rounded up to a float).
+constexpr float kFarScale = 1.00000048f;
+
+struct RayF {
+    float ix, iy, iz;      // 1 / d (tiny components clamped so that the products stay finite)
+    float oix, oiy, oiz;   // o * inv for the frame in use (world for the BVH, patch-anchored inside a patch)
+};
+
+CCS_DEV float safe_inv(float d)
+{
+    const float eps = 1e-20f;
+    return 1.0f / (fabsf(d) < eps ? copysignf(eps, d) : d);
+}
+
+// Ray interval inside box [lo, hi], intersected with [c0, c1]: t0 = max(c0, near), t1 = min(c1, far).
+// Monotone in the box bounds, so a box inside another gives an interval inside the other's.
+CCS_DEV void slab(const RayF &r, float lox, float loy, float loz, float hix, float hiy, float hiz, float c0,
+                  float c1, float &t0, float &t1)
+{
+    float ax = fmaf(lox, r.ix, -r.oix), bx = fmaf(hix, r.ix, -r.oix);
+    float ay = fmaf(loy, r.iy, -r.oiy), by = fmaf(hiy, r.iy, -r.oiy);
+    float az = fmaf(loz, r.iz, -r.oiz), bz = fmaf(hiz, r.iz, -r.oiz);
+    float tn = max3f(fminf(ax, bx), fminf(ay, by), fminf(az, bz));
+    float tf = min3f(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
+    t0 = fmaxf(tn, c0);
+    t1 = fminf(__fmul_rn(tf, kFarScale), c1);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Control-point grid in registers: g[c*16 + a*4 + b], c = component, split axis a.  After a split the
+// kept half is written transposed (the next split is along the other parameter), so every split
+// runs the same code (Sec. 3.5: transposing the control grid removes the divergence of the axis).
+// At even tree levels a = u index i and b = v index j; at odd levels a = j and b = i.
+// ------------------------------------------------------------------------------------------------
+
+struct Box6 {
+    float lx, ly, lz, hx, hy, hz;
+};
+
+// Boxes of both de Casteljau halves along a; when keep >= 0 also replace g by the kept half (0 = lower,
+// 1 = upper), transposed.  Split and selection are fused so both see the same midpoints.
+template <bool BOXES>
+CCS_DEV void split_grid(float (&g)[48], Box6 &L, Box6 &R, int keep)
+{
+    float lmin[3], lmax[3], rmin[3], rmax[3];
+    float ng[48];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lmin[c] = rmin[c] = __int_as_float(0x7f800000);
+        lmax[c] = rmax[c] = -__int_as_float(0x7f800000);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float b0 = g[c * 16 + 0 * 4 + b], b1 = g[c * 16 + 1 * 4 + b];
+            const float b2 = g[c * 16 + 2 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
+            const float m01 = mid(b0, b1), m12 = mid(b1, b2), m23 = mid(b2, b3);
+            const float m012 = mid(m01, m12), m123 = mid(m12, m23);
+            const float m = mid(m012, m123);
+            if (BOXES) {
+                lmin[c] = min3f(lmin[c], b0, m01);
+                lmin[c] = min3f(lmin[c], m012, m);
+                lmax[c] = max3f(lmax[c], b0, m01);
+                lmax[c] = max3f(lmax[c], m012, m);
+                rmin[c] = min3f(rmin[c], m, m123);
+                rmin[c] = min3f(rmin[c], m23, b3);
+                rmax[c] = max3f(rmax[c], m, m123);
+                rmax[c] = max3f(rmax[c], m23, b3);
+            }
+            const bool up = keep == 1;
+            ng[c * 16 + b * 4 + 0] = up ? m : b0;
+            ng[c * 16 + b * 4 + 1] = up ? m123 : m01;
+            ng[c * 16 + b * 4 + 2] = up ? m23 : m012;
+            ng[c * 16 + b * 4 + 3] = up ? b3 : m;
+        }
+    }
+    if (BOXES) {
+        L = {lmin[0], lmin[1], lmin[2], lmax[0], lmax[1], lmax[2]};
+        R = {rmin[0], rmin[1], rmin[2], rmax[0], rmax[1], rmax[2]};
+    }
+    if (keep >= 0) {
+#pragma unroll
+        for (int k = 0; k < 48; ++k) g[k] = ng[k];
+    }
+}
+
+// Root grid of a Bezier record at level 0 (a = i along u): g[c][i][j] = slot 4j + i.
+CCS_DEV void load_grid(const float4 *__restrict__ rec, float (&g)[48])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldg(rec + c * 4 + q);   // slots 4q .. 4q+3: j = q, i = 0..3
+            g[c * 16 + 0 * 4 + q] = v.x;
+            g[c * 16 + 1 * 4 + q] = v.y;
+            g[c * 16 + 2 * 4 + q] = v.z;
+            g[c * 16 + 3 * 4 + q] = v.w;
+        }
+    }
+}
+
+// Canonical control points of the Bezier node reached by `path` at `level`: de Casteljau descent from
+// the root, one half per level.  Identical arithmetic to the descent of the traversal, so a node's
+// points (and boxes) do not depend on how it was reached (the paper recomputes with Algorithm 1
+// after backtracking; that is cheaper for deep nodes but makes boxes path-dependent in FP32).
+CCS_DEV void redescend(const float4 *__restrict__ rec, uint32_t path, int level, float (&g)[48])
+{
+    load_grid(rec, g);
+    Box6 dummy;
+    for (int k = 0; k < level; ++k) split_grid<false>(g, dummy, dummy, (path >> k) & 1u);
+}
+
+// Domain of the node (path, level): positions on the 2^L grid of leaf cells.
+CCS_DEV uint32_t compact_even_bits(uint32_t x)
+{
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
+}
+
+// u and v cell coordinates (first split = most significant bit) of a node, on the 2^L grid
+CCS_DEV void path_cells(uint32_t path, int L, uint32_t &cu, uint32_t &cv)
+{
+    cu = __brev(compact_even_bits(path)) >> (32 - L);
+    cv = __brev(compact_even_bits(path >> 1)) >> (32 - L);
+}
+
+CCS_DEV void node_domain(uint32_t path, int level, int L, float &u0, float &u1, float &v0, float &v1)
+{
+    uint32_t cu, cv;
+    path_cells(path & ((1u << level) - 1u), L, cu, cv);
+    const int su = (level + 1) >> 1, sv = level >> 1;
+    const float cell = __int_as_float((127 - L) << 23);   // 2^-L, exact
+    u0 = (float)cu * cell;
+    v0 = (float)cv * cell;
+    u1 = u0 + __int_as_float((127 - su) << 23);           // + 2^-su, exact
+    v1 = v0 + __int_as_float((127 - sv) << 23);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Gregory patches (Sec. 3.2): Algorithm 2 with the crop of Algorithm 1, in FP32.
+// Weight of p^u (Algorithm 2's convention): h_11 = u/(u+v), h_21 = (1-u)/((1-u)+v),
+// h_12 = u/(u+(1-v)), h_22 = (1-u)/((1-u)+(1-v)); each is monotone in u and in v, so its extremes over
+// a domain sit at two opposite corners.  0/0 cannot occur on a non-empty domain here.
+// ------------------------------------------------------------------------------------------------
+
+CCS_DEV float ratio(float a, float b)
+{
+    const float s = a + b;
+    return s == 0.0f ? 0.5f : __fdiv_rn(a, s);
+}
+
+CCS_DEV void bern4(float t, float (&B)[4], float (&D)[4])
+{
+    const float s = 1.0f - t;
+    B[0] = s * s * s;
+    B[1] = 3.0f * t * s * s;
+    B[2] = 3.0f * t * t * s;
+    B[3] = t * t * t;
+    D[0] = -3.0f * s * s;
+    D[1] = 3.0f * s * (s - 2.0f * t);
+    D[2] = 3.0f * t * (2.0f * s - t);
+    D[3] = 3.0f * t * t;
+}
+
+CCS_DEV float wbar1(float t0, float t1)   // max of B_1^3 = 3t(1-t)^2 over [t0, t1]
+{
+    const float w = (t0 <= (1.0f / 3.0f) && t1 >= (1.0f / 3.0f)) ? (1.0f / 3.0f) : (t1 <= (1.0f / 3.0f) ? t1 : t0);
+    return 3.0f * w * (1.0f - w) * (1.0f - w);
+}
+
+CCS_DEV float wbar2(float t0, float t1)   // max of B_2^3 = 3t^2(1-t) over [t0, t1]
+{
+    const float w = (t0 <= (2.0f / 3.0f) && t1 >= (2.0f / 3.0f)) ? (2.0f / 3.0f) : (t1 < (2.0f / 3.0f) ? t1 : t0);
+    return 3.0f * w * w * (1.0f - w);
+}
+
+// Lower bounding patch of the Gregory record restricted to [u0,u1]x[v0,v1], cropped (Algorithm 1),
+// written into g oriented for a split at `level`; d receives the displacement of the upper bound.
+CCS_DEV void gregory_node(const float4 *__restrict__ rec, float u0, float u1, float v0, float v1, int level,
+                          float (&g)[48], float &dx, float &dy, float &dz)
+{
+    // extreme weights of the four inner points: (1,1), (2,1), (1,2), (2,2)
+    const float hA[4] = {ratio(u0, v1), ratio(1.0f - u0, v0), ratio(u1, 1.0f - v1), ratio(1.0f - u1, 1.0f - v0)};
+    const float hB[4] = {ratio(u1, v0), ratio(1.0f - u1, v1), ratio(u0, 1.0f - v0), ratio(1.0f - u0, 1.0f - v1)};
+    const float wu1 = wbar1(u0, u1), wu2 = wbar2(u0, u1), wv1 = wbar1(v0, v1), wv2 = wbar2(v0, v1);
+    const float wk[4] = {wu1 * wv1, wu2 * wv1, wu1 * wv2, wu2 * wv2};
+    const int inner[4] = {5, 6, 9, 10};
+    float Bu0[4], Du0[4], Bu1[4], Du1[4], Bv0[4], Dv0[4], Bv1[4], Dv1[4];
+    bern4(u0, Bu0, Du0);
+    bern4(u1, Bu1, Du1);
+    bern4(v0, Bv0, Dv0);
+    bern4(v1, Bv1, Dv1);
+    const float Du = (u1 - u0) * (1.0f / 3.0f), Dv = (v1 - v0) * (1.0f / 3.0f), Duv = Du * Dv;
+    const bool odd = level & 1;
+    float dcomp[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float p[16];
+        const float4 *pl = rec + c * 4;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v = __ldg(pl + q);
+            p[4 * q + 0] = v.x;
+            p[4 * q + 1] = v.y;
+            p[4 * q + 2] = v.z;
+            p[4 * q + 3] = v.w;
+        }
+        const float4 pv4 = __ldg(rec + 12 + c);
+        const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+        float dd = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float pu = p[inner[k]];
+            const float a = fmaf(hA[k], pu - pv[k], pv[k]);
+            const float b = fmaf(hB[k], pu - pv[k], pv[k]);
+            p[inner[k]] = fminf(a, b);
+            dd = fmaf(wk[k], fabsf(a - b), dd);
+        }
+        dcomp[c] = dd;
+        // rows j: A = sum_i B_i(u) p_ij, E = sum_i B_i'(u) p_ij at u0 and u1
+        float A0[4], E0[4], A1[4], E1[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float a0 = 0, e0 = 0, a1 = 0, e1 = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float pij = p[4 * j + i];
+                a0 = fmaf(Bu0[i], pij, a0);
+                e0 = fmaf(Du0[i], pij, e0);
+                a1 = fmaf(Bu1[i], pij, a1);
+                e1 = fmaf(Du1[i], pij, e1);
+            }
+            A0[j] = a0; E0[j] = e0; A1[j] = a1; E1[j] = e1;
+        }
+        // corner values: f, f_u, f_v, f_uv at (u0,v0), (u1,v0), (u0,v1), (u1,v1)
+        float f[4], fu[4], fv[4], fuv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float *A = (k & 1) ? A1 : A0;
+            const float *E = (k & 1) ? E1 : E0;
+            const float *Bv = (k & 2) ? Bv1 : Bv0;
+            const float *Dv_ = (k & 2) ? Dv1 : Dv0;
+            float a = 0, b = 0, cc = 0, e = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                a = fmaf(Bv[j], A[j], a);
+                b = fmaf(Bv[j], E[j], b);
+                cc = fmaf(Dv_[j], A[j], cc);
+                e = fmaf(Dv_[j], E[j], e);
+            }
+            f[k] = a; fu[k] = b; fv[k] = cc; fuv[k] = e;
+        }
+        // Algorithm 1: q_{i,j} at slot 4j + i
+        float q[16];
+        q[0] = f[0];
+        q[3] = f[1];
+        q[12] = f[2];
+        q[15] = f[3];
+        q[1] = fmaf(Du, fu[0], q[0]);
+        q[2] = fmaf(-Du, fu[1], q[3]);
+        q[4] = fmaf(Dv, fv[0], q[0]);
+        q[7] = fmaf(Dv, fv[1], q[3]);
+        q[8] = fmaf(-Dv, fv[2], q[12]);
+        q[11] = fmaf(-Dv, fv[3], q[15]);
+        q[13] = fmaf(Du, fu[2], q[12]);
+        q[14] = fmaf(-Du, fu[3], q[15]);
+        q[5] = fmaf(Duv, fuv[0], fmaf(Dv, fv[0], q[1]));
+        q[6] = fmaf(-Duv, fuv[1], fmaf(-Du, fu[1], q[7]));
+        q[9] = fmaf(-Duv, fuv[2], fmaf(-Dv, fv[2], q[13]));
+        q[10] = fmaf(Duv, fuv[3], fmaf(-Dv, fv[3], q[14]));
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) g[c * 16 + a * 4 + b] = odd ? q[4 * a + b] : q[4 * b + a];
+    }
+    dx = dcomp[0];
+    dy = dcomp[1];
+    dz = dcomp[2];
+}
+
+// ------------------------------------------------------------------------------------------------
+// Closest-hit key (t, patch id, cell index).
+// ------------------------------------------------------------------------------------------------
+struct Best {
+    float t;
+    uint32_t pid, cell;
+};
+
+CCS_DEV bool key_less(float t, uint32_t pid, uint32_t cell, const Best &b)
+{
+    if (t != b.t) return t < b.t;
+    if (pid != b.pid) return pid < b.pid;
+    return cell < b.cell;
+}
+
+struct Counters {
+    unsigned long long v[kNumCounters];
+};
+
+// ------------------------------------------------------------------------------------------------
+// Algorithm 3 for one (ray, patch) pair, stackless with one bit trail over tree levels.
+//   path  bit l = the node at level l+1 is the upper half of its parent's split;
+//   trail bit l = the sibling of that node is still pending.
+// Split axis is fixed by the level (u at even levels), so one trail encodes both of the paper's
+// trails.  The entry/exit interval of every pending sibling is kept in `sib` (2 floats per level,
+// shared memory); on backtracking a sibling whose entry exceeds the best distance is dropped without
+// recomputing anything, and Gregory children are clipped to their parent's interval, which keeps
+// the answer independent of the visiting order.  Returns false if the iteration cap was hit.
+// ------------------------------------------------------------------------------------------------
+template <bool STATS>
+CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float wox, float woy, float woz,
+                             const RayF &wr, float c0, float c1, int L, Best &best, float2 *sib, int sib_stride,
+                             uint32_t &iters_left, Counters &cnt, uint32_t skip_path = 0xFFFFFFFFu,
+                             int skip_level = -1)
+{
+    const float4 an = __ldg(rec + 15);
+    const bool greg = an.w != 0.0f;
+    RayF r = wr;
+    r.oix = (wox - an.x) * wr.ix;
+    r.oiy = (woy - an.y) * wr.iy;
+    r.oiz = (woz - an.z) * wr.iz;
+    float g[48];
+    float dx = 0.0f, dy = 0.0f, dz = 0.0f;
+    int level = 0;
+    uint32_t path = 0, trail = 0;
+    if (greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, dx, dy, dz);
+    else load_grid(rec, g);
+    const int leaf_level = 2 * L;
+    for (;;) {
+        if (iters_left == 0) return false;
+        --iters_left;
+        bool descend = false;
+        if (level == leaf_level) {
+            uint32_t cu, cv;
+            path_cells(path, L, cu, cv);
+            const uint32_t cell = (cv << L) | cu;
+            if (STATS) cnt.v[3]++;
+            if (key_less(c0, pid, cell, best)) {
+                best.t = c0;
+                best.pid = pid;
+                best.cell = cell;
+            }
+        } else {
+            Box6 BL, BR;
+            split_grid<true>(g, BL, BR, -1);
+            if (STATS) cnt.v[greg ? 2 : 1]++;
+            float l0, l1, r0, r1;
+            slab(r, BL.lx, BL.ly, BL.lz, BL.hx + dx, BL.hy + dy, BL.hz + dz, c0, c1, l0, l1);
+            slab(r, BR.lx, BR.ly, BR.lz, BR.hx + dx, BR.hy + dy, BR.hz + dz, c0, c1, r0, r1);
+            bool hitL = l0 <= l1 && l0 <= best.t;
+            bool hitR = r0 <= r1 && r0 <= best.t;
+            if (skip_level == level + 1) {   // the subtree already searched by a directed descent
+                if ((skip_path & ((1u << level) - 1u)) == (path & ((1u << level) - 1u))) {
+                    if ((skip_path >> level) & 1u) hitR = false; else hitL = false;
+                }
+            }
+            if (hitL || hitR) {
+                const bool goR = hitR && (!hitL || r0 < l0);
+                const uint32_t bit = 1u << level;
+                if (hitL && hitR) {
+                    trail |= bit;
+                    sib[level * sib_stride] = goR ? make_float2(l0, l1) : make_float2(r0, r1);
+                }
+                path = goR ? (path | bit) : path;
+                c0 = goR ? r0 : l0;
+                c1 = goR ? r1 : l1;
+                ++level;
+                if (greg) {
+                    float u0, u1, v0, v1;
+                    node_domain(path, level, L, u0, u1, v0, v1);
+                    gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
+                } else {
+                    split_grid<false>(g, BL, BR, goR ? 1 : 0);
+                }
+                descend = true;
+            }
+        }
+        if (descend) continue;
+        // backtrack to the deepest pending sibling that can still hold a closer leaf
+        bool resumed = false;
+        while (trail != 0u) {
+            const int l = 31 - __clz(trail);
+            const uint32_t bit = 1u << l;
+            trail ^= bit;
+            const float2 s = sib[l * sib_stride];
+            if (s.x > best.t) {
+                if (STATS) cnt.v[6]++;
+                continue;
+            }
+            path = (path & (bit - 1u)) | (~path & bit);
+            level = l + 1;
+            c0 = s.x;
+            c1 = s.y;
+            if (STATS) cnt.v[4]++;
+            if (greg) {
+                float u0, u1, v0, v1;
+                node_domain(path, level, L, u0, u1, v0, v1);
+                gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
+            } else {
+                if (STATS) cnt.v[5] += level;
+                redescend(rec, path, level, g);
+            }
+            resumed = true;
+            break;
+        }
+        if (!resumed) return true;
+    }
+}
+
+// World-space slab test against one child box of a BVH node.
+CCS_DEV void node_child_boxes(const float4 *__restrict__ nodes, int idx, const RayF &r, float c0, float c1, float &a0,
+                              float &a1, float &b0, float &b1, int &ch0, int &ch1)
+{
+    const float4 n0 = __ldg(nodes + idx * kNodeF4 + 0);
+    const float4 n1 = __ldg(nodes + idx * kNodeF4 + 1);
+    const float4 n2 = __ldg(nodes + idx * kNodeF4 + 2);
+    const float4 n3 = __ldg(nodes + idx * kNodeF4 + 3);
+    slab(r, n0.x, n0.z, n2.x, n0.y, n0.w, n2.y, c0, c1, a0, a1);
+    slab(r, n1.x, n1.z, n2.z, n1.y, n1.w, n2.w, c0, c1, b0, b1);
+    ch0 = __float_as_int(n3.x);
+    ch1 = __float_as_int(n3.y);
+}
+
+constexpr int kBvhStack = 64;
+constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
+
+// Closest hit of one ray over a scene: BVH traversal with a node stack (nearer child first, nodes
+// pruned by entry distance), Algorithm 3 at every leaf.  Returns false on the iteration cap.
+template <bool STATS>
+CCS_DEV bool trace_ray(const DevScene &sc, float ox, float oy, float oz, float dx_, float dy_, float dz_, float tmin,
+                       float tmax, int L, Best &best, float2 *sib, int sib_stride, uint32_t iter_cap, Counters &cnt)
+{
+    best.t = tmax;
+    best.pid = kMissId;
+    best.cell = kMissId;
+    if (!(tmin <= tmax) || sc.n_nodes == 0) return true;   // also rejects NaN bounds
+    if (isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx_) || isnan(dy_) || isnan(dz_)) return true;
+    RayF r;
+    r.ix = safe_inv(dx_);
+    r.iy = safe_inv(dy_);
+    r.iz = safe_inv(dz_);
+    r.oix = ox * r.ix;
+    r.oiy = oy * r.iy;
+    r.oiz = oz * r.iz;
+    int stk_node[kBvhStack];
+    float2 stk_t[kBvhStack];
+    int sp = 0;
+    int node = 0;
+    float n0 = tmin, n1 = tmax;   // interval of `node` (root: the ray interval)
+    uint32_t iters = iter_cap;
+    for (;;) {
+        if (node >= 0) {
+            if (iters == 0) return false;
+            --iters;
+            if (STATS) cnt.v[0]++;
+            float a0, a1, b0, b1;
+            int c0, c1;
+            node_child_boxes(sc.nodes, node, r, tmin, tmax, a0, a1, b0, b1, c0, c1);
+            const bool ha = a0 <= a1 && a0 <= best.t && c0 != kEmptyChild;
+            const bool hb = b0 <= b1 && b0 <= best.t && c1 != kEmptyChild;
+            if (ha && hb) {
+                const bool bfirst = b0 < a0;
+                if (sp < kBvhStack) {
+                    stk_node[sp] = bfirst ? c0 : c1;
+                    stk_t[sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
+                    ++sp;
+                }
+                node = bfirst ? c1 : c0;
+                n0 = bfirst ? b0 : a0;
+                n1 = bfirst ? b1 : a1;
+                continue;
+            } else if (ha || hb) {
+                node = ha ? c0 : c1;
+                n0 = ha ? a0 : b0;
+                n1 = ha ? a1 : b1;
+                continue;
+            }
+        } else {
+            // leaf: patch ~node with root interval [n0, n1]
+            const uint32_t pid = (uint32_t)(~node);
+            if (n0 <= best.t) {
+                if (STATS) cnt.v[7]++;
+                if (!intersect_patch<STATS>(sc.rec + (size_t)pid * kRecF4, pid, ox, oy, oz, r, n0, n1, L, best, sib,
+                                            sib_stride, iters, cnt))
+                    return false;
+            }
+        }
+        // pop
+        bool found = false;
+        while (sp > 0) {
+            --sp;
+            const float2 t = stk_t[sp];
+            if (t.x > best.t) continue;
+            node = stk_node[sp];
+            n0 = t.x;
+            n1 = t.y;
+            found = true;
+            break;
+        }
+        if (!found) return true;
+    }
+}
+
+}  // namespace ccs

@@ -1,0 +1,277 @@
+"""GPU parity of the plain closest-hit kernel against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_03510_gb300 import ccs, scenegen as sg
+from parity import MISS, compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_03510_gb300 import build_ext
+    build_ext.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+
+
+def gpu_run(P, types, rays, L=8, scene=None, **kw):
+    own = scene is None
+    sc = scene or ccs.Scene(P, types)
+    hits = ccs.intersect(sc, ccs.rays_to_device(rays.soa()), ccs.make_opts(leaf_depth=L, **kw))
+    torch.cuda.synchronize()
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    out = ccs.hits_to_numpy(hits)
+    if own:
+        sc.close()
+    return out
+
+
+def surface_rays(s, n_primary_w, n_primary_h, seed, L=8):
+    """Outgoing rays from the oracle's primary hits: origin on the hit leaf surface point, offset along
+    the normal, random direction in the normal's hemisphere (incoherent secondary rays)."""
+    cam = sg.pinhole_rays(n_primary_w, n_primary_h)
+    o = oracle.intersect(s.P, s.types, cam.soa(), L=L)
+    idx = np.nonzero(o["pid"] != MISS)[0]
+    rng = np.random.default_rng(seed)
+    org, dirs = [], []
+    for i in idx:
+        pid = int(o["pid"][i])
+        f, fu, fv = oracle.patch_frame(s.P[pid].astype(float), bool(s.types[pid]), float(o["u"][i]), float(o["v"][i]))
+        nrm = np.cross(fu, fv)
+        nrm /= np.linalg.norm(nrm)
+        if nrm @ cam.d[i] > 0:
+            nrm = -nrm
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        if d @ nrm < 0:
+            d = -d
+        org.append(f + 2e-3 * nrm)
+        dirs.append(d)
+    org, dirs = np.array(org), np.array(dirs)
+    n = len(org)
+    return sg.Rays(org.astype(np.float32), dirs.astype(np.float32), np.zeros(n, np.float32),
+                   np.full(n, np.inf, np.float32))
+
+
+def test_cfg1_primary_rays_all_match():
+    s = sg.config_scene(1)
+    r = sg.pinhole_rays(64, 64)
+    g = gpu_run(s.P, s.types, r, 8)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
+    rep = compare(g, o, 8)
+    assert rep["hits"] > 500
+
+
+def test_cfg1_random_incoherent_rays():
+    s = sg.config_scene(1)
+    r = sg.random_rays(20000, seed=11)
+    g = gpu_run(s.P, s.types, r, 8)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
+    rep = compare(g, o, 8)
+    assert rep["hits"] > 5000
+
+
+def test_gregory_heavy_scene():
+    """8x8 noisy cube-sphere with the 2-ring of each extraordinary vertex as Gregory patches (6.25 %)."""
+    s = sg.make_scene(8, 0.05, 3, 1, gregory_ring=True)
+    r = sg.random_rays(20000, seed=12, target=1.0)
+    g = gpu_run(s.P, s.types, r, 8)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
+    rep = compare(g, o, 8)
+    greg_hits = np.isin(o["pid"], np.nonzero(s.types == 1)[0]).sum()
+    assert greg_hits > 100, rep
+
+
+def test_secondary_rays_from_surface():
+    s = sg.config_scene(2)
+    r = surface_rays(s, 160, 90, seed=3)
+    g = gpu_run(s.P, s.types, r, 8)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
+    compare(g, o, 8)
+
+
+@pytest.mark.parametrize("L", [1, 2, 5, 11, 15])
+def test_leaf_depths(L):
+    s = sg.config_scene(1)
+    r = sg.random_rays(3000, seed=100 + L)
+    g = gpu_run(s.P, s.types, r, L)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=L, flags=True)
+    compare(g, o, L, max_flagged_frac=0.05)
+
+
+def test_full_size_primary_launch_sampled():
+    """1920 x 1080 primary rays of the 1536-patch scene in one launch (the benchmark's launch
+    configuration); the oracle checks a sample of 4000 rays, half of them inside the sphere's outline."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(1920, 1080)
+    g = gpu_run(s.P, s.types, r, 8)
+    rng = np.random.default_rng(7)
+    hit_idx = np.nonzero(g["pid"] != MISS)[0]
+    assert 0.1 < len(hit_idx) / r.n < 0.3
+    pick = np.unique(np.concatenate([rng.choice(r.n, 2000, replace=False), rng.choice(hit_idx, 2000, replace=False)]))
+    sub = r.subset(pick)
+    o = oracle.intersect(s.P, s.types, sub.soa(), L=8, flags=True)
+    gs = {k: v[pick] for k, v in g.items()}
+    compare(gs, o, 8)
+
+
+def test_edge_cases_nan_inverted_interval_and_short_tmax():
+    s = sg.config_scene(1)
+    r = sg.pinhole_rays(32, 32)
+    n = r.n
+    o = r.o.copy()
+    d = r.d.copy()
+    tmin = r.tmin.copy()
+    tmax = r.tmax.copy()
+    o[0, 0] = np.nan
+    d[1, 2] = np.nan
+    tmin[2], tmax[2] = 5.0, 1.0          # inverted interval
+    tmax[3:200] = 0.5                    # ends before the sphere
+    tmin[200:300] = 100.0                # starts after it
+    # exactly representable axis-aligned directions
+    d[300] = [0, 0, -1]
+    o[300] = [0, 0, 3]
+    d[301] = [0, -1, 0]
+    o[301] = [0.1, 3, 0.05]
+    rr = sg.Rays(o, d, tmin, tmax)
+    g = gpu_run(s.P, s.types, rr, 8)
+    assert (g["pid"][:300] == MISS).all()
+    assert np.isinf(g["t"][:300]).all()
+    orc = oracle.intersect(s.P, s.types, rr.soa(), L=8, flags=True)
+    compare(g, orc, 8)
+    assert g["pid"][300] != MISS and g["pid"][301] != MISS
+
+
+def test_tmax_bound_is_inclusive_and_tmin_clips():
+    s = sg.config_scene(1)
+    r = sg.pinhole_rays(48, 48)
+    g0 = gpu_run(s.P, s.types, r, 8)
+    hit = g0["pid"] != MISS
+    # with tmax equal to the reported t the same leaf is still found
+    r2 = sg.Rays(r.o, r.d, r.tmin, np.where(hit, g0["t"], np.inf).astype(np.float32))
+    g1 = gpu_run(s.P, s.types, r2, 8)
+    assert np.array_equal(g1["pid"], g0["pid"]) and np.array_equal(g1["t"][hit], g0["t"][hit])
+    # a tmin past the front surface finds the back side
+    r3 = sg.Rays(r.o, r.d, np.where(hit, g0["t"] + 0.2, 0).astype(np.float32), r.tmax)
+    g3 = gpu_run(s.P, s.types, r3, 8)
+    assert (g3["t"][hit] > g0["t"][hit]).all()
+    o3 = oracle.intersect(s.P, s.types, r3.soa(), L=8, flags=True)
+    compare(g3, o3, 8)
+
+
+def test_empty_and_single_patch_scenes():
+    s = sg.config_scene(1)
+    r = sg.random_rays(2000, seed=4)
+    g = gpu_run(s.P[:0], s.types[:0], r, 8)
+    assert (g["pid"] == MISS).all()
+    for p in (0, 5, 40):   # Bezier and Gregory singles
+        P1, t1 = s.P[p:p + 1], s.types[p:p + 1]
+        c = P1[0].mean(0)
+        rr = sg.random_rays(3000, seed=p, radius=2.0)
+        rr = sg.Rays(rr.o, (c[None] + 0.05 * np.random.default_rng(p).normal(size=(3000, 3)) - rr.o).astype(np.float32),
+                     rr.tmin, rr.tmax)
+        g = gpu_run(P1, t1, rr, 8)
+        o = oracle.intersect(P1, t1, rr.soa(), L=8, flags=True)
+        rep = compare(g, o, 8)
+        assert rep["hits"] > 100
+
+
+def test_zero_rays_is_a_no_op():
+    s = sg.config_scene(1)
+    sc = ccs.Scene(s.P, s.types)
+    hits = ccs.alloc_hits(1)
+    rays = ccs.rays_to_device(sg.pinhole_rays(1, 1).soa())
+    ccs.ccs_intersect(sc.handle, rays, 0, hits, ccs.make_opts())
+    torch.cuda.synchronize()
+    sc.close()
+
+
+def test_host_buffer_path_matches_device_path():
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(320, 180)
+    sc = ccs.Scene(s.P, s.types)
+    g = gpu_run(s.P, s.types, r, 8, scene=sc)
+    planes = [np.ascontiguousarray(a) for a in r.soa()]
+    ht = np.empty(r.n, np.float32)
+    hu = np.empty(r.n, np.float32)
+    hv = np.empty(r.n, np.float32)
+    hp = np.empty(r.n, np.uint32)
+    ccs.ccs_intersect_host(sc.handle, [a.ctypes.data for a in planes], r.n,
+                           [ht.ctypes.data, hu.ctypes.data, hv.ctypes.data, hp.ctypes.data], ccs.make_opts())
+    assert np.array_equal(hp, g["pid"]) and np.array_equal(ht, g["t"]) and np.array_equal(hu, g["u"])
+    sc.close()
+
+
+def test_bit_identical_across_launch_configurations():
+    """The answer does not depend on scheduling: block size, warps per SM and queue chunk."""
+    s = sg.make_scene(8, 0.05, 3, 1, gregory_ring=True)
+    r = sg.random_rays(30000, seed=21)
+    sc = ccs.Scene(s.P, s.types)
+    ref = gpu_run(s.P, s.types, r, 8, scene=sc)
+    for kw in [dict(block_threads=32), dict(block_threads=64, chunk=256), dict(blocks_per_sm=1, chunk=1024)]:
+        g = gpu_run(s.P, s.types, r, 8, scene=sc, **kw)
+        for k in ("t", "u", "v", "pid"):
+            assert np.array_equal(g[k], ref[k]), (kw, k)
+    sc.close()
+
+
+def test_iteration_cap_reports_status_and_context_survives():
+    s = sg.config_scene(1)
+    r = sg.pinhole_rays(64, 64)
+    sc = ccs.Scene(s.P, s.types)
+    hits = ccs.intersect(sc, ccs.rays_to_device(r.soa()), ccs.make_opts(iter_cap=5))
+    torch.cuda.synchronize()
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_ERR_TRAVERSAL_LIMIT
+    g = ccs.hits_to_numpy(hits)
+    assert (g["pid"] == MISS).all()
+    # status was cleared; a normal launch works
+    g2 = gpu_run(s.P, s.types, r, 8, scene=sc)
+    assert (g2["pid"] != MISS).sum() > 500
+    sc.close()
+
+
+def test_refit_after_update_equals_fresh_build():
+    """Deformed control points through update + refit give the same hits as a scene built from them."""
+    s = sg.config_scene(2)
+    P1 = sg.deform(s.P, 2, 8, seed=5)
+    r = sg.random_rays(20000, seed=9)
+    sc = ccs.Scene(s.P, s.types)
+    x = torch.from_numpy(np.ascontiguousarray(P1[..., 0]).reshape(-1)).cuda()
+    y = torch.from_numpy(np.ascontiguousarray(P1[..., 1]).reshape(-1)).cuda()
+    z = torch.from_numpy(np.ascontiguousarray(P1[..., 2]).reshape(-1)).cuda()
+    ccs.ccs_scene_update_points(sc.handle, x, y, z)
+    ccs.ccs_bvh_refit(sc.handle)
+    g = gpu_run(P1, s.types, r, 8, scene=sc)
+    fresh = gpu_run(P1, s.types, r, 8)
+    for k in ("t", "u", "v", "pid"):
+        assert np.array_equal(g[k], fresh[k]), k
+    o = oracle.intersect(P1, s.types, r.soa(), L=8, flags=True)
+    compare(g, o, 8)
+    sc.close()
+
+
+def test_counters_count_the_work():
+    s = sg.config_scene(1)
+    r = sg.pinhole_rays(64, 64)
+    sc = ccs.Scene(s.P, s.types)
+    cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    rays = ccs.rays_to_device(r.soa())
+    hits = ccs.alloc_hits(r.n)
+    ccs.ccs_intersect(sc.handle, rays, r.n, hits, ccs.make_opts(counters=cnt))
+    torch.cuda.synchronize()
+    c = dict(zip(ccs.COUNTER_NAMES, cnt.cpu().tolist()))
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, stats=True)
+    exp_b = int(o["stats"][:, 1].sum())
+    exp_g = int(o["stats"][:, 2].sum())
+    assert c["pairs"] > 0 and c["leaves"] > 0
+    # same visiting order as the oracle's stack: split counts agree up to FP32 box differences
+    assert abs(c["bezier_splits"] - exp_b) <= 0.02 * exp_b
+    assert abs(c["gregory_splits"] - exp_g) <= 0.05 * exp_g + 10
+    sc.close()
