@@ -58,17 +58,23 @@ typedef struct {
     uint32_t *patch_id;
 } ccs_hits;
 
-/* Launch and method options.  Zero-initialised fields take the defaults given in brackets. */
+/* Launch and method options.  Zero-initialised fields take the defaults given in brackets (except
+ * cache_slots, whose 0 is meaningful: pass CCS_CACHE_DEFAULT for the default).  None of them changes
+ * the answer: hits are bit-identical for every launch configuration. */
 typedef struct {
     uint32_t leaf_depth;      /* L, splits per axis of the (u,v) domain, 1..15 [8] */
     uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
-    uint32_t blocks_per_sm;   /* resident blocks per SM of the persistent launch [4] */
-    uint32_t chunk;           /* rays taken per warp from the global work queue, multiple of 32 [32] */
+    uint32_t blocks_per_sm;   /* blocks per SM of the persistent launch, clamped to what fits [4] */
+    uint32_t refill;          /* a warp takes new rays from the global queue once at least this many of
+                                 its 32 lanes are idle, 1..32 [16] */
+    uint32_t cache_slots;     /* grids of pending Bezier siblings kept in shared memory per thread,
+                                 0 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root */
     uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
 } ccs_trace_opts;
 
+#define CCS_CACHE_DEFAULT 0xFFFFFFFFu
 #define CCS_TRACE_COUNT 1u          /* accumulate traversal counters into opts->counters */
 #define CCS_NUM_COUNTERS 8          /* bvh nodes, bezier splits, gregory splits, leaves, backtracks,
                                        re-descent levels, pruned siblings, pairs */

@@ -54,12 +54,14 @@ def num_cores() -> int:
     return lib().orc_num_cores()
 
 
-def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool = False, rel_tie: float = 1e-5,
-              delta: float = 1e-4, stats: bool = False) -> dict:
+def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | int = False, rel_t: float = 1e-4,
+              eps: float = 5e-7, perturb: float = 1e-4, stats: bool = False) -> dict:
     """Closest hit of every ray.  P: [n, 20, 3] float32 patch points, types [n] uint8, rays_soa: eight
     float32 arrays (ox, oy, oz, dx, dy, dz, tmin, tmax).  Returns t (f64, inf on miss), u, v (f32 cell
-    centre), pid (u32, 0xFFFFFFFF on miss), cell (u64, v_cell * 2^L + u_cell), and with flags=True 'flags' (bit0 patch near tie,
-    bit1 far-cell near tie, bit2 silhouette) and 't2'; with stats=True 'stats' [n, 5]
+    centre), pid (u32, 0xFFFFFFFF on miss), cell (u64, v_cell * 2^L + u_cell); with flags 'flags' and 't2'
+    under the FP32 error model (boxes within eps, far distances within 1 + 1e-6; bit0 another patch may
+    win, bit1 a far cell of the patch may win, bit2 hit/miss may flip, bit3 t may leave rel_t; flags=2
+    adds bit4, the origin perturbation test by +-perturb); with stats=True 'stats' [n, 5]
     (bvh nodes, Bezier expansions, Gregory expansions, leaves, pops) and 'threads'."""
     P = np.ascontiguousarray(P, dtype=np.float32)
     n = P.shape[0]
@@ -77,7 +79,7 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool = Fa
     nt = lib().orc_intersect(
         _p(x, _F), _p(y, _F), _p(z, _F), _p(types, _U8), ctypes.c_uint32(n),
         *[_p(a, _F) for a in planes], ctypes.c_uint32(m), ctypes.c_int(L), ctypes.c_int(threads),
-        ctypes.c_int(1 if flags else 0), ctypes.c_double(rel_tie), ctypes.c_double(delta),
+        ctypes.c_int(int(flags)), ctypes.c_double(rel_t), ctypes.c_double(eps), ctypes.c_double(perturb),
         _p(out["t"], _D), _p(out["u"], _F), _p(out["v"], _F), _p(out["pid"], _U32), _p(out["cell"], _U64),
         _p(fl, _U8) if flags else None, _p(t2, _D) if flags else None, _p(st, _U64) if stats else None)
     if nt < 0:

@@ -310,12 +310,20 @@ static uint64_t leaf_cell(uint64_t pu, uint64_t pv, int L)
 }
 
 /* mode 0: closest hit (best updated as leaves are found).
- * mode 1: enumerate every alive leaf with entry <= bound (bound fixed), calling back for each. */
-typedef void (*leaf_cb)(void *ctx, uint32_t pid, uint64_t cell, double t);
+ * mode 1: enumerate, with loose and strict intervals (see enumerate_patch), every leaf that is alive
+ *         under the loose boxes and enters before a fixed bound, calling back for each. */
+typedef void (*leaf_cb)(void *ctx, uint32_t pid, uint64_t cell, double t_loose, int strict, double t_strict);
+
+static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double bound, double eps, leaf_cb cb,
+                            void *ctx);
 
 static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *best, stats_t *st,
-                            int mode, double bound, leaf_cb cb, void *ctx)
+                            int mode, double bound, leaf_cb cb, void *ctx, double eps)
 {
+    if (mode == 1) {
+        enumerate_patch(P, r, L, bound, eps, cb, ctx);
+        return;
+    }
     node_t stack[2 * ORC_MAX_L + 4];
     int sp = 0;
     double lim = mode == 0 ? best->t : bound;
@@ -343,8 +351,6 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
                     best->cell = cell;
                     best->hit = 1;
                 }
-            } else {
-                cb(ctx, P->id, cell, N.t0);
             }
             continue;
         }
@@ -383,6 +389,113 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
             C->pv = N.pv + (axis == 1 && s == 1 ? half : 0);
             C->t0 = c0[s];
             C->t1 = c1[s];
+        }
+    }
+}
+
+
+/* ------------------------------------------------------------------------------------------------
+ * FP32 error model for the parity flags.  The CUDA path computes the same boxes in FP32; its boxes
+ * lie within `eps` (absolute, coordinates) of these and its far distances are scaled up by at most
+ * 1 + 1e-6.  A leaf is "loose-alive" if the ray meets every box of its chain inflated by eps (with
+ * far distances scaled up), and "strict-alive" if it meets every box deflated by eps (a box thinner
+ * than 2 eps along an axis collapses to its mid-plane there).  Every strict-alive leaf is alive for
+ * the FP32 path and every leaf alive for the FP32 path is loose-alive, so the FP32 answer is one of
+ * the loose-alive leaves entering no later than the nearest strict-alive one.
+ * ---------------------------------------------------------------------------------------------- */
+typedef struct {
+    v3 q[16];
+    int level;
+    uint64_t pu, pv;
+    double l0, l1;    /* loose interval */
+    double s0, s1;    /* strict interval (valid if strict) */
+    int strict;
+} enode_t;
+
+static void grow_box(v3 *lo, v3 *hi, double eps, int deflate)
+{
+    if (!deflate) {
+        *lo = sub(*lo, v3make(eps, eps, eps));
+        *hi = add(*hi, v3make(eps, eps, eps));
+        return;
+    }
+    double l[3] = {lo->x, lo->y, lo->z}, h[3] = {hi->x, hi->y, hi->z};
+    for (int k = 0; k < 3; ++k) {
+        if (h[k] - l[k] > 2.0 * eps) { l[k] += eps; h[k] -= eps; }
+        else { double m = 0.5 * (l[k] + h[k]); l[k] = h[k] = m; }
+    }
+    *lo = v3make(l[0], l[1], l[2]);
+    *hi = v3make(h[0], h[1], h[2]);
+}
+
+static const double ORC_FAR_SCALE = 1.0 + 1e-6;
+
+static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double bound, double eps, leaf_cb cb,
+                            void *ctx)
+{
+    enode_t stack[2 * ORC_MAX_L + 4];
+    int sp = 0;
+    v3 lo = P->lo, hi = P->hi;
+    double a, b;
+    grow_box(&lo, &hi, eps, 0);
+    if (!slab(r, lo, hi, r->tmin, r->tmax, &a, &b)) return;
+    b *= ORC_FAR_SCALE;
+    if (a > bound || a > b) return;
+    enode_t *root = &stack[sp++];
+    memcpy(root->q, P->g, sizeof(root->q));
+    root->level = 0;
+    root->pu = root->pv = 0;
+    root->l0 = a;
+    root->l1 = b;
+    lo = P->lo;
+    hi = P->hi;
+    grow_box(&lo, &hi, eps, 1);
+    root->strict = slab(r, lo, hi, r->tmin, r->tmax, &root->s0, &root->s1);
+    while (sp > 0) {
+        enode_t N = stack[--sp];
+        if (N.level == 2 * L) {
+            cb(ctx, P->id, leaf_cell(N.pu, N.pv, L), N.l0, N.strict, N.s0);
+            continue;
+        }
+        int axis = N.level & 1;
+        v3 q[16], d;
+        if (P->greg) {
+            double u0, u1, v0, v1;
+            node_domain(N.level, N.pu, N.pv, &u0, &u1, &v0, &v1);
+            calcPointsAndD(P->g, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
+        } else {
+            memcpy(q, N.q, sizeof(q));
+            d = v3make(0, 0, 0);
+        }
+        v3 H[2][16];
+        subdivideDeCasteljau(q, axis, H[0], H[1]);
+        int su = (N.level + 1) / 2, sv = N.level / 2;
+        uint64_t half = axis == 0 ? (1ull << (ORC_SCALE_BITS - su - 1)) : (1ull << (ORC_SCALE_BITS - sv - 1));
+        for (int s = 0; s < 2; ++s) {
+            v3 blo = H[s][0], bhi = H[s][0];
+            for (int k = 1; k < 16; ++k) { blo = vmin(blo, H[s][k]); bhi = vmax(bhi, H[s][k]); }
+            bhi = add(bhi, d);
+            v3 llo = blo, lhi = bhi;
+            grow_box(&llo, &lhi, eps, 0);
+            double c0, c1;
+            if (!slab(r, llo, lhi, -INFINITY, INFINITY, &c0, &c1)) continue;
+            c1 *= ORC_FAR_SCALE;
+            c0 = fmax(c0, N.l0);
+            c1 = fmin(c1, N.l1);
+            if (c0 > c1 || c0 > bound) continue;
+            enode_t *C = &stack[sp++];
+            memcpy(C->q, H[s], sizeof(C->q));
+            C->level = N.level + 1;
+            C->pu = N.pu + (axis == 0 && s == 1 ? half : 0);
+            C->pv = N.pv + (axis == 1 && s == 1 ? half : 0);
+            C->l0 = c0;
+            C->l1 = c1;
+            C->strict = 0;
+            if (N.strict) {
+                v3 slo = blo, shi = bhi;
+                grow_box(&slo, &shi, eps, 1);
+                C->strict = slab(r, slo, shi, N.s0, N.s1, &C->s0, &C->s1);
+            }
         }
     }
 }
@@ -507,7 +620,7 @@ static void scene_free(scene_t *S)
 
 /* closest hit over the scene (mode 0), or leaf enumeration below a fixed bound (mode 1) */
 static void trace(const scene_t *S, const ray_t *r, int L, best_t *best, stats_t *st, int mode, double bound,
-                  leaf_cb cb, void *ctx)
+                  leaf_cb cb, void *ctx, double eps)
 {
     if (S->nnodes == 0) return;
     int stack[256];
@@ -518,10 +631,12 @@ static void trace(const scene_t *S, const ray_t *r, int L, best_t *best, stats_t
         double lim = mode == 0 ? best->t : bound;
         double t0, t1;
         if (st) st->bvh_nodes++;
-        if (!slab(r, nd->lo, nd->hi, r->tmin, r->tmax, &t0, &t1) || t0 > lim) continue;
+        v3 lo = nd->lo, hi = nd->hi;
+        if (mode == 1) grow_box(&lo, &hi, eps, 0);
+        if (!slab(r, lo, hi, r->tmin, r->tmax, &t0, &t1) || t0 > lim) continue;
         if (nd->left < 0) {
             for (int i = 0; i < nd->count; ++i)
-                intersect_patch(&S->P[S->order[nd->first + i]], r, L, best, st, mode, bound, cb, ctx);
+                intersect_patch(&S->P[S->order[nd->first + i]], r, L, best, st, mode, bound, cb, ctx, eps);
             continue;
         }
         stack[sp++] = nd->right;
@@ -538,32 +653,93 @@ static void make_ray(ray_t *r, const float *const planes[8], uint32_t i)
 }
 
 /* ------------------------------------------------------------------------------------------------
- * Flags that exclude rays whose answer FP32 cannot be expected to reproduce:
- *   bit 0 near tie between patches: another patch has an alive leaf with entry <= t (1 + rel);
- *   bit 1 near tie inside the patch: a leaf of the hit patch with entry <= t (1 + rel) lies more than
- *         one cell away from the hit cell;
- *   bit 2 silhouette: hit/miss changes when the origin moves by +-delta along two axes normal to d.
+ * Flags that exclude rays whose answer FP32 cannot be expected to reproduce (FP32 error model of
+ * enumerate_patch; t* is the oracle's entry distance, R the nearest strict-alive entry):
+ *   bit 0 another patch has a loose-alive leaf entering no later than min(R, t* (1 + rel_t));
+ *   bit 1 the hit patch has such a leaf more than one cell away from the hit cell;
+ *   bit 2 hit/miss may differ: a miss with a loose-alive leaf, or a hit without any strict-alive leaf;
+ *   bit 3 t may leave the tolerance: such a leaf enters before t* (1 - rel_t), or R > t* (1 + rel_t);
+ *   bit 4 (flags_mode 2) hit/miss changes when the origin moves by +-perturb along two axes normal to d.
  * ---------------------------------------------------------------------------------------------- */
 typedef struct {
     uint32_t pid;
     uint64_t cell;
-    uint32_t L;
-    int other_patch, far_cell;
-    double t_other;
-} tie_ctx;
+    double tl, ts;
+    int strict;
+} leaf_rec;
 
-static void tie_cb(void *vctx, uint32_t pid, uint64_t cell, double t)
+typedef struct {
+    leaf_rec *v;
+    size_t n, cap;
+} leaf_list;
+
+static void list_cb(void *vctx, uint32_t pid, uint64_t cell, double tl, int strict, double ts)
 {
-    tie_ctx *c = (tie_ctx *)vctx;
-    if (pid != c->pid) {
-        c->other_patch = 1;
-        if (t < c->t_other) c->t_other = t;
-        return;
+    leaf_list *l = (leaf_list *)vctx;
+    if (l->n == l->cap) {
+        size_t cap = l->cap ? 2 * l->cap : 64;
+        leaf_rec *nv = (leaf_rec *)realloc(l->v, cap * sizeof(leaf_rec));
+        if (!nv) return;
+        l->v = nv;
+        l->cap = cap;
     }
-    int64_t mask = (1ll << c->L) - 1;
-    int64_t du = (int64_t)(cell & mask) - (int64_t)(c->cell & mask);
-    int64_t dv = (int64_t)(cell >> c->L) - (int64_t)(c->cell >> c->L);
-    if (du < -1 || du > 1 || dv < -1 || dv > 1) c->far_cell = 1;
+    leaf_rec *e = &l->v[l->n++];
+    e->pid = pid; e->cell = cell; e->tl = tl; e->strict = strict; e->ts = ts;
+}
+
+static int far_cell(uint64_t a, uint64_t b, int L)
+{
+    int64_t mask = (1ll << L) - 1;
+    int64_t du = (int64_t)(a & mask) - (int64_t)(b & mask);
+    int64_t dv = (int64_t)(a >> L) - (int64_t)(b >> L);
+    return du < -1 || du > 1 || dv < -1 || dv > 1;
+}
+
+static double min_strict(const leaf_list *l)
+{
+    double R = INFINITY;
+    for (size_t i = 0; i < l->n; ++i)
+        if (l->v[i].strict && l->v[i].ts < R) R = l->v[i].ts;
+    return R;
+}
+
+static uint8_t fp32_flags(const scene_t *S, const ray_t *r, int L, const best_t *b, double rel_t, double eps,
+                          double *t2)
+{
+    leaf_list l = {NULL, 0, 0};
+    best_t dummy = {0, 0, 0, 0};
+    uint8_t flags = 0;
+    *t2 = INFINITY;
+    if (!b->hit) {
+        trace(S, r, L, &dummy, NULL, 1, r->tmax, list_cb, &l, eps);
+        if (l.n) flags |= 4;
+        free(l.v);
+        return flags;
+    }
+    const double B = b->t + fabs(b->t) * rel_t;
+    trace(S, r, L, &dummy, NULL, 1, B, list_cb, &l, eps);
+    double R = min_strict(&l);
+    if (R > B) {
+        leaf_list all = {NULL, 0, 0};
+        trace(S, r, L, &dummy, NULL, 1, r->tmax, list_cb, &all, eps);
+        double Ra = min_strict(&all);
+        flags |= isinf(Ra) ? 4 : 8;
+        free(all.v);
+    }
+    const double lim = R < B ? R : B;
+    for (size_t i = 0; i < l.n; ++i) {
+        const leaf_rec *e = &l.v[i];
+        if (e->tl > lim) continue;
+        if (e->pid != b->pid) {
+            flags |= 1;
+            if (e->tl < *t2) *t2 = e->tl;
+        } else if (far_cell(e->cell, b->cell, L)) {
+            flags |= 2;
+        }
+        if (e->tl < b->t - fabs(b->t) * rel_t) flags |= 8;
+    }
+    free(l.v);
+    return flags;
 }
 
 static void ortho_basis(v3 d, v3 *e1, v3 *e2)
@@ -589,7 +765,7 @@ typedef struct {
     uint32_t n_rays;
     int L;
     int flags_mode;
-    double rel_tie, delta;
+    double rel_t, eps, perturb;
     double *t_out;
     float *u_out, *v_out;
     uint32_t *pid_out;
@@ -609,7 +785,7 @@ static void run_one(job_t *J, uint32_t i)
     stats_t st = {0, 0, 0, 0, 0};
     int valid = !(isnan(r.o.x) || isnan(r.o.y) || isnan(r.o.z) || isnan(r.d.x) || isnan(r.d.y) || isnan(r.d.z) ||
                   isnan(r.tmin) || isnan(r.tmax) || r.tmin > r.tmax);
-    if (valid) trace(J->S, &r, J->L, &b, &st, 0, 0.0, NULL, NULL);
+    if (valid) trace(J->S, &r, J->L, &b, &st, 0, 0.0, NULL, NULL, 0.0);
     double cells = ldexp(1.0, J->L);
     if (b.hit) {
         J->t_out[i] = b.t;
@@ -633,26 +809,19 @@ static void run_one(job_t *J, uint32_t i)
         if (J->t2_out) J->t2_out[i] = INFINITY;
         return;
     }
-    uint8_t flags = 0;
     double t2 = INFINITY;
-    if (b.hit) {
-        tie_ctx c = {b.pid, b.cell, (uint32_t)J->L, 0, 0, INFINITY};
-        double bound = b.t + fabs(b.t) * J->rel_tie;
-        best_t dummy = {bound, 0, 0, 0};
-        trace(J->S, &r, J->L, &dummy, NULL, 1, bound, tie_cb, &c);
-        if (c.other_patch) flags |= 1;
-        if (c.far_cell) flags |= 2;
-        t2 = c.t_other;
-    }
-    v3 e1, e2;
-    ortho_basis(r.d, &e1, &e2);
-    for (int k = 0; k < 4 && !(flags & 4); ++k) {
-        ray_t rp = r;
-        v3 off = scl(k < 2 ? e1 : e2, (k & 1) ? -J->delta : J->delta);
-        rp.o = add(r.o, off);
-        best_t bp = {rp.tmax, 0xFFFFFFFFu, ~0ull, 0};
-        trace(J->S, &rp, J->L, &bp, NULL, 0, 0.0, NULL, NULL);
-        if (bp.hit != b.hit) flags |= 4;
+    uint8_t flags = fp32_flags(J->S, &r, J->L, &b, J->rel_t, J->eps, &t2);
+    if (J->flags_mode == 2) {
+        v3 e1, e2;
+        ortho_basis(r.d, &e1, &e2);
+        for (int k = 0; k < 4 && !(flags & 16); ++k) {
+            ray_t rp = r;
+            v3 off = scl(k < 2 ? e1 : e2, (k & 1) ? -J->perturb : J->perturb);
+            rp.o = add(r.o, off);
+            best_t bp = {rp.tmax, 0xFFFFFFFFu, ~0ull, 0};
+            trace(J->S, &rp, J->L, &bp, NULL, 0, 0.0, NULL, NULL, 0.0);
+            if (bp.hit != b.hit) flags |= 16;
+        }
     }
     J->flag_out[i] = flags;
     if (J->t2_out) J->t2_out[i] = t2;
@@ -682,11 +851,12 @@ int orc_num_cores(void) { long n = sysconf(_SC_NPROCESSORS_ONLN); return n > 0 ?
 /* Closest hit of every ray.  Inputs: patch planes x,y,z [n*20] (layout of the module header), types
  * [n] (0 Bezier, 1 Gregory), ray planes ox..tmax [n_rays].  Outputs per ray: t (INF on miss), u, v
  * (cell centre), patch id (0xFFFFFFFF on miss), cell index v_cell * 2^L + u_cell; optionally flags
- * (flags_mode != 0), t2 and 5 traversal counters.  Returns the number of threads used. */
+ * (flags_mode 1: FP32 error model with box error eps and t tolerance rel_t; 2: also the origin
+ * perturbation test), t2 and 5 traversal counters.  Returns the number of threads used. */
 int orc_intersect(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n_patches,
                   const float *ox, const float *oy, const float *oz, const float *dx, const float *dy,
                   const float *dz, const float *tmin, const float *tmax, uint32_t n_rays, int L, int n_threads,
-                  int flags_mode, double rel_tie, double delta, double *t_out, float *u_out, float *v_out,
+                  int flags_mode, double rel_t, double eps, double perturb, double *t_out, float *u_out, float *v_out,
                   uint32_t *pid_out, uint64_t *cell_out, uint8_t *flag_out, double *t2_out, uint64_t *stats_out)
 {
     if (L < 1 || L > ORC_MAX_L) return -1;
@@ -697,7 +867,7 @@ int orc_intersect(const float *x, const float *y, const float *z, const uint8_t 
     J.S = &S;
     J.planes[0] = ox; J.planes[1] = oy; J.planes[2] = oz; J.planes[3] = dx; J.planes[4] = dy; J.planes[5] = dz;
     J.planes[6] = tmin; J.planes[7] = tmax;
-    J.n_rays = n_rays; J.L = L; J.flags_mode = flags_mode; J.rel_tie = rel_tie; J.delta = delta;
+    J.n_rays = n_rays; J.L = L; J.flags_mode = flags_mode; J.rel_t = rel_t; J.eps = eps; J.perturb = perturb;
     J.t_out = t_out; J.u_out = u_out; J.v_out = v_out; J.pid_out = pid_out; J.cell_out = cell_out;
     J.flag_out = flag_out; J.t2_out = t2_out; J.stats_out = stats_out;
     pthread_mutex_init(&J.mu, NULL);
@@ -748,7 +918,7 @@ int orc_intersect_patch(const double *g60, int greg, const double *r8, int L, in
         double t0, t1;
         if (slab(&r, P.lo, P.hi, r.tmin, r.tmax, &t0, &t1)) brute_rec(&P, &r, L, P.g, 0, 0, 0, t0, t1, &b);
     } else {
-        intersect_patch(&P, &r, L, &b, &st, 0, 0.0, NULL, NULL);
+        intersect_patch(&P, &r, L, &b, &st, 0, 0.0, NULL, NULL, 0.0);
     }
     if (stats5) { stats5[0] = st.bvh_nodes; stats5[1] = st.expand_bez; stats5[2] = st.expand_greg; stats5[3] = st.leaves; stats5[4] = st.pops; }
     *t = b.hit ? b.t : INFINITY;

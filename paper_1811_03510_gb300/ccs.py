@@ -43,7 +43,8 @@ class ccs_hits(ctypes.Structure):
 
 class ccs_trace_opts(ctypes.Structure):
     _fields_ = [("leaf_depth", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("chunk", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32),
+                ("iter_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
 
 
@@ -127,12 +128,17 @@ def _stream(s) -> int:
     return int(s.cuda_stream)
 
 
-def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, chunk=0, iter_cap=0, counters=None) -> ccs_trace_opts:
+CCS_CACHE_DEFAULT = 0xFFFFFFFF
+
+
+def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, cache_slots=CCS_CACHE_DEFAULT, iter_cap=0,
+              counters=None) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
     o.blocks_per_sm = blocks_per_sm
-    o.chunk = chunk
+    o.refill = refill
+    o.cache_slots = cache_slots
     o.iter_cap = iter_cap
     o.flags = CCS_TRACE_COUNT if counters is not None else 0
     o.counters = _ptr(counters) if counters is not None else None

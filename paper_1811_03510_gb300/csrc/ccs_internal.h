@@ -29,7 +29,7 @@ constexpr int kMaxLeafDepth = 15;
 constexpr int kNumCounters = CCS_NUM_COUNTERS;
 
 struct LaunchCfg {
-    uint32_t leaf_depth, block_threads, blocks_per_sm, chunk, iter_cap, flags;
+    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, cache_slots, iter_cap, flags;
     unsigned long long *counters;
 };
 
@@ -49,6 +49,7 @@ struct DevHits {
 };
 
 // kernels (intersect.cu, scene.cu)
+size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K);
 cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
                           float4 *rec, float4 *leaf_box, cudaStream_t s);
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,

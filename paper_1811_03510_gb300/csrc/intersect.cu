@@ -1,60 +1,124 @@
-// Plain closest-hit kernel: persistent blocks, warps take chunks of rays from a global work queue,
-// each lane traverses the BVH and runs the bit-trail patch subdivision (Algorithm 3) at its leaves.
+// Plain closest-hit kernel.  Persistent blocks; each warp keeps 32 rays in flight and takes new rays
+// from a global work queue whenever enough of its lanes are idle (warp-aggregated atomic).  Every
+// iteration of the warp loop is two phases separated by __syncwarp: BVH traversal until each lane
+// stands on a patch leaf (or is finished), then Algorithm 3 on those leaves with all such lanes
+// together, so that the expensive patch subdivision runs converged (while-while traversal).
 #include "traverse.cuh"
 
 namespace ccs {
 
-template <bool STATS>
+template <bool STATS, int K>
 __global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, DevHits hits, uint32_t n, int L,
-                                                   uint32_t chunk, uint32_t iter_cap, uint32_t *queue,
+                                                   uint32_t refill, uint32_t iter_cap, uint32_t *queue,
                                                    uint32_t *status, unsigned long long *counters)
 {
-    extern __shared__ float2 sib_smem[];
-    float2 *sib = sib_smem + threadIdx.x;
+    extern __shared__ float smem[];
     const int stride = blockDim.x;
+    Scratch scr;
+    scr.stride = stride;
+    scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
+    scr.cache = smem + 2 * 2 * L * stride + threadIdx.x;
+    scr.tag = reinterpret_cast<int *>(smem + (2 * 2 * L + 48 * K) * stride) + threadIdx.x;
     Counters cnt;
 #pragma unroll
     for (int k = 0; k < kNumCounters; ++k) cnt.v[k] = 0;
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
     const float cellw = __int_as_float((127 - L) << 23);
+    RayState s;
+    BvhStack stk;
+    bool has = false, exhausted = false;
+    uint32_t ray_i = 0;
     for (;;) {
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(queue, chunk);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= n) break;
-        const uint32_t end = min(base + chunk, n);
-        for (uint32_t i = base + lane; i < end; i += 32) {
-            Best b;
-            const bool ok = trace_ray<STATS>(sc, __ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i),
-                                             __ldg(rays.dx + i), __ldg(rays.dy + i), __ldg(rays.dz + i),
-                                             __ldg(rays.tmin + i), __ldg(rays.tmax + i), L, b, sib, stride, iter_cap,
-                                             cnt);
+        const unsigned idle = __ballot_sync(FULL, !has);
+        if (!exhausted && idle != 0u && ((uint32_t)__popc(idle) >= refill || idle == FULL)) {
+            const int cnt_idle = __popc(idle), leader = __ffs(idle) - 1;
+            uint32_t base = 0;
+            if (lane == leader) base = atomicAdd(queue, (uint32_t)cnt_idle);
+            base = __shfl_sync(FULL, base, leader);
+            if (base + (uint32_t)cnt_idle >= n) exhausted = true;
+            if (!has) {
+                const uint32_t i = base + (uint32_t)__popc(idle & lt_mask);
+                if (i < n) {
+                    has = true;
+                    ray_i = i;
+                    begin_ray(s, sc, __ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i), __ldg(rays.dx + i),
+                              __ldg(rays.dy + i), __ldg(rays.dz + i), __ldg(rays.tmin + i), __ldg(rays.tmax + i),
+                              iter_cap);
+                }
+            }
+        }
+        if (__ballot_sync(FULL, has) == 0u) {
+            if (exhausted) break;
+            continue;
+        }
+        bool ok = true;
+        if (has) ok = bvh_advance<STATS>(s, stk, sc, cnt);
+        __syncwarp();
+        if (has && ok && s.node != kDone) ok = leaf_step<STATS, K>(s, stk, sc, L, scr, cnt);
+        if (has && (!ok || s.node == kDone)) {
             if (!ok) {
                 atomicOr(status, 1u);
-                b.pid = kMissId;
+                s.best.pid = kMissId;
             }
-            if (b.pid != kMissId) {
-                const uint32_t cu = b.cell & ((1u << L) - 1u), cv = b.cell >> L;
-                hits.t[i] = b.t;
+            const uint32_t i = ray_i;
+            if (s.best.pid != kMissId) {
+                const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
+                hits.t[i] = s.best.t;
                 hits.u[i] = ((float)cu + 0.5f) * cellw;
                 hits.v[i] = ((float)cv + 0.5f) * cellw;
-                hits.pid[i] = b.pid;
+                hits.pid[i] = s.best.pid;
             } else {
                 hits.t[i] = __int_as_float(0x7f800000);
                 hits.u[i] = 0.0f;
                 hits.v[i] = 0.0f;
                 hits.pid[i] = kMissId;
             }
+            has = false;
         }
+        __syncwarp();
     }
     if (STATS) {
 #pragma unroll
         for (int k = 0; k < kNumCounters; ++k) {
             unsigned long long v = cnt.v[k];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
             if (lane == 0 && v) atomicAdd(counters + k, v);
         }
     }
+}
+
+size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
+{
+    return (size_t)threads * (2 * 2 * L + 48 * K + K) * sizeof(float);
+}
+
+template <bool STATS, int K>
+static cudaError_t launch_one(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
+                              uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
+{
+    auto kern = k_intersect<STATS, K>;
+    const uint32_t threads = cfg.block_threads;
+    const size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
+    static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
+    if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+    }
+    int max_active = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_active, kern, (int)threads, smem);
+    if (e != cudaSuccess) return e;
+    if (max_active < 1) return cudaErrorInvalidConfiguration;
+    uint32_t per_sm = cfg.blocks_per_sm < (uint32_t)max_active ? cfg.blocks_per_sm : (uint32_t)max_active;
+    uint32_t blocks = (uint32_t)num_sms * per_sm;
+    const uint32_t needed = (n + threads - 1) / threads;
+    if (blocks > needed) blocks = needed;
+    if (blocks == 0) blocks = 1;
+    kern<<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth, cfg.refill, cfg.iter_cap, queue, status,
+                                       cfg.counters);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
@@ -63,21 +127,12 @@ cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits
     if (n == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const uint32_t threads = cfg.block_threads;
-    const size_t smem = (size_t)threads * 2 * cfg.leaf_depth * sizeof(float2);
-    const uint32_t warps_needed = (n + cfg.chunk - 1) / cfg.chunk;
-    uint32_t blocks = (uint32_t)num_sms * cfg.blocks_per_sm;
-    const uint32_t blocks_needed = (warps_needed * 32 + threads - 1) / threads;
-    if (blocks > blocks_needed) blocks = blocks_needed;
-    if (blocks == 0) blocks = 1;
-    if (cfg.flags & CCS_TRACE_COUNT) {
-        k_intersect<true><<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth,
-                                                        cfg.chunk, cfg.iter_cap, queue, status, cfg.counters);
-    } else {
-        k_intersect<false><<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth, cfg.chunk, cfg.iter_cap,
-                                                         queue, status, cfg.counters);
-    }
-    return cudaGetLastError();
+    const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
+    if (cfg.cache_slots == 0)
+        return stats ? launch_one<true, 0>(sc, r, h, n, cfg, queue, status, num_sms, s)
+                     : launch_one<false, 0>(sc, r, h, n, cfg, queue, status, num_sms, s);
+    return stats ? launch_one<true, 2>(sc, r, h, n, cfg, queue, status, num_sms, s)
+                 : launch_one<false, 2>(sc, r, h, n, cfg, queue, status, num_sms, s);
 }
 
 }  // namespace ccs

@@ -336,18 +336,108 @@ struct Counters {
 };
 
 // ------------------------------------------------------------------------------------------------
+// Shared-memory scratch of one thread (addresses strided by the block size, so a warp's accesses hit
+// 32 consecutive words): the entry/exit interval of every pending sibling (one per tree level) and a
+// K-slot cache of the control grids of the most recently pushed Bezier siblings.
+// ------------------------------------------------------------------------------------------------
+struct Scratch {
+    float2 *sib;     // [level * stride]
+    float *cache;    // [(slot * 48 + k) * stride]
+    int *tag;        // [slot * stride]
+    int stride;
+};
+
+// One subdivision step of a Bezier/Gregory node (Algorithm 3, the body of the while loop): de Casteljau
+// split of the node grid along its fixed axis, the two child boxes (Gregory: upper corner + d), both
+// slab tests clipped to the node's interval, closer-first choice (ties: lower half).  On return g holds
+// the chosen child (transposed for its own split) unless neither child is hit; if both are hit the
+// other child's interval is written to *sib_slot and, if store_sibling, its grid to the cache slot.
+struct StepOut {
+    bool hitL, hitR, goR;
+    float l0, l1, r0, r1;
+};
+
+template <int K>
+CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, float dz, float c0, float c1, float tb,
+                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL = true, bool allowR = true)
+{
+    float m01[12], m012[12], mm[12], m123[12], m23[12];
+    float lmin[3], lmax[3], rmin[3], rmax[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        lmin[c] = rmin[c] = __int_as_float(0x7f800000);
+        lmax[c] = rmax[c] = -__int_as_float(0x7f800000);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const int q = c * 4 + b;
+            const float b0 = g[c * 16 + 0 * 4 + b], b1 = g[c * 16 + 1 * 4 + b];
+            const float b2 = g[c * 16 + 2 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
+            m01[q] = mid(b0, b1);
+            const float m12 = mid(b1, b2);
+            m23[q] = mid(b2, b3);
+            m012[q] = mid(m01[q], m12);
+            m123[q] = mid(m12, m23[q]);
+            mm[q] = mid(m012[q], m123[q]);
+            lmin[c] = min3f(lmin[c], b0, m01[q]);
+            lmin[c] = min3f(lmin[c], m012[q], mm[q]);
+            lmax[c] = max3f(lmax[c], b0, m01[q]);
+            lmax[c] = max3f(lmax[c], m012[q], mm[q]);
+            rmin[c] = min3f(rmin[c], mm[q], m123[q]);
+            rmin[c] = min3f(rmin[c], m23[q], b3);
+            rmax[c] = max3f(rmax[c], mm[q], m123[q]);
+            rmax[c] = max3f(rmax[c], m23[q], b3);
+        }
+    }
+    StepOut o;
+    slab(r, lmin[0], lmin[1], lmin[2], lmax[0] + dx, lmax[1] + dy, lmax[2] + dz, c0, c1, o.l0, o.l1);
+    slab(r, rmin[0], rmin[1], rmin[2], rmax[0] + dx, rmax[1] + dy, rmax[2] + dz, c0, c1, o.r0, o.r1);
+    o.hitL = allowL && o.l0 <= o.l1 && o.l0 <= tb;
+    o.hitR = allowR && o.r0 <= o.r1 && o.r0 <= tb;
+    o.goR = o.hitR && (!o.hitL || o.r0 < o.l0);
+    if ((o.hitL || o.hitR) && keep_grid) {
+        const bool up = o.goR;
+        const bool store = K > 0 && cache_slot >= 0 && o.hitL && o.hitR;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int q = c * 4 + b;
+                const float b0 = g[c * 16 + 0 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
+                const float k0 = up ? mm[q] : b0, k1 = up ? m123[q] : m01[q];
+                const float k2 = up ? m23[q] : m012[q], k3 = up ? b3 : mm[q];
+                if (K > 0 && store) {
+                    // the other child, in the same transposed layout
+                    float *dst = sc.cache + (size_t)(cache_slot * 48) * sc.stride;
+                    dst[(c * 16 + b * 4 + 0) * sc.stride] = up ? b0 : mm[q];
+                    dst[(c * 16 + b * 4 + 1) * sc.stride] = up ? m01[q] : m123[q];
+                    dst[(c * 16 + b * 4 + 2) * sc.stride] = up ? m012[q] : m23[q];
+                    dst[(c * 16 + b * 4 + 3) * sc.stride] = up ? mm[q] : b3;
+                }
+                g[c * 16 + b * 4 + 0] = k0;
+                g[c * 16 + b * 4 + 1] = k1;
+                g[c * 16 + b * 4 + 2] = k2;
+                g[c * 16 + b * 4 + 3] = k3;
+            }
+        }
+    }
+    return o;
+}
+
+// ------------------------------------------------------------------------------------------------
 // Algorithm 3 for one (ray, patch) pair, stackless with one bit trail over tree levels.
 //   path  bit l = the node at level l+1 is the upper half of its parent's split;
 //   trail bit l = the sibling of that node is still pending.
-// Split axis is fixed by the level (u at even levels), so one trail encodes both of the paper's
-// trails.  The entry/exit interval of every pending sibling is kept in `sib` (2 floats per level,
-// shared memory); on backtracking a sibling whose entry exceeds the best distance is dropped without
-// recomputing anything, and Gregory children are clipped to their parent's interval, which keeps
-// the answer independent of the visiting order.  Returns false if the iteration cap was hit.
+// The split axis is fixed by the level (u at even levels), so one trail encodes both of the paper's
+// trails.  The entry/exit interval of every pending sibling is kept in shared memory (2 floats per
+// level): on backtracking, a sibling whose entry exceeds the best distance is dropped without any
+// recomputation, and Gregory children are clipped to their parent's interval, which keeps the answer
+// independent of the visiting order.  A Bezier sibling's grid comes from the K-slot cache when it is
+// still there, else from a de Casteljau re-descent from the root (same arithmetic as the descent).
+// Returns false if the iteration cap was hit.
 // ------------------------------------------------------------------------------------------------
-template <bool STATS>
+template <bool STATS, int K>
 CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float wox, float woy, float woz,
-                             const RayF &wr, float c0, float c1, int L, Best &best, float2 *sib, int sib_stride,
+                             const RayF &wr, float c0, float c1, int L, Best &best, const Scratch &scr,
                              uint32_t &iters_left, Counters &cnt, uint32_t skip_path = 0xFFFFFFFFu,
                              int skip_level = -1)
 {
@@ -361,6 +451,7 @@ CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float
     float dx = 0.0f, dy = 0.0f, dz = 0.0f;
     int level = 0;
     uint32_t path = 0, trail = 0;
+    int ctop = 0, cvalid = 0;   // cache: pushes so far (slot = ctop % K) and valid entries
     if (greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, dx, dy, dz);
     else load_grid(rec, g);
     const int leaf_level = 2 * L;
@@ -379,36 +470,33 @@ CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float
                 best.cell = cell;
             }
         } else {
-            Box6 BL, BR;
-            split_grid<true>(g, BL, BR, -1);
             if (STATS) cnt.v[greg ? 2 : 1]++;
-            float l0, l1, r0, r1;
-            slab(r, BL.lx, BL.ly, BL.lz, BL.hx + dx, BL.hy + dy, BL.hz + dz, c0, c1, l0, l1);
-            slab(r, BR.lx, BR.ly, BR.lz, BR.hx + dx, BR.hy + dy, BR.hz + dz, c0, c1, r0, r1);
-            bool hitL = l0 <= l1 && l0 <= best.t;
-            bool hitR = r0 <= r1 && r0 <= best.t;
-            if (skip_level == level + 1) {   // the subtree already searched by a directed descent
-                if ((skip_path & ((1u << level) - 1u)) == (path & ((1u << level) - 1u))) {
-                    if ((skip_path >> level) & 1u) hitR = false; else hitL = false;
-                }
+            const int slot = (K > 0 && !greg) ? (ctop % (K > 0 ? K : 1)) : -1;
+            // a subtree already searched by a directed descent is not entered again
+            bool allowL = true, allowR = true;
+            if (skip_level == level + 1 && ((skip_path ^ path) & ((1u << level) - 1u)) == 0u) {
+                if ((skip_path >> level) & 1u) allowR = false; else allowL = false;
             }
-            if (hitL || hitR) {
-                const bool goR = hitR && (!hitL || r0 < l0);
+            StepOut o = split_step<K>(g, r, dx, dy, dz, c0, c1, best.t, !greg, scr, slot, allowL, allowR);
+            if (o.hitL || o.hitR) {
                 const uint32_t bit = 1u << level;
-                if (hitL && hitR) {
+                if (o.hitL && o.hitR) {
                     trail |= bit;
-                    sib[level * sib_stride] = goR ? make_float2(l0, l1) : make_float2(r0, r1);
+                    scr.sib[level * scr.stride] = o.goR ? make_float2(o.l0, o.l1) : make_float2(o.r0, o.r1);
+                    if (K > 0 && !greg) {
+                        scr.tag[slot * scr.stride] = level;
+                        ++ctop;
+                        cvalid = cvalid < K ? cvalid + 1 : K;
+                    }
                 }
-                path = goR ? (path | bit) : path;
-                c0 = goR ? r0 : l0;
-                c1 = goR ? r1 : l1;
+                path = o.goR ? (path | bit) : path;
+                c0 = o.goR ? o.r0 : o.l0;
+                c1 = o.goR ? o.r1 : o.l1;
                 ++level;
                 if (greg) {
                     float u0, u1, v0, v1;
                     node_domain(path, level, L, u0, u1, v0, v1);
                     gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
-                } else {
-                    split_grid<false>(g, BL, BR, goR ? 1 : 0);
                 }
                 descend = true;
             }
@@ -420,7 +508,17 @@ CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float
             const int l = 31 - __clz(trail);
             const uint32_t bit = 1u << l;
             trail ^= bit;
-            const float2 s = sib[l * sib_stride];
+            bool cached = false;
+            int cslot = 0;
+            if (K > 0 && !greg && cvalid > 0) {
+                cslot = (ctop - 1) % (K > 0 ? K : 1);
+                if (scr.tag[cslot * scr.stride] == l) {
+                    cached = true;
+                    --ctop;
+                    --cvalid;
+                }
+            }
+            const float2 s = scr.sib[l * scr.stride];
             if (s.x > best.t) {
                 if (STATS) cnt.v[6]++;
                 continue;
@@ -434,6 +532,10 @@ CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float
                 float u0, u1, v0, v1;
                 node_domain(path, level, L, u0, u1, v0, v1);
                 gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
+            } else if (cached) {
+                const float *src = scr.cache + (size_t)(cslot * 48) * scr.stride;
+#pragma unroll
+                for (int k = 0; k < 48; ++k) g[k] = src[k * scr.stride];
             } else {
                 if (STATS) cnt.v[5] += level;
                 redescend(rec, path, level, g);
@@ -445,7 +547,7 @@ CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float
     }
 }
 
-// World-space slab test against one child box of a BVH node.
+// World-space slab test against both child boxes of a BVH node.
 CCS_DEV void node_child_boxes(const float4 *__restrict__ nodes, int idx, const RayF &r, float c0, float c1, float &a0,
                               float &a1, float &b0, float &b1, int &ch0, int &ch1)
 {
@@ -461,82 +563,114 @@ CCS_DEV void node_child_boxes(const float4 *__restrict__ nodes, int idx, const R
 
 constexpr int kBvhStack = 64;
 constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
+constexpr int kDone = (int)0x80000000;    // traversal finished
 
-// Closest hit of one ray over a scene: BVH traversal with a node stack (nearer child first, nodes
-// pruned by entry distance), Algorithm 3 at every leaf.  Returns false on the iteration cap.
-template <bool STATS>
-CCS_DEV bool trace_ray(const DevScene &sc, float ox, float oy, float oz, float dx_, float dy_, float dz_, float tmin,
-                       float tmax, int L, Best &best, float2 *sib, int sib_stride, uint32_t iter_cap, Counters &cnt)
-{
-    best.t = tmax;
-    best.pid = kMissId;
-    best.cell = kMissId;
-    if (!(tmin <= tmax) || sc.n_nodes == 0) return true;   // also rejects NaN bounds
-    if (isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx_) || isnan(dy_) || isnan(dz_)) return true;
+// Per-ray traversal state of the BVH (node stack in local memory).
+struct RayState {
+    float ox, oy, oz, tmin, tmax;
     RayF r;
-    r.ix = safe_inv(dx_);
-    r.iy = safe_inv(dy_);
-    r.iz = safe_inv(dz_);
-    r.oix = ox * r.ix;
-    r.oiy = oy * r.iy;
-    r.oiz = oz * r.iz;
-    int stk_node[kBvhStack];
-    float2 stk_t[kBvhStack];
-    int sp = 0;
-    int node = 0;
-    float n0 = tmin, n1 = tmax;   // interval of `node` (root: the ray interval)
-    uint32_t iters = iter_cap;
-    for (;;) {
-        if (node >= 0) {
-            if (iters == 0) return false;
-            --iters;
-            if (STATS) cnt.v[0]++;
-            float a0, a1, b0, b1;
-            int c0, c1;
-            node_child_boxes(sc.nodes, node, r, tmin, tmax, a0, a1, b0, b1, c0, c1);
-            const bool ha = a0 <= a1 && a0 <= best.t && c0 != kEmptyChild;
-            const bool hb = b0 <= b1 && b0 <= best.t && c1 != kEmptyChild;
-            if (ha && hb) {
-                const bool bfirst = b0 < a0;
-                if (sp < kBvhStack) {
-                    stk_node[sp] = bfirst ? c0 : c1;
-                    stk_t[sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
-                    ++sp;
-                }
-                node = bfirst ? c1 : c0;
-                n0 = bfirst ? b0 : a0;
-                n1 = bfirst ? b1 : a1;
-                continue;
-            } else if (ha || hb) {
-                node = ha ? c0 : c1;
-                n0 = ha ? a0 : b0;
-                n1 = ha ? a1 : b1;
-                continue;
-            }
-        } else {
-            // leaf: patch ~node with root interval [n0, n1]
-            const uint32_t pid = (uint32_t)(~node);
-            if (n0 <= best.t) {
-                if (STATS) cnt.v[7]++;
-                if (!intersect_patch<STATS>(sc.rec + (size_t)pid * kRecF4, pid, ox, oy, oz, r, n0, n1, L, best, sib,
-                                            sib_stride, iters, cnt))
-                    return false;
-            }
-        }
-        // pop
-        bool found = false;
-        while (sp > 0) {
-            --sp;
-            const float2 t = stk_t[sp];
-            if (t.x > best.t) continue;
-            node = stk_node[sp];
-            n0 = t.x;
-            n1 = t.y;
-            found = true;
-            break;
-        }
-        if (!found) return true;
+    int node;          // >= 0 internal node, kDone, else leaf of patch ~node
+    float n0, n1;      // interval of `node`
+    int sp;
+    uint32_t iters;
+    Best best;
+};
+
+// BVH node stack of one thread (local memory): node index and its interval.
+struct BvhStack {
+    int node[kBvhStack];
+    float2 t[kBvhStack];
+};
+
+CCS_DEV void begin_ray(RayState &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
+                       float tmin, float tmax, uint32_t iter_cap)
+{
+    s.best.t = tmax;
+    s.best.pid = kMissId;
+    s.best.cell = kMissId;
+    s.sp = 0;
+    s.iters = iter_cap;
+    s.ox = ox; s.oy = oy; s.oz = oz;
+    s.tmin = tmin; s.tmax = tmax;
+    s.node = 0;
+    s.n0 = tmin;
+    s.n1 = tmax;
+    const bool bad = !(tmin <= tmax) || sc.n_nodes == 0 || isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx) ||
+                     isnan(dy) || isnan(dz);
+    if (bad) {
+        s.node = kDone;
+        return;
     }
+    s.r.ix = safe_inv(dx);
+    s.r.iy = safe_inv(dy);
+    s.r.iz = safe_inv(dz);
+    s.r.oix = ox * s.r.ix;
+    s.r.oiy = oy * s.r.iy;
+    s.r.oiz = oz * s.r.iz;
+}
+
+CCS_DEV void pop_next(RayState &s, BvhStack &stk)
+{
+    while (s.sp > 0) {
+        --s.sp;
+        const float2 t = stk.t[s.sp];
+        if (t.x > s.best.t) continue;
+        s.node = stk.node[s.sp];
+        s.n0 = t.x;
+        s.n1 = t.y;
+        return;
+    }
+    s.node = kDone;
+}
+
+// BVH traversal until `node` is a leaf or the traversal is finished (nearer child first, nodes
+// pruned by entry distance).  Returns false on the iteration cap.
+template <bool STATS>
+CCS_DEV bool bvh_advance(RayState &s, BvhStack &stk, const DevScene &sc, Counters &cnt)
+{
+    while (s.node >= 0) {
+        if (s.iters == 0) return false;
+        --s.iters;
+        if (STATS) cnt.v[0]++;
+        float a0, a1, b0, b1;
+        int c0, c1;
+        node_child_boxes(sc.nodes, s.node, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
+        const bool ha = a0 <= a1 && a0 <= s.best.t && c0 != kEmptyChild;
+        const bool hb = b0 <= b1 && b0 <= s.best.t && c1 != kEmptyChild;
+        if (ha && hb) {
+            const bool bfirst = b0 < a0;
+            if (s.sp < kBvhStack) {
+                stk.node[s.sp] = bfirst ? c0 : c1;
+                stk.t[s.sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
+                ++s.sp;
+            }
+            s.node = bfirst ? c1 : c0;
+            s.n0 = bfirst ? b0 : a0;
+            s.n1 = bfirst ? b1 : a1;
+        } else if (ha || hb) {
+            s.node = ha ? c0 : c1;
+            s.n0 = ha ? a0 : b0;
+            s.n1 = ha ? a1 : b1;
+        } else {
+            pop_next(s, stk);
+        }
+    }
+    return true;
+}
+
+// Algorithm 3 on the leaf patch `node`, then continue with the next stacked node.
+template <bool STATS, int K>
+CCS_DEV bool leaf_step(RayState &s, BvhStack &stk, const DevScene &sc, int L, const Scratch &scr, Counters &cnt)
+{
+    const uint32_t pid = (uint32_t)(~s.node);
+    if (s.n0 <= s.best.t) {
+        if (STATS) cnt.v[7]++;
+        if (!intersect_patch<STATS, K>(sc.rec + (size_t)pid * kRecF4, pid, s.ox, s.oy, s.oz, s.r, s.n0, s.n1, L,
+                                       s.best, scr, s.iters, cnt))
+            return false;
+    }
+    pop_next(s, stk);
+    return true;
 }
 
 }  // namespace ccs

@@ -215,7 +215,8 @@ def test_bit_identical_across_launch_configurations():
     r = sg.random_rays(30000, seed=21)
     sc = ccs.Scene(s.P, s.types)
     ref = gpu_run(s.P, s.types, r, 8, scene=sc)
-    for kw in [dict(block_threads=32), dict(block_threads=64, chunk=256), dict(blocks_per_sm=1, chunk=1024)]:
+    for kw in [dict(block_threads=32), dict(block_threads=64, refill=1), dict(blocks_per_sm=1, refill=32),
+               dict(cache_slots=0), dict(cache_slots=0, refill=8, block_threads=96)]:
         g = gpu_run(s.P, s.types, r, 8, scene=sc, **kw)
         for k in ("t", "u", "v", "pid"):
             assert np.array_equal(g[k], ref[k]), (kw, k)

@@ -64,7 +64,7 @@ def test_agrees_with_dense_tessellation(scene2):
     agrees with the oracle's leaf at depth 12 within the chordal error plus the leaf size."""
     L, N = 12, 256
     cam = sg.pinhole_rays(48, 27)
-    out = oracle.intersect(scene2.P, scene2.types, cam.soa(), L=L, flags=True, delta=1e-3)
+    out = oracle.intersect(scene2.P, scene2.types, cam.soa(), L=L, flags=True)
     hit = np.nonzero((out["pid"] != 0xFFFFFFFF) & (out["flags"] == 0))[0]
     pick = RNG.choice(hit, size=12, replace=False)
     P = scene2.P.astype(float)
@@ -118,8 +118,8 @@ def test_rays_through_shared_edges_and_corners_never_miss():
 
 
 def test_silhouette_flag_marks_rays_at_the_outline(scene2):
-    """Rays found by bisection at the hit/miss boundary are flagged as silhouette; rays far inside the
-    outline are not."""
+    """Rays found by bisection at the hit/miss boundary are flagged (hit/miss may flip under FP32 box
+    errors, and under a 1e-4 origin perturbation); rays well inside the outline carry no flag."""
     o = np.array([0.0, 0.0, 3.0])
     rays, inner = [], []
     for ang in np.linspace(0, 2 * np.pi, 24, endpoint=False):
@@ -139,7 +139,11 @@ def test_silhouette_flag_marks_rays_at_the_outline(scene2):
         n = len(d)
         soa = [np.full(n, o[0]), np.full(n, o[1]), np.full(n, o[2]), d[:, 0], d[:, 1], d[:, 2], np.zeros(n),
                np.full(n, np.inf)]
-        out = oracle.intersect(scene2.P, scene2.types, [np.asarray(x, np.float32) for x in soa], L=8, flags=True,
-                               delta=1e-4)
-        sil = (out["flags"] & 4) != 0
-        assert sil.all() if expect else not sil.any()
+        out = oracle.intersect(scene2.P, scene2.types, [np.asarray(x, np.float32) for x in soa], L=8, flags=2,
+                               perturb=1e-4)
+        fragile = (out["flags"] & 4) != 0      # FP32 error model: hit/miss may flip
+        moved = (out["flags"] & 16) != 0       # origin perturbation by 1e-4 flips hit/miss
+        if expect:
+            assert fragile.all() and moved.all()
+        else:
+            assert out["flags"].max() == 0
