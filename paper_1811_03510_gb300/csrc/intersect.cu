@@ -1,8 +1,8 @@
 // Plain closest-hit kernel.  Persistent blocks; each warp keeps 32 rays in flight and takes new rays
-// from a global work queue whenever enough of its lanes are idle (warp-aggregated atomic).  Every
-// iteration of the warp loop is two phases separated by __syncwarp: BVH traversal until each lane
-// stands on a patch leaf (or is finished), then Algorithm 3 on those leaves with all such lanes
-// together, so that the expensive patch subdivision runs converged (while-while traversal).
+// from a global work queue whenever enough of its lanes are idle (warp-aggregated atomic).  Each
+// iteration of the warp loop advances every lane by one unit of work (lane_step), so lanes in
+// different phases (BVH, subdivision, re-descent) cost one step each instead of serialising whole
+// patch traversals.
 #include "traverse.cuh"
 
 namespace ccs {
@@ -26,8 +26,9 @@ __global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, De
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float cellw = __int_as_float((127 - L) << 23);
-    RayState s;
+    Lane s;
     BvhStack stk;
+    float g[48];
     bool has = false, exhausted = false;
     uint32_t ray_i = 0;
     for (;;) {
@@ -53,31 +54,29 @@ __global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, De
             if (exhausted) break;
             continue;
         }
-        bool ok = true;
-        if (has) ok = bvh_advance<STATS>(s, stk, sc, cnt);
-        __syncwarp();
-        if (has && ok && s.node != kDone) ok = leaf_step<STATS, K>(s, stk, sc, L, scr, cnt);
-        if (has && (!ok || s.node == kDone)) {
-            if (!ok) {
-                atomicOr(status, 1u);
-                s.best.pid = kMissId;
+        if (has) {
+            const bool ok = lane_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
+            if (!ok || lane_done(s)) {
+                if (!ok) {
+                    atomicOr(status, 1u);
+                    s.best.pid = kMissId;
+                }
+                const uint32_t i = ray_i;
+                if (s.best.pid != kMissId) {
+                    const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
+                    hits.t[i] = s.best.t;
+                    hits.u[i] = ((float)cu + 0.5f) * cellw;
+                    hits.v[i] = ((float)cv + 0.5f) * cellw;
+                    hits.pid[i] = s.best.pid;
+                } else {
+                    hits.t[i] = __int_as_float(0x7f800000);
+                    hits.u[i] = 0.0f;
+                    hits.v[i] = 0.0f;
+                    hits.pid[i] = kMissId;
+                }
+                has = false;
             }
-            const uint32_t i = ray_i;
-            if (s.best.pid != kMissId) {
-                const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
-                hits.t[i] = s.best.t;
-                hits.u[i] = ((float)cu + 0.5f) * cellw;
-                hits.v[i] = ((float)cv + 0.5f) * cellw;
-                hits.pid[i] = s.best.pid;
-            } else {
-                hits.t[i] = __int_as_float(0x7f800000);
-                hits.u[i] = 0.0f;
-                hits.v[i] = 0.0f;
-                hits.pid[i] = kMissId;
-            }
-            has = false;
         }
-        __syncwarp();
     }
     if (STATS) {
 #pragma unroll

@@ -359,9 +359,9 @@ struct StepOut {
 
 template <int K>
 CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, float dz, float c0, float c1, float tb,
-                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL = true, bool allowR = true)
+                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR, int force)
 {
-    float m01[12], m012[12], mm[12], m123[12], m23[12];
+    float e0[12], e3[12], m01[12], m012[12], mm[12], m123[12], m23[12];
     float lmin[3], lmax[3], rmin[3], rmax[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -372,6 +372,8 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
             const int q = c * 4 + b;
             const float b0 = g[c * 16 + 0 * 4 + b], b1 = g[c * 16 + 1 * 4 + b];
             const float b2 = g[c * 16 + 2 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
+            e0[q] = b0;
+            e3[q] = b3;
             m01[q] = mid(b0, b1);
             const float m12 = mid(b1, b2);
             m23[q] = mid(b2, b3);
@@ -393,16 +395,16 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
     slab(r, rmin[0], rmin[1], rmin[2], rmax[0] + dx, rmax[1] + dy, rmax[2] + dz, c0, c1, o.r0, o.r1);
     o.hitL = allowL && o.l0 <= o.l1 && o.l0 <= tb;
     o.hitR = allowR && o.r0 <= o.r1 && o.r0 <= tb;
-    o.goR = o.hitR && (!o.hitL || o.r0 < o.l0);
-    if ((o.hitL || o.hitR) && keep_grid) {
+    o.goR = force >= 0 ? force == 1 : (o.hitR && (!o.hitL || o.r0 < o.l0));
+    if ((force >= 0 || o.hitL || o.hitR) && keep_grid) {
         const bool up = o.goR;
-        const bool store = K > 0 && cache_slot >= 0 && o.hitL && o.hitR;
+        const bool store = K > 0 && force < 0 && cache_slot >= 0 && o.hitL && o.hitR;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int q = c * 4 + b;
-                const float b0 = g[c * 16 + 0 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
+                const float b0 = e0[q], b3 = e3[q];   // g is overwritten in place (transposed) below
                 const float k0 = up ? mm[q] : b0, k1 = up ? m123[q] : m01[q];
                 const float k2 = up ? m23[q] : m012[q], k3 = up ? b3 : mm[q];
                 if (K > 0 && store) {
@@ -423,130 +425,6 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
     return o;
 }
 
-// ------------------------------------------------------------------------------------------------
-// Algorithm 3 for one (ray, patch) pair, stackless with one bit trail over tree levels.
-//   path  bit l = the node at level l+1 is the upper half of its parent's split;
-//   trail bit l = the sibling of that node is still pending.
-// The split axis is fixed by the level (u at even levels), so one trail encodes both of the paper's
-// trails.  The entry/exit interval of every pending sibling is kept in shared memory (2 floats per
-// level): on backtracking, a sibling whose entry exceeds the best distance is dropped without any
-// recomputation, and Gregory children are clipped to their parent's interval, which keeps the answer
-// independent of the visiting order.  A Bezier sibling's grid comes from the K-slot cache when it is
-// still there, else from a de Casteljau re-descent from the root (same arithmetic as the descent).
-// Returns false if the iteration cap was hit.
-// ------------------------------------------------------------------------------------------------
-template <bool STATS, int K>
-CCS_DEV bool intersect_patch(const float4 *__restrict__ rec, uint32_t pid, float wox, float woy, float woz,
-                             const RayF &wr, float c0, float c1, int L, Best &best, const Scratch &scr,
-                             uint32_t &iters_left, Counters &cnt, uint32_t skip_path = 0xFFFFFFFFu,
-                             int skip_level = -1)
-{
-    const float4 an = __ldg(rec + 15);
-    const bool greg = an.w != 0.0f;
-    RayF r = wr;
-    r.oix = (wox - an.x) * wr.ix;
-    r.oiy = (woy - an.y) * wr.iy;
-    r.oiz = (woz - an.z) * wr.iz;
-    float g[48];
-    float dx = 0.0f, dy = 0.0f, dz = 0.0f;
-    int level = 0;
-    uint32_t path = 0, trail = 0;
-    int ctop = 0, cvalid = 0;   // cache: pushes so far (slot = ctop % K) and valid entries
-    if (greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, dx, dy, dz);
-    else load_grid(rec, g);
-    const int leaf_level = 2 * L;
-    for (;;) {
-        if (iters_left == 0) return false;
-        --iters_left;
-        bool descend = false;
-        if (level == leaf_level) {
-            uint32_t cu, cv;
-            path_cells(path, L, cu, cv);
-            const uint32_t cell = (cv << L) | cu;
-            if (STATS) cnt.v[3]++;
-            if (key_less(c0, pid, cell, best)) {
-                best.t = c0;
-                best.pid = pid;
-                best.cell = cell;
-            }
-        } else {
-            if (STATS) cnt.v[greg ? 2 : 1]++;
-            const int slot = (K > 0 && !greg) ? (ctop % (K > 0 ? K : 1)) : -1;
-            // a subtree already searched by a directed descent is not entered again
-            bool allowL = true, allowR = true;
-            if (skip_level == level + 1 && ((skip_path ^ path) & ((1u << level) - 1u)) == 0u) {
-                if ((skip_path >> level) & 1u) allowR = false; else allowL = false;
-            }
-            StepOut o = split_step<K>(g, r, dx, dy, dz, c0, c1, best.t, !greg, scr, slot, allowL, allowR);
-            if (o.hitL || o.hitR) {
-                const uint32_t bit = 1u << level;
-                if (o.hitL && o.hitR) {
-                    trail |= bit;
-                    scr.sib[level * scr.stride] = o.goR ? make_float2(o.l0, o.l1) : make_float2(o.r0, o.r1);
-                    if (K > 0 && !greg) {
-                        scr.tag[slot * scr.stride] = level;
-                        ++ctop;
-                        cvalid = cvalid < K ? cvalid + 1 : K;
-                    }
-                }
-                path = o.goR ? (path | bit) : path;
-                c0 = o.goR ? o.r0 : o.l0;
-                c1 = o.goR ? o.r1 : o.l1;
-                ++level;
-                if (greg) {
-                    float u0, u1, v0, v1;
-                    node_domain(path, level, L, u0, u1, v0, v1);
-                    gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
-                }
-                descend = true;
-            }
-        }
-        if (descend) continue;
-        // backtrack to the deepest pending sibling that can still hold a closer leaf
-        bool resumed = false;
-        while (trail != 0u) {
-            const int l = 31 - __clz(trail);
-            const uint32_t bit = 1u << l;
-            trail ^= bit;
-            bool cached = false;
-            int cslot = 0;
-            if (K > 0 && !greg && cvalid > 0) {
-                cslot = (ctop - 1) % (K > 0 ? K : 1);
-                if (scr.tag[cslot * scr.stride] == l) {
-                    cached = true;
-                    --ctop;
-                    --cvalid;
-                }
-            }
-            const float2 s = scr.sib[l * scr.stride];
-            if (s.x > best.t) {
-                if (STATS) cnt.v[6]++;
-                continue;
-            }
-            path = (path & (bit - 1u)) | (~path & bit);
-            level = l + 1;
-            c0 = s.x;
-            c1 = s.y;
-            if (STATS) cnt.v[4]++;
-            if (greg) {
-                float u0, u1, v0, v1;
-                node_domain(path, level, L, u0, u1, v0, v1);
-                gregory_node(rec, u0, u1, v0, v1, level, g, dx, dy, dz);
-            } else if (cached) {
-                const float *src = scr.cache + (size_t)(cslot * 48) * scr.stride;
-#pragma unroll
-                for (int k = 0; k < 48; ++k) g[k] = src[k * scr.stride];
-            } else {
-                if (STATS) cnt.v[5] += level;
-                redescend(rec, path, level, g);
-            }
-            resumed = true;
-            break;
-        }
-        if (!resumed) return true;
-    }
-}
-
 // World-space slab test against both child boxes of a BVH node.
 CCS_DEV void node_child_boxes(const float4 *__restrict__ nodes, int idx, const RayF &r, float c0, float c1, float &a0,
                               float &a1, float &b0, float &b1, int &ch0, int &ch1)
@@ -565,24 +443,49 @@ constexpr int kBvhStack = 64;
 constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
 constexpr int kDone = (int)0x80000000;    // traversal finished
 
-// Per-ray traversal state of the BVH (node stack in local memory).
-struct RayState {
-    float ox, oy, oz, tmin, tmax;
-    RayF r;
-    int node;          // >= 0 internal node, kDone, else leaf of patch ~node
-    float n0, n1;      // interval of `node`
-    int sp;
-    uint32_t iters;
-    Best best;
-};
-
 // BVH node stack of one thread (local memory): node index and its interval.
 struct BvhStack {
     int node[kBvhStack];
     float2 t[kBvhStack];
 };
 
-CCS_DEV void begin_ray(RayState &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
+// ------------------------------------------------------------------------------------------------
+// Per-lane state machine.  A lane owns one ray; every call of lane_step() does one unit of work:
+// one BVH node, the start of a patch, one subdivision step of Algorithm 3, one level of a re-descent,
+// or one leaf / backtrack.  All subdivision and re-descent steps go through one call of split_step,
+// so lanes of a warp in different phases of Algorithm 3 stay converged on the expensive part.
+//
+// Algorithm 3 with one bit trail over tree levels:
+//   path  bit l = the node at level l+1 is the upper half of its parent's split;
+//   trail bit l = the sibling of that node is still pending.
+// The split axis is fixed by the level (u at even levels), so one trail encodes both of the paper's
+// trails.  The entry/exit interval of every pending sibling is kept in shared memory: on backtracking
+// a sibling whose entry exceeds the best distance is dropped with no recomputation, and Gregory
+// children are clipped to their parent's interval, which keeps the answer independent of the
+// visiting order.  A Bezier sibling's grid comes from the K-slot cache when it is still there, else
+// from a de Casteljau re-descent from the root along the path bits (same arithmetic as the descent).
+// ------------------------------------------------------------------------------------------------
+struct Lane {
+    float ox, oy, oz, tmin, tmax;   // ray, world frame
+    RayF r;
+    Best best;
+    uint32_t iters;
+    int node;                       // BVH: >= 0 internal node, kDone, else leaf of patch ~node
+    float n0, n1;                   // interval of `node`
+    int sp;
+    bool in_pair, greg;             // Algorithm 3 on patch `pid`
+    uint32_t pid;
+    RayF pr;                        // ray in the patch's anchored frame
+    float dx, dy, dz;               // Gregory displacement of the current node
+    int level, rd_target;           // tree level; re-descent target level (-1: none)
+    uint32_t path, trail;
+    float c0, c1;                   // interval of the current node
+    int ctop, cvalid;               // sibling cache: pushes (slot = ctop % K) and valid entries
+    uint32_t skip_path;             // subtree (skip_path, skip_level) not to enter again
+    int skip_level;
+};
+
+CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
                        float tmin, float tmax, uint32_t iter_cap)
 {
     s.best.t = tmax;
@@ -595,6 +498,9 @@ CCS_DEV void begin_ray(RayState &s, const DevScene &sc, float ox, float oy, floa
     s.node = 0;
     s.n0 = tmin;
     s.n1 = tmax;
+    s.in_pair = false;
+    s.skip_level = -1;
+    s.skip_path = 0xFFFFFFFFu;
     const bool bad = !(tmin <= tmax) || sc.n_nodes == 0 || isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx) ||
                      isnan(dy) || isnan(dz);
     if (bad) {
@@ -609,7 +515,9 @@ CCS_DEV void begin_ray(RayState &s, const DevScene &sc, float ox, float oy, floa
     s.r.oiz = oz * s.r.iz;
 }
 
-CCS_DEV void pop_next(RayState &s, BvhStack &stk)
+CCS_DEV bool lane_done(const Lane &s) { return !s.in_pair && s.node == kDone; }
+
+CCS_DEV void pop_next(Lane &s, BvhStack &stk)
 {
     while (s.sp > 0) {
         --s.sp;
@@ -623,53 +531,188 @@ CCS_DEV void pop_next(RayState &s, BvhStack &stk)
     s.node = kDone;
 }
 
-// BVH traversal until `node` is a leaf or the traversal is finished (nearer child first, nodes
-// pruned by entry distance).  Returns false on the iteration cap.
-template <bool STATS>
-CCS_DEV bool bvh_advance(RayState &s, BvhStack &stk, const DevScene &sc, Counters &cnt)
+CCS_DEV const float4 *rec_of(const DevScene &sc, uint32_t pid) { return sc.rec + (size_t)pid * kRecF4; }
+
+// Begin Algorithm 3 on patch pid with root interval [c0, c1].
+CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pid, float c0, float c1)
 {
-    while (s.node >= 0) {
-        if (s.iters == 0) return false;
-        --s.iters;
-        if (STATS) cnt.v[0]++;
-        float a0, a1, b0, b1;
-        int c0, c1;
-        node_child_boxes(sc.nodes, s.node, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
-        const bool ha = a0 <= a1 && a0 <= s.best.t && c0 != kEmptyChild;
-        const bool hb = b0 <= b1 && b0 <= s.best.t && c1 != kEmptyChild;
-        if (ha && hb) {
-            const bool bfirst = b0 < a0;
-            if (s.sp < kBvhStack) {
-                stk.node[s.sp] = bfirst ? c0 : c1;
-                stk.t[s.sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
-                ++s.sp;
+    const float4 *rec = rec_of(sc, pid);
+    const float4 an = __ldg(rec + 15);
+    s.in_pair = true;
+    s.greg = an.w != 0.0f;
+    s.pid = pid;
+    s.pr = s.r;
+    s.pr.oix = (s.ox - an.x) * s.r.ix;
+    s.pr.oiy = (s.oy - an.y) * s.r.iy;
+    s.pr.oiz = (s.oz - an.z) * s.r.iz;
+    s.dx = s.dy = s.dz = 0.0f;
+    s.level = 0;
+    s.rd_target = -1;
+    s.path = s.trail = 0u;
+    s.c0 = c0;
+    s.c1 = c1;
+    s.ctop = s.cvalid = 0;
+    if (s.greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, s.dx, s.dy, s.dz);
+    else load_grid(rec, g);
+}
+
+// Backtrack to the deepest pending sibling that can still hold a closer leaf, or end the pair.
+template <bool STATS, int K>
+CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
+                       Counters &cnt)
+{
+    while (s.trail != 0u) {
+        const int l = 31 - __clz(s.trail);
+        const uint32_t bit = 1u << l;
+        s.trail ^= bit;
+        bool cached = false;
+        int cslot = 0;
+        if (K > 0 && !s.greg && s.cvalid > 0) {
+            cslot = (s.ctop - 1) % (K > 0 ? K : 1);
+            if (scr.tag[cslot * scr.stride] == l) {
+                cached = true;
+                --s.ctop;
+                --s.cvalid;
             }
-            s.node = bfirst ? c1 : c0;
-            s.n0 = bfirst ? b0 : a0;
-            s.n1 = bfirst ? b1 : a1;
-        } else if (ha || hb) {
-            s.node = ha ? c0 : c1;
-            s.n0 = ha ? a0 : b0;
-            s.n1 = ha ? a1 : b1;
+        }
+        const float2 sb = scr.sib[l * scr.stride];
+        if (sb.x > s.best.t) {
+            if (STATS) cnt.v[6]++;
+            continue;
+        }
+        s.path = (s.path & (bit - 1u)) | (~s.path & bit);
+        s.c0 = sb.x;
+        s.c1 = sb.y;
+        if (STATS) cnt.v[4]++;
+        const float4 *rec = rec_of(sc, s.pid);
+        if (s.greg) {
+            s.level = l + 1;
+            float u0, u1, v0, v1;
+            node_domain(s.path, s.level, L, u0, u1, v0, v1);
+            gregory_node(rec, u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+        } else if (cached) {
+            s.level = l + 1;
+            const float *src = scr.cache + (size_t)(cslot * 48) * scr.stride;
+#pragma unroll
+            for (int k = 0; k < 48; ++k) g[k] = src[k * scr.stride];
+        } else {
+            if (STATS) cnt.v[5] += l + 1;
+            load_grid(rec, g);
+            s.level = 0;
+            s.rd_target = l + 1;
+        }
+        return;
+    }
+    s.in_pair = false;
+    pop_next(s, stk);
+}
+
+// One step of Algorithm 3 on the lane's current pair.
+template <bool STATS, int K>
+CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
+                       Counters &cnt)
+{
+    const bool redesc = s.rd_target >= 0;
+    if (!redesc && s.level == 2 * L) {
+        uint32_t cu, cv;
+        path_cells(s.path, L, cu, cv);
+        const uint32_t cell = (cv << L) | cu;
+        if (STATS) cnt.v[3]++;
+        if (key_less(s.c0, s.pid, cell, s.best)) {
+            s.best.t = s.c0;
+            s.best.pid = s.pid;
+            s.best.cell = cell;
+        }
+        backtrack<STATS, K>(s, g, stk, sc, L, scr, cnt);
+        return;
+    }
+    const int force = redesc ? (int)((s.path >> s.level) & 1u) : -1;
+    const int slot = (!redesc && K > 0 && !s.greg) ? (s.ctop % (K > 0 ? K : 1)) : -1;
+    bool allowL = true, allowR = true;   // a subtree already searched by a directed descent is not entered
+    if (!redesc && s.skip_level == s.level + 1 && ((s.skip_path ^ s.path) & ((1u << s.level) - 1u)) == 0u) {
+        if ((s.skip_path >> s.level) & 1u) allowR = false; else allowL = false;
+    }
+    if (STATS && !redesc) cnt.v[s.greg ? 2 : 1]++;
+    const StepOut o = split_step<K>(g, s.pr, s.dx, s.dy, s.dz, s.c0, s.c1, s.best.t, redesc || !s.greg, scr, slot,
+                                    allowL, allowR, force);
+    if (redesc) {
+        if (++s.level == s.rd_target) s.rd_target = -1;
+        return;
+    }
+    if (o.hitL || o.hitR) {
+        const uint32_t bit = 1u << s.level;
+        if (o.hitL && o.hitR) {
+            s.trail |= bit;
+            scr.sib[s.level * scr.stride] = o.goR ? make_float2(o.l0, o.l1) : make_float2(o.r0, o.r1);
+            if (K > 0 && !s.greg) {
+                scr.tag[slot * scr.stride] = s.level;
+                ++s.ctop;
+                s.cvalid = s.cvalid < K ? s.cvalid + 1 : K;
+            }
+        }
+        s.path = o.goR ? (s.path | bit) : s.path;
+        s.c0 = o.goR ? o.r0 : o.l0;
+        s.c1 = o.goR ? o.r1 : o.l1;
+        ++s.level;
+        if (s.greg) {
+            float u0, u1, v0, v1;
+            node_domain(s.path, s.level, L, u0, u1, v0, v1);
+            gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+        }
+        return;
+    }
+    backtrack<STATS, K>(s, g, stk, sc, L, scr, cnt);
+}
+
+// One BVH step: expand an internal node (nearer child first), or start the pair of a leaf.
+template <bool STATS>
+CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, Counters &cnt)
+{
+    if (s.node == kDone) return;
+    if (s.node < 0) {
+        const uint32_t pid = (uint32_t)(~s.node);
+        if (s.n0 <= s.best.t) {
+            if (STATS) cnt.v[7]++;
+            start_pair(s, g, sc, pid, s.n0, s.n1);
         } else {
             pop_next(s, stk);
         }
+        return;
     }
-    return true;
+    if (STATS) cnt.v[0]++;
+    float a0, a1, b0, b1;
+    int c0, c1;
+    node_child_boxes(sc.nodes, s.node, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
+    const bool ha = a0 <= a1 && a0 <= s.best.t && c0 != kEmptyChild;
+    const bool hb = b0 <= b1 && b0 <= s.best.t && c1 != kEmptyChild;
+    if (ha && hb) {
+        const bool bfirst = b0 < a0;
+        if (s.sp < kBvhStack) {
+            stk.node[s.sp] = bfirst ? c0 : c1;
+            stk.t[s.sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
+            ++s.sp;
+        }
+        s.node = bfirst ? c1 : c0;
+        s.n0 = bfirst ? b0 : a0;
+        s.n1 = bfirst ? b1 : a1;
+    } else if (ha || hb) {
+        s.node = ha ? c0 : c1;
+        s.n0 = ha ? a0 : b0;
+        s.n1 = ha ? a1 : b1;
+    } else {
+        pop_next(s, stk);
+    }
 }
 
-// Algorithm 3 on the leaf patch `node`, then continue with the next stacked node.
+// One unit of work; returns false when the iteration cap is reached.
 template <bool STATS, int K>
-CCS_DEV bool leaf_step(RayState &s, BvhStack &stk, const DevScene &sc, int L, const Scratch &scr, Counters &cnt)
+CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
+                       Counters &cnt)
 {
-    const uint32_t pid = (uint32_t)(~s.node);
-    if (s.n0 <= s.best.t) {
-        if (STATS) cnt.v[7]++;
-        if (!intersect_patch<STATS, K>(sc.rec + (size_t)pid * kRecF4, pid, s.ox, s.oy, s.oz, s.r, s.n0, s.n1, L,
-                                       s.best, scr, s.iters, cnt))
-            return false;
-    }
-    pop_next(s, stk);
+    if (s.iters == 0) return false;
+    --s.iters;
+    if (s.in_pair) pair_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
+    else bvh_step<STATS>(s, g, stk, sc, cnt);
     return true;
 }
 
