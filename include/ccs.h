@@ -65,8 +65,12 @@ typedef struct {
     uint32_t leaf_depth;      /* L, splits per axis of the (u,v) domain, 1..15 [8] */
     uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
     uint32_t blocks_per_sm;   /* blocks per SM of the persistent launch, clamped to what fits [4] */
-    uint32_t refill;          /* a warp takes new rays from the global queue once at least this many of
-                                 its 32 lanes are idle, 1..32 [16] */
+    uint32_t refill;          /* a warp hands new rays to its idle lanes once at least this many of its
+                                 32 lanes are idle, 1..32 [1] */
+    uint32_t chunk;           /* rays a warp takes from the global work queue at a time, multiple of 32,
+                                 32..4096 [128] */
+    uint32_t bvh_burst;       /* BVH steps a traversing lane takes per subdivision step of the others,
+                                 1..16 [4] */
     uint32_t cache_slots;     /* grids of pending Bezier siblings kept in shared memory per thread,
                                  0 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root */
     uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
@@ -144,6 +148,23 @@ ccs_status ccs_scene_info(const ccs_scene *scene, uint32_t *n_patches, uint32_t 
  * Asynchronous on `stream`. */
 ccs_status ccs_gen_diffuse(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
                            uint64_t seed, uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
+
+/* One measured candidate of ccs_autotune. */
+typedef struct {
+    ccs_trace_opts opts;
+    float ms;                 /* mean time of one ccs_intersect launch */
+} ccs_autotune_trial;
+
+/* Autotuner: coordinate descent (two passes) over threads per block {64, 96, 128}, blocks per SM
+ * {1..4}, refill {1, 2, 4, 8}, chunk {32..1024}, bvh_burst {1..16} and cache_slots {0, 2}, starting from
+ * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so
+ * tuning is safe.  Each candidate is timed with CUDA events over `reps` launches (after one warm-up)
+ * of ccs_intersect on the caller's device rays/hits on `stream`, which is synchronised.  The fastest
+ * is written to *best and its mean launch time to *best_ms; if `trials` is given, up to max_trials
+ * measurements are recorded and *n_trials receives the number made. */
+ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                        const ccs_trace_opts *base, uint32_t reps, ccs_trace_opts *best, float *best_ms,
+                        ccs_autotune_trial *trials, uint32_t max_trials, uint32_t *n_trials, void *stream);
 
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *ccs_last_error(void);

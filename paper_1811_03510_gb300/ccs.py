@@ -43,9 +43,13 @@ class ccs_hits(ctypes.Structure):
 
 class ccs_trace_opts(ctypes.Structure):
     _fields_ = [("leaf_depth", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
-                ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32),
-                ("iter_cap", ctypes.c_uint32),
+                ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
+                ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
+
+
+class ccs_autotune_trial(ctypes.Structure):
+    _fields_ = [("opts", ccs_trace_opts), ("ms", ctypes.c_float)]
 
 
 class ccs_bvh_params(ctypes.Structure):
@@ -69,6 +73,10 @@ _SIGS = {
     "ccs_scene_sync_status": [ctypes.c_void_p, ctypes.c_void_p],
     "ccs_gen_diffuse": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays), ctypes.c_void_p],
+    "ccs_autotune": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.POINTER(ccs_hits),
+                     ctypes.POINTER(ccs_trace_opts), ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts),
+                     ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ccs_autotune_trial), ctypes.c_uint32,
+                     ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -131,13 +139,15 @@ def _stream(s) -> int:
 CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 
-def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, cache_slots=CCS_CACHE_DEFAULT, iter_cap=0,
-              counters=None) -> ccs_trace_opts:
+def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
+              cache_slots=CCS_CACHE_DEFAULT, iter_cap=0, counters=None) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
     o.blocks_per_sm = blocks_per_sm
     o.refill = refill
+    o.chunk = chunk
+    o.bvh_burst = bvh_burst
     o.cache_slots = cache_slots
     o.iter_cap = iter_cap
     o.flags = CCS_TRACE_COUNT if counters is not None else 0
@@ -214,6 +224,26 @@ def gen_diffuse(scene: "Scene", rays_dev, hits, seed: int, leaf_depth: int = 8, 
     planes = [o[:n], o[n:2 * n], o[2 * n:], d[:n], d[n:2 * n], d[2 * n:], tmin, tmax]
     ccs_gen_diffuse(scene.handle, rays_dev, hits, n, seed, leaf_depth, offset_abs, planes, stream)
     return planes
+
+
+def ccs_autotune(scene: int, rays, n: int, hits, base: ccs_trace_opts | None = None, reps: int = 3, stream=None,
+                 max_trials: int = 256):
+    """Returns (best opts, best ms, list of (opts, ms) trials)."""
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    best = ccs_trace_opts()
+    ms = ctypes.c_float()
+    tr = (ccs_autotune_trial * max_trials)()
+    nt = ctypes.c_uint32()
+    _check(lib().ccs_autotune(scene, ctypes.byref(r), n, ctypes.byref(h), ctypes.byref(base) if base else None, reps,
+                              ctypes.byref(best), ctypes.byref(ms), tr, max_trials, ctypes.byref(nt), _stream(stream)))
+    trials = [(tr[i].opts, tr[i].ms) for i in range(min(nt.value, max_trials))]
+    return best, ms.value, trials
+
+
+def opts_dict(o: ccs_trace_opts) -> dict:
+    return {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
+                                             "bvh_burst", "cache_slots")}
 
 
 def ccs_scene_sync_status(scene: int, stream=None) -> int:

@@ -59,7 +59,9 @@ ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.leaf_depth = o && o->leaf_depth ? o->leaf_depth : 8;
     c.block_threads = o && o->block_threads ? o->block_threads : 128;
     c.blocks_per_sm = o && o->blocks_per_sm ? o->blocks_per_sm : 4;
-    c.refill = o && o->refill ? o->refill : 16;
+    c.refill = o && o->refill ? o->refill : 1;
+    c.chunk = o && o->chunk ? o->chunk : 128;
+    c.bvh_burst = o && o->bvh_burst ? o->bvh_burst : 4;
     c.cache_slots = (!o || o->cache_slots == CCS_CACHE_DEFAULT) ? 2 : o->cache_slots;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
@@ -69,6 +71,8 @@ ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
             "block_threads must be a multiple of 32 in 32..128");
     CCS_ARG(c.blocks_per_sm >= 1 && c.blocks_per_sm <= 64, "blocks_per_sm must be in 1..64");
     CCS_ARG(c.refill >= 1 && c.refill <= 32, "refill must be in 1..32");
+    CCS_ARG(c.chunk % 32 == 0 && c.chunk >= 32 && c.chunk <= 4096, "chunk must be a multiple of 32 in 32..4096");
+    CCS_ARG(c.bvh_burst >= 1 && c.bvh_burst <= 16, "bvh_burst must be in 1..16");
     CCS_ARG(c.cache_slots == 0 || c.cache_slots == 2, "cache_slots must be 0 or 2");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;

@@ -1,0 +1,101 @@
+// Autotuner of the closest-hit launch: coordinate descent over options that cannot change the answer
+// (threads per block, blocks per SM, warp refill threshold, queue chunk, BVH burst, sibling cache),
+// each candidate timed with CUDA events over `reps` launches on the caller's rays.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <string>
+#include <vector>
+
+#include "ccs_internal.h"
+
+using namespace ccs;
+
+extern "C" {
+
+ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                        const ccs_trace_opts *base, uint32_t reps, ccs_trace_opts *best, float *best_ms,
+                        ccs_autotune_trial *trials, uint32_t max_trials, uint32_t *n_trials, void *stream)
+{
+    if (!scene || !rays || !hits || !best || n == 0) {
+        set_error("ccs_autotune: scene, rays, hits and best must be given and n > 0");
+        return CCS_ERR_INVALID_ARG;
+    }
+    if (reps == 0) reps = 3;
+    cudaStream_t s = (cudaStream_t)stream;
+    ccs_trace_opts cur{};
+    if (base) cur = *base;
+    cur.flags = 0;
+    cur.counters = nullptr;
+    if (!cur.leaf_depth) cur.leaf_depth = 8;
+    if (!cur.block_threads) cur.block_threads = 128;
+    if (!cur.blocks_per_sm) cur.blocks_per_sm = 4;
+    if (!cur.refill) cur.refill = 1;
+    if (!cur.chunk) cur.chunk = 128;
+    if (!cur.bvh_burst) cur.bvh_burst = 4;
+    if (cur.cache_slots == CCS_CACHE_DEFAULT) cur.cache_slots = 2;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        set_error("ccs_autotune: cudaEventCreate failed");
+        return CCS_ERR_CUDA;
+    }
+    uint32_t count = 0;
+    auto measure = [&](const ccs_trace_opts &o, float &ms) -> ccs_status {
+        ccs_status st = ccs_intersect(scene, rays, n, hits, &o, stream);   // warm-up
+        if (st != CCS_OK) return st;
+        cudaEventRecord(e0, s);
+        for (uint32_t r = 0; r < reps; ++r)
+            if ((st = ccs_intersect(scene, rays, n, hits, &o, stream)) != CCS_OK) return st;
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            set_error("ccs_autotune: launch failed");
+            return CCS_ERR_CUDA;
+        }
+        cudaEventElapsedTime(&ms, e0, e1);
+        ms /= (float)reps;
+        if (trials && count < max_trials) {
+            trials[count].opts = o;
+            trials[count].ms = ms;
+        }
+        ++count;
+        return CCS_OK;
+    };
+    float cur_ms = FLT_MAX;
+    ccs_status st = measure(cur, cur_ms);
+    const std::vector<uint32_t> threads_c = {64, 96, 128};
+    const std::vector<uint32_t> bps_c = {1, 2, 3, 4};
+    const std::vector<uint32_t> refill_c = {1, 2, 4, 8};
+    const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
+    const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
+    const std::vector<uint32_t> cache_c = {0, 2};
+    for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
+        for (int knob = 0; knob < 6 && st == CCS_OK; ++knob) {
+            const std::vector<uint32_t> &cand =
+                knob == 0 ? threads_c : knob == 1 ? bps_c : knob == 2 ? refill_c : knob == 3 ? chunk_c
+                                                                                               : knob == 4 ? burst_c
+                                                                                                           : cache_c;
+            for (uint32_t v : cand) {
+                ccs_trace_opts o = cur;
+                uint32_t *field = knob == 0 ? &o.block_threads : knob == 1 ? &o.blocks_per_sm : knob == 2 ? &o.refill
+                                  : knob == 3 ? &o.chunk : knob == 4 ? &o.bvh_burst : &o.cache_slots;
+                if (*field == v) continue;
+                *field = v;
+                float ms = FLT_MAX;
+                if ((st = measure(o, ms)) != CCS_OK) break;
+                if (ms < cur_ms) {
+                    cur_ms = ms;
+                    cur = o;
+                }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != CCS_OK) return st;
+    *best = cur;
+    if (best_ms) *best_ms = cur_ms;
+    if (n_trials) *n_trials = count;
+    return CCS_OK;
+}
+
+}  // extern "C"

@@ -9,8 +9,8 @@ namespace ccs {
 
 template <bool STATS, int K>
 __global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, DevHits hits, uint32_t n, int L,
-                                                   uint32_t refill, uint32_t iter_cap, uint32_t *queue,
-                                                   uint32_t *status, unsigned long long *counters)
+                                                   uint32_t refill, uint32_t chunk, int burst, uint32_t iter_cap,
+                                                   uint32_t *queue, uint32_t *status, unsigned long long *counters)
 {
     extern __shared__ float smem[];
     const int stride = blockDim.x;
@@ -31,31 +31,39 @@ __global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, De
     float g[48];
     bool has = false, exhausted = false;
     uint32_t ray_i = 0;
+    uint32_t wnext = 0, wend = 0;   // warp-uniform range of rays taken from the queue, not yet handed out
     for (;;) {
         const unsigned idle = __ballot_sync(FULL, !has);
-        if (!exhausted && idle != 0u && ((uint32_t)__popc(idle) >= refill || idle == FULL)) {
-            const int cnt_idle = __popc(idle), leader = __ffs(idle) - 1;
-            uint32_t base = 0;
-            if (lane == leader) base = atomicAdd(queue, (uint32_t)cnt_idle);
-            base = __shfl_sync(FULL, base, leader);
-            if (base + (uint32_t)cnt_idle >= n) exhausted = true;
-            if (!has) {
-                const uint32_t i = base + (uint32_t)__popc(idle & lt_mask);
-                if (i < n) {
-                    has = true;
-                    ray_i = i;
-                    begin_ray(s, sc, __ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i), __ldg(rays.dx + i),
-                              __ldg(rays.dy + i), __ldg(rays.dz + i), __ldg(rays.tmin + i), __ldg(rays.tmax + i),
-                              iter_cap);
+        if (idle != 0u && ((uint32_t)__popc(idle) >= refill || idle == FULL)) {
+            if (wnext == wend && !exhausted) {
+                uint32_t base = 0;
+                if (lane == 0) base = atomicAdd(queue, chunk);
+                base = __shfl_sync(FULL, base, 0);
+                if (base >= n) {
+                    exhausted = true;
+                } else {
+                    wnext = base;
+                    wend = min(base + chunk, n);
                 }
             }
+            const uint32_t avail = wend - wnext;
+            const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
+            if (!has && rank < avail) {
+                const uint32_t i = wnext + rank;
+                has = true;
+                ray_i = i;
+                begin_ray(s, sc, __ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i), __ldg(rays.dx + i),
+                          __ldg(rays.dy + i), __ldg(rays.dz + i), __ldg(rays.tmin + i), __ldg(rays.tmax + i), iter_cap);
+            }
+            const uint32_t taken = avail < (uint32_t)__popc(idle) ? avail : (uint32_t)__popc(idle);
+            wnext += taken;
         }
         if (__ballot_sync(FULL, has) == 0u) {
-            if (exhausted) break;
+            if (exhausted && wnext == wend) break;
             continue;
         }
         if (has) {
-            const bool ok = lane_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
+            const bool ok = lane_step<STATS, K>(s, g, stk, sc, L, scr, cnt, burst);
             if (!ok || lane_done(s)) {
                 if (!ok) {
                     atomicOr(status, 1u);
@@ -115,8 +123,8 @@ static cudaError_t launch_one(const DevScene &sc, const DevRays &r, const DevHit
     const uint32_t needed = (n + threads - 1) / threads;
     if (blocks > needed) blocks = needed;
     if (blocks == 0) blocks = 1;
-    kern<<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth, cfg.refill, cfg.iter_cap, queue, status,
-                                       cfg.counters);
+    kern<<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
+                                       cfg.iter_cap, queue, status, cfg.counters);
     return cudaGetLastError();
 }
 

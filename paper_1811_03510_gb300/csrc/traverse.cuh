@@ -37,8 +37,8 @@ CCS_DEV float mid(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
 constexpr float kFarScale = 1.00000048f;
 
 struct RayF {
-    float ix, iy, iz;      // 1 / d (tiny components clamped so that the products stay finite)
-    float oix, oiy, oiz;   // o * inv for the frame in use (world for the BVH, patch-anchored inside a patch)
+    float ix, iy, iz;   // 1 / d (tiny components clamped so that the products stay finite)
+    float ox, oy, oz;   // origin in the frame in use (world for the BVH, patch-anchored inside a patch)
 };
 
 CCS_DEV float safe_inv(float d)
@@ -48,13 +48,15 @@ CCS_DEV float safe_inv(float d)
 }
 
 // Ray interval inside box [lo, hi], intersected with [c0, c1]: t0 = max(c0, near), t1 = min(c1, far).
-// Monotone in the box bounds, so a box inside another gives an interval inside the other's.
+// Monotone in the box bounds, so a box inside another gives an interval inside the other's.  The
+// difference is rounded before the product, so a bound lying exactly on the origin gives exactly 0
+// even for a clamped (huge) inverse: rays along a shared boundary plane stay inside both boxes.
 CCS_DEV void slab(const RayF &r, float lox, float loy, float loz, float hix, float hiy, float hiz, float c0,
                   float c1, float &t0, float &t1)
 {
-    float ax = fmaf(lox, r.ix, -r.oix), bx = fmaf(hix, r.ix, -r.oix);
-    float ay = fmaf(loy, r.iy, -r.oiy), by = fmaf(hiy, r.iy, -r.oiy);
-    float az = fmaf(loz, r.iz, -r.oiz), bz = fmaf(hiz, r.iz, -r.oiz);
+    const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
+    const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
+    const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
     float tn = max3f(fminf(ax, bx), fminf(ay, by), fminf(az, bz));
     float tf = min3f(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
     t0 = fmaxf(tn, c0);
@@ -510,9 +512,9 @@ CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz
     s.r.ix = safe_inv(dx);
     s.r.iy = safe_inv(dy);
     s.r.iz = safe_inv(dz);
-    s.r.oix = ox * s.r.ix;
-    s.r.oiy = oy * s.r.iy;
-    s.r.oiz = oz * s.r.iz;
+    s.r.ox = ox;
+    s.r.oy = oy;
+    s.r.oz = oz;
 }
 
 CCS_DEV bool lane_done(const Lane &s) { return !s.in_pair && s.node == kDone; }
@@ -542,9 +544,9 @@ CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pi
     s.greg = an.w != 0.0f;
     s.pid = pid;
     s.pr = s.r;
-    s.pr.oix = (s.ox - an.x) * s.r.ix;
-    s.pr.oiy = (s.oy - an.y) * s.r.iy;
-    s.pr.oiz = (s.oz - an.z) * s.r.iz;
+    s.pr.ox = s.ox - an.x;
+    s.pr.oy = s.oy - an.y;
+    s.pr.oz = s.oz - an.z;
     s.dx = s.dy = s.dz = 0.0f;
     s.level = 0;
     s.rd_target = -1;
@@ -704,15 +706,23 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
     }
 }
 
-// One unit of work; returns false when the iteration cap is reached.
+// One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
+// so lanes that traverse catch up while the others subdivide).  Returns false on the iteration cap.
 template <bool STATS, int K>
 CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt)
+                       Counters &cnt, int burst)
 {
-    if (s.iters == 0) return false;
-    --s.iters;
-    if (s.in_pair) pair_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
-    else bvh_step<STATS>(s, g, stk, sc, cnt);
+    if (s.in_pair) {
+        if (s.iters == 0) return false;
+        --s.iters;
+        pair_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
+        return true;
+    }
+    for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
+        if (s.iters == 0) return false;
+        --s.iters;
+        bvh_step<STATS>(s, g, stk, sc, cnt);
+    }
     return true;
 }
 

