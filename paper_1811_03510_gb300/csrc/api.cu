@@ -63,6 +63,7 @@ ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.chunk = o && o->chunk ? o->chunk : 128;
     c.bvh_burst = o && o->bvh_burst ? o->bvh_burst : 4;
     c.cache_slots = (!o || o->cache_slots == CCS_CACHE_DEFAULT) ? 2 : o->cache_slots;
+    c.min_blocks = o ? o->min_blocks : 0;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
@@ -74,6 +75,7 @@ ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.chunk % 32 == 0 && c.chunk >= 32 && c.chunk <= 4096, "chunk must be a multiple of 32 in 32..4096");
     CCS_ARG(c.bvh_burst >= 1 && c.bvh_burst <= 16, "bvh_burst must be in 1..16");
     CCS_ARG(c.cache_slots == 0 || c.cache_slots == 2, "cache_slots must be 0 or 2");
+    CCS_ARG(c.min_blocks == 0 || c.min_blocks == 4, "min_blocks must be 0 or 4");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;
 }

@@ -68,16 +68,15 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> cache_c = {0, 2};
+    const std::vector<uint32_t> minb_c = {0, 4};
+    const std::vector<uint32_t> *cands[7] = {&threads_c, &bps_c, &refill_c, &chunk_c, &burst_c, &cache_c, &minb_c};
     for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
-        for (int knob = 0; knob < 6 && st == CCS_OK; ++knob) {
-            const std::vector<uint32_t> &cand =
-                knob == 0 ? threads_c : knob == 1 ? bps_c : knob == 2 ? refill_c : knob == 3 ? chunk_c
-                                                                                               : knob == 4 ? burst_c
-                                                                                                           : cache_c;
-            for (uint32_t v : cand) {
+        for (int knob = 0; knob < 7 && st == CCS_OK; ++knob) {
+            for (uint32_t v : *cands[knob]) {
                 ccs_trace_opts o = cur;
-                uint32_t *field = knob == 0 ? &o.block_threads : knob == 1 ? &o.blocks_per_sm : knob == 2 ? &o.refill
-                                  : knob == 3 ? &o.chunk : knob == 4 ? &o.bvh_burst : &o.cache_slots;
+                uint32_t *fields[7] = {&o.block_threads, &o.blocks_per_sm, &o.refill, &o.chunk, &o.bvh_burst,
+                                       &o.cache_slots, &o.min_blocks};
+                uint32_t *field = fields[knob];
                 if (*field == v) continue;
                 *field = v;
                 float ms = FLT_MAX;

@@ -29,7 +29,7 @@ constexpr int kMaxLeafDepth = 15;
 constexpr int kNumCounters = CCS_NUM_COUNTERS;
 
 struct LaunchCfg {
-    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, iter_cap, flags;
+    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, iter_cap, flags;
     unsigned long long *counters;
 };
 

@@ -7,8 +7,8 @@
 
 namespace ccs {
 
-template <bool STATS, int K>
-__global__ void __launch_bounds__(128) k_intersect(DevScene sc, DevRays rays, DevHits hits, uint32_t n, int L,
+template <bool STATS, int K, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_intersect(DevScene sc, DevRays rays, DevHits hits, uint32_t n, int L,
                                                    uint32_t refill, uint32_t chunk, int burst, uint32_t iter_cap,
                                                    uint32_t *queue, uint32_t *status, unsigned long long *counters)
 {
@@ -101,11 +101,11 @@ size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
     return (size_t)threads * (2 * 2 * L + 48 * K + K) * sizeof(float);
 }
 
-template <bool STATS, int K>
+template <bool STATS, int K, int MINB>
 static cudaError_t launch_one(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
                               uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
 {
-    auto kern = k_intersect<STATS, K>;
+    auto kern = k_intersect<STATS, K, MINB>;
     const uint32_t threads = cfg.block_threads;
     const size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
     static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
@@ -135,11 +135,14 @@ cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
-    if (cfg.cache_slots == 0)
-        return stats ? launch_one<true, 0>(sc, r, h, n, cfg, queue, status, num_sms, s)
-                     : launch_one<false, 0>(sc, r, h, n, cfg, queue, status, num_sms, s);
-    return stats ? launch_one<true, 2>(sc, r, h, n, cfg, queue, status, num_sms, s)
-                 : launch_one<false, 2>(sc, r, h, n, cfg, queue, status, num_sms, s);
+    if (stats)   // counting runs are not timed: one register budget is enough
+        return cfg.cache_slots == 0 ? launch_one<true, 0, 1>(sc, r, h, n, cfg, queue, status, num_sms, s)
+                                    : launch_one<true, 2, 1>(sc, r, h, n, cfg, queue, status, num_sms, s);
+    if (cfg.min_blocks >= 4)
+        return cfg.cache_slots == 0 ? launch_one<false, 0, 4>(sc, r, h, n, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, 4>(sc, r, h, n, cfg, queue, status, num_sms, s);
+    return cfg.cache_slots == 0 ? launch_one<false, 0, 1>(sc, r, h, n, cfg, queue, status, num_sms, s)
+                                : launch_one<false, 2, 1>(sc, r, h, n, cfg, queue, status, num_sms, s);
 }
 
 }  // namespace ccs
