@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
-    ap.add_argument("--variant", default="plain", choices=["plain"])
+    ap.add_argument("--variant", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
@@ -155,6 +156,100 @@ def run_reference(args, rank, world):
     return out
 
 
+WORKLOAD_BATCHED = ("batched: 32 cube-spheres with 4..64 quads/face (24 n^2 patches each, 1.13M total), 8 frames of "
+                    "sinusoidal control-point offsets (amp 0.02), 512x512 primary + diffuse rays per scene, L=8")
+
+
+def run_batched(args, dev, stream, world):
+    """Per frame: update + refit + closest hit of all 32 scenes, as one CUDA-graph replay of the batch
+    (one launch per stage over all scenes) versus the same calls scene by scene."""
+    import torch
+    from paper_1811_03510_gb300 import ccs, scenegen as sg
+    sizes = sg.batched_sizes()
+    scenes = [sg.make_scene(n, 0.0, name=f"n={n}") for n in sizes]
+    handles = [ccs.Scene(s.P, s.types) for s in scenes]
+    cam = sg.pinhole_rays(512, 512)
+    prim = ccs.rays_to_device(cam.soa(), dev)
+    opts = ccs.make_opts(leaf_depth=8)
+    rays, hits, n_prim, n_diff = [], [], 0, 0
+    for sc in handles:
+        hp = ccs.alloc_hits(cam.n, dev)
+        ccs.ccs_intersect(sc.handle, prim, cam.n, hp, opts, stream)
+        d = ccs.gen_diffuse(sc, prim, hp, seed=1, leaf_depth=8, stream=stream)
+        torch.cuda.synchronize()
+        act = (d[7] >= d[6]).nonzero().squeeze(1)
+        rays.append([torch.cat([p, q.index_select(0, act)]).contiguous() for p, q in zip(prim, d)])
+        hits.append(ccs.alloc_hits(int(rays[-1][0].numel()), dev))
+        n_prim += cam.n
+        n_diff += int(act.numel())
+    # frames: deformed control points, a function of the rest position (device, FP32)
+    gen = torch.Generator().manual_seed(1)
+    w = (torch.rand(3, generator=gen) * 4 + 2).to(dev)
+    phi = (torch.rand(3, generator=gen) * 6.283185307179586).to(dev)
+    rest = [torch.from_numpy(s.P).to(dev) for s in scenes]
+    frames = []
+    for f in range(args.frames):
+        fr = []
+        for P in rest:
+            Q = P + 0.02 * torch.sin(w * P + phi + 6.283185307179586 * f / args.frames)
+            fr.append([Q[..., c].contiguous().reshape(-1) for c in range(3)])
+        frames.append(fr)
+    b = ccs.ccs_batch_create(handles, rays, hits)
+    stages = ccs.CCS_BATCH_UPDATE | ccs.CCS_BATCH_REFIT | ccs.CCS_BATCH_INTERSECT
+    for i in range(len(handles)):
+        ccs.ccs_batch_set_points(b, i, *frames[0][i])
+    ccs.ccs_batch_capture(b, stages, opts)
+
+    def batched_frame(f):
+        for i in range(len(handles)):
+            ccs.ccs_batch_set_points(b, i, *frames[f][i])
+        ccs.ccs_batch_launch(b, stream)
+
+    def plain_frame(f):
+        for i, sc in enumerate(handles):
+            ccs.ccs_scene_update_points(sc.handle, *frames[f][i], stream)
+            ccs.ccs_bvh_refit(sc.handle, stream)
+            ccs.ccs_intersect(sc.handle, rays[i], int(rays[i][0].numel()), hits[i], opts, stream)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    res = {}
+    for name, fn in (("plain", plain_frame), ("batched", batched_frame)):
+        for k in range(args.warmup):
+            fn(k % args.frames)
+        torch.cuda.synchronize()
+        times = []
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn(k % args.frames)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+        res[name] = times
+        if name == "plain":
+            ref = [[h.clone() for h in hh] for hh in hits]
+    assert ccs.ccs_batch_sync_status(b, stream) == ccs.CCS_OK
+    last = (args.steps - 1) % args.frames
+    plain_frame(last)
+    torch.cuda.synchronize()
+    ref = [[h.clone() for h in hh] for hh in hits]
+    batched_frame(last)
+    torch.cuda.synchronize()
+    identical = all(torch.equal(a, c) for hh, rr in zip(hits, ref) for a, c in zip(hh, rr))
+    ccs.ccs_batch_destroy(b)
+    for h in handles:
+        h.close()
+    n_step = n_prim + n_diff
+    T_b, T_p = sum(res["batched"]), sum(res["plain"])
+    return {"rays_per_frame": n_step, "primary_rays": n_prim, "diffuse_rays": n_diff,
+            "batched_mrays_s": n_step * args.steps / T_b / 1e6, "plain_mrays_s": n_step * args.steps / T_p / 1e6,
+            "batched_ms_per_frame": 1e3 * T_b / args.steps, "plain_ms_per_frame": 1e3 * T_p / args.steps,
+            "speedup": T_p / T_b, "identical_hits": bool(identical),
+            "launches_per_frame": {"batched": 1, "plain": 3 * len(handles)}}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -180,6 +275,17 @@ def main():
     stream = torch.cuda.current_stream(dev)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
+    if args.variant == "batched":
+        out = run_batched(args, dev, stream, world)
+        res = {"metric": METRIC, "value": out["batched_mrays_s"] * world, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["batched_ms_per_frame"],
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": {"workload": WORKLOAD_BATCHED, "variant": "batched",
+                                               "l2": "flushed (256 MB write) before every timed frame"},
+               "batched": out, "gpu_launches": 3 * args.steps}
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
     s, r = build_workload(args.width, args.height)
     scene = ccs.Scene(s.P, s.types)
     prim = ccs.rays_to_device(r.soa(), dev)

@@ -151,6 +151,48 @@ ccs_status ccs_scene_info(const ccs_scene *scene, uint32_t *n_patches, uint32_t 
 ccs_status ccs_gen_diffuse(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
                            uint64_t seed, uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
 
+/* ---- Batched scenes (many scenes and their rays per launch; CUDA-graph capturable) ---------------- */
+typedef struct ccs_batch ccs_batch;   /* opaque; created and freed by the library */
+
+#define CCS_BATCH_UPDATE 1u      /* repack new control points of every scene that has a point source */
+#define CCS_BATCH_REFIT 2u       /* refit every scene's BVH */
+#define CCS_BATCH_INTERSECT 4u   /* one persistent closest-hit launch over the rays of all scenes */
+
+/* Group n_scenes built scenes with their rays (device planes, n_rays[s] rays for scene s) and hit
+ * buffers.  The batch keeps pointers to the scenes and buffers, which must outlive it.  The rays of
+ * all scenes share one work queue, so uneven scenes load-balance within a single launch.  Blocks. */
+ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t n_scenes, const ccs_rays *rays,
+                            const uint32_t *n_rays, const ccs_hits *hits);
+
+/* Source of new control points of scene `scene_index` for the update stage: device planes in the
+ * layout of ccs_scene_create (same patch count and types); NULL leaves the scene's points unchanged.
+ * Host-side only: the batch's scene table is copied to the device at the start of every run (also
+ * inside a captured graph), so a new source applies to every later run or graph launch.  Do not call
+ * while a run of this batch may still be copying its table (synchronise the stream first). */
+ccs_status ccs_batch_set_points(ccs_batch *b, uint32_t scene_index, const float *x, const float *y, const float *z);
+
+/* Enqueue the selected stages (CCS_BATCH_* bits) on `stream`: the table copy, one repack launch,
+ * one refit launch and one intersect launch.  Allocates nothing and does not synchronise.  Answers
+ * are bit-identical to ccs_intersect on each scene alone. */
+ccs_status ccs_batch_run(ccs_batch *b, uint32_t stages, const ccs_trace_opts *opts, void *stream);
+
+/* Run once, then capture ccs_batch_run(stages, opts) into a CUDA graph owned by the batch (on an
+ * internal stream) and instantiate it.  Blocks. */
+ccs_status ccs_batch_capture(ccs_batch *b, uint32_t stages, const ccs_trace_opts *opts);
+
+/* Launch the captured graph on `stream` (asynchronous). */
+ccs_status ccs_batch_launch(ccs_batch *b, void *stream);
+
+/* Wait for `stream`, then return and clear the batch's latched device status. */
+ccs_status ccs_batch_sync_status(ccs_batch *b, void *stream);
+
+ccs_status ccs_batch_destroy(ccs_batch *b);
+
+/* One-shot closest hit of several scenes' rays in one persistent launch (creates a temporary batch,
+ * runs CCS_BATCH_INTERSECT and frees it; synchronises `stream`). */
+ccs_status ccs_intersect_batched(ccs_scene *const *scenes, const ccs_rays *rays_per_scene, const uint32_t *n_per_scene,
+                                 ccs_hits *hits_per_scene, uint32_t n_scenes, const ccs_trace_opts *opts, void *stream);
+
 /* One measured candidate of ccs_autotune. */
 typedef struct {
     ccs_trace_opts opts;

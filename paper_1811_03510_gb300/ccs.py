@@ -78,6 +78,17 @@ _SIGS = {
                      ctypes.POINTER(ccs_trace_opts), ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts),
                      ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ccs_autotune_trial), ctypes.c_uint32,
                      ctypes.POINTER(ctypes.c_uint32), ctypes.c_void_p],
+    "ccs_batch_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint32,
+                         ctypes.POINTER(ccs_rays), ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ccs_hits)],
+    "ccs_batch_set_points": [ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_batch_run": [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_batch_capture": [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts)],
+    "ccs_batch_launch": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_batch_sync_status": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_batch_destroy": [ctypes.c_void_p],
+    "ccs_intersect_batched": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ccs_rays), ctypes.POINTER(ctypes.c_uint32),
+                              ctypes.POINTER(ccs_hits), ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts),
+                              ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -241,6 +252,62 @@ def ccs_autotune(scene: int, rays, n: int, hits, base: ccs_trace_opts | None = N
                               ctypes.byref(best), ctypes.byref(ms), tr, max_trials, ctypes.byref(nt), _stream(stream)))
     trials = [(tr[i].opts, tr[i].ms) for i in range(min(nt.value, max_trials))]
     return best, ms.value, trials
+
+
+CCS_BATCH_UPDATE = 1
+CCS_BATCH_REFIT = 2
+CCS_BATCH_INTERSECT = 4
+
+
+def _batch_arrays(scenes, rays_list, hits_list):
+    n = len(scenes)
+    sc = (ctypes.c_void_p * n)(*[s if isinstance(s, int) else s.handle for s in scenes])
+    r = (ccs_rays * n)(*[x if isinstance(x, ccs_rays) else rays_struct(x) for x in rays_list])
+    h = (ccs_hits * n)(*[x if isinstance(x, ccs_hits) else hits_struct(x) for x in hits_list])
+    cnt = (ctypes.c_uint32 * n)(*[int(x[0].numel()) if not isinstance(x, ccs_rays) else 0 for x in rays_list])
+    return sc, r, cnt, h
+
+
+def ccs_batch_create(scenes, rays_list, hits_list, n_rays=None) -> int:
+    sc, r, cnt, h = _batch_arrays(scenes, rays_list, hits_list)
+    if n_rays is not None:
+        cnt = (ctypes.c_uint32 * len(scenes))(*n_rays)
+    b = ctypes.c_void_p()
+    _check(lib().ccs_batch_create(ctypes.byref(b), sc, len(scenes), r, cnt, h))
+    return b.value
+
+
+def ccs_batch_set_points(batch: int, scene_index: int, x, y, z):
+    _check(lib().ccs_batch_set_points(batch, scene_index, _ptr(x), _ptr(y), _ptr(z)))
+
+
+def ccs_batch_run(batch: int, stages: int, opts: ccs_trace_opts | None = None, stream=None):
+    _check(lib().ccs_batch_run(batch, stages, ctypes.byref(opts) if opts else None, _stream(stream)))
+
+
+def ccs_batch_capture(batch: int, stages: int, opts: ccs_trace_opts | None = None):
+    _check(lib().ccs_batch_capture(batch, stages, ctypes.byref(opts) if opts else None))
+
+
+def ccs_batch_launch(batch: int, stream=None):
+    _check(lib().ccs_batch_launch(batch, _stream(stream)))
+
+
+def ccs_batch_sync_status(batch: int, stream=None) -> int:
+    st = lib().ccs_batch_sync_status(batch, _stream(stream))
+    if st not in (CCS_OK, CCS_ERR_TRAVERSAL_LIMIT):
+        _check(st)
+    return st
+
+
+def ccs_batch_destroy(batch: int):
+    _check(lib().ccs_batch_destroy(batch))
+
+
+def ccs_intersect_batched(scenes, rays_list, hits_list, opts: ccs_trace_opts | None = None, stream=None):
+    sc, r, cnt, h = _batch_arrays(scenes, rays_list, hits_list)
+    _check(lib().ccs_intersect_batched(sc, r, cnt, h, len(scenes), ctypes.byref(opts) if opts else None,
+                                       _stream(stream)))
 
 
 def opts_dict(o: ccs_trace_opts) -> dict:

@@ -54,7 +54,9 @@ void free_scene(ccs_scene *s)
     delete s;
 }
 
-ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
+}  // namespace
+
+ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
 {
     c.leaf_depth = o && o->leaf_depth ? o->leaf_depth : 8;
     c.block_threads = o && o->block_threads ? o->block_threads : 128;
@@ -79,6 +81,8 @@ ccs_status fill_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;
 }
+
+namespace {
 
 ccs_status check_rays(const ccs_rays *r, const ccs_hits *h)
 {
@@ -244,7 +248,7 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
         return CCS_ERR_NOT_BUILT;
     }
     LaunchCfg cfg;
-    if ((st = fill_cfg(opts, cfg)) != CCS_OK) return st;
+    if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
     DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};

@@ -48,6 +48,18 @@ struct DevHits {
     uint32_t *pid;
 };
 
+// One scene of a batch (device table): where its data, rays and hits live.
+struct BatchEntry {
+    DevScene sc;
+    DevRays rays;
+    DevHits hits;
+    const float *px, *py, *pz;   // new control points for the update stage (device), or null
+    const uint8_t *types;
+    float4 *rec, *leaf_box, *nodes;
+    const int *leaf_parent;
+    uint32_t *refit_flags;
+};
+
 // kernels (intersect.cu, scene.cu)
 size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K);
 cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
@@ -56,6 +68,14 @@ cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *le
                          uint32_t n_patches, uint32_t n_nodes, cudaStream_t s);
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
                              const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s);
+cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
+                                   uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
+                                   int num_sms, cudaStream_t s);
+cudaError_t launch_batch_repack(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
+                                uint32_t n_patches, cudaStream_t s);
+cudaError_t launch_batch_refit(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
+                               uint32_t n_patches, uint32_t *flags, uint32_t n_flag_words, cudaStream_t s);
+ccs_status fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c);
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,

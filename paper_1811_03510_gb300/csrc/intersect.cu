@@ -1,16 +1,59 @@
-// Plain closest-hit kernel.  Persistent blocks; each warp keeps 32 rays in flight and takes new rays
-// from a global work queue whenever enough of its lanes are idle (warp-aggregated atomic).  Each
-// iteration of the warp loop advances every lane by one unit of work (lane_step), so lanes in
-// different phases (BVH, subdivision, re-descent) cost one step each instead of serialising whole
-// patch traversals.
+// Closest-hit kernels.  Persistent blocks; each warp keeps 32 rays in flight, takes ranges of rays from
+// a global work queue and hands them to its idle lanes.  Each iteration of the warp loop advances every
+// lane by one unit of work (lane_step), so lanes in different phases (BVH, subdivision, re-descent)
+// cost one step each instead of serialising whole patch traversals.  The same loop serves one scene
+// (SingleSource) or a table of scenes whose rays share one queue (BatchSource, batched launches).
 #include "traverse.cuh"
 
 namespace ccs {
 
-template <bool STATS, int K, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_intersect(DevScene sc, DevRays rays, DevHits hits, uint32_t n, int L,
-                                                   uint32_t refill, uint32_t chunk, int burst, uint32_t iter_cap,
-                                                   uint32_t *queue, uint32_t *status, unsigned long long *counters)
+// Rays of one scene (the scene descriptor stays in kernel-parameter space, uniform over lanes).
+struct SingleSource {
+    DevScene sc;
+    DevRays rays;
+    DevHits hits;
+    uint32_t n;
+    struct LaneScene {};
+    CCS_DEV uint32_t total() const { return n; }
+    CCS_DEV const DevScene &scene(const LaneScene &) const { return sc; }
+    CCS_DEV void locate(uint32_t i, LaneScene &, uint32_t &scene, uint32_t &local) const
+    {
+        scene = 0;
+        local = i;
+    }
+    CCS_DEV const DevRays &rays_of(uint32_t) const { return rays; }
+    CCS_DEV const DevHits &hits_of(uint32_t) const { return hits; }
+};
+
+// Rays of many scenes, concatenated in scene order (ray_prefix[s] = first global index of scene s).
+struct BatchSource {
+    const BatchEntry *entries;
+    const uint32_t *ray_prefix;   // n_scenes + 1
+    uint32_t n_scenes, n;
+    struct LaneScene {
+        DevScene sc;
+    };
+    CCS_DEV uint32_t total() const { return n; }
+    CCS_DEV const DevScene &scene(const LaneScene &l) const { return l.sc; }
+    CCS_DEV void locate(uint32_t i, LaneScene &lsc, uint32_t &scene, uint32_t &local) const
+    {
+        uint32_t lo = 0, hi = n_scenes;   // largest s with ray_prefix[s] <= i
+        while (hi - lo > 1) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (__ldg(ray_prefix + m) <= i) lo = m; else hi = m;
+        }
+        scene = lo;
+        local = i - __ldg(ray_prefix + lo);
+        lsc.sc = entries[lo].sc;
+    }
+    CCS_DEV const DevRays &rays_of(uint32_t s) const { return entries[s].rays; }
+    CCS_DEV const DevHits &hits_of(uint32_t s) const { return entries[s].hits; }
+};
+
+template <bool STATS, int K, int MINB, class Src>
+__global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_t refill, uint32_t chunk, int burst,
+                                                         uint32_t iter_cap, uint32_t *queue, uint32_t *status,
+                                                         unsigned long long *counters)
 {
     extern __shared__ float smem[];
     const int stride = blockDim.x;
@@ -26,11 +69,13 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(DevScene sc, DevRays ra
     const int lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
     const float cellw = __int_as_float((127 - L) << 23);
+    const uint32_t n = src.total();
     Lane s;
     BvhStack stk;
     float g[48];
+    typename Src::LaneScene lsc;
     bool has = false, exhausted = false;
-    uint32_t ray_i = 0;
+    uint32_t ray_scene = 0, ray_local = 0;
     uint32_t wnext = 0, wend = 0;   // warp-uniform range of rays taken from the queue, not yet handed out
     for (;;) {
         const unsigned idle = __ballot_sync(FULL, !has);
@@ -51,9 +96,11 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(DevScene sc, DevRays ra
             if (!has && rank < avail) {
                 const uint32_t i = wnext + rank;
                 has = true;
-                ray_i = i;
-                begin_ray(s, sc, __ldg(rays.ox + i), __ldg(rays.oy + i), __ldg(rays.oz + i), __ldg(rays.dx + i),
-                          __ldg(rays.dy + i), __ldg(rays.dz + i), __ldg(rays.tmin + i), __ldg(rays.tmax + i), iter_cap);
+                src.locate(i, lsc, ray_scene, ray_local);
+                const DevRays &rr = src.rays_of(ray_scene);
+                const uint32_t j = ray_local;
+                begin_ray(s, src.scene(lsc), __ldg(rr.ox + j), __ldg(rr.oy + j), __ldg(rr.oz + j), __ldg(rr.dx + j),
+                          __ldg(rr.dy + j), __ldg(rr.dz + j), __ldg(rr.tmin + j), __ldg(rr.tmax + j), iter_cap);
             }
             const uint32_t taken = avail < (uint32_t)__popc(idle) ? avail : (uint32_t)__popc(idle);
             wnext += taken;
@@ -63,24 +110,25 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(DevScene sc, DevRays ra
             continue;
         }
         if (has) {
-            const bool ok = lane_step<STATS, K>(s, g, stk, sc, L, scr, cnt, burst);
+            const bool ok = lane_step<STATS, K>(s, g, stk, src.scene(lsc), L, scr, cnt, burst);
             if (!ok || lane_done(s)) {
                 if (!ok) {
                     atomicOr(status, 1u);
                     s.best.pid = kMissId;
                 }
-                const uint32_t i = ray_i;
+                const DevHits &hh = src.hits_of(ray_scene);
+                const uint32_t i = ray_local;
                 if (s.best.pid != kMissId) {
                     const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
-                    hits.t[i] = s.best.t;
-                    hits.u[i] = ((float)cu + 0.5f) * cellw;
-                    hits.v[i] = ((float)cv + 0.5f) * cellw;
-                    hits.pid[i] = s.best.pid;
+                    hh.t[i] = s.best.t;
+                    hh.u[i] = ((float)cu + 0.5f) * cellw;
+                    hh.v[i] = ((float)cv + 0.5f) * cellw;
+                    hh.pid[i] = s.best.pid;
                 } else {
-                    hits.t[i] = __int_as_float(0x7f800000);
-                    hits.u[i] = 0.0f;
-                    hits.v[i] = 0.0f;
-                    hits.pid[i] = kMissId;
+                    hh.t[i] = __int_as_float(0x7f800000);
+                    hh.u[i] = 0.0f;
+                    hh.v[i] = 0.0f;
+                    hh.pid[i] = kMissId;
                 }
                 has = false;
             }
@@ -101,11 +149,11 @@ size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
     return (size_t)threads * (2 * 2 * L + 48 * K + K) * sizeof(float);
 }
 
-template <bool STATS, int K, int MINB>
-static cudaError_t launch_one(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
-                              uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
+template <bool STATS, int K, int MINB, class Src>
+static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms,
+                              cudaStream_t s)
 {
-    auto kern = k_intersect<STATS, K, MINB>;
+    auto kern = k_intersect<STATS, K, MINB, Src>;
     const uint32_t threads = cfg.block_threads;
     const size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
     static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
@@ -120,29 +168,46 @@ static cudaError_t launch_one(const DevScene &sc, const DevRays &r, const DevHit
     if (max_active < 1) return cudaErrorInvalidConfiguration;
     uint32_t per_sm = cfg.blocks_per_sm < (uint32_t)max_active ? cfg.blocks_per_sm : (uint32_t)max_active;
     uint32_t blocks = (uint32_t)num_sms * per_sm;
+    const uint32_t n = src.n;
     const uint32_t needed = (n + threads - 1) / threads;
     if (blocks > needed) blocks = needed;
     if (blocks == 0) blocks = 1;
-    kern<<<blocks, threads, smem, s>>>(sc, r, h, n, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
+    kern<<<blocks, threads, smem, s>>>(src, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
                                        cfg.iter_cap, queue, status, cfg.counters);
     return cudaGetLastError();
+}
+
+template <class Src>
+static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms,
+                            cudaStream_t s)
+{
+    if (src.n == 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
+    if (stats)   // counting runs are not timed: one register budget is enough
+        return cfg.cache_slots == 0 ? launch_one<true, 0, 3>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<true, 2, 3>(src, cfg, queue, status, num_sms, s);
+    if (cfg.min_blocks >= 4)
+        return cfg.cache_slots == 0 ? launch_one<false, 0, 4>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, 4>(src, cfg, queue, status, num_sms, s);
+    return cfg.cache_slots == 0 ? launch_one<false, 0, 3>(src, cfg, queue, status, num_sms, s)
+                                : launch_one<false, 2, 3>(src, cfg, queue, status, num_sms, s);
 }
 
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
                              uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
 {
-    if (n == 0) return cudaSuccess;
-    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
-    if (e != cudaSuccess) return e;
-    const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
-    if (stats)   // counting runs are not timed: one register budget is enough
-        return cfg.cache_slots == 0 ? launch_one<true, 0, 1>(sc, r, h, n, cfg, queue, status, num_sms, s)
-                                    : launch_one<true, 2, 1>(sc, r, h, n, cfg, queue, status, num_sms, s);
-    if (cfg.min_blocks >= 4)
-        return cfg.cache_slots == 0 ? launch_one<false, 0, 4>(sc, r, h, n, cfg, queue, status, num_sms, s)
-                                    : launch_one<false, 2, 4>(sc, r, h, n, cfg, queue, status, num_sms, s);
-    return cfg.cache_slots == 0 ? launch_one<false, 0, 1>(sc, r, h, n, cfg, queue, status, num_sms, s)
-                                : launch_one<false, 2, 1>(sc, r, h, n, cfg, queue, status, num_sms, s);
+    SingleSource src{sc, r, h, n};
+    return dispatch(src, cfg, queue, status, num_sms, s);
+}
+
+cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
+                                   uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
+                                   int num_sms, cudaStream_t s)
+{
+    BatchSource src{entries, ray_prefix, n_scenes, n_total};
+    return dispatch(src, cfg, queue, status, num_sms, s);
 }
 
 }  // namespace ccs

@@ -1,0 +1,81 @@
+// Device routines of the scene store shared by the single-scene and batched kernels.
+#pragma once
+
+#include "ccs_internal.h"
+
+namespace ccs {
+
+// Patch p of SoA points (20 slots per patch) -> 256-byte record anchored at its box centre
+// (Sec. 3.4, anchoring), plus its leaf box (AABB of 16 or 20 points: convex hull, Sec. 3.1/3.2).
+__device__ __forceinline__ void repack_one(const float *__restrict__ x, const float *__restrict__ y,
+                                           const float *__restrict__ z, const uint8_t *__restrict__ types, uint32_t p,
+                                           float4 *__restrict__ rec, float4 *__restrict__ leaf_box)
+{
+    const bool greg = types[p] != 0;
+    const float *pl[3] = {x + (size_t)20 * p, y + (size_t)20 * p, z + (size_t)20 * p};
+    float lo[3], hi[3], an[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float a = pl[c][0], b = pl[c][0];
+        for (int k = 1; k < 16; ++k) { a = fminf(a, pl[c][k]); b = fmaxf(b, pl[c][k]); }
+        if (greg)
+            for (int k = 16; k < 20; ++k) { a = fminf(a, pl[c][k]); b = fmaxf(b, pl[c][k]); }
+        lo[c] = a;
+        hi[c] = b;
+        an[c] = __fmul_rn(__fadd_rn(a, b), 0.5f);
+    }
+    float4 *r = rec + (size_t)p * kRecF4;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        for (int q = 0; q < 4; ++q)
+            r[c * 4 + q] = make_float4(pl[c][4 * q] - an[c], pl[c][4 * q + 1] - an[c], pl[c][4 * q + 2] - an[c],
+                                       pl[c][4 * q + 3] - an[c]);
+        if (greg)
+            r[12 + c] = make_float4(pl[c][16] - an[c], pl[c][17] - an[c], pl[c][18] - an[c], pl[c][19] - an[c]);
+        else
+            r[12 + c] = make_float4(pl[c][5] - an[c], pl[c][6] - an[c], pl[c][9] - an[c], pl[c][10] - an[c]);
+    }
+    r[15] = make_float4(an[0], an[1], an[2], greg ? 1.0f : 0.0f);
+    leaf_box[2 * (size_t)p] = make_float4(lo[0], lo[1], lo[2], 0.0f);
+    leaf_box[2 * (size_t)p + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
+}
+
+__device__ __forceinline__ void write_child_box(float4 *nodes, int node, int slot, float4 lo, float4 hi)
+{
+    float4 *nd = nodes + (size_t)node * kNodeF4;
+    // slot 0: [0] = (lo.x, hi.x, lo.y, hi.y), [2].xy = (lo.z, hi.z); slot 1 uses [1] and [2].zw
+    float *xy = reinterpret_cast<float *>(nd + slot);
+    xy[0] = lo.x;
+    xy[1] = hi.x;
+    xy[2] = lo.y;
+    xy[3] = hi.y;
+    float *zz = reinterpret_cast<float *>(nd + 2) + 2 * slot;
+    zz[0] = lo.z;
+    zz[1] = hi.z;
+}
+
+// Refit from leaf p: write its box into its parent's slot; the second thread to arrive at a node (per
+// node arrival counter) takes the union of both children up to the node's parent.  Sibling boxes are
+// read through L2 (.cg) after a fence; the climb is bounded by the tree depth.
+__device__ __forceinline__ void refit_one(float4 *nodes, const int *__restrict__ leaf_parent,
+                                          const float4 *__restrict__ leaf_box, uint32_t *flags, uint32_t p)
+{
+    float4 lo = leaf_box[2 * (size_t)p], hi = leaf_box[2 * (size_t)p + 1];
+    int link = leaf_parent[p];
+    for (int guard = 0; guard < 128; ++guard) {
+        const int node = link >> 1, slot = link & 1;
+        write_child_box(nodes, node, slot, lo, hi);
+        __threadfence();
+        if (atomicAdd(flags + node, 1u) == 0u) return;
+        __threadfence();
+        const float4 *nd = nodes + (size_t)node * kNodeF4;
+        const float4 a = __ldcg(nd + 0), b = __ldcg(nd + 1), c = __ldcg(nd + 2), d = __ldcg(nd + 3);
+        lo = make_float4(fminf(a.x, b.x), fminf(a.z, b.z), fminf(c.x, c.z), 0.0f);
+        hi = make_float4(fmaxf(a.y, b.y), fmaxf(a.w, b.w), fmaxf(c.y, c.w), 0.0f);
+        const int parent = __float_as_int(d.z);
+        if (parent < 0) return;
+        link = (parent << 1) | __float_as_int(d.w);
+    }
+}
+
+}  // namespace ccs
