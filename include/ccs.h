@@ -193,6 +193,26 @@ ccs_status ccs_batch_destroy(ccs_batch *b);
 ccs_status ccs_intersect_batched(ccs_scene *const *scenes, const ccs_rays *rays_per_scene, const uint32_t *n_per_scene,
                                  ccs_hits *hits_per_scene, uint32_t n_scenes, const ccs_trace_opts *opts, void *stream);
 
+/* Allocation-free variant of ccs_intersect_batched (the paper has no counterpart; this is an
+ * integration entry point).  For callers that cannot call cudaMalloc at the time they trace: code
+ * running under a host that owns all device memory through its own arena or pool, real-time loops
+ * with a fixed memory budget, or threads that must not take the CUDA allocator's locks.  The caller
+ * passes the built scenes, its rays and its hit buffers as for ccs_intersect_batched; the per-call
+ * scratch that ccs_intersect_batched allocates (scene table, ray prefix, work-queue head, status word)
+ * lives instead in one fixed file-scope device array sized for CCS_NOALLOC_MAX_SCENES scenes (about
+ * 50 KB), which every GPU that loads the library holds until the process exits.
+ *  - The first call on a device looks up that array's device address (once per device, with the
+ *    device current); make that first call before any stream capture.
+ *  - More than CCS_NOALLOC_MAX_SCENES scenes: CCS_ERR_INVALID_ARG with a message; nothing runs.
+ *  - Calls no cudaMalloc / cudaFree; the queue head and status word are reset at every call.
+ *  - All calls share the one array: calls whose work overlaps on the GPU (other threads or streams)
+ *    race on it.  The call synchronises `stream` before it returns, so calls from one thread do not.
+ * Answers are bit-identical to ccs_intersect_batched and ccs_intersect. */
+#define CCS_NOALLOC_MAX_SCENES 256
+ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, const ccs_rays *rays_per_scene,
+                                         const uint32_t *n_per_scene, ccs_hits *hits_per_scene, uint32_t n_scenes,
+                                         const ccs_trace_opts *opts, void *stream);
+
 /* One measured candidate of ccs_autotune. */
 typedef struct {
     ccs_trace_opts opts;

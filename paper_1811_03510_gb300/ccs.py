@@ -89,6 +89,9 @@ _SIGS = {
     "ccs_intersect_batched": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ccs_rays), ctypes.POINTER(ctypes.c_uint32),
                               ctypes.POINTER(ccs_hits), ctypes.c_uint32, ctypes.POINTER(ccs_trace_opts),
                               ctypes.c_void_p],
+    "ccs_intersect_batched_noalloc": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ccs_rays),
+                                      ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
+                                      ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -308,6 +311,16 @@ def ccs_intersect_batched(scenes, rays_list, hits_list, opts: ccs_trace_opts | N
     sc, r, cnt, h = _batch_arrays(scenes, rays_list, hits_list)
     _check(lib().ccs_intersect_batched(sc, r, cnt, h, len(scenes), ctypes.byref(opts) if opts else None,
                                        _stream(stream)))
+
+
+CCS_NOALLOC_MAX_SCENES = 256
+
+
+def ccs_intersect_batched_noalloc(scenes, rays_list, hits_list, opts: ccs_trace_opts | None = None, stream=None):
+    """Allocation-free batched closest hit: scratch in the library's static device array."""
+    sc, r, cnt, h = _batch_arrays(scenes, rays_list, hits_list)
+    _check(lib().ccs_intersect_batched_noalloc(sc, r, cnt, h, len(scenes), ctypes.byref(opts) if opts else None,
+                                               _stream(stream)))
 
 
 def opts_dict(o: ccs_trace_opts) -> dict:
