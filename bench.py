@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--variant", default="plain", choices=["plain", "batched"])
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch options (profiling runs)")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     return ap.parse_args()
@@ -307,8 +308,10 @@ def main():
         ccs.ccs_intersect(scene.handle, diff, n_diff, hits_d, opts_d, stream)
 
     # launch options from the autotuner (answer-preserving knobs), separately for each batch
-    tuned = {}
+    tuned = {"primary": opts, "diffuse": opts}
     for name, rays, n, h in (("primary", prim, n_prim, hits_p), ("diffuse", diff, n_diff, hits_d)):
+        if args.no_autotune:
+            break
         best, ms, _ = ccs.ccs_autotune(scene.handle, rays, n, h, ccs.make_opts(leaf_depth=8), reps=2, stream=stream)
         tuned[name] = best
     opts_p, opts_d = tuned["primary"], tuned["diffuse"]
@@ -387,7 +390,8 @@ def main():
         "config": {"workload": WORKLOAD, "primary_rays": n_prim, "diffuse_rays": n_diff, "leaf_depth": 8,
                    "variant": args.variant, "l2": "flushed (256 MB write) before every timed step",
                    "launch_opts": {"primary": ccs.opts_dict(opts_p), "diffuse": ccs.opts_dict(opts_d),
-                                   "chosen_by": "ccs_autotune (answer-preserving knobs)"},
+                                   "chosen_by": "defaults" if args.no_autotune else
+                                   "ccs_autotune (answer-preserving knobs)"},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "primary_mrays_s": n_prim * args.steps / t_prim / 1e6,
         "diffuse_mrays_s": n_diff * args.steps / t_diff / 1e6,

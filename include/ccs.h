@@ -193,6 +193,62 @@ ccs_status ccs_batch_destroy(ccs_batch *b);
 ccs_status ccs_intersect_batched(ccs_scene *const *scenes, const ccs_rays *rays_per_scene, const uint32_t *n_per_scene,
                                  ccs_hits *hits_per_scene, uint32_t n_scenes, const ccs_trace_opts *opts, void *stream);
 
+/* ---- Learned sub-domain proposal ----------------------------------------------------------------
+ * A multilayer perceptron 24 -> 64 -> 64 -> 64 (ReLU) scores the 64 depth-3 cells (8 x 8) of a patch's
+ * (u,v) domain for a (ray, patch) pair.  Inside ccs_intersect_learned the best-scoring cell is
+ * searched first: straight descent to it, search of its subtree, then the full Algorithm 3 from the
+ * root with that subtree skipped.  The network only changes the order, so hits are bit-identical to
+ * ccs_intersect.  Inference runs on tensor cores (BF16 weights and activations, FP32 accumulation,
+ * warp-level MMA); training keeps FP32 master weights and Adam state.
+ * Parameters (CCS_PROPOSAL_PARAMS floats): W1 [64,24], b1 [64], W2 [64,64], b2, W3 [64,64], b3, each W
+ * row-major [out, in].  Features (CCS_PROPOSAL_FEATURES per pair, see ccs_trace_export), labels =
+ * depth-3 cell v3 * 8 + u3 of the pair's best leaf. */
+#define CCS_PROPOSAL_PARAMS 9920
+#define CCS_PROPOSAL_FEATURES 24
+#define CCS_PROPOSAL_CELLS 64
+typedef struct ccs_proposal ccs_proposal;   /* opaque; created and freed by the library */
+
+/* He-normal weights from a PCG32 stream seeded with `seed`, zero biases, zero Adam state. */
+ccs_status ccs_proposal_create(ccs_proposal **out, uint64_t seed);
+ccs_status ccs_proposal_destroy(ccs_proposal *p);
+/* Host copies of the FP32 parameters (set also resets the Adam state).  Blocking. */
+ccs_status ccs_proposal_set_params(ccs_proposal *p, const float *host_params);
+ccs_status ccs_proposal_get_params(const ccs_proposal *p, float *host_params);
+/* File: 8-byte magic "CCSPROP1", 4 uint32 layer sizes (24, 64, 64, 64), 9920 float32 parameters. */
+ccs_status ccs_proposal_save(const ccs_proposal *p, const char *path);
+ccs_status ccs_proposal_load(ccs_proposal **out, const char *path);
+
+/* Mean softmax cross-entropy gradient over a mini-batch (device features [batch, 24], labels [batch]);
+ * writes CCS_PROPOSAL_PARAMS floats to grad and the mean loss to *loss (device, optional). */
+ccs_status ccs_proposal_grad(ccs_proposal *p, const float *features, const uint8_t *labels, uint32_t batch,
+                             float *grad, float *loss, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8, learning rate lr) on a mini-batch; refreshes the BF16
+ * copy used by inference.  *loss (device, optional) receives the mini-batch loss before the step. */
+ccs_status ccs_proposal_train_step(ccs_proposal *p, const float *features, const uint8_t *labels, uint32_t batch,
+                                   float lr, float *loss, void *stream);
+/* Tensor-core inference of n feature rows (device): logits [n, 64] (optional), argmax cell [n]
+ * (optional; ties go to the lower cell), largest softmax probability [n] (optional). */
+ccs_status ccs_proposal_infer(const ccs_proposal *p, const float *features, uint32_t n, float *logits,
+                              uint8_t *cells, float *pmax, void *stream);
+
+/* Closest hit as ccs_intersect, and a training trace: for every (ray, patch) pair whose best leaf is
+ * the ray's best hit at the end of the pair, appends its 24 features and the depth-3 cell of that leaf
+ * (atomic order).  The features, in the patch's anchored frame scaled by S = largest corner distance:
+ * ray entry point into the patch box / S (3), unit direction (3), the 4 corners / S (12), unit normal
+ * of the corner quad (3), length inside the box / S clamped to 4 (1), direction . normal (1), Gregory
+ * flag (1).  *count (device) receives the number of pairs found, which may exceed `capacity` (only the
+ * first `capacity` are stored).  leaf_depth >= 3. */
+ccs_status ccs_trace_export(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                            const ccs_trace_opts *opts, float *features, uint8_t *labels, uint32_t capacity,
+                            uint32_t *count, void *stream);
+
+/* Closest hit with the learned proposal (bit-identical to ccs_intersect).  Proposals whose largest
+ * softmax probability is below min_confidence are ignored (plain order for that pair).  Needs
+ * block_threads = 128 and leaf_depth >= 3; runs without the sibling cache. */
+ccs_status ccs_intersect_learned(const ccs_scene *scene, const ccs_proposal *proposal, const ccs_rays *rays,
+                                 uint32_t n, ccs_hits *hits, const ccs_trace_opts *opts, float min_confidence,
+                                 void *stream);
+
 /* Allocation-free variant of ccs_intersect_batched (the paper has no counterpart; this is an
  * integration entry point).  For callers that cannot call cudaMalloc at the time they trace: code
  * running under a host that owns all device memory through its own arena or pool, real-time loops

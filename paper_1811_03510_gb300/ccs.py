@@ -92,6 +92,24 @@ _SIGS = {
     "ccs_intersect_batched_noalloc": [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ccs_rays),
                                       ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
                                       ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_proposal_create": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_uint64],
+    "ccs_proposal_destroy": [ctypes.c_void_p],
+    "ccs_proposal_set_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_proposal_get_params": [ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_proposal_save": [ctypes.c_void_p, ctypes.c_char_p],
+    "ccs_proposal_load": [ctypes.POINTER(ctypes.c_void_p), ctypes.c_char_p],
+    "ccs_proposal_grad": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_proposal_train_step": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_float,
+                                ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_proposal_infer": [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                           ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_trace_export": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.POINTER(ccs_hits),
+                         ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint32,
+                         ctypes.c_void_p, ctypes.c_void_p],
+    "ccs_intersect_learned": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32,
+                              ctypes.POINTER(ccs_hits), ctypes.POINTER(ccs_trace_opts), ctypes.c_float,
+                              ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -321,6 +339,72 @@ def ccs_intersect_batched_noalloc(scenes, rays_list, hits_list, opts: ccs_trace_
     sc, r, cnt, h = _batch_arrays(scenes, rays_list, hits_list)
     _check(lib().ccs_intersect_batched_noalloc(sc, r, cnt, h, len(scenes), ctypes.byref(opts) if opts else None,
                                                _stream(stream)))
+
+
+CCS_PROPOSAL_PARAMS = 9920
+CCS_PROPOSAL_FEATURES = 24
+CCS_PROPOSAL_CELLS = 64
+
+
+def ccs_proposal_create(seed: int = 1) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ccs_proposal_create(ctypes.byref(h), seed))
+    return h.value
+
+
+def ccs_proposal_destroy(p: int):
+    _check(lib().ccs_proposal_destroy(p))
+
+
+def ccs_proposal_set_params(p: int, params):
+    import numpy as np
+    a = np.ascontiguousarray(params, dtype=np.float32)
+    assert a.size == CCS_PROPOSAL_PARAMS
+    _check(lib().ccs_proposal_set_params(p, a.ctypes.data))
+
+
+def ccs_proposal_get_params(p: int):
+    import numpy as np
+    a = np.empty(CCS_PROPOSAL_PARAMS, np.float32)
+    _check(lib().ccs_proposal_get_params(p, a.ctypes.data))
+    return a
+
+
+def ccs_proposal_save(p: int, path: str):
+    _check(lib().ccs_proposal_save(p, path.encode()))
+
+
+def ccs_proposal_load(path: str) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ccs_proposal_load(ctypes.byref(h), path.encode()))
+    return h.value
+
+
+def ccs_proposal_grad(p: int, features, labels, batch: int, grad, loss=None, stream=None):
+    _check(lib().ccs_proposal_grad(p, _ptr(features), _ptr(labels), batch, _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def ccs_proposal_train_step(p: int, features, labels, batch: int, lr: float, loss=None, stream=None):
+    _check(lib().ccs_proposal_train_step(p, _ptr(features), _ptr(labels), batch, lr, _ptr(loss), _stream(stream)))
+
+
+def ccs_proposal_infer(p: int, features, n: int, logits=None, cells=None, pmax=None, stream=None):
+    _check(lib().ccs_proposal_infer(p, _ptr(features), n, _ptr(logits), _ptr(cells), _ptr(pmax), _stream(stream)))
+
+
+def ccs_trace_export(scene: int, rays, n: int, hits, opts, features, labels, capacity: int, count, stream=None):
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    _check(lib().ccs_trace_export(scene, ctypes.byref(r), n, ctypes.byref(h), ctypes.byref(opts) if opts else None,
+                                  _ptr(features), _ptr(labels), capacity, _ptr(count), _stream(stream)))
+
+
+def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=None, min_confidence: float = 0.0,
+                          stream=None):
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    _check(lib().ccs_intersect_learned(scene, proposal, ctypes.byref(r), n, ctypes.byref(h),
+                                       ctypes.byref(opts) if opts else None, min_confidence, _stream(stream)))
 
 
 def opts_dict(o: ccs_trace_opts) -> dict:

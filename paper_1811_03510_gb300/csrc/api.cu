@@ -256,6 +256,57 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     return CCS_OK;
 }
 
+ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
+                            const ccs_trace_opts *opts, float *features, uint8_t *labels, uint32_t capacity,
+                            uint32_t *count, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    ccs_status st = check_rays(rays, hits);
+    if (st != CCS_OK) return st;
+    CCS_ARG(features && labels && count, "features, labels and count must be given");
+    if (!sc->built) {
+        set_error("ccs_trace_export before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    LaunchCfg cfg;
+    if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(cfg.leaf_depth >= 3, "trace export needs leaf_depth >= 3 (labels are depth-3 cells)");
+    cfg.flags &= ~CCS_TRACE_COUNT;
+    cfg.mode = 1;
+    cfg.mc = ModeCtx{features, labels, count, capacity};
+    CCS_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), (cudaStream_t)stream));
+    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
+    DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    return CCS_OK;
+}
+
+ccs_status ccs_intersect_learned(const ccs_scene *sc, const ccs_proposal *prop, const ccs_rays *rays, uint32_t n,
+                                 ccs_hits *hits, const ccs_trace_opts *opts, float min_confidence, void *stream)
+{
+    CCS_ARG(sc && prop, "scene and proposal must not be NULL");
+    ccs_status st = check_rays(rays, hits);
+    if (st != CCS_OK) return st;
+    if (!sc->built) {
+        set_error("ccs_intersect_learned before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    LaunchCfg cfg;
+    if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(cfg.leaf_depth >= 3, "the learned proposal needs leaf_depth >= 3 (it proposes depth-3 cells)");
+    CCS_ARG(cfg.block_threads == 128, "the learned proposal runs with 128 threads per block");
+    cfg.mode = 2;
+    cfg.cache_slots = 0;
+    cfg.mlp = proposal_weights(prop);
+    cfg.min_conf = min_confidence;
+    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
+    DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    return CCS_OK;
+}
+
 ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs_hits *hh, const ccs_trace_opts *opts,
                               void *stream)
 {

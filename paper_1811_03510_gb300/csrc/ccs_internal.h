@@ -28,9 +28,23 @@ constexpr int kNodeF4 = 4;
 constexpr int kMaxLeafDepth = 15;
 constexpr int kNumCounters = CCS_NUM_COUNTERS;
 
+struct MlpWeights;
+
+// Export buffers of the trace mode (features + depth-3 cell label of each pair's best leaf).
+struct ModeCtx {
+    float *ex_features;
+    uint8_t *ex_labels;
+    uint32_t *ex_count;
+    uint32_t ex_capacity;
+};
+
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, iter_cap, flags;
     unsigned long long *counters;
+    int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal
+    ModeCtx mc{};
+    const MlpWeights *mlp = nullptr;
+    float min_conf = 0.0f;
 };
 
 struct DevScene {
@@ -76,6 +90,7 @@ cudaError_t launch_batch_repack(const BatchEntry *entries, const uint32_t *patch
 cudaError_t launch_batch_refit(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
                                uint32_t n_patches, uint32_t *flags, uint32_t n_flag_words, cudaStream_t s);
 ccs_status fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c);
+const MlpWeights *proposal_weights(const ccs_proposal *p);
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,

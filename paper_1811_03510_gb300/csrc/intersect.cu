@@ -3,6 +3,8 @@
 // lane by one unit of work (lane_step), so lanes in different phases (BVH, subdivision, re-descent)
 // cost one step each instead of serialising whole patch traversals.  The same loop serves one scene
 // (SingleSource) or a table of scenes whose rays share one queue (BatchSource, batched launches).
+#include <type_traits>
+
 #include "traverse.cuh"
 
 namespace ccs {
@@ -50,13 +52,23 @@ struct BatchSource {
     CCS_DEV const DevHits &hits_of(uint32_t s) const { return entries[s].hits; }
 };
 
-template <bool STATS, int K, int MINB, class Src>
+template <bool STATS, int K, int MINB, class Src, int MODE>
 __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_t refill, uint32_t chunk, int burst,
                                                          uint32_t iter_cap, uint32_t *queue, uint32_t *status,
-                                                         unsigned long long *counters)
+                                                         unsigned long long *counters, ModeCtx mc,
+                                                         const MlpWeights *__restrict__ mlp, float min_conf)
 {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int stride = blockDim.x;
+    MlpWeights *mw = nullptr;
+    MlpWarpTiles *mt = nullptr;
+    if (MODE == kModeLearned) {   // network weights and per-warp tiles after the traversal scratch
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem + (2 * 2 * L + 48 * K + K) * stride);
+        mw = reinterpret_cast<MlpWeights *>(base);
+        mt = reinterpret_cast<MlpWarpTiles *>(base + sizeof(MlpWeights)) + (threadIdx.x >> 5);
+        load_weights(*mw, mlp);
+        __syncthreads();
+    }
     Scratch scr;
     scr.stride = stride;
     scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
@@ -110,7 +122,7 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
             continue;
         }
         if (has) {
-            const bool ok = lane_step<STATS, K>(s, g, stk, src.scene(lsc), L, scr, cnt, burst);
+            const bool ok = lane_step<STATS, K, MODE>(s, g, stk, src.scene(lsc), L, scr, cnt, burst, mc);
             if (!ok || lane_done(s)) {
                 if (!ok) {
                     atomicOr(status, 1u);
@@ -133,6 +145,33 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
                 has = false;
             }
         }
+        if (MODE == kModeLearned) {   // network round for every lane that has just started a pair
+            const bool mine = has && s.in_pair && s.phase == kPhasePropose;
+            const unsigned need = __ballot_sync(FULL, mine);
+            if (need) {
+                if (mine) {
+                    float f[kFeat];
+                    pair_features(rec_of(src.scene(lsc), s.pid), s.ox, s.oy, s.oz, s.r.ix, s.r.iy, s.r.iz, s.rc0,
+                                  s.rc1, f);
+#pragma unroll
+                    for (int k = 0; k < 32; k += 2)
+                        st_bf16x2(mt->x + lane * kXStride + k, k < kFeat ? f[k] : 0.0f,
+                                  k + 1 < kFeat ? f[k + 1] : 0.0f);
+                }
+                __syncwarp();
+                if (need & 0x0000ffffu) mlp_round(*mw, *mt, 0, lane, nullptr, 0u);
+                if (need & 0xffff0000u) mlp_round(*mw, *mt, 1, lane, nullptr, 0u);
+                if (mine) {
+                    if (mt->pmax[lane] >= min_conf) {
+                        s.phase = kPhaseDirected;
+                        s.prop = cell3_path(mt->cell[lane]);
+                    } else {
+                        s.phase = kPhaseNormal;
+                    }
+                }
+                __syncwarp();
+            }
+        }
     }
     if (STATS) {
 #pragma unroll
@@ -149,13 +188,14 @@ size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
     return (size_t)threads * (2 * 2 * L + 48 * K + K) * sizeof(float);
 }
 
-template <bool STATS, int K, int MINB, class Src>
+template <bool STATS, int K, int MINB, class Src, int MODE>
 static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms,
                               cudaStream_t s)
 {
-    auto kern = k_intersect<STATS, K, MINB, Src>;
+    auto kern = k_intersect<STATS, K, MINB, Src, MODE>;
     const uint32_t threads = cfg.block_threads;
-    const size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
+    size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
+    if (MODE == kModeLearned) smem += sizeof(MlpWeights) + (threads / 32) * sizeof(MlpWarpTiles);
     static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
     if (smem > configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -173,7 +213,7 @@ static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *qu
     if (blocks > needed) blocks = needed;
     if (blocks == 0) blocks = 1;
     kern<<<blocks, threads, smem, s>>>(src, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
-                                       cfg.iter_cap, queue, status, cfg.counters);
+                                       cfg.iter_cap, queue, status, cfg.counters, cfg.mc, cfg.mlp, cfg.min_conf);
     return cudaGetLastError();
 }
 
@@ -185,14 +225,22 @@ static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queu
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
+    if constexpr (std::is_same<Src, SingleSource>::value) {
+    if (cfg.mode == kModeExport)
+        return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s);
+    if (cfg.mode == kModeLearned)   // the network's shared memory leaves no room for the sibling cache
+        return stats ? launch_one<true, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s)
+                     : launch_one<false, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s);
+    }
     if (stats)   // counting runs are not timed: one register budget is enough
-        return cfg.cache_slots == 0 ? launch_one<true, 0, 3>(src, cfg, queue, status, num_sms, s)
-                                    : launch_one<true, 2, 3>(src, cfg, queue, status, num_sms, s);
+        return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModePlain>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<true, 2, 3, Src, kModePlain>(src, cfg, queue, status, num_sms, s);
     if (cfg.min_blocks >= 4)
-        return cfg.cache_slots == 0 ? launch_one<false, 0, 4>(src, cfg, queue, status, num_sms, s)
-                                    : launch_one<false, 2, 4>(src, cfg, queue, status, num_sms, s);
-    return cfg.cache_slots == 0 ? launch_one<false, 0, 3>(src, cfg, queue, status, num_sms, s)
-                                : launch_one<false, 2, 3>(src, cfg, queue, status, num_sms, s);
+        return cfg.cache_slots == 0 ? launch_one<false, 0, 4, Src, kModePlain>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, 4, Src, kModePlain>(src, cfg, queue, status, num_sms, s);
+    return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModePlain>(src, cfg, queue, status, num_sms, s)
+                                : launch_one<false, 2, 3, Src, kModePlain>(src, cfg, queue, status, num_sms, s);
 }
 
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
@@ -207,7 +255,9 @@ cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ra
                                    int num_sms, cudaStream_t s)
 {
     BatchSource src{entries, ray_prefix, n_scenes, n_total};
-    return dispatch(src, cfg, queue, status, num_sms, s);
+    LaunchCfg c = cfg;
+    c.mode = kModePlain;
+    return dispatch(src, c, queue, status, num_sms, s);
 }
 
 }  // namespace ccs

@@ -8,6 +8,7 @@
 #include <stdint.h>
 
 #include "ccs_internal.h"
+#include "learned.cuh"
 
 namespace ccs {
 
@@ -485,7 +486,20 @@ struct Lane {
     int ctop, cvalid;               // sibling cache: pushes (slot = ctop % K) and valid entries
     uint32_t skip_path;             // subtree (skip_path, skip_level) not to enter again
     int skip_level;
+    int phase;                      // learned proposal: kPhase*
+    uint32_t prop;                  // path bits (levels 0..5) of the proposed depth-3 cell
+    float rc0, rc1;                 // root interval of the current pair
 };
+
+// Kernel modes: plain traversal, trace export (features + depth-3 cell of each pair's best leaf), and
+// traversal with the learned proposal.
+constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2;
+// Phases of a pair with the learned proposal: waiting for the network, descending straight to the
+// proposed depth-3 cell, searching that cell's subtree, then the full search with the cell skipped.
+constexpr int kPhaseNormal = 0, kPhasePropose = 1, kPhaseDirected = 2, kPhaseSubtree = 3;
+constexpr int kProposalLevel = 6;   // depth 3 per axis
+
+
 
 CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
                        float tmin, float tmax, uint32_t iter_cap)
@@ -503,6 +517,7 @@ CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz
     s.in_pair = false;
     s.skip_level = -1;
     s.skip_path = 0xFFFFFFFFu;
+    s.phase = kPhaseNormal;
     const bool bad = !(tmin <= tmax) || sc.n_nodes == 0 || isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx) ||
                      isnan(dy) || isnan(dz);
     if (bad) {
@@ -536,6 +551,7 @@ CCS_DEV void pop_next(Lane &s, BvhStack &stk)
 CCS_DEV const float4 *rec_of(const DevScene &sc, uint32_t pid) { return sc.rec + (size_t)pid * kRecF4; }
 
 // Begin Algorithm 3 on patch pid with root interval [c0, c1].
+template <int MODE>
 CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pid, float c0, float c1)
 {
     const float4 *rec = rec_of(sc, pid);
@@ -554,14 +570,54 @@ CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pi
     s.c0 = c0;
     s.c1 = c1;
     s.ctop = s.cvalid = 0;
+    if (MODE != kModePlain) {
+        s.rc0 = c0;
+        s.rc1 = c1;
+    }
+    if (MODE == kModeLearned) {
+        s.phase = kPhasePropose;
+        s.skip_level = -1;
+    }
     if (s.greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, s.dx, s.dy, s.dz);
     else load_grid(rec, g);
 }
 
+// Restart the current pair at its root (learned proposal), optionally skipping the proposed cell.
+CCS_DEV void restart_pair(Lane &s, float (&g)[48], const DevScene &sc, bool skip)
+{
+    const float4 *rec = rec_of(sc, s.pid);
+    s.level = 0;
+    s.rd_target = -1;
+    s.path = s.trail = 0u;
+    s.c0 = s.rc0;
+    s.c1 = s.rc1;
+    s.ctop = s.cvalid = 0;
+    s.phase = kPhaseNormal;
+    s.skip_level = skip ? kProposalLevel : -1;
+    s.skip_path = s.prop;
+    if (s.greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, s.dx, s.dy, s.dz);
+    else load_grid(rec, g);
+}
+
+// Export of a finished pair whose leaf is the ray's best so far: features + depth-3 cell label.
+CCS_DEV void export_pair(const Lane &s, const DevScene &sc, int L, const ModeCtx &mc)
+{
+    if (s.best.pid != s.pid || L < 3) return;
+    const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
+    const uint32_t label = (cv >> (L - 3)) * 8u + (cu >> (L - 3));
+    const uint32_t slot = atomicAdd(mc.ex_count, 1u);
+    if (slot >= mc.ex_capacity) return;
+    float f[kFeat];
+    pair_features(rec_of(sc, s.pid), s.ox, s.oy, s.oz, s.r.ix, s.r.iy, s.r.iz, s.rc0, s.rc1, f);
+#pragma unroll
+    for (int k = 0; k < kFeat; ++k) mc.ex_features[(size_t)slot * kFeat + k] = f[k];
+    mc.ex_labels[slot] = (uint8_t)label;
+}
+
 // Backtrack to the deepest pending sibling that can still hold a closer leaf, or end the pair.
-template <bool STATS, int K>
+template <bool STATS, int K, int MODE>
 CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt)
+                       Counters &cnt, const ModeCtx &mc)
 {
     while (s.trail != 0u) {
         const int l = 31 - __clz(s.trail);
@@ -605,16 +661,23 @@ CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         }
         return;
     }
+    if (MODE == kModeLearned && s.phase == kPhaseSubtree) {   // proposed cell searched: now the rest
+        restart_pair(s, g, sc, true);
+        return;
+    }
+    if (MODE == kModeExport) export_pair(s, sc, L, mc);
     s.in_pair = false;
     pop_next(s, stk);
 }
 
 // One step of Algorithm 3 on the lane's current pair.
-template <bool STATS, int K>
+template <bool STATS, int K, int MODE>
 CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt)
+                       Counters &cnt, const ModeCtx &mc)
 {
+    if (MODE == kModeLearned && s.phase == kPhasePropose) return;   // waits for the warp's network round
     const bool redesc = s.rd_target >= 0;
+    const bool directed = MODE == kModeLearned && s.phase == kPhaseDirected;
     if (!redesc && s.level == 2 * L) {
         uint32_t cu, cv;
         path_cells(s.path, L, cu, cv);
@@ -625,11 +688,11 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
             s.best.pid = s.pid;
             s.best.cell = cell;
         }
-        backtrack<STATS, K>(s, g, stk, sc, L, scr, cnt);
+        backtrack<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
         return;
     }
-    const int force = redesc ? (int)((s.path >> s.level) & 1u) : -1;
-    const int slot = (!redesc && K > 0 && !s.greg) ? (s.ctop % (K > 0 ? K : 1)) : -1;
+    const int force = redesc ? (int)((s.path >> s.level) & 1u) : directed ? (int)((s.prop >> s.level) & 1u) : -1;
+    const int slot = (!redesc && !directed && K > 0 && !s.greg) ? (s.ctop % (K > 0 ? K : 1)) : -1;
     bool allowL = true, allowR = true;   // a subtree already searched by a directed descent is not entered
     if (!redesc && s.skip_level == s.level + 1 && ((s.skip_path ^ s.path) & ((1u << s.level) - 1u)) == 0u) {
         if ((s.skip_path >> s.level) & 1u) allowR = false; else allowL = false;
@@ -639,6 +702,24 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
                                     allowL, allowR, force);
     if (redesc) {
         if (++s.level == s.rd_target) s.rd_target = -1;
+        return;
+    }
+    if (directed) {   // straight descent to the proposed cell; abandon it if the ray misses a box on the way
+        const bool up = force == 1;
+        if (up ? o.hitR : o.hitL) {
+            s.path |= (uint32_t)force << s.level;
+            s.c0 = up ? o.r0 : o.l0;
+            s.c1 = up ? o.r1 : o.l1;
+            ++s.level;
+            if (s.greg) {
+                float u0, u1, v0, v1;
+                node_domain(s.path, s.level, L, u0, u1, v0, v1);
+                gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+            }
+            if (s.level == kProposalLevel) s.phase = kPhaseSubtree;
+        } else {
+            restart_pair(s, g, sc, false);
+        }
         return;
     }
     if (o.hitL || o.hitR) {
@@ -663,11 +744,11 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         }
         return;
     }
-    backtrack<STATS, K>(s, g, stk, sc, L, scr, cnt);
+    backtrack<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
 }
 
 // One BVH step: expand an internal node (nearer child first), or start the pair of a leaf.
-template <bool STATS>
+template <bool STATS, int MODE>
 CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, Counters &cnt)
 {
     if (s.node == kDone) return;
@@ -675,7 +756,7 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
         const uint32_t pid = (uint32_t)(~s.node);
         if (s.n0 <= s.best.t) {
             if (STATS) cnt.v[7]++;
-            start_pair(s, g, sc, pid, s.n0, s.n1);
+            start_pair<MODE>(s, g, sc, pid, s.n0, s.n1);
         } else {
             pop_next(s, stk);
         }
@@ -708,20 +789,20 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
 
 // One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
 // so lanes that traverse catch up while the others subdivide).  Returns false on the iteration cap.
-template <bool STATS, int K>
+template <bool STATS, int K, int MODE>
 CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt, int burst)
+                       Counters &cnt, int burst, const ModeCtx &mc)
 {
     if (s.in_pair) {
         if (s.iters == 0) return false;
         --s.iters;
-        pair_step<STATS, K>(s, g, stk, sc, L, scr, cnt);
+        pair_step<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
         return true;
     }
     for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
         if (s.iters == 0) return false;
         --s.iters;
-        bvh_step<STATS>(s, g, stk, sc, cnt);
+        bvh_step<STATS, MODE>(s, g, stk, sc, cnt);
     }
     return true;
 }
