@@ -70,7 +70,9 @@ def test_tensor_core_inference_matches_reference_in_kernel_precision():
     top2 = np.sort(ref, axis=1)[:, -2:]
     clear = (top2[:, 1] - top2[:, 0]) > 1e-2 * scale
     assert (c[clear] == ref[clear].argmax(1)).all()
-    assert clear.mean() > 0.9
+    assert clear.mean() > 0.5
+    # where the top two are close, the chosen cell is still a maximum within the logit tolerance
+    assert (ref[np.arange(n), c] >= ref.max(1) - 4e-3 * scale).all()
     e = np.exp(ref - ref.max(1, keepdims=True))
     np.testing.assert_allclose(pmax.cpu().numpy(), 1 / e.sum(1), rtol=5e-3)
     ccs.ccs_proposal_destroy(p)
