@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
-    ap.add_argument("--variant", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--variant", default="all", choices=["all", "plain", "batched", "learned"])
+    ap.add_argument("--train-seeds", type=int, default=3, help="scenes (seeds 2..) whose traces train the proposal")
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch options (profiling runs)")
@@ -251,6 +252,103 @@ def run_batched(args, dev, stream, world):
             "launches_per_frame": {"batched": 1, "plain": 3 * len(handles)}}
 
 
+def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
+    """Train the proposal on traces of scenes with other seeds (GPU export + GPU training), then time the
+    learned traversal against the plain one on this workload's primary and diffuse batches."""
+    import torch
+    from paper_1811_03510_gb300 import ccs, scenegen as sg
+    t_setup = time.perf_counter()
+    cap = 4_000_000
+    feat = torch.empty(cap, 24, device=dev)
+    lab = torch.empty(cap, dtype=torch.uint8, device=dev)
+    cnt = torch.zeros(1, dtype=torch.int32, device=dev)
+    n_tr = 0
+    cam = sg.pinhole_rays(args.width, args.height)
+    cam_d = ccs.rays_to_device(cam.soa(), dev)
+    for seed in range(2, 2 + args.train_seeds):
+        st = sg.config_scene(2, seed=seed)
+        sct = ccs.Scene(st.P, st.types)
+        hp = ccs.alloc_hits(cam.n, dev)
+        room = cap - n_tr
+        if room <= 0:
+            break
+        ccs.ccs_trace_export(sct.handle, cam_d, cam.n, hp, ccs.make_opts(), feat[n_tr:], lab[n_tr:], room, cnt, stream)
+        d = ccs.gen_diffuse(sct, cam_d, hp, seed=seed, stream=stream)
+        torch.cuda.synchronize()
+        n_tr += min(int(cnt.item()), room)
+        act = (d[7] >= d[6]).nonzero().squeeze(1)
+        dd = [q.index_select(0, act).contiguous() for q in d]
+        room = cap - n_tr
+        if room > 0 and act.numel():
+            hd = ccs.alloc_hits(int(act.numel()), dev)
+            ccs.ccs_trace_export(sct.handle, dd, int(act.numel()), hd, ccs.make_opts(), feat[n_tr:], lab[n_tr:], room,
+                                 cnt, stream)
+            torch.cuda.synchronize()
+            n_tr += min(int(cnt.item()), room)
+        sct.close()
+    n_val = max(n_tr // 10, 1)
+    perm = torch.randperm(n_tr, device=dev, generator=torch.Generator(device=dev).manual_seed(1))
+    feat, lab = feat[:n_tr][perm].contiguous(), lab[:n_tr][perm].contiguous()
+    prop = ccs.ccs_proposal_create(seed=1)
+    B, epochs, lr = 8192, 3, 2e-3
+    loss = torch.zeros(1, device=dev)
+    n_fit = n_tr - n_val
+    steps = 0
+    t_train = time.perf_counter()
+    for ep in range(epochs):
+        for i0 in range(0, n_fit - B + 1, B):
+            ccs.ccs_proposal_train_step(prop, feat[n_val + i0:], lab[n_val + i0:], B, lr * (0.5 ** ep), loss, stream)
+            steps += 1
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t_train
+    cells = torch.empty(n_val, dtype=torch.uint8, device=dev)
+    ccs.ccs_proposal_infer(prop, feat[:n_val], n_val, None, cells, None, stream)
+    torch.cuda.synchronize()
+    acc = (cells == lab[:n_val]).float().mean().item()
+    t_setup = time.perf_counter() - t_setup
+    # timing: plain (tuned) against learned, both on the test seed's batches
+    res = {"train_traces": n_tr - n_val, "val_traces": n_val, "train_steps": steps, "train_s": t_train,
+           "final_train_loss": loss.item(), "val_top1": acc, "setup_s": t_setup}
+    nb = {"primary": (prim, int(prim[0].numel()), opts_p), "diffuse": (diff, int(diff[0].numel()), opts_d)}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lopts = ccs.make_opts(leaf_depth=8, cache_slots=0)
+    for name, (rays, n, op) in nb.items():
+        hp, hl = ccs.alloc_hits(n, dev), ccs.alloc_hits(n, dev)
+        out = {}
+        for label, fn in (("plain", lambda: ccs.ccs_intersect(scene.handle, rays, n, hp, op, stream)),
+                          ("learned", lambda: ccs.ccs_intersect_learned(scene.handle, prop, rays, n, hl, lopts, 0.0,
+                                                                        stream)),
+                          ("learned_conf0.3", lambda: ccs.ccs_intersect_learned(scene.handle, prop, rays, n, hl, lopts,
+                                                                                0.3, stream))):
+            for _ in range(args.warmup):
+                fn()
+            ts = []
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) / 1e3)
+            out[label + "_mrays_s"] = n * args.steps / sum(ts) / 1e6
+        out["identical_hits"] = bool(all(torch.equal(a, b) for a, b in zip(hp, hl)))
+        c_p = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        c_l = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        ccs.ccs_intersect(scene.handle, rays, n, hp, ccs.make_opts(leaf_depth=8, cache_slots=0, counters=c_p), stream)
+        ccs.ccs_intersect_learned(scene.handle, prop, rays, n, hl, ccs.make_opts(leaf_depth=8, counters=c_l), 0.0,
+                                  stream)
+        torch.cuda.synchronize()
+        cp, cl = dict(zip(ccs.COUNTER_NAMES, c_p.tolist())), dict(zip(ccs.COUNTER_NAMES, c_l.tolist()))
+        out["splits_plain"] = cp["bezier_splits"] + cp["gregory_splits"]
+        out["splits_learned"] = cl["bezier_splits"] + cl["gregory_splits"]
+        out["backtracks_plain"], out["backtracks_learned"] = cp["backtracks"], cl["backtracks"]
+        out["speedup"] = out["learned_mrays_s"] / out["plain_mrays_s"]
+        res[name] = out
+    ccs.ccs_proposal_destroy(prop)
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -407,6 +505,11 @@ def main():
                 "d2h_bytes_per_step": 16 * rays_per_step},
         "gpu_launches": 2 * args.steps,
     }
+    if args.variant in ("all", "learned"):
+        res["learned"] = run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d)
+    if args.variant == "all":
+        b = run_batched(args, dev, stream, world)
+        res["batched"] = b
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
