@@ -66,11 +66,11 @@ typedef struct {
     uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
     uint32_t blocks_per_sm;   /* blocks per SM of the persistent launch, clamped to what fits [4] */
     uint32_t refill;          /* a warp hands new rays to its idle lanes once at least this many of its
-                                 32 lanes are idle, 1..32 [1] */
+                                 32 lanes are idle, 1..32 [8] */
     uint32_t chunk;           /* rays a warp takes from the global work queue at a time, multiple of 32,
-                                 32..4096 [128] */
+                                 32..4096 [32] */
     uint32_t bvh_burst;       /* BVH steps a traversing lane takes per subdivision step of the others,
-                                 1..16 [4] */
+                                 1..16 [8] */
     uint32_t cache_slots;     /* grids of pending Bezier siblings kept in shared memory per thread,
                                  0 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root */
     uint32_t min_blocks;      /* 0: kernel compiled for its natural register count; 4: compiled for at

@@ -61,9 +61,9 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.leaf_depth = o && o->leaf_depth ? o->leaf_depth : 8;
     c.block_threads = o && o->block_threads ? o->block_threads : 128;
     c.blocks_per_sm = o && o->blocks_per_sm ? o->blocks_per_sm : 4;
-    c.refill = o && o->refill ? o->refill : 1;
-    c.chunk = o && o->chunk ? o->chunk : 128;
-    c.bvh_burst = o && o->bvh_burst ? o->bvh_burst : 4;
+    c.refill = o && o->refill ? o->refill : 8;
+    c.chunk = o && o->chunk ? o->chunk : 32;
+    c.bvh_burst = o && o->bvh_burst ? o->bvh_burst : 8;
     c.cache_slots = (!o || o->cache_slots == CCS_CACHE_DEFAULT) ? 2 : o->cache_slots;
     c.min_blocks = o ? o->min_blocks : 0;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);

@@ -30,9 +30,9 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     if (!cur.leaf_depth) cur.leaf_depth = 8;
     if (!cur.block_threads) cur.block_threads = 128;
     if (!cur.blocks_per_sm) cur.blocks_per_sm = 4;
-    if (!cur.refill) cur.refill = 1;
-    if (!cur.chunk) cur.chunk = 128;
-    if (!cur.bvh_burst) cur.bvh_burst = 4;
+    if (!cur.refill) cur.refill = 8;
+    if (!cur.chunk) cur.chunk = 32;
+    if (!cur.bvh_burst) cur.bvh_burst = 8;
     if (cur.cache_slots == CCS_CACHE_DEFAULT) cur.cache_slots = 2;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {

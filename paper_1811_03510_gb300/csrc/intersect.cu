@@ -148,7 +148,9 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
         if (MODE == kModeLearned) {   // network round for every lane that has just started a pair
             const bool mine = has && s.in_pair && s.phase == kPhasePropose;
             const unsigned need = __ballot_sync(FULL, mine);
-            if (need) {
+            // rounds are batched: run once a quarter of the warp waits, or when every active lane does
+            const unsigned active = __ballot_sync(FULL, has);
+            if (need && (__popc(need) >= 8 || need == active)) {
                 if (mine) {
                     float f[kFeat];
                     pair_features(rec_of(src.scene(lsc), s.pid), s.ox, s.oy, s.oz, s.r.ix, s.r.iy, s.r.iz, s.rc0,
