@@ -287,6 +287,11 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
                         const ccs_trace_opts *base, uint32_t reps, ccs_trace_opts *best, float *best_ms,
                         ccs_autotune_trial *trials, uint32_t max_trials, uint32_t *n_trials, void *stream);
 
+/* Mirror-reflection rays, as ccs_gen_diffuse but with direction d - 2 (d . n) n (the incoming direction
+ * reflected about the hit normal). */
+ccs_status ccs_gen_mirror(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
+                          uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 const char *ccs_last_error(void);
 

@@ -33,9 +33,9 @@ def pcg32_pair(seed: int, seq: int):
     return a, b
 
 
-def diffuse_rays(P, types, rays_soa, hits, seed: int, L: int = 8, offset_abs: float = 1e-4):
+def diffuse_rays(P, types, rays_soa, hits, seed: int, L: int = 8, offset_abs: float = 1e-4, mirror: bool = False):
     """rays_soa: the incoming rays (eight planes); hits: dict with pid, u, v.  Returns eight float32
-    planes of diffuse rays, one per slot."""
+    planes of diffuse rays (mirror=True: reflections d - 2 (d.n) n), one per slot."""
     n = len(hits["pid"])
     o = np.zeros((n, 3))
     d = np.zeros((n, 3))
@@ -56,6 +56,12 @@ def diffuse_rays(P, types, rays_soa, hits, seed: int, L: int = 8, offset_abs: fl
         pts = g if greg else g[:16]
         l1 = np.ptp(pts, axis=0).sum()
         off = offset_abs + 2.0 * l1 * 2.0 ** -L
+        o[i] = f + off * nrm
+        tmin[i] = 0.0
+        tmax[i] = np.inf
+        if mirror:
+            d[i] = din[i] - 2.0 * (din[i] @ nrm) * nrm
+            continue
         a, b = pcg32_pair(seed, int(i))
         u1 = (a >> 8) / 16777216.0
         u2 = (b >> 8) / 16777216.0
@@ -66,9 +72,6 @@ def diffuse_rays(P, types, rays_soa, hits, seed: int, L: int = 8, offset_abs: fl
         bb = nrm[0] * nrm[1] * aa
         b1 = np.array([1 + sg_ * nrm[0] ** 2 * aa, sg_ * bb, -sg_ * nrm[0]])
         b2 = np.array([bb, sg_ + nrm[1] ** 2 * aa, -nrm[1]])
-        o[i] = f + off * nrm
         d[i] = lx * b1 + ly * b2 + lz * nrm
-        tmin[i] = 0.0
-        tmax[i] = np.inf
     planes = [o[:, 0], o[:, 1], o[:, 2], d[:, 0], d[:, 1], d[:, 2], tmin, tmax]
     return [np.ascontiguousarray(a, dtype=np.float32) for a in planes]

@@ -110,6 +110,8 @@ _SIGS = {
     "ccs_intersect_learned": [ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32,
                               ctypes.POINTER(ccs_hits), ctypes.POINTER(ccs_trace_opts), ctypes.c_float,
                               ctypes.c_void_p],
+    "ccs_gen_mirror": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
+                       ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays), ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
 }
 
@@ -244,6 +246,27 @@ def ccs_gen_diffuse(scene: int, in_rays, hits, n: int, seed: int, leaf_depth: in
     o = out_rays if isinstance(out_rays, ccs_rays) else rays_struct(out_rays)
     _check(lib().ccs_gen_diffuse(scene, ctypes.byref(r), ctypes.byref(h), n, seed, leaf_depth, offset_abs,
                                  ctypes.byref(o), _stream(stream)))
+
+
+def ccs_gen_mirror(scene: int, in_rays, hits, n: int, leaf_depth: int, offset_abs: float, out_rays, stream=None):
+    r = in_rays if isinstance(in_rays, ccs_rays) else rays_struct(in_rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    o = out_rays if isinstance(out_rays, ccs_rays) else rays_struct(out_rays)
+    _check(lib().ccs_gen_mirror(scene, ctypes.byref(r), ctypes.byref(h), n, leaf_depth, offset_abs, ctypes.byref(o),
+                                _stream(stream)))
+
+
+def gen_mirror(scene: "Scene", rays_dev, hits, leaf_depth: int = 8, offset_abs: float = 1e-4, stream=None):
+    """Mirror rays for every slot (inactive slots have tmin > tmax); returns eight device planes."""
+    import torch
+    n = int(rays_dev[0].numel())
+    o = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    d = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    tmin = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    tmax = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    planes = [o[:n], o[n:2 * n], o[2 * n:], d[:n], d[n:2 * n], d[2 * n:], tmin, tmax]
+    ccs_gen_mirror(scene.handle, rays_dev, hits, n, leaf_depth, offset_abs, planes, stream)
+    return planes
 
 
 def gen_diffuse(scene: "Scene", rays_dev, hits, seed: int, leaf_depth: int = 8, offset_abs: float = 1e-4,

@@ -338,8 +338,8 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     return CCS_OK;
 }
 
-ccs_status ccs_gen_diffuse(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
-                           uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
+static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
+                                uint32_t leaf_depth, float offset_abs, ccs_rays *out, int mirror, void *stream)
 {
     CCS_ARG(sc && out, "scene and out_rays must not be NULL");
     ccs_status st = check_rays(in, hits);
@@ -354,8 +354,21 @@ ccs_status ccs_gen_diffuse(const ccs_scene *sc, const ccs_rays *in, const ccs_hi
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_gen_diffuse(sc->d_rec, sc->d_leaf_box, sc->n, dr, dh, n, seed, (int)leaf_depth, offset_abs,
                                 const_cast<float *>(out->ox), const_cast<float *>(out->dx),
-                                const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), (cudaStream_t)stream));
+                                const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), mirror,
+                                (cudaStream_t)stream));
     return CCS_OK;
+}
+
+ccs_status ccs_gen_diffuse(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
+                           uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
+{
+    return gen_secondary(sc, in, hits, n, seed, leaf_depth, offset_abs, out, 0, stream);
+}
+
+ccs_status ccs_gen_mirror(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n,
+                          uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
+{
+    return gen_secondary(sc, in, hits, n, 0, leaf_depth, offset_abs, out, 1, stream);
 }
 
 ccs_status ccs_scene_sync_status(ccs_scene *sc, void *stream)

@@ -94,7 +94,7 @@ const MlpWeights *proposal_weights(const ccs_proposal *p);
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, cudaStream_t s);
+                               float *tmin, float *tmax, int mirror, cudaStream_t s);
 
 void set_error(const std::string &msg);
 

@@ -75,7 +75,7 @@ __device__ void patch_frame(const float4 *__restrict__ rec, float u, float v, fl
 
 __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__restrict__ leaf_box, uint32_t n_patches,
                               DevRays in, DevHits hits, uint32_t n, unsigned long long seed, int L, float offset_abs,
-                              float *out_o, float *out_d, float *out_tmin, float *out_tmax)
+                              float *out_o, float *out_d, float *out_tmin, float *out_tmax, int mirror)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -98,32 +98,41 @@ __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__re
     const float4 lo = leaf_box[2 * (size_t)pid], hi = leaf_box[2 * (size_t)pid + 1];
     const float l1 = (hi.x - lo.x) + (hi.y - lo.y) + (hi.z - lo.z);
     const float off = offset_abs + 2.0f * l1 * __int_as_float((127 - L) << 23);
-    Pcg32 rng(seed, i);
-    const float u1 = unit24(rng.next()), u2 = unit24(rng.next());
-    const float rr = sqrtf(u1), phi = 6.283185307179586f * u2;
-    const float lx = rr * cosf(phi), ly = rr * sinf(phi), lz = sqrtf(fmaxf(0.0f, 1.0f - u1));
-    // orthonormal basis around n (Duff et al. 2017)
-    const float sg = copysignf(1.0f, nz);
-    const float a = -1.0f / (sg + nz);
-    const float b = nx * ny * a;
-    const float b1x = 1.0f + sg * nx * nx * a, b1y = sg * b, b1z = -sg * nx;
-    const float b2x = b, b2y = sg + ny * ny * a, b2z = -ny;
     out_o[i] = f[0] + off * nx;
     out_o[(size_t)n + i] = f[1] + off * ny;
     out_o[2 * (size_t)n + i] = f[2] + off * nz;
-    out_d[i] = lx * b1x + ly * b2x + lz * nx;
-    out_d[(size_t)n + i] = lx * b1y + ly * b2y + lz * ny;
-    out_d[2 * (size_t)n + i] = lx * b1z + ly * b2z + lz * nz;
+    if (mirror) {   // reflection of the incoming direction about the normal
+        const float ix = in.dx[i], iy = in.dy[i], iz = in.dz[i];
+        const float k = 2.0f * (ix * nx + iy * ny + iz * nz);
+        out_d[i] = ix - k * nx;
+        out_d[(size_t)n + i] = iy - k * ny;
+        out_d[2 * (size_t)n + i] = iz - k * nz;
+    } else {
+        Pcg32 rng(seed, i);
+        const float u1 = unit24(rng.next()), u2 = unit24(rng.next());
+        const float rr = sqrtf(u1), phi = 6.283185307179586f * u2;
+        const float lx = rr * cosf(phi), ly = rr * sinf(phi), lz = sqrtf(fmaxf(0.0f, 1.0f - u1));
+        // orthonormal basis around n (Duff et al. 2017)
+        const float sg = copysignf(1.0f, nz);
+        const float a = -1.0f / (sg + nz);
+        const float b = nx * ny * a;
+        const float b1x = 1.0f + sg * nx * nx * a, b1y = sg * b, b1z = -sg * nx;
+        const float b2x = b, b2y = sg + ny * ny * a, b2z = -ny;
+        out_d[i] = lx * b1x + ly * b2x + lz * nx;
+        out_d[(size_t)n + i] = lx * b1y + ly * b2y + lz * ny;
+        out_d[2 * (size_t)n + i] = lx * b1z + ly * b2z + lz * nz;
+    }
     out_tmin[i] = 0.0f;
     out_tmax[i] = __int_as_float(0x7f800000);
 }
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, cudaStream_t s)
+                               float *tmin, float *tmax, int mirror, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_gen_diffuse<<<(n + 255) / 256, 256, 0, s>>>(rec, leaf_box, n_patches, in, hits, n, seed, L, offset_abs, o, d, tmin, tmax);
+    k_gen_diffuse<<<(n + 255) / 256, 256, 0, s>>>(rec, leaf_box, n_patches, in, hits, n, seed, L, offset_abs, o, d, tmin, tmax,
+                                                   mirror);
     return cudaGetLastError();
 }
 

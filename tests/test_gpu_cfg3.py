@@ -1,0 +1,69 @@
+"""The 393,216-patch cube-sphere (128 x 128 quads per face, noise 0.1 with 5 octaves): full-size launches
+(3840 x 2160 primary rays, autotuned), sampled against the oracle; diffuse and mirror secondary rays
+generated from oracle hits checked in full; full-size secondary generations run on the device."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.raygen import diffuse_rays
+from paper_1811_03510_gb300 import ccs, scenegen as sg
+from parity import MISS, compare
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def big():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1811_03510_gb300 import build_ext
+    build_ext.build()
+    oracle.build()
+    torch.cuda.set_device(0)
+    s = sg.config_scene(3)
+    sc = ccs.Scene(s.P, s.types)
+    yield s, sc
+    sc.close()
+
+
+def test_full_size_primary_sampled_and_secondaries(big):
+    s, sc = big
+    assert s.n == 393216
+    cam = sg.pinhole_rays(3840, 2160)
+    rays = ccs.rays_to_device(cam.soa())
+    hits = ccs.alloc_hits(cam.n)
+    best, ms, _ = ccs.ccs_autotune(sc.handle, rays, cam.n, hits, ccs.make_opts(), reps=1)
+    ccs.ccs_intersect(sc.handle, rays, cam.n, hits, best)
+    torch.cuda.synchronize()
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    g = ccs.hits_to_numpy(hits)
+    hit_idx = np.nonzero(g["pid"] != MISS)[0]
+    assert 0.1 < len(hit_idx) / cam.n < 0.3
+    rng = np.random.default_rng(3)
+    pick = np.unique(np.concatenate([rng.choice(cam.n, 1500, replace=False), rng.choice(hit_idx, 1500, replace=False)]))
+    sub = cam.subset(pick)
+    o = oracle.intersect(s.P, s.types, sub.soa(), L=8, flags=True)
+    compare({k: v[pick] for k, v in g.items()}, o, 8)
+    # secondary rays from the oracle's hits of the sample, intersected by both sides
+    for mirror in (False, True):
+        sec = diffuse_rays(s.P, s.types, sub.soa(), o, seed=1, mirror=mirror)
+        act = sec[7] >= sec[6]
+        sr = [a[act] for a in sec]
+        n = int(act.sum())
+        hs = ccs.alloc_hits(n)
+        ccs.ccs_intersect(sc.handle, ccs.rays_to_device(sr), n, hs, best)
+        torch.cuda.synchronize()
+        os_ = oracle.intersect(s.P, s.types, sr, L=8, flags=True)
+        compare(ccs.hits_to_numpy(hs), os_, 8)
+    # full-size generations on the device (one slot per pixel, inactive slots miss)
+    for gen in (lambda: ccs.gen_diffuse(sc, rays, hits, seed=1), lambda: ccs.gen_mirror(sc, rays, hits)):
+        planes = gen()
+        h2 = ccs.alloc_hits(cam.n)
+        ccs.ccs_intersect(sc.handle, planes, cam.n, h2, best)
+        torch.cuda.synchronize()
+        assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+        g2 = ccs.hits_to_numpy(h2)
+        inactive = g["pid"] == MISS
+        assert (g2["pid"][inactive] == MISS).all()
