@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     MlpWeights *mw = nullptr;
     MlpWarpTiles *mt = nullptr;
     if (MODE == kModeLearned) {   // network weights and per-warp tiles after the traversal scratch
-        unsigned char *base = reinterpret_cast<unsigned char *>(smem + (2 * 2 * L + 48 * K + K) * stride);
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem + ((2 * 2 * L + 48 * K + K + 3) / 4 * 4 + 16) * stride);
         mw = reinterpret_cast<MlpWeights *>(base);
         mt = reinterpret_cast<MlpWarpTiles *>(base + sizeof(MlpWeights)) + (threadIdx.x >> 5);
         load_weights(*mw, mlp);
@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
     scr.cache = smem + 2 * 2 * L * stride + threadIdx.x;
     scr.tag = reinterpret_cast<int *>(smem + (2 * 2 * L + 48 * K) * stride) + threadIdx.x;
+    scr.node = reinterpret_cast<float4 *>(smem + (2 * 2 * L + 48 * K + K + 3) / 4 * 4 * stride) + threadIdx.x;
     Counters cnt;
 #pragma unroll
     for (int k = 0; k < kNumCounters; ++k) cnt.v[k] = 0;
@@ -187,7 +188,8 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
 
 size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
 {
-    return (size_t)threads * (2 * 2 * L + 48 * K + K) * sizeof(float);
+    // sibling intervals, sibling grid cache and tags, padded to 16 bytes per thread, then the BVH node slot
+    return (size_t)threads * (((2 * 2 * L + 48 * K + K + 3) / 4) * 4 + 16) * sizeof(float);
 }
 
 template <bool STATS, int K, int MINB, class Src, int MODE>

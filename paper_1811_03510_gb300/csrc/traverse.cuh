@@ -75,51 +75,6 @@ struct Box6 {
     float lx, ly, lz, hx, hy, hz;
 };
 
-// Boxes of both de Casteljau halves along a; when keep >= 0 also replace g by the kept half (0 = lower,
-// 1 = upper), transposed.  Split and selection are fused so both see the same midpoints.
-template <bool BOXES>
-CCS_DEV void split_grid(float (&g)[48], Box6 &L, Box6 &R, int keep)
-{
-    float lmin[3], lmax[3], rmin[3], rmax[3];
-    float ng[48];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        lmin[c] = rmin[c] = __int_as_float(0x7f800000);
-        lmax[c] = rmax[c] = -__int_as_float(0x7f800000);
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float b0 = g[c * 16 + 0 * 4 + b], b1 = g[c * 16 + 1 * 4 + b];
-            const float b2 = g[c * 16 + 2 * 4 + b], b3 = g[c * 16 + 3 * 4 + b];
-            const float m01 = mid(b0, b1), m12 = mid(b1, b2), m23 = mid(b2, b3);
-            const float m012 = mid(m01, m12), m123 = mid(m12, m23);
-            const float m = mid(m012, m123);
-            if (BOXES) {
-                lmin[c] = min3f(lmin[c], b0, m01);
-                lmin[c] = min3f(lmin[c], m012, m);
-                lmax[c] = max3f(lmax[c], b0, m01);
-                lmax[c] = max3f(lmax[c], m012, m);
-                rmin[c] = min3f(rmin[c], m, m123);
-                rmin[c] = min3f(rmin[c], m23, b3);
-                rmax[c] = max3f(rmax[c], m, m123);
-                rmax[c] = max3f(rmax[c], m23, b3);
-            }
-            const bool up = keep == 1;
-            ng[c * 16 + b * 4 + 0] = up ? m : b0;
-            ng[c * 16 + b * 4 + 1] = up ? m123 : m01;
-            ng[c * 16 + b * 4 + 2] = up ? m23 : m012;
-            ng[c * 16 + b * 4 + 3] = up ? b3 : m;
-        }
-    }
-    if (BOXES) {
-        L = {lmin[0], lmin[1], lmin[2], lmax[0], lmax[1], lmax[2]};
-        R = {rmin[0], rmin[1], rmin[2], rmax[0], rmax[1], rmax[2]};
-    }
-    if (keep >= 0) {
-#pragma unroll
-        for (int k = 0; k < 48; ++k) g[k] = ng[k];
-    }
-}
-
 // Root grid of a Bezier record at level 0 (a = i along u): g[c][i][j] = slot 4j + i.
 CCS_DEV void load_grid(const float4 *__restrict__ rec, float (&g)[48])
 {
@@ -134,17 +89,6 @@ CCS_DEV void load_grid(const float4 *__restrict__ rec, float (&g)[48])
             g[c * 16 + 3 * 4 + q] = v.w;
         }
     }
-}
-
-// Canonical control points of the Bezier node reached by `path` at `level`: de Casteljau descent from
-// the root, one half per level.  Identical arithmetic to the descent of the traversal, so a node's
-// points (and boxes) do not depend on how it was reached (the paper recomputes with Algorithm 1
-// after backtracking; that is cheaper for deep nodes but makes boxes path-dependent in FP32).
-CCS_DEV void redescend(const float4 *__restrict__ rec, uint32_t path, int level, float (&g)[48])
-{
-    load_grid(rec, g);
-    Box6 dummy;
-    for (int k = 0; k < level; ++k) split_grid<false>(g, dummy, dummy, (path >> k) & 1u);
 }
 
 // Domain of the node (path, level): positions on the 2^L grid of leaf cells.
@@ -347,8 +291,18 @@ struct Scratch {
     float2 *sib;     // [level * stride]
     float *cache;    // [(slot * 48 + k) * stride]
     int *tag;        // [slot * stride]
+    float4 *node;    // [k * stride], k < 4: prefetched BVH node of the lane
     int stride;
 };
+
+// Asynchronous 16-byte global -> shared copies (cached in L1 and L2), per thread.
+CCS_DEV void cp_async16(void *smem_dst, const void *gsrc)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+CCS_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+CCS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // One subdivision step of a Bezier/Gregory node (Algorithm 3, the body of the while loop): de Casteljau
 // split of the node grid along its fixed axis, the two child boxes (Gregory: upper corner + d), both
@@ -368,8 +322,7 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
     float lmin[3], lmax[3], rmin[3], rmax[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        lmin[c] = rmin[c] = __int_as_float(0x7f800000);
-        lmax[c] = rmax[c] = -__int_as_float(0x7f800000);
+        float cl[4], cL[4], cr[4], cR[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int q = c * 4 + b;
@@ -383,15 +336,15 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
             m012[q] = mid(m01[q], m12);
             m123[q] = mid(m12, m23[q]);
             mm[q] = mid(m012[q], m123[q]);
-            lmin[c] = min3f(lmin[c], b0, m01[q]);
-            lmin[c] = min3f(lmin[c], m012[q], mm[q]);
-            lmax[c] = max3f(lmax[c], b0, m01[q]);
-            lmax[c] = max3f(lmax[c], m012[q], mm[q]);
-            rmin[c] = min3f(rmin[c], mm[q], m123[q]);
-            rmin[c] = min3f(rmin[c], m23[q], b3);
-            rmax[c] = max3f(rmax[c], mm[q], m123[q]);
-            rmax[c] = max3f(rmax[c], m23[q], b3);
+            cl[b] = min3f(b0, m01[q], fminf(m012[q], mm[q]));   // per column, then a tree over columns
+            cL[b] = max3f(b0, m01[q], fmaxf(m012[q], mm[q]));
+            cr[b] = min3f(mm[q], m123[q], fminf(m23[q], b3));
+            cR[b] = max3f(mm[q], m123[q], fmaxf(m23[q], b3));
         }
+        lmin[c] = fminf(min3f(cl[0], cl[1], cl[2]), cl[3]);
+        lmax[c] = fmaxf(max3f(cL[0], cL[1], cL[2]), cL[3]);
+        rmin[c] = fminf(min3f(cr[0], cr[1], cr[2]), cr[3]);
+        rmax[c] = fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]);
     }
     StepOut o;
     slab(r, lmin[0], lmin[1], lmin[2], lmax[0] + dx, lmax[1] + dy, lmax[2] + dz, c0, c1, o.l0, o.l1);
@@ -429,13 +382,9 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
 }
 
 // World-space slab test against both child boxes of a BVH node.
-CCS_DEV void node_child_boxes(const float4 *__restrict__ nodes, int idx, const RayF &r, float c0, float c1, float &a0,
-                              float &a1, float &b0, float &b1, int &ch0, int &ch1)
+CCS_DEV void node_child_boxes(const float4 &n0, const float4 &n1, const float4 &n2, const float4 &n3, const RayF &r,
+                              float c0, float c1, float &a0, float &a1, float &b0, float &b1, int &ch0, int &ch1)
 {
-    const float4 n0 = __ldg(nodes + idx * kNodeF4 + 0);
-    const float4 n1 = __ldg(nodes + idx * kNodeF4 + 1);
-    const float4 n2 = __ldg(nodes + idx * kNodeF4 + 2);
-    const float4 n3 = __ldg(nodes + idx * kNodeF4 + 3);
     slab(r, n0.x, n0.z, n2.x, n0.y, n0.w, n2.y, c0, c1, a0, a1);
     slab(r, n1.x, n1.z, n2.z, n1.y, n1.w, n2.w, c0, c1, b0, b1);
     ch0 = __float_as_int(n3.x);
@@ -486,6 +435,7 @@ struct Lane {
     int ctop, cvalid;               // sibling cache: pushes (slot = ctop % K) and valid entries
     uint32_t skip_path;             // subtree (skip_path, skip_level) not to enter again
     int skip_level;
+    int pf;                         // BVH node whose data sits in the lane's prefetch slot (-1: none)
     int phase;                      // learned proposal: kPhase*
     uint32_t prop;                  // path bits (levels 0..5) of the proposed depth-3 cell
     float rc0, rc1;                 // root interval of the current pair
@@ -518,6 +468,7 @@ CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz
     s.skip_level = -1;
     s.skip_path = 0xFFFFFFFFu;
     s.phase = kPhaseNormal;
+    s.pf = -1;
     const bool bad = !(tmin <= tmax) || sc.n_nodes == 0 || isnan(ox) || isnan(oy) || isnan(oz) || isnan(dx) ||
                      isnan(dy) || isnan(dz);
     if (bad) {
@@ -749,7 +700,7 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
 
 // One BVH step: expand an internal node (nearer child first), or start the pair of a leaf.
 template <bool STATS, int MODE>
-CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, Counters &cnt)
+CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, Counters &cnt, const Scratch &scr)
 {
     if (s.node == kDone) return;
     if (s.node < 0) {
@@ -763,9 +714,17 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
         return;
     }
     if (STATS) cnt.v[0]++;
+    float4 q0, q1, q2, q3;
+    if (s.pf == s.node) {   // fetched during the previous iteration
+        cp_async_wait_all();
+        q0 = scr.node[0]; q1 = scr.node[scr.stride]; q2 = scr.node[2 * scr.stride]; q3 = scr.node[3 * scr.stride];
+    } else {
+        const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
+        q0 = __ldg(nd); q1 = __ldg(nd + 1); q2 = __ldg(nd + 2); q3 = __ldg(nd + 3);
+    }
     float a0, a1, b0, b1;
     int c0, c1;
-    node_child_boxes(sc.nodes, s.node, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
+    node_child_boxes(q0, q1, q2, q3, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
     const bool ha = a0 <= a1 && a0 <= s.best.t && c0 != kEmptyChild;
     const bool hb = b0 <= b1 && b0 <= s.best.t && c1 != kEmptyChild;
     if (ha && hb) {
@@ -789,6 +748,18 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
 
 // One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
 // so lanes that traverse catch up while the others subdivide).  Returns false on the iteration cap.
+// The data of the next BVH node goes to the lane's shared-memory slot asynchronously, so its latency
+// overlaps the other lanes' subdivision step of the next warp iteration.
+CCS_DEV void prefetch_node(Lane &s, const DevScene &sc, const Scratch &scr)
+{
+    if (s.in_pair || s.node < 0 || s.node == s.pf) return;
+    const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) cp_async16(scr.node + k * scr.stride, nd + k);
+    cp_async_commit();
+    s.pf = s.node;
+}
+
 template <bool STATS, int K, int MODE>
 CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
                        Counters &cnt, int burst, const ModeCtx &mc)
@@ -797,13 +768,14 @@ CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         if (s.iters == 0) return false;
         --s.iters;
         pair_step<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
-        return true;
+    } else {
+        for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
+            if (s.iters == 0) return false;
+            --s.iters;
+            bvh_step<STATS, MODE>(s, g, stk, sc, cnt, scr);
+        }
     }
-    for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
-        if (s.iters == 0) return false;
-        --s.iters;
-        bvh_step<STATS, MODE>(s, g, stk, sc, cnt);
-    }
+    prefetch_node(s, sc, scr);
     return true;
 }
 
