@@ -73,8 +73,11 @@ typedef struct {
                                  1..16 [8] */
     uint32_t cache_slots;     /* grids of pending Bezier siblings kept in shared memory per thread,
                                  0 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root */
-    uint32_t min_blocks;      /* 0: kernel compiled for its natural register count; 4: compiled for at
-                                 least 4 blocks of 128 threads per SM (128 registers, spills to L1) [0] */
+    uint32_t min_blocks;      /* 0: kernel compiled for 3 blocks of 128 threads per SM (168 registers);
+                                 4: compiled for 4 blocks (128 registers, spills to L1) [0] */
+    uint32_t vote;            /* 0: every lane steps every iteration; v > 0: per iteration a warp steps
+                                 only its lanes inside a patch while at least v of them are, else only
+                                 its lanes traversing the BVH, 0..32 [0] */
     uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
@@ -276,8 +279,8 @@ typedef struct {
 } ccs_autotune_trial;
 
 /* Autotuner: coordinate descent (two passes) over threads per block {64, 96, 128}, blocks per SM
- * {1..4}, refill {1, 2, 4, 8}, chunk {32..1024}, bvh_burst {1..16}, cache_slots {0, 2} and min_blocks
- * {0, 4}, starting from
+ * {1..4}, refill {1, 2, 4, 8}, chunk {32..1024}, bvh_burst {1..16}, cache_slots {0, 2}, min_blocks
+ * {0, 4} and vote {0, 4, 8, 12, 16, 20, 24}, starting from
  * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so
  * tuning is safe.  Each candidate is timed with CUDA events over `reps` launches (after one warm-up)
  * of ccs_intersect on the caller's device rays/hits on `stream`, which is synchronised.  The fastest

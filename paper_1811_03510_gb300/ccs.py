@@ -45,7 +45,7 @@ class ccs_trace_opts(ctypes.Structure):
     _fields_ = [("leaf_depth", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("min_blocks", ctypes.c_uint32),
-                ("iter_cap", ctypes.c_uint32),
+                ("vote", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
 
 
@@ -175,7 +175,7 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
-              cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, iter_cap=0, counters=None) -> ccs_trace_opts:
+              cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, iter_cap=0, counters=None) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -184,6 +184,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.chunk = chunk
     o.bvh_burst = bvh_burst
     o.min_blocks = min_blocks
+    o.vote = vote
     o.cache_slots = cache_slots
     o.iter_cap = iter_cap
     o.flags = CCS_TRACE_COUNT if counters is not None else 0
@@ -432,7 +433,7 @@ def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=No
 
 def opts_dict(o: ccs_trace_opts) -> dict:
     return {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
-                                             "bvh_burst", "cache_slots", "min_blocks")}
+                                             "bvh_burst", "cache_slots", "min_blocks", "vote")}
 
 
 def ccs_scene_sync_status(scene: int, stream=None) -> int:

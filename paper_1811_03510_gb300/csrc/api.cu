@@ -66,6 +66,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.bvh_burst = o && o->bvh_burst ? o->bvh_burst : 8;
     c.cache_slots = (!o || o->cache_slots == CCS_CACHE_DEFAULT) ? 2 : o->cache_slots;
     c.min_blocks = o ? o->min_blocks : 0;
+    c.vote = o ? o->vote : 0;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
@@ -78,6 +79,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.bvh_burst >= 1 && c.bvh_burst <= 16, "bvh_burst must be in 1..16");
     CCS_ARG(c.cache_slots == 0 || c.cache_slots == 2, "cache_slots must be 0 or 2");
     CCS_ARG(c.min_blocks == 0 || c.min_blocks == 4, "min_blocks must be 0 or 4");
+    CCS_ARG(c.vote <= 32, "vote must be in 0..32");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;
 }

@@ -69,12 +69,14 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> cache_c = {0, 2};
     const std::vector<uint32_t> minb_c = {0, 4};
-    const std::vector<uint32_t> *cands[7] = {&threads_c, &bps_c, &refill_c, &chunk_c, &burst_c, &cache_c, &minb_c};
+    const std::vector<uint32_t> vote_c = {0, 4, 8, 12, 16, 20, 24};
+    const std::vector<uint32_t> *cands[8] = {&vote_c, &threads_c, &bps_c, &refill_c, &chunk_c, &burst_c, &cache_c,
+                                             &minb_c};
     for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
-        for (int knob = 0; knob < 7 && st == CCS_OK; ++knob) {
+        for (int knob = 0; knob < 8 && st == CCS_OK; ++knob) {
             for (uint32_t v : *cands[knob]) {
                 ccs_trace_opts o = cur;
-                uint32_t *fields[7] = {&o.block_threads, &o.blocks_per_sm, &o.refill, &o.chunk, &o.bvh_burst,
+                uint32_t *fields[8] = {&o.vote, &o.block_threads, &o.blocks_per_sm, &o.refill, &o.chunk, &o.bvh_burst,
                                        &o.cache_slots, &o.min_blocks};
                 uint32_t *field = fields[knob];
                 if (*field == v) continue;

@@ -39,7 +39,8 @@ struct ModeCtx {
 };
 
 struct LaunchCfg {
-    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, iter_cap, flags;
+    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote, iter_cap,
+        flags;
     unsigned long long *counters;
     int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal
     ModeCtx mc{};

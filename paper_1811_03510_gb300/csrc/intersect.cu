@@ -56,7 +56,8 @@ template <bool STATS, int K, int MINB, class Src, int MODE>
 __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_t refill, uint32_t chunk, int burst,
                                                          uint32_t iter_cap, uint32_t *queue, uint32_t *status,
                                                          unsigned long long *counters, ModeCtx mc,
-                                                         const MlpWeights *__restrict__ mlp, float min_conf)
+                                                         const MlpWeights *__restrict__ mlp, float min_conf,
+                                                         uint32_t vote)
 {
     extern __shared__ __align__(16) float smem[];
     const int stride = blockDim.x;
@@ -122,7 +123,16 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
             if (exhausted && wnext == wend) break;
             continue;
         }
-        if (has) {
+        // phase vote: with vote > 0 the warp runs only subdivision steps while at least `vote` lanes are in
+        // a patch, else only BVH steps, so each iteration pays for one code path (while-while schedule)
+        bool step_me = has;
+        if (vote) {
+            const unsigned in_patch = __ballot_sync(FULL, has && s.in_pair);
+            const unsigned in_bvh = __ballot_sync(FULL, has && !s.in_pair);
+            const bool patch_turn = (uint32_t)__popc(in_patch) >= vote || in_bvh == 0u;
+            step_me = has && (s.in_pair == patch_turn);
+        }
+        if (step_me) {
             const bool ok = lane_step<STATS, K, MODE>(s, g, stk, src.scene(lsc), L, scr, cnt, burst, mc);
             if (!ok || lane_done(s)) {
                 if (!ok) {
@@ -217,7 +227,8 @@ static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *qu
     if (blocks > needed) blocks = needed;
     if (blocks == 0) blocks = 1;
     kern<<<blocks, threads, smem, s>>>(src, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
-                                       cfg.iter_cap, queue, status, cfg.counters, cfg.mc, cfg.mlp, cfg.min_conf);
+                                       cfg.iter_cap, queue, status, cfg.counters, cfg.mc, cfg.mlp, cfg.min_conf,
+                                       cfg.vote);
     return cudaGetLastError();
 }
 

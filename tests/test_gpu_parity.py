@@ -218,7 +218,7 @@ def test_bit_identical_across_launch_configurations():
     ref = gpu_run(s.P, s.types, r, 8, scene=sc)
     for kw in [dict(block_threads=32), dict(block_threads=64, refill=16, chunk=32), dict(blocks_per_sm=1, refill=32),
                dict(cache_slots=0, bvh_burst=1), dict(cache_slots=0, refill=8, block_threads=96, chunk=1024, bvh_burst=16),
-               dict(min_blocks=4), dict(min_blocks=4, cache_slots=0)]:
+               dict(min_blocks=4), dict(min_blocks=4, cache_slots=0), dict(vote=12), dict(vote=24, bvh_burst=1)]:
         g = gpu_run(s.P, s.types, r, 8, scene=sc, **kw)
         for k in ("t", "u", "v", "pid"):
             assert np.array_equal(g[k], ref[k]), (kw, k)
