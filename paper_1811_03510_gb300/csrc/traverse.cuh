@@ -426,6 +426,7 @@ struct Lane {
     float n0, n1;                   // interval of `node`
     int sp;
     bool in_pair, greg;             // Algorithm 3 on patch `pid`
+    bool gpend;                     // Gregory node (path, level) still needs its (q, d): next step computes it
     uint32_t pid;
     RayF pr;                        // ray in the patch's anchored frame
     float dx, dy, dz;               // Gregory displacement of the current node
@@ -465,6 +466,7 @@ CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz
     s.n0 = tmin;
     s.n1 = tmax;
     s.in_pair = false;
+    s.gpend = false;
     s.skip_level = -1;
     s.skip_path = 0xFFFFFFFFu;
     s.phase = kPhaseNormal;
@@ -529,8 +531,8 @@ CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pi
         s.phase = kPhasePropose;
         s.skip_level = -1;
     }
-    if (s.greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, s.dx, s.dy, s.dz);
-    else load_grid(rec, g);
+    s.gpend = s.greg;   // the Gregory root's (q, d) is computed by the next step (one code copy)
+    if (!s.greg) load_grid(rec, g);
 }
 
 // Restart the current pair at its root (learned proposal), optionally skipping the proposed cell.
@@ -546,8 +548,8 @@ CCS_DEV void restart_pair(Lane &s, float (&g)[48], const DevScene &sc, bool skip
     s.phase = kPhaseNormal;
     s.skip_level = skip ? kProposalLevel : -1;
     s.skip_path = s.prop;
-    if (s.greg) gregory_node(rec, 0.0f, 1.0f, 0.0f, 1.0f, 0, g, s.dx, s.dy, s.dz);
-    else load_grid(rec, g);
+    s.gpend = s.greg;
+    if (!s.greg) load_grid(rec, g);
 }
 
 // Export of a finished pair whose leaf is the ray's best so far: features + depth-3 cell label.
@@ -596,9 +598,7 @@ CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         const float4 *rec = rec_of(sc, s.pid);
         if (s.greg) {
             s.level = l + 1;
-            float u0, u1, v0, v1;
-            node_domain(s.path, s.level, L, u0, u1, v0, v1);
-            gregory_node(rec, u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+            s.gpend = s.level < 2 * L;   // a leaf needs no bound
         } else if (cached) {
             s.level = l + 1;
             const float *src = scr.cache + (size_t)(cslot * 48) * scr.stride;
@@ -627,6 +627,13 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
                        Counters &cnt, const ModeCtx &mc)
 {
     if (MODE == kModeLearned && s.phase == kPhasePropose) return;   // waits for the warp's network round
+    if (s.gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level)
+        float u0, u1, v0, v1;
+        node_domain(s.path, s.level, L, u0, u1, v0, v1);
+        gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+        s.gpend = false;
+        return;
+    }
     const bool redesc = s.rd_target >= 0;
     const bool directed = MODE == kModeLearned && s.phase == kPhaseDirected;
     if (!redesc && s.level == 2 * L) {
@@ -662,11 +669,7 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
             s.c0 = up ? o.r0 : o.l0;
             s.c1 = up ? o.r1 : o.l1;
             ++s.level;
-            if (s.greg) {
-                float u0, u1, v0, v1;
-                node_domain(s.path, s.level, L, u0, u1, v0, v1);
-                gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
-            }
+            s.gpend = s.greg;
             if (s.level == kProposalLevel) s.phase = kPhaseSubtree;
         } else {
             restart_pair(s, g, sc, false);
@@ -688,11 +691,7 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         s.c0 = o.goR ? o.r0 : o.l0;
         s.c1 = o.goR ? o.r1 : o.l1;
         ++s.level;
-        if (s.greg) {
-            float u0, u1, v0, v1;
-            node_domain(s.path, s.level, L, u0, u1, v0, v1);
-            gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
-        }
+        s.gpend = s.greg && s.level < 2 * L;
         return;
     }
     backtrack<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
