@@ -66,7 +66,7 @@ typedef struct {
     uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
     uint32_t blocks_per_sm;   /* blocks per SM of the persistent launch, clamped to what fits [4] */
     uint32_t refill;          /* a warp hands new rays to its idle lanes once at least this many of its
-                                 32 lanes are idle, 1..32 [8] */
+                                 rays are idle, 1..32 [8] */
     uint32_t chunk;           /* rays a warp takes from the global work queue at a time, multiple of 32,
                                  32..4096 [32] */
     uint32_t bvh_burst;       /* BVH steps a traversing lane takes per subdivision step of the others,
@@ -78,6 +78,11 @@ typedef struct {
     uint32_t vote;            /* 0: every lane steps every iteration; v > 0: per iteration a warp steps
                                  only its lanes inside a patch while at least v of them are, else only
                                  its lanes traversing the BVH, 0..32 [0] */
+    uint32_t lanes_per_ray;   /* 1: a lane holds all three components of its ray, 32 rays per warp;
+                                 3: a group of three lanes holds one ray, one component per lane, and
+                                 combines the per-axis slab results by shuffles (Sec. 3.5), 10 rays per
+                                 warp; refill and vote then count rays, not lanes.  The trace export and
+                                 learned entry points use 1 [1] */
     uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
@@ -85,8 +90,15 @@ typedef struct {
 
 #define CCS_CACHE_DEFAULT 0xFFFFFFFFu
 #define CCS_TRACE_COUNT 1u          /* accumulate traversal counters into opts->counters */
-#define CCS_NUM_COUNTERS 8          /* bvh nodes, bezier splits, gregory splits, leaves, backtracks,
-                                       re-descent levels, pruned siblings, pairs */
+#define CCS_NUM_COUNTERS 20         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
+                                       splits, leaves, backtracks, re-descent levels, pruned siblings, pairs;
+                                       schedule of the warps, summed over warp iterations (8..19): warp
+                                       iterations, resident rays, then for each step kind (subdivision,
+                                       Gregory bound, leaf, BVH burst) the rays doing it and the
+                                       iterations in which any ray does it (the BVH pair is followed by
+                                       the longest burst of the iteration), then warp refills.  The
+                                       schedule counts depend on the launch options, the work counts do
+                                       not. */
 
 typedef struct {
     uint32_t bins;            /* SAH bins per axis, 4..64 [16] */
@@ -278,9 +290,9 @@ typedef struct {
     float ms;                 /* mean time of one ccs_intersect launch */
 } ccs_autotune_trial;
 
-/* Autotuner: coordinate descent (two passes) over threads per block {64, 96, 128}, blocks per SM
- * {1..4}, refill {1, 2, 4, 8}, chunk {32..1024}, bvh_burst {1..16}, cache_slots {0, 2}, min_blocks
- * {0, 4} and vote {0, 4, 8, 12, 16, 20, 24}, starting from
+/* Autotuner: coordinate descent (two passes) over lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
+ * threads per block {64, 96, 128}, blocks per SM {1..6}, refill {1, 2, 4, 8}, chunk {32..1024},
+ * bvh_burst {1..16}, cache_slots {0, 2} and min_blocks {0, 4}, starting from
  * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so
  * tuning is safe.  Each candidate is timed with CUDA events over `reps` launches (after one warm-up)
  * of ccs_intersect on the caller's device rays/hits on `stream`, which is synchronised.  The fastest

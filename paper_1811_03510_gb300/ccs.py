@@ -18,9 +18,13 @@ CCS_ERR_NOT_BUILT = 5
 CCS_BEZIER = 0
 CCS_GREGORY = 1
 CCS_TRACE_COUNT = 1
-CCS_NUM_COUNTERS = 8
+CCS_NUM_COUNTERS = 20
 COUNTER_NAMES = ("bvh_nodes", "bezier_splits", "gregory_splits", "leaves", "backtracks", "redescent_levels",
-                 "pruned_siblings", "pairs")
+                 "pruned_siblings", "pairs",
+                 # schedule of the warps (depends on the launch options)
+                 "warp_iters", "resident_rays", "split_rays", "split_iters", "gregory_rays", "gregory_iters",
+                 "leaf_rays", "leaf_iters", "bvh_rays", "bvh_iters", "bvh_burst_steps", "refills")
+NUM_WORK_COUNTERS = 8
 MISS = 0xFFFFFFFF
 
 _STATUS = {0: "CCS_OK", 1: "CCS_ERR_INVALID_ARG", 2: "CCS_ERR_CUDA", 3: "CCS_ERR_OOM",
@@ -45,7 +49,7 @@ class ccs_trace_opts(ctypes.Structure):
     _fields_ = [("leaf_depth", ctypes.c_uint32), ("block_threads", ctypes.c_uint32),
                 ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("min_blocks", ctypes.c_uint32),
-                ("vote", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
+                ("vote", ctypes.c_uint32), ("lanes_per_ray", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
 
 
@@ -175,7 +179,8 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
-              cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, iter_cap=0, counters=None) -> ccs_trace_opts:
+              cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
+              counters=None) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -185,6 +190,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.bvh_burst = bvh_burst
     o.min_blocks = min_blocks
     o.vote = vote
+    o.lanes_per_ray = lanes_per_ray
     o.cache_slots = cache_slots
     o.iter_cap = iter_cap
     o.flags = CCS_TRACE_COUNT if counters is not None else 0
@@ -433,7 +439,7 @@ def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=No
 
 def opts_dict(o: ccs_trace_opts) -> dict:
     return {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
-                                             "bvh_burst", "cache_slots", "min_blocks", "vote")}
+                                             "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray")}
 
 
 def ccs_scene_sync_status(scene: int, stream=None) -> int:

@@ -67,6 +67,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.cache_slots = (!o || o->cache_slots == CCS_CACHE_DEFAULT) ? 2 : o->cache_slots;
     c.min_blocks = o ? o->min_blocks : 0;
     c.vote = o ? o->vote : 0;
+    c.lanes_per_ray = o && o->lanes_per_ray ? o->lanes_per_ray : 1;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
@@ -80,6 +81,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.cache_slots == 0 || c.cache_slots == 2, "cache_slots must be 0 or 2");
     CCS_ARG(c.min_blocks == 0 || c.min_blocks == 4, "min_blocks must be 0 or 4");
     CCS_ARG(c.vote <= 32, "vote must be in 0..32");
+    CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;
 }

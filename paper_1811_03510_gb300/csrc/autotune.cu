@@ -1,5 +1,6 @@
 // Autotuner of the closest-hit launch: coordinate descent over options that cannot change the answer
-// (threads per block, blocks per SM, warp refill threshold, queue chunk, BVH burst, sibling cache),
+// (lanes per ray, phase vote, threads per block, blocks per SM, warp refill threshold, queue chunk, BVH
+// burst, sibling cache, register budget),
 // each candidate timed with CUDA events over `reps` launches on the caller's rays.
 #include <cuda_runtime.h>
 
@@ -34,6 +35,7 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     if (!cur.chunk) cur.chunk = 32;
     if (!cur.bvh_burst) cur.bvh_burst = 8;
     if (cur.cache_slots == CCS_CACHE_DEFAULT) cur.cache_slots = 2;
+    if (!cur.lanes_per_ray) cur.lanes_per_ray = 1;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
         set_error("ccs_autotune: cudaEventCreate failed");
@@ -63,21 +65,22 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     float cur_ms = FLT_MAX;
     ccs_status st = measure(cur, cur_ms);
     const std::vector<uint32_t> threads_c = {64, 96, 128};
-    const std::vector<uint32_t> bps_c = {1, 2, 3, 4};
+    const std::vector<uint32_t> lanes_c = {1, 3};
+    const std::vector<uint32_t> bps_c = {1, 2, 3, 4, 5, 6};
     const std::vector<uint32_t> refill_c = {1, 2, 4, 8};
     const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> cache_c = {0, 2};
     const std::vector<uint32_t> minb_c = {0, 4};
     const std::vector<uint32_t> vote_c = {0, 4, 8, 12, 16, 20, 24};
-    const std::vector<uint32_t> *cands[8] = {&vote_c, &threads_c, &bps_c, &refill_c, &chunk_c, &burst_c, &cache_c,
-                                             &minb_c};
+    const std::vector<uint32_t> *cands[9] = {&lanes_c, &vote_c, &threads_c, &bps_c, &refill_c, &chunk_c, &burst_c,
+                                             &cache_c, &minb_c};
     for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
-        for (int knob = 0; knob < 8 && st == CCS_OK; ++knob) {
+        for (int knob = 0; knob < 9 && st == CCS_OK; ++knob) {
             for (uint32_t v : *cands[knob]) {
                 ccs_trace_opts o = cur;
-                uint32_t *fields[8] = {&o.vote, &o.block_threads, &o.blocks_per_sm, &o.refill, &o.chunk, &o.bvh_burst,
-                                       &o.cache_slots, &o.min_blocks};
+                uint32_t *fields[9] = {&o.lanes_per_ray, &o.vote, &o.block_threads, &o.blocks_per_sm, &o.refill,
+                                       &o.chunk, &o.bvh_burst, &o.cache_slots, &o.min_blocks};
                 uint32_t *field = fields[knob];
                 if (*field == v) continue;
                 *field = v;

@@ -34,10 +34,10 @@ struct Task {
 void set_child(std::vector<float> &nodes, int node, int slot, const Aabb &b, int child)
 {
     float *nd = &nodes[(size_t)node * 16];
-    float *xy = nd + 4 * slot;
-    xy[0] = b.lo[0]; xy[1] = b.hi[0]; xy[2] = b.lo[1]; xy[3] = b.hi[1];
-    float *zz = nd + 8 + 2 * slot;
-    zz[0] = b.lo[2]; zz[1] = b.hi[2];
+    for (int a = 0; a < 3; ++a) {   // float4 a = axis a: (c0.lo, c0.hi, c1.lo, c1.hi)
+        nd[4 * a + 2 * slot] = b.lo[a];
+        nd[4 * a + 2 * slot + 1] = b.hi[a];
+    }
     std::memcpy(nd + 12 + slot, &child, 4);
 }
 

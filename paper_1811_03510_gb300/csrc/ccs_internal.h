@@ -17,9 +17,10 @@ namespace ccs {
 //   [15] anchor xyz (box centre), w = 1 for Gregory, 0 for Bezier.
 constexpr int kRecF4 = 16;
 
-// BVH node = 4 float4 = 64 bytes (both children's boxes stored in the parent):
-//   [0] (c0.lo.x, c0.hi.x, c0.lo.y, c0.hi.y)
-//   [1] (c1.lo.x, c1.hi.x, c1.lo.y, c1.hi.y)
+// BVH node = 4 float4 = 64 bytes (both children's boxes stored in the parent), one float4 per axis so
+// that the lane of a component loads one vector:
+//   [0] (c0.lo.x, c0.hi.x, c1.lo.x, c1.hi.x)
+//   [1] (c0.lo.y, c0.hi.y, c1.lo.y, c1.hi.y)
 //   [2] (c0.lo.z, c0.hi.z, c1.lo.z, c1.hi.z)
 //   [3] (child0, child1, parent, slot in parent) as int bits; child >= 0 is a node index,
 //       child < 0 is the leaf of patch ~child.  Node 0 is the root (parent -1).
@@ -39,8 +40,8 @@ struct ModeCtx {
 };
 
 struct LaunchCfg {
-    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote, iter_cap,
-        flags;
+    uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
+        lanes_per_ray, iter_cap, flags;
     unsigned long long *counters;
     int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal
     ModeCtx mc{};
@@ -76,7 +77,7 @@ struct BatchEntry {
 };
 
 // kernels (intersect.cu, scene.cu)
-size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K);
+size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K, uint32_t NC);
 cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
                           float4 *rec, float4 *leaf_box, cudaStream_t s);
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,

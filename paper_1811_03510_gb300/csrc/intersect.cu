@@ -52,19 +52,29 @@ struct BatchSource {
     CCS_DEV const DevHits &hits_of(uint32_t s) const { return entries[s].hits; }
 };
 
-template <bool STATS, int K, int MINB, class Src, int MODE>
+// Shared memory per thread, in floats: sibling intervals (2L float2), the sibling grid cache (K slots of
+// 16 * NC floats), the K cache tags, padded to 16 bytes; then NC + 1 float4 of the BVH prefetch slot.
+__host__ __device__ constexpr int scratch_floats(int L, int K, int NC) { return (4 * L + 16 * NC * K + K + 3) / 4 * 4; }
+__host__ __device__ constexpr int scratch_total_floats(int L, int K, int NC) { return scratch_floats(L, K, NC) + 4 * (NC + 1); }
+
+// NC = 3: one lane per ray, 32 rays per warp.  NC = 1: groups of three lanes per ray (lanes 3q .. 3q+2,
+// component = lane - 3q), 10 rays per warp; lanes 30 and 31 take no ray.  Queue, refill and vote work on
+// the group leaders (component 0); every lane of a group loads the ray and runs the same control.
+template <bool STATS, int K, int MINB, class Src, int MODE, int NC>
 __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_t refill, uint32_t chunk, int burst,
                                                          uint32_t iter_cap, uint32_t *queue, uint32_t *status,
                                                          unsigned long long *counters, ModeCtx mc,
                                                          const MlpWeights *__restrict__ mlp, float min_conf,
                                                          uint32_t vote)
 {
+    static_assert(NC == 3 || MODE == kModePlain, "groups of three lanes run the plain traversal only");
     extern __shared__ __align__(16) float smem[];
     const int stride = blockDim.x;
+    const int sf = scratch_floats(L, K, NC);
     MlpWeights *mw = nullptr;
     MlpWarpTiles *mt = nullptr;
     if (MODE == kModeLearned) {   // network weights and per-warp tiles after the traversal scratch
-        unsigned char *base = reinterpret_cast<unsigned char *>(smem + ((2 * 2 * L + 48 * K + K + 3) / 4 * 4 + 16) * stride);
+        unsigned char *base = reinterpret_cast<unsigned char *>(smem + scratch_total_floats(L, K, NC) * stride);
         mw = reinterpret_cast<MlpWeights *>(base);
         mt = reinterpret_cast<MlpWarpTiles *>(base + sizeof(MlpWeights)) + (threadIdx.x >> 5);
         load_weights(*mw, mlp);
@@ -73,27 +83,37 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     Scratch scr;
     scr.stride = stride;
     scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
-    scr.cache = smem + 2 * 2 * L * stride + threadIdx.x;
-    scr.tag = reinterpret_cast<int *>(smem + (2 * 2 * L + 48 * K) * stride) + threadIdx.x;
-    scr.node = reinterpret_cast<float4 *>(smem + (2 * 2 * L + 48 * K + K + 3) / 4 * 4 * stride) + threadIdx.x;
+    scr.cache = smem + 4 * L * stride + threadIdx.x;
+    scr.tag = reinterpret_cast<int *>(smem + (4 * L + 16 * NC * K) * stride) + threadIdx.x;
+    scr.node = reinterpret_cast<float4 *>(smem + sf * stride) + threadIdx.x;
     Counters cnt;
 #pragma unroll
     for (int k = 0; k < kNumCounters; ++k) cnt.v[k] = 0;
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned lt_mask = (1u << lane) - 1u;
+    constexpr int kRaysPerWarp = NC == 3 ? 32 : 10;
+    const int grp = NC == 3 ? lane : lane / 3;
+    Grp G;
+    G.c = NC == 3 ? 0 : lane - 3 * grp;
+    G.mask = NC == 3 ? FULL : (7u << (3 * grp)) & FULL;
+    G.l1 = 3 * grp + (G.c + 1) % 3;
+    G.l2 = 3 * grp + (G.c + 2) % 3;
+    const bool valid = grp < kRaysPerWarp;
+    const bool lead = valid && G.c == 0;
+    const unsigned lead_mask = NC == 3 ? FULL : 0x09249249u;                 // lanes 0, 3, ..., 27
+    const unsigned before_me = NC == 3 ? (1u << lane) - 1u : (1u << (3 * grp)) - 1u;   // leaders of earlier rays
     const float cellw = __int_as_float((127 - L) << 23);
     const uint32_t n = src.total();
-    Lane s;
+    Lane<NC> s;
     BvhStack stk;
-    float g[48];
+    float g[16 * NC];
     typename Src::LaneScene lsc;
     bool has = false, exhausted = false;
     uint32_t ray_scene = 0, ray_local = 0;
     uint32_t wnext = 0, wend = 0;   // warp-uniform range of rays taken from the queue, not yet handed out
     for (;;) {
-        const unsigned idle = __ballot_sync(FULL, !has);
-        if (idle != 0u && ((uint32_t)__popc(idle) >= refill || idle == FULL)) {
+        const unsigned idle = __ballot_sync(FULL, lead && !has);
+        if (idle != 0u && ((uint32_t)__popc(idle) >= refill || idle == lead_mask)) {
             if (wnext == wend && !exhausted) {
                 uint32_t base = 0;
                 if (lane == 0) base = atomicAdd(queue, chunk);
@@ -105,58 +125,85 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
                     wend = min(base + chunk, n);
                 }
             }
+            if (STATS && lane == 0 && wnext != wend) cnt.v[19] += 1;
             const uint32_t avail = wend - wnext;
-            const uint32_t rank = (uint32_t)__popc(idle & lt_mask);
-            if (!has && rank < avail) {
+            const uint32_t rank = (uint32_t)__popc(idle & before_me);
+            if (valid && !has && rank < avail) {
                 const uint32_t i = wnext + rank;
                 has = true;
                 src.locate(i, lsc, ray_scene, ray_local);
                 const DevRays &rr = src.rays_of(ray_scene);
                 const uint32_t j = ray_local;
-                begin_ray(s, src.scene(lsc), __ldg(rr.ox + j), __ldg(rr.oy + j), __ldg(rr.oz + j), __ldg(rr.dx + j),
-                          __ldg(rr.dy + j), __ldg(rr.dz + j), __ldg(rr.tmin + j), __ldg(rr.tmax + j), iter_cap);
+                begin_ray<NC>(s, src.scene(lsc), __ldg(rr.ox + j), __ldg(rr.oy + j), __ldg(rr.oz + j),
+                              __ldg(rr.dx + j), __ldg(rr.dy + j), __ldg(rr.dz + j), __ldg(rr.tmin + j),
+                              __ldg(rr.tmax + j), iter_cap, G);
             }
             const uint32_t taken = avail < (uint32_t)__popc(idle) ? avail : (uint32_t)__popc(idle);
             wnext += taken;
         }
-        if (__ballot_sync(FULL, has) == 0u) {
+        const unsigned resident = __ballot_sync(FULL, lead && has);
+        if (resident == 0u) {
             if (exhausted && wnext == wend) break;
             continue;
         }
-        // phase vote: with vote > 0 the warp runs only subdivision steps while at least `vote` lanes are in
+        // phase vote: with vote > 0 the warp runs only subdivision steps while at least `vote` rays are in
         // a patch, else only BVH steps, so each iteration pays for one code path (while-while schedule)
         bool step_me = has;
         if (vote) {
-            const unsigned in_patch = __ballot_sync(FULL, has && s.in_pair);
-            const unsigned in_bvh = __ballot_sync(FULL, has && !s.in_pair);
+            const unsigned in_patch = __ballot_sync(FULL, lead && has && s.in_pair);
+            const unsigned in_bvh = __ballot_sync(FULL, lead && has && !s.in_pair);
             const bool patch_turn = (uint32_t)__popc(in_patch) >= vote || in_bvh == 0u;
             step_me = has && (s.in_pair == patch_turn);
         }
+        int kind = kStepNone, bsteps = 0;
         if (step_me) {
-            const bool ok = lane_step<STATS, K, MODE>(s, g, stk, src.scene(lsc), L, scr, cnt, burst, mc);
+            kind = lane_step<STATS, K, MODE, NC>(s, g, stk, src.scene(lsc), L, scr, cnt, burst, mc, G, bsteps);
+            const bool ok = kind != kStepCap;
             if (!ok || lane_done(s)) {
                 if (!ok) {
-                    atomicOr(status, 1u);
+                    if (lead) atomicOr(status, 1u);
                     s.best.pid = kMissId;
                 }
-                const DevHits &hh = src.hits_of(ray_scene);
-                const uint32_t i = ray_local;
-                if (s.best.pid != kMissId) {
-                    const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
-                    hh.t[i] = s.best.t;
-                    hh.u[i] = ((float)cu + 0.5f) * cellw;
-                    hh.v[i] = ((float)cv + 0.5f) * cellw;
-                    hh.pid[i] = s.best.pid;
-                } else {
-                    hh.t[i] = __int_as_float(0x7f800000);
-                    hh.u[i] = 0.0f;
-                    hh.v[i] = 0.0f;
-                    hh.pid[i] = kMissId;
+                if (lead) {
+                    const DevHits &hh = src.hits_of(ray_scene);
+                    const uint32_t i = ray_local;
+                    if (s.best.pid != kMissId) {
+                        const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
+                        hh.t[i] = s.best.t;
+                        hh.u[i] = ((float)cu + 0.5f) * cellw;
+                        hh.v[i] = ((float)cv + 0.5f) * cellw;
+                        hh.pid[i] = s.best.pid;
+                    } else {
+                        hh.t[i] = __int_as_float(0x7f800000);
+                        hh.u[i] = 0.0f;
+                        hh.v[i] = 0.0f;
+                        hh.pid[i] = kMissId;
+                    }
                 }
                 has = false;
             }
         }
-        if (MODE == kModeLearned) {   // network round for every lane that has just started a pair
+        if constexpr (STATS) {   // schedule of this warp iteration, counted in rays (group leaders)
+            const unsigned ks = __ballot_sync(FULL, lead && kind == kStepSplit);
+            const unsigned kg = __ballot_sync(FULL, lead && kind == kStepGregory);
+            const unsigned kl = __ballot_sync(FULL, lead && kind == kStepLeaf);
+            const unsigned kb = __ballot_sync(FULL, lead && kind == kStepBvh);
+            const int longest = __reduce_max_sync(FULL, bsteps);
+            if (lane == 0) {
+                cnt.v[8] += 1;
+                cnt.v[9] += __popc(resident);
+                cnt.v[10] += __popc(ks);
+                cnt.v[11] += ks != 0u;
+                cnt.v[12] += __popc(kg);
+                cnt.v[13] += kg != 0u;
+                cnt.v[14] += __popc(kl);
+                cnt.v[15] += kl != 0u;
+                cnt.v[16] += __popc(kb);
+                cnt.v[17] += kb != 0u;
+                cnt.v[18] += (unsigned)longest;
+            }
+        }
+        if constexpr (MODE == kModeLearned) {   // network round for every lane that has just started a pair
             const bool mine = has && s.in_pair && s.phase == kPhasePropose;
             const unsigned need = __ballot_sync(FULL, mine);
             // rounds are batched: run once a quarter of the warp waits, or when every active lane does
@@ -164,8 +211,8 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
             if (need && (__popc(need) >= 8 || need == active)) {
                 if (mine) {
                     float f[kFeat];
-                    pair_features(rec_of(src.scene(lsc), s.pid), s.ox, s.oy, s.oz, s.r.ix, s.r.iy, s.r.iz, s.rc0,
-                                  s.rc1, f);
+                    pair_features(rec_of(src.scene(lsc), s.pid), s.o[0], s.o[1], s.o[2], s.r.inv[0], s.r.inv[1],
+                                  s.r.inv[2], s.rc0, s.rc1, f);
 #pragma unroll
                     for (int k = 0; k < 32; k += 2)
                         st_bf16x2(mt->x + lane * kXStride + k, k < kFeat ? f[k] : 0.0f,
@@ -186,29 +233,29 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
             }
         }
     }
-    if (STATS) {
+    cp_async_wait_all();
+    if (STATS) {   // every lane of a group holds the same counts: the leader reports them
 #pragma unroll
         for (int k = 0; k < kNumCounters; ++k) {
-            unsigned long long v = cnt.v[k];
+            unsigned long long v = lead ? cnt.v[k] : 0ull;
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
             if (lane == 0 && v) atomicAdd(counters + k, v);
         }
     }
 }
 
-size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K)
+size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K, uint32_t NC)
 {
-    // sibling intervals, sibling grid cache and tags, padded to 16 bytes per thread, then the BVH node slot
-    return (size_t)threads * (((2 * 2 * L + 48 * K + K + 3) / 4) * 4 + 16) * sizeof(float);
+    return (size_t)threads * scratch_total_floats((int)L, (int)K, (int)NC) * sizeof(float);
 }
 
-template <bool STATS, int K, int MINB, class Src, int MODE>
+template <bool STATS, int K, int MINB, class Src, int MODE, int NC = 3>
 static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms,
                               cudaStream_t s)
 {
-    auto kern = k_intersect<STATS, K, MINB, Src, MODE>;
+    auto kern = k_intersect<STATS, K, MINB, Src, MODE, NC>;
     const uint32_t threads = cfg.block_threads;
-    size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K);
+    size_t smem = intersect_smem_bytes(threads, cfg.leaf_depth, K, NC);
     if (MODE == kModeLearned) smem += sizeof(MlpWeights) + (threads / 32) * sizeof(MlpWarpTiles);
     static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
     if (smem > configured) {
@@ -223,7 +270,8 @@ static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *qu
     uint32_t per_sm = cfg.blocks_per_sm < (uint32_t)max_active ? cfg.blocks_per_sm : (uint32_t)max_active;
     uint32_t blocks = (uint32_t)num_sms * per_sm;
     const uint32_t n = src.n;
-    const uint32_t needed = (n + threads - 1) / threads;
+    const uint32_t rays_per_block = NC == 3 ? threads : threads / 32 * 10;
+    const uint32_t needed = (n + rays_per_block - 1) / rays_per_block;
     if (blocks > needed) blocks = needed;
     if (blocks == 0) blocks = 1;
     kern<<<blocks, threads, smem, s>>>(src, (int)cfg.leaf_depth, cfg.refill, cfg.chunk, (int)cfg.bvh_burst,
@@ -231,6 +279,8 @@ static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *qu
                                        cfg.vote);
     return cudaGetLastError();
 }
+
+constexpr int kMinbG3 = 6;   // blocks of 128 threads per SM the grouped kernel is compiled for
 
 template <class Src>
 static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms,
@@ -247,6 +297,13 @@ static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queu
     if (cfg.mode == kModeLearned)   // the network's shared memory leaves no room for the sibling cache
         return stats ? launch_one<true, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s)
                      : launch_one<false, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s);
+    }
+    if (cfg.lanes_per_ray == 3) {   // groups of three lanes per ray (plain traversal)
+        if (stats)
+            return cfg.cache_slots == 0 ? launch_one<true, 0, kMinbG3, Src, kModePlain, 1>(src, cfg, queue, status, num_sms, s)
+                                        : launch_one<true, 2, kMinbG3, Src, kModePlain, 1>(src, cfg, queue, status, num_sms, s);
+        return cfg.cache_slots == 0 ? launch_one<false, 0, kMinbG3, Src, kModePlain, 1>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, kMinbG3, Src, kModePlain, 1>(src, cfg, queue, status, num_sms, s);
     }
     if (stats)   // counting runs are not timed: one register budget is enough
         return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModePlain>(src, cfg, queue, status, num_sms, s)

@@ -42,16 +42,14 @@ __device__ __forceinline__ void repack_one(const float *__restrict__ x, const fl
 
 __device__ __forceinline__ void write_child_box(float4 *nodes, int node, int slot, float4 lo, float4 hi)
 {
-    float4 *nd = nodes + (size_t)node * kNodeF4;
-    // slot 0: [0] = (lo.x, hi.x, lo.y, hi.y), [2].xy = (lo.z, hi.z); slot 1 uses [1] and [2].zw
-    float *xy = reinterpret_cast<float *>(nd + slot);
-    xy[0] = lo.x;
-    xy[1] = hi.x;
-    xy[2] = lo.y;
-    xy[3] = hi.y;
-    float *zz = reinterpret_cast<float *>(nd + 2) + 2 * slot;
-    zz[0] = lo.z;
-    zz[1] = hi.z;
+    float *nd = reinterpret_cast<float *>(nodes + (size_t)node * kNodeF4);
+    // float4 a = axis a: (c0.lo, c0.hi, c1.lo, c1.hi)
+    nd[0 + 2 * slot] = lo.x;
+    nd[1 + 2 * slot] = hi.x;
+    nd[4 + 2 * slot] = lo.y;
+    nd[5 + 2 * slot] = hi.y;
+    nd[8 + 2 * slot] = lo.z;
+    nd[9 + 2 * slot] = hi.z;
 }
 
 // Refit from leaf p: write its box into its parent's slot; the second thread to arrive at a node (per
@@ -70,8 +68,8 @@ __device__ __forceinline__ void refit_one(float4 *nodes, const int *__restrict__
         __threadfence();
         const float4 *nd = nodes + (size_t)node * kNodeF4;
         const float4 a = __ldcg(nd + 0), b = __ldcg(nd + 1), c = __ldcg(nd + 2), d = __ldcg(nd + 3);
-        lo = make_float4(fminf(a.x, b.x), fminf(a.z, b.z), fminf(c.x, c.z), 0.0f);
-        hi = make_float4(fmaxf(a.y, b.y), fmaxf(a.w, b.w), fmaxf(c.y, c.w), 0.0f);
+        lo = make_float4(fminf(a.x, a.z), fminf(b.x, b.z), fminf(c.x, c.z), 0.0f);
+        hi = make_float4(fmaxf(a.y, a.w), fmaxf(b.y, b.w), fmaxf(c.y, c.w), 0.0f);
         const int parent = __float_as_int(d.z);
         if (parent < 0) return;
         link = (parent << 1) | __float_as_int(d.w);

@@ -1,7 +1,8 @@
 // Device routines of the closest-hit path: ray/box slab test, de Casteljau split with child boxes,
 // Gregory lower patch and displacement (Algorithm 2 with the crop of Algorithm 1), the per-patch
 // stackless bit-trail traversal (Algorithm 3) and the BVH traversal.  Shared by every kernel that
-// intersects, so plain, learned and batched launches compute bit-identical answers.
+// intersects, with one lane or a group of three lanes per ray, so plain, grouped, learned and batched
+// launches compute bit-identical answers.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -37,9 +38,45 @@ CCS_DEV float mid(float a, float b) { return __fmul_rn(__fadd_rn(a, b), 0.5f); }
 // Robustness factor on the far slab distance (Ize 2013, 1 + 2 gamma_3 rounded up to a float).
 constexpr float kFarScale = 1.00000048f;
 
-struct RayF {
-    float ix, iy, iz;   // 1 / d (tiny components clamped so that the products stay finite)
-    float ox, oy, oz;   // origin in the frame in use (world for the BVH, patch-anchored inside a patch)
+// ------------------------------------------------------------------------------------------------
+// Components of one ray per lane.  NC = 3: a lane holds all three components of its ray.  NC = 1: a
+// group of three consecutive lanes holds one ray, one component per lane (Sec. 3.5, thread groups of
+// three): component-wise arithmetic (de Casteljau, box extents, the per-axis slab, Algorithm 2) runs in
+// the lane of its component, and the three per-axis slab results are combined with shuffles inside the
+// group.  Control state is computed identically in all three lanes of a group, so they stay converged.
+// ------------------------------------------------------------------------------------------------
+struct Grp {
+    int c;           // first component held by this lane
+    unsigned mask;   // the group's lanes (NC = 1)
+    int l1, l2;      // the group's other two lanes (NC = 1)
+};
+
+template <int NC>
+CCS_DEV int comp(const Grp &G, int k)
+{
+    return NC == 3 ? k : G.c;
+}
+
+CCS_DEV float pick(int c, float x, float y, float z) { return c == 0 ? x : (c == 1 ? y : z); }
+
+template <int NC>
+CCS_DEV float grp_max(const Grp &G, float v)
+{
+    if constexpr (NC == 3) return v;
+    else return max3f(v, __shfl_sync(G.mask, v, G.l1), __shfl_sync(G.mask, v, G.l2));
+}
+
+template <int NC>
+CCS_DEV float grp_min(const Grp &G, float v)
+{
+    if constexpr (NC == 3) return v;
+    else return min3f(v, __shfl_sync(G.mask, v, G.l1), __shfl_sync(G.mask, v, G.l2));
+}
+
+template <int NC>
+struct RayG {
+    float inv[NC];   // 1 / d (tiny components clamped so that the products stay finite)
+    float org[NC];   // origin in the frame in use (world for the BVH, patch-anchored inside a patch)
 };
 
 CCS_DEV float safe_inv(float d)
@@ -51,42 +88,53 @@ CCS_DEV float safe_inv(float d)
 // Ray interval inside box [lo, hi], intersected with [c0, c1]: t0 = max(c0, near), t1 = min(c1, far).
 // Monotone in the box bounds, so a box inside another gives an interval inside the other's.  The
 // difference is rounded before the product, so a bound lying exactly on the origin gives exactly 0
-// even for a clamped (huge) inverse: rays along a shared boundary plane stay inside both boxes.
-CCS_DEV void slab(const RayF &r, float lox, float loy, float loz, float hix, float hiy, float hiz, float c0,
-                  float c1, float &t0, float &t1)
+// even for a clamped (huge) inverse: rays along a shared boundary plane stay inside both boxes.  The
+// minima and maxima are exact, so a group of three lanes gets the same interval as a single lane.
+template <int NC>
+CCS_DEV void slab(const RayG<NC> &r, const float (&lo)[NC], const float (&hi)[NC], float c0, float c1, const Grp &G,
+                  float &t0, float &t1)
 {
-    const float ax = __fmul_rn(__fsub_rn(lox, r.ox), r.ix), bx = __fmul_rn(__fsub_rn(hix, r.ox), r.ix);
-    const float ay = __fmul_rn(__fsub_rn(loy, r.oy), r.iy), by = __fmul_rn(__fsub_rn(hiy, r.oy), r.iy);
-    const float az = __fmul_rn(__fsub_rn(loz, r.oz), r.iz), bz = __fmul_rn(__fsub_rn(hiz, r.oz), r.iz);
-    float tn = max3f(fminf(ax, bx), fminf(ay, by), fminf(az, bz));
-    float tf = min3f(fmaxf(ax, bx), fmaxf(ay, by), fmaxf(az, bz));
+    float tn, tf;
+    if constexpr (NC == 3) {
+        float a[3], b[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            a[k] = __fmul_rn(__fsub_rn(lo[k], r.org[k]), r.inv[k]);
+            b[k] = __fmul_rn(__fsub_rn(hi[k], r.org[k]), r.inv[k]);
+        }
+        tn = max3f(fminf(a[0], b[0]), fminf(a[1], b[1]), fminf(a[2], b[2]));
+        tf = min3f(fmaxf(a[0], b[0]), fmaxf(a[1], b[1]), fmaxf(a[2], b[2]));
+    } else {
+        const float a = __fmul_rn(__fsub_rn(lo[0], r.org[0]), r.inv[0]);
+        const float b = __fmul_rn(__fsub_rn(hi[0], r.org[0]), r.inv[0]);
+        tn = grp_max<1>(G, fminf(a, b));
+        tf = grp_min<1>(G, fmaxf(a, b));
+    }
     t0 = fmaxf(tn, c0);
     t1 = fminf(__fmul_rn(tf, kFarScale), c1);
 }
 
 // ------------------------------------------------------------------------------------------------
-// Control-point grid in registers: g[c*16 + a*4 + b], c = component, split axis a.  After a split the
-// kept half is written transposed (the next split is along the other parameter), so every split
-// runs the same code (Sec. 3.5: transposing the control grid removes the divergence of the axis).
-// At even tree levels a = u index i and b = v index j; at odd levels a = j and b = i.
+// Control-point grid in registers: g[k*16 + a*4 + b], k = component held by the lane, split axis a.
+// After a split the kept half is written transposed (the next split is along the other parameter), so
+// every split runs the same code (Sec. 3.5: transposing the control grid removes the divergence of the
+// axis).  At even tree levels a = u index i and b = v index j; at odd levels a = j and b = i.
 // ------------------------------------------------------------------------------------------------
 
-struct Box6 {
-    float lx, ly, lz, hx, hy, hz;
-};
-
-// Root grid of a Bezier record at level 0 (a = i along u): g[c][i][j] = slot 4j + i.
-CCS_DEV void load_grid(const float4 *__restrict__ rec, float (&g)[48])
+// Root grid of a Bezier record at level 0 (a = i along u): g[k][i][j] = slot 4j + i.
+template <int NC>
+CCS_DEV void load_grid(const float4 *__restrict__ rec, const Grp &G, float (&g)[16 * NC])
 {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int k = 0; k < NC; ++k) {
+        const float4 *pl = rec + comp<NC>(G, k) * 4;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            const float4 v = __ldg(rec + c * 4 + q);   // slots 4q .. 4q+3: j = q, i = 0..3
-            g[c * 16 + 0 * 4 + q] = v.x;
-            g[c * 16 + 1 * 4 + q] = v.y;
-            g[c * 16 + 2 * 4 + q] = v.z;
-            g[c * 16 + 3 * 4 + q] = v.w;
+            const float4 v = __ldg(pl + q);   // slots 4q .. 4q+3: j = q, i = 0..3
+            g[k * 16 + 0 * 4 + q] = v.x;
+            g[k * 16 + 1 * 4 + q] = v.y;
+            g[k * 16 + 2 * 4 + q] = v.z;
+            g[k * 16 + 3 * 4 + q] = v.w;
         }
     }
 }
@@ -125,7 +173,8 @@ CCS_DEV void node_domain(uint32_t path, int level, int L, float &u0, float &u1, 
 // Gregory patches (Sec. 3.2): Algorithm 2 with the crop of Algorithm 1, in FP32.
 // Weight of p^u (Algorithm 2's convention): h_11 = u/(u+v), h_21 = (1-u)/((1-u)+v),
 // h_12 = u/(u+(1-v)), h_22 = (1-u)/((1-u)+(1-v)); each is monotone in u and in v, so its extremes over
-// a domain sit at two opposite corners.  0/0 cannot occur on a non-empty domain here.
+// a domain sit at two opposite corners.  0/0 cannot occur on a non-empty domain here.  Every product
+// and sum is written out (fmaf where fused), so all kernels round a node's points the same way.
 // ------------------------------------------------------------------------------------------------
 
 CCS_DEV float ratio(float a, float b)
@@ -142,8 +191,8 @@ CCS_DEV void bern4(float t, float (&B)[4], float (&D)[4])
     B[2] = 3.0f * t * t * s;
     B[3] = t * t * t;
     D[0] = -3.0f * s * s;
-    D[1] = 3.0f * s * (s - 2.0f * t);
-    D[2] = 3.0f * t * (2.0f * s - t);
+    D[1] = 3.0f * s * fmaf(-2.0f, t, s);
+    D[2] = 3.0f * t * fmaf(2.0f, s, -t);
     D[3] = 3.0f * t * t;
 }
 
@@ -159,108 +208,134 @@ CCS_DEV float wbar2(float t0, float t1)   // max of B_2^3 = 3t^2(1-t) over [t0, 
     return 3.0f * w * w * (1.0f - w);
 }
 
-// Lower bounding patch of the Gregory record restricted to [u0,u1]x[v0,v1], cropped (Algorithm 1),
-// written into g oriented for a split at `level`; d receives the displacement of the upper bound.
-CCS_DEV void gregory_node(const float4 *__restrict__ rec, float u0, float u1, float v0, float v1, int level,
-                          float (&g)[48], float &dx, float &dy, float &dz)
+// Weights of a Gregory node on [u0,u1]x[v0,v1], the same for every component.
+struct GregW {
+    float hA[4], hB[4], wk[4];                                    // extreme inner weights, weight bounds
+    float Bu0[4], Du0[4], Bu1[4], Du1[4], Bv0[4], Dv0[4], Bv1[4], Dv1[4];   // Bernstein values, derivatives
+    float Du, Dv, Duv;                                            // (u1-u0)/3, (v1-v0)/3, product
+};
+
+CCS_DEV void gregory_weights(float u0, float u1, float v0, float v1, GregW &W)
 {
     // extreme weights of the four inner points: (1,1), (2,1), (1,2), (2,2)
-    const float hA[4] = {ratio(u0, v1), ratio(1.0f - u0, v0), ratio(u1, 1.0f - v1), ratio(1.0f - u1, 1.0f - v0)};
-    const float hB[4] = {ratio(u1, v0), ratio(1.0f - u1, v1), ratio(u0, 1.0f - v0), ratio(1.0f - u0, 1.0f - v1)};
+    W.hA[0] = ratio(u0, v1);
+    W.hA[1] = ratio(1.0f - u0, v0);
+    W.hA[2] = ratio(u1, 1.0f - v1);
+    W.hA[3] = ratio(1.0f - u1, 1.0f - v0);
+    W.hB[0] = ratio(u1, v0);
+    W.hB[1] = ratio(1.0f - u1, v1);
+    W.hB[2] = ratio(u0, 1.0f - v0);
+    W.hB[3] = ratio(1.0f - u0, 1.0f - v1);
     const float wu1 = wbar1(u0, u1), wu2 = wbar2(u0, u1), wv1 = wbar1(v0, v1), wv2 = wbar2(v0, v1);
-    const float wk[4] = {wu1 * wv1, wu2 * wv1, wu1 * wv2, wu2 * wv2};
+    W.wk[0] = wu1 * wv1;
+    W.wk[1] = wu2 * wv1;
+    W.wk[2] = wu1 * wv2;
+    W.wk[3] = wu2 * wv2;
+    bern4(u0, W.Bu0, W.Du0);
+    bern4(u1, W.Bu1, W.Du1);
+    bern4(v0, W.Bv0, W.Dv0);
+    bern4(v1, W.Bv1, W.Dv1);
+    W.Du = (u1 - u0) * (1.0f / 3.0f);
+    W.Dv = (v1 - v0) * (1.0f / 3.0f);
+    W.Duv = W.Du * W.Dv;
+}
+
+// Component c of the node's lower patch, cropped (Algorithm 1), written into g[k*16 ..] oriented for a
+// split at a level of parity `odd`; dd receives component c of the upper bound's displacement.
+template <int N>
+CCS_DEV void gregory_comp(const float4 *__restrict__ rec, int c, const GregW &W, bool odd, float (&g)[N], int k,
+                          float &dd)
+{
     const int inner[4] = {5, 6, 9, 10};
-    float Bu0[4], Du0[4], Bu1[4], Du1[4], Bv0[4], Dv0[4], Bv1[4], Dv1[4];
-    bern4(u0, Bu0, Du0);
-    bern4(u1, Bu1, Du1);
-    bern4(v0, Bv0, Dv0);
-    bern4(v1, Bv1, Dv1);
-    const float Du = (u1 - u0) * (1.0f / 3.0f), Dv = (v1 - v0) * (1.0f / 3.0f), Duv = Du * Dv;
-    const bool odd = level & 1;
-    float dcomp[3];
+    float p[16];
+    const float4 *pl = rec + c * 4;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        float p[16];
-        const float4 *pl = rec + c * 4;
+    for (int q = 0; q < 4; ++q) {
+        const float4 v = __ldg(pl + q);
+        p[4 * q + 0] = v.x;
+        p[4 * q + 1] = v.y;
+        p[4 * q + 2] = v.z;
+        p[4 * q + 3] = v.w;
+    }
+    const float4 pv4 = __ldg(rec + 12 + c);
+    const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
+    dd = 0.0f;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float4 v = __ldg(pl + q);
-            p[4 * q + 0] = v.x;
-            p[4 * q + 1] = v.y;
-            p[4 * q + 2] = v.z;
-            p[4 * q + 3] = v.w;
+    for (int m = 0; m < 4; ++m) {
+        const float pu = p[inner[m]];
+        const float a = fmaf(W.hA[m], pu - pv[m], pv[m]);
+        const float b = fmaf(W.hB[m], pu - pv[m], pv[m]);
+        p[inner[m]] = fminf(a, b);
+        dd = fmaf(W.wk[m], fabsf(a - b), dd);
+    }
+    // rows j: A = sum_i B_i(u) p_ij, E = sum_i B_i'(u) p_ij at u0 and u1
+    float A0[4], E0[4], A1[4], E1[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float a0 = 0, e0 = 0, a1 = 0, e1 = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float pij = p[4 * j + i];
+            a0 = fmaf(W.Bu0[i], pij, a0);
+            e0 = fmaf(W.Du0[i], pij, e0);
+            a1 = fmaf(W.Bu1[i], pij, a1);
+            e1 = fmaf(W.Du1[i], pij, e1);
         }
-        const float4 pv4 = __ldg(rec + 12 + c);
-        const float pv[4] = {pv4.x, pv4.y, pv4.z, pv4.w};
-        float dd = 0.0f;
+        A0[j] = a0; E0[j] = e0; A1[j] = a1; E1[j] = e1;
+    }
+    // corner values: f, f_u, f_v, f_uv at (u0,v0), (u1,v0), (u0,v1), (u1,v1)
+    float f[4], fu[4], fv[4], fuv[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float pu = p[inner[k]];
-            const float a = fmaf(hA[k], pu - pv[k], pv[k]);
-            const float b = fmaf(hB[k], pu - pv[k], pv[k]);
-            p[inner[k]] = fminf(a, b);
-            dd = fmaf(wk[k], fabsf(a - b), dd);
-        }
-        dcomp[c] = dd;
-        // rows j: A = sum_i B_i(u) p_ij, E = sum_i B_i'(u) p_ij at u0 and u1
-        float A0[4], E0[4], A1[4], E1[4];
+    for (int m = 0; m < 4; ++m) {
+        const float *A = (m & 1) ? A1 : A0;
+        const float *E = (m & 1) ? E1 : E0;
+        const float *Bv = (m & 2) ? W.Bv1 : W.Bv0;
+        const float *Dv_ = (m & 2) ? W.Dv1 : W.Dv0;
+        float a = 0, b = 0, cc = 0, e = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            float a0 = 0, e0 = 0, a1 = 0, e1 = 0;
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float pij = p[4 * j + i];
-                a0 = fmaf(Bu0[i], pij, a0);
-                e0 = fmaf(Du0[i], pij, e0);
-                a1 = fmaf(Bu1[i], pij, a1);
-                e1 = fmaf(Du1[i], pij, e1);
-            }
-            A0[j] = a0; E0[j] = e0; A1[j] = a1; E1[j] = e1;
+            a = fmaf(Bv[j], A[j], a);
+            b = fmaf(Bv[j], E[j], b);
+            cc = fmaf(Dv_[j], A[j], cc);
+            e = fmaf(Dv_[j], E[j], e);
         }
-        // corner values: f, f_u, f_v, f_uv at (u0,v0), (u1,v0), (u0,v1), (u1,v1)
-        float f[4], fu[4], fv[4], fuv[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const float *A = (k & 1) ? A1 : A0;
-            const float *E = (k & 1) ? E1 : E0;
-            const float *Bv = (k & 2) ? Bv1 : Bv0;
-            const float *Dv_ = (k & 2) ? Dv1 : Dv0;
-            float a = 0, b = 0, cc = 0, e = 0;
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                a = fmaf(Bv[j], A[j], a);
-                b = fmaf(Bv[j], E[j], b);
-                cc = fmaf(Dv_[j], A[j], cc);
-                e = fmaf(Dv_[j], E[j], e);
-            }
-            f[k] = a; fu[k] = b; fv[k] = cc; fuv[k] = e;
-        }
-        // Algorithm 1: q_{i,j} at slot 4j + i
-        float q[16];
-        q[0] = f[0];
-        q[3] = f[1];
-        q[12] = f[2];
-        q[15] = f[3];
-        q[1] = fmaf(Du, fu[0], q[0]);
-        q[2] = fmaf(-Du, fu[1], q[3]);
-        q[4] = fmaf(Dv, fv[0], q[0]);
-        q[7] = fmaf(Dv, fv[1], q[3]);
-        q[8] = fmaf(-Dv, fv[2], q[12]);
-        q[11] = fmaf(-Dv, fv[3], q[15]);
-        q[13] = fmaf(Du, fu[2], q[12]);
-        q[14] = fmaf(-Du, fu[3], q[15]);
-        q[5] = fmaf(Duv, fuv[0], fmaf(Dv, fv[0], q[1]));
-        q[6] = fmaf(-Duv, fuv[1], fmaf(-Du, fu[1], q[7]));
-        q[9] = fmaf(-Duv, fuv[2], fmaf(-Dv, fv[2], q[13]));
-        q[10] = fmaf(Duv, fuv[3], fmaf(-Dv, fv[3], q[14]));
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 4; ++b) g[c * 16 + a * 4 + b] = odd ? q[4 * a + b] : q[4 * b + a];
+        f[m] = a; fu[m] = b; fv[m] = cc; fuv[m] = e;
     }
-    dx = dcomp[0];
-    dy = dcomp[1];
-    dz = dcomp[2];
+    const float Du = W.Du, Dv = W.Dv, Duv = W.Duv;
+    // Algorithm 1: q_{i,j} at slot 4j + i
+    float q[16];
+    q[0] = f[0];
+    q[3] = f[1];
+    q[12] = f[2];
+    q[15] = f[3];
+    q[1] = fmaf(Du, fu[0], q[0]);
+    q[2] = fmaf(-Du, fu[1], q[3]);
+    q[4] = fmaf(Dv, fv[0], q[0]);
+    q[7] = fmaf(Dv, fv[1], q[3]);
+    q[8] = fmaf(-Dv, fv[2], q[12]);
+    q[11] = fmaf(-Dv, fv[3], q[15]);
+    q[13] = fmaf(Du, fu[2], q[12]);
+    q[14] = fmaf(-Du, fu[3], q[15]);
+    q[5] = fmaf(Duv, fuv[0], fmaf(Dv, fv[0], q[1]));
+    q[6] = fmaf(-Duv, fuv[1], fmaf(-Du, fu[1], q[7]));
+    q[9] = fmaf(-Duv, fuv[2], fmaf(-Dv, fv[2], q[13]));
+    q[10] = fmaf(Duv, fuv[3], fmaf(-Dv, fv[3], q[14]));
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) g[k * 16 + a * 4 + b] = odd ? q[4 * a + b] : q[4 * b + a];
+}
+
+// Lower bounding patch of the Gregory record restricted to [u0,u1]x[v0,v1], cropped (Algorithm 1),
+// written into g oriented for a split at `level`; d receives the displacement of the upper bound.
+template <int NC>
+CCS_DEV void gregory_node(const float4 *__restrict__ rec, float u0, float u1, float v0, float v1, int level,
+                          const Grp &G, float (&g)[16 * NC], float (&d)[NC])
+{
+    GregW W;
+    gregory_weights(u0, u1, v0, v1, W);
+#pragma unroll
+    for (int k = 0; k < NC; ++k) gregory_comp(rec, comp<NC>(G, k), W, (level & 1) != 0, g, k, d[k]);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -284,18 +359,19 @@ struct Counters {
 
 // ------------------------------------------------------------------------------------------------
 // Shared-memory scratch of one thread (addresses strided by the block size, so a warp's accesses hit
-// 32 consecutive words): the entry/exit interval of every pending sibling (one per tree level) and a
-// K-slot cache of the control grids of the most recently pushed Bezier siblings.
+// 32 consecutive words): the entry/exit interval of every pending sibling (one per tree level), a
+// K-slot cache of the lane's components of the most recently pushed Bezier siblings' grids, and the
+// prefetch slot of the next BVH node.
 // ------------------------------------------------------------------------------------------------
 struct Scratch {
     float2 *sib;     // [level * stride]
-    float *cache;    // [(slot * 48 + k) * stride]
+    float *cache;    // [(slot * 16 * NC + k) * stride]
     int *tag;        // [slot * stride]
-    float4 *node;    // [k * stride], k < 4: prefetched BVH node of the lane
+    float4 *node;    // [k * stride], k <= NC: prefetched float4s of a BVH node
     int stride;
 };
 
-// Asynchronous 16-byte global -> shared copies (cached in L1 and L2), per thread.
+// Asynchronous 16-byte global -> shared copy (cached in L1 and L2), per thread.
 CCS_DEV void cp_async16(void *smem_dst, const void *gsrc)
 {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -308,20 +384,21 @@ CCS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "me
 // split of the node grid along its fixed axis, the two child boxes (Gregory: upper corner + d), both
 // slab tests clipped to the node's interval, closer-first choice (ties: lower half).  On return g holds
 // the chosen child (transposed for its own split) unless neither child is hit; if both are hit the
-// other child's interval is written to *sib_slot and, if store_sibling, its grid to the cache slot.
+// other child's grid goes to the cache slot when one is given.
 struct StepOut {
     bool hitL, hitR, goR;
     float l0, l1, r0, r1;
 };
 
-template <int K>
-CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, float dz, float c0, float c1, float tb,
-                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR, int force)
+template <int K, int NC>
+CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (&d)[NC], float c0, float c1, float tb,
+                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR, int force,
+                           const Grp &G)
 {
-    float e0[12], e3[12], m01[12], m012[12], mm[12], m123[12], m23[12];
-    float lmin[3], lmax[3], rmin[3], rmax[3];
+    float e0[4 * NC], e3[4 * NC], m01[4 * NC], m012[4 * NC], mm[4 * NC], m123[4 * NC], m23[4 * NC];
+    float lmin[NC], lmax[NC], rmin[NC], rmax[NC];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < NC; ++c) {
         float cl[4], cL[4], cr[4], cR[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -342,13 +419,13 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
             cR[b] = max3f(mm[q], m123[q], fmaxf(m23[q], b3));
         }
         lmin[c] = fminf(min3f(cl[0], cl[1], cl[2]), cl[3]);
-        lmax[c] = fmaxf(max3f(cL[0], cL[1], cL[2]), cL[3]);
+        lmax[c] = __fadd_rn(fmaxf(max3f(cL[0], cL[1], cL[2]), cL[3]), d[c]);
         rmin[c] = fminf(min3f(cr[0], cr[1], cr[2]), cr[3]);
-        rmax[c] = fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]);
+        rmax[c] = __fadd_rn(fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]), d[c]);
     }
     StepOut o;
-    slab(r, lmin[0], lmin[1], lmin[2], lmax[0] + dx, lmax[1] + dy, lmax[2] + dz, c0, c1, o.l0, o.l1);
-    slab(r, rmin[0], rmin[1], rmin[2], rmax[0] + dx, rmax[1] + dy, rmax[2] + dz, c0, c1, o.r0, o.r1);
+    slab<NC>(r, lmin, lmax, c0, c1, G, o.l0, o.l1);
+    slab<NC>(r, rmin, rmax, c0, c1, G, o.r0, o.r1);
     o.hitL = allowL && o.l0 <= o.l1 && o.l0 <= tb;
     o.hitR = allowR && o.r0 <= o.r1 && o.r0 <= tb;
     o.goR = force >= 0 ? force == 1 : (o.hitR && (!o.hitL || o.r0 < o.l0));
@@ -356,7 +433,7 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
         const bool up = o.goR;
         const bool store = K > 0 && force < 0 && cache_slot >= 0 && o.hitL && o.hitR;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
+        for (int c = 0; c < NC; ++c) {
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const int q = c * 4 + b;
@@ -365,7 +442,7 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
                 const float k2 = up ? m23[q] : m012[q], k3 = up ? b3 : mm[q];
                 if (K > 0 && store) {
                     // the other child, in the same transposed layout
-                    float *dst = sc.cache + (size_t)(cache_slot * 48) * sc.stride;
+                    float *dst = sc.cache + (size_t)(cache_slot * 16 * NC) * sc.stride;
                     dst[(c * 16 + b * 4 + 0) * sc.stride] = up ? b0 : mm[q];
                     dst[(c * 16 + b * 4 + 1) * sc.stride] = up ? m01[q] : m123[q];
                     dst[(c * 16 + b * 4 + 2) * sc.stride] = up ? m012[q] : m23[q];
@@ -381,14 +458,21 @@ CCS_DEV StepOut split_step(float (&g)[48], const RayF &r, float dx, float dy, fl
     return o;
 }
 
-// World-space slab test against both child boxes of a BVH node.
-CCS_DEV void node_child_boxes(const float4 &n0, const float4 &n1, const float4 &n2, const float4 &n3, const RayF &r,
-                              float c0, float c1, float &a0, float &a1, float &b0, float &b1, int &ch0, int &ch1)
+// Slab tests against both child boxes of a BVH node; q[k] = the node's float4 of component comp(k).
+template <int NC>
+CCS_DEV void node_child_boxes(const float4 (&q)[NC], const RayG<NC> &r, float c0, float c1, const Grp &G, float &a0,
+                              float &a1, float &b0, float &b1)
 {
-    slab(r, n0.x, n0.z, n2.x, n0.y, n0.w, n2.y, c0, c1, a0, a1);
-    slab(r, n1.x, n1.z, n2.z, n1.y, n1.w, n2.w, c0, c1, b0, b1);
-    ch0 = __float_as_int(n3.x);
-    ch1 = __float_as_int(n3.y);
+    float lo0[NC], hi0[NC], lo1[NC], hi1[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        lo0[k] = q[k].x;
+        hi0[k] = q[k].y;
+        lo1[k] = q[k].z;
+        hi1[k] = q[k].w;
+    }
+    slab<NC>(r, lo0, hi0, c0, c1, G, a0, a1);
+    slab<NC>(r, lo1, hi1, c0, c1, G, b0, b1);
 }
 
 constexpr int kBvhStack = 64;
@@ -402,10 +486,11 @@ struct BvhStack {
 };
 
 // ------------------------------------------------------------------------------------------------
-// Per-lane state machine.  A lane owns one ray; every call of lane_step() does one unit of work:
-// one BVH node, the start of a patch, one subdivision step of Algorithm 3, one level of a re-descent,
-// or one leaf / backtrack.  All subdivision and re-descent steps go through one call of split_step,
-// so lanes of a warp in different phases of Algorithm 3 stay converged on the expensive part.
+// Per-ray state machine.  A lane (NC = 3) or a group of three lanes (NC = 1) owns one ray; every call
+// of lane_step() does one unit of work: one BVH node, the start of a patch, one subdivision step of
+// Algorithm 3, one level of a re-descent, or one leaf / backtrack.  All subdivision and re-descent
+// steps go through one call of split_step, so lanes of a warp in different phases of Algorithm 3 stay
+// converged on the expensive part.
 //
 // Algorithm 3 with one bit trail over tree levels:
 //   path  bit l = the node at level l+1 is the upper half of its parent's split;
@@ -417,9 +502,10 @@ struct BvhStack {
 // visiting order.  A Bezier sibling's grid comes from the K-slot cache when it is still there, else
 // from a de Casteljau re-descent from the root along the path bits (same arithmetic as the descent).
 // ------------------------------------------------------------------------------------------------
+template <int NC>
 struct Lane {
-    float ox, oy, oz, tmin, tmax;   // ray, world frame
-    RayF r;
+    float o[NC], tmin, tmax;        // ray origin (the lane's components, world frame) and interval
+    RayG<NC> r;
     Best best;
     uint32_t iters;
     int node;                       // BVH: >= 0 internal node, kDone, else leaf of patch ~node
@@ -428,8 +514,8 @@ struct Lane {
     bool in_pair, greg;             // Algorithm 3 on patch `pid`
     bool gpend;                     // Gregory node (path, level) still needs its (q, d): next step computes it
     uint32_t pid;
-    RayF pr;                        // ray in the patch's anchored frame
-    float dx, dy, dz;               // Gregory displacement of the current node
+    RayG<NC> pr;                    // ray in the patch's anchored frame
+    float d[NC];                    // Gregory displacement of the current node
     int level, rd_target;           // tree level; re-descent target level (-1: none)
     uint32_t path, trail;
     float c0, c1;                   // interval of the current node
@@ -450,18 +536,17 @@ constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2;
 constexpr int kPhaseNormal = 0, kPhasePropose = 1, kPhaseDirected = 2, kPhaseSubtree = 3;
 constexpr int kProposalLevel = 6;   // depth 3 per axis
 
-
-
-CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
-                       float tmin, float tmax, uint32_t iter_cap)
+template <int NC>
+CCS_DEV void begin_ray(Lane<NC> &s, const DevScene &sc, float ox, float oy, float oz, float dx, float dy, float dz,
+                       float tmin, float tmax, uint32_t iter_cap, const Grp &G)
 {
     s.best.t = tmax;
     s.best.pid = kMissId;
     s.best.cell = kMissId;
     s.sp = 0;
     s.iters = iter_cap;
-    s.ox = ox; s.oy = oy; s.oz = oz;
-    s.tmin = tmin; s.tmax = tmax;
+    s.tmin = tmin;
+    s.tmax = tmax;
     s.node = 0;
     s.n0 = tmin;
     s.n1 = tmax;
@@ -477,17 +562,23 @@ CCS_DEV void begin_ray(Lane &s, const DevScene &sc, float ox, float oy, float oz
         s.node = kDone;
         return;
     }
-    s.r.ix = safe_inv(dx);
-    s.r.iy = safe_inv(dy);
-    s.r.iz = safe_inv(dz);
-    s.r.ox = ox;
-    s.r.oy = oy;
-    s.r.oz = oz;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int c = comp<NC>(G, k);
+        s.o[k] = pick(c, ox, oy, oz);
+        s.r.org[k] = s.o[k];
+        s.r.inv[k] = safe_inv(pick(c, dx, dy, dz));
+    }
 }
 
-CCS_DEV bool lane_done(const Lane &s) { return !s.in_pair && s.node == kDone; }
+template <int NC>
+CCS_DEV bool lane_done(const Lane<NC> &s)
+{
+    return !s.in_pair && s.node == kDone;
+}
 
-CCS_DEV void pop_next(Lane &s, BvhStack &stk)
+template <int NC>
+CCS_DEV void pop_next(Lane<NC> &s, BvhStack &stk)
 {
     while (s.sp > 0) {
         --s.sp;
@@ -504,8 +595,9 @@ CCS_DEV void pop_next(Lane &s, BvhStack &stk)
 CCS_DEV const float4 *rec_of(const DevScene &sc, uint32_t pid) { return sc.rec + (size_t)pid * kRecF4; }
 
 // Begin Algorithm 3 on patch pid with root interval [c0, c1].
-template <int MODE>
-CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pid, float c0, float c1)
+template <int MODE, int NC>
+CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, uint32_t pid, float c0, float c1,
+                        const Grp &G)
 {
     const float4 *rec = rec_of(sc, pid);
     const float4 an = __ldg(rec + 15);
@@ -513,10 +605,11 @@ CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pi
     s.greg = an.w != 0.0f;
     s.pid = pid;
     s.pr = s.r;
-    s.pr.ox = s.ox - an.x;
-    s.pr.oy = s.oy - an.y;
-    s.pr.oz = s.oz - an.z;
-    s.dx = s.dy = s.dz = 0.0f;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        s.pr.org[k] = s.o[k] - pick(comp<NC>(G, k), an.x, an.y, an.z);
+        s.d[k] = 0.0f;
+    }
     s.level = 0;
     s.rd_target = -1;
     s.path = s.trail = 0u;
@@ -532,11 +625,12 @@ CCS_DEV void start_pair(Lane &s, float (&g)[48], const DevScene &sc, uint32_t pi
         s.skip_level = -1;
     }
     s.gpend = s.greg;   // the Gregory root's (q, d) is computed by the next step (one code copy)
-    if (!s.greg) load_grid(rec, g);
+    if (!s.greg) load_grid<NC>(rec, G, g);
 }
 
 // Restart the current pair at its root (learned proposal), optionally skipping the proposed cell.
-CCS_DEV void restart_pair(Lane &s, float (&g)[48], const DevScene &sc, bool skip)
+template <int NC>
+CCS_DEV void restart_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, bool skip, const Grp &G)
 {
     const float4 *rec = rec_of(sc, s.pid);
     s.level = 0;
@@ -549,28 +643,32 @@ CCS_DEV void restart_pair(Lane &s, float (&g)[48], const DevScene &sc, bool skip
     s.skip_level = skip ? kProposalLevel : -1;
     s.skip_path = s.prop;
     s.gpend = s.greg;
-    if (!s.greg) load_grid(rec, g);
+    if (!s.greg) load_grid<NC>(rec, G, g);
 }
 
 // Export of a finished pair whose leaf is the ray's best so far: features + depth-3 cell label.
-CCS_DEV void export_pair(const Lane &s, const DevScene &sc, int L, const ModeCtx &mc)
+template <int NC>
+CCS_DEV void export_pair(const Lane<NC> &s, const DevScene &sc, int L, const ModeCtx &mc)
 {
-    if (s.best.pid != s.pid || L < 3) return;
-    const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
-    const uint32_t label = (cv >> (L - 3)) * 8u + (cu >> (L - 3));
-    const uint32_t slot = atomicAdd(mc.ex_count, 1u);
-    if (slot >= mc.ex_capacity) return;
-    float f[kFeat];
-    pair_features(rec_of(sc, s.pid), s.ox, s.oy, s.oz, s.r.ix, s.r.iy, s.r.iz, s.rc0, s.rc1, f);
+    if constexpr (NC == 3) {
+        if (s.best.pid != s.pid || L < 3) return;
+        const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
+        const uint32_t label = (cv >> (L - 3)) * 8u + (cu >> (L - 3));
+        const uint32_t slot = atomicAdd(mc.ex_count, 1u);
+        if (slot >= mc.ex_capacity) return;
+        float f[kFeat];
+        pair_features(rec_of(sc, s.pid), s.o[0], s.o[1], s.o[2], s.r.inv[0], s.r.inv[1], s.r.inv[2], s.rc0, s.rc1,
+                      f);
 #pragma unroll
-    for (int k = 0; k < kFeat; ++k) mc.ex_features[(size_t)slot * kFeat + k] = f[k];
-    mc.ex_labels[slot] = (uint8_t)label;
+        for (int k = 0; k < kFeat; ++k) mc.ex_features[(size_t)slot * kFeat + k] = f[k];
+        mc.ex_labels[slot] = (uint8_t)label;
+    }
 }
 
 // Backtrack to the deepest pending sibling that can still hold a closer leaf, or end the pair.
-template <bool STATS, int K, int MODE>
-CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt, const ModeCtx &mc)
+template <bool STATS, int K, int MODE, int NC>
+CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, int L,
+                       const Scratch &scr, Counters &cnt, const ModeCtx &mc, const Grp &G)
 {
     while (s.trail != 0u) {
         const int l = 31 - __clz(s.trail);
@@ -595,44 +693,46 @@ CCS_DEV void backtrack(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         s.c0 = sb.x;
         s.c1 = sb.y;
         if (STATS) cnt.v[4]++;
-        const float4 *rec = rec_of(sc, s.pid);
         if (s.greg) {
             s.level = l + 1;
             s.gpend = s.level < 2 * L;   // a leaf needs no bound
         } else if (cached) {
             s.level = l + 1;
-            const float *src = scr.cache + (size_t)(cslot * 48) * scr.stride;
+            const float *src = scr.cache + (size_t)(cslot * 16 * NC) * scr.stride;
 #pragma unroll
-            for (int k = 0; k < 48; ++k) g[k] = src[k * scr.stride];
+            for (int k = 0; k < 16 * NC; ++k) g[k] = src[k * scr.stride];
         } else {
             if (STATS) cnt.v[5] += l + 1;
-            load_grid(rec, g);
+            load_grid<NC>(rec_of(sc, s.pid), G, g);
             s.level = 0;
             s.rd_target = l + 1;
         }
         return;
     }
     if (MODE == kModeLearned && s.phase == kPhaseSubtree) {   // proposed cell searched: now the rest
-        restart_pair(s, g, sc, true);
+        restart_pair<NC>(s, g, sc, true, G);
         return;
     }
-    if (MODE == kModeExport) export_pair(s, sc, L, mc);
+    if (MODE == kModeExport) export_pair<NC>(s, sc, L, mc);
     s.in_pair = false;
-    pop_next(s, stk);
+    pop_next<NC>(s, stk);
 }
 
-// One step of Algorithm 3 on the lane's current pair.
-template <bool STATS, int K, int MODE>
-CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt, const ModeCtx &mc)
+// Kinds of a unit of work, for the schedule counters.
+constexpr int kStepNone = 0, kStepSplit = 1, kStepGregory = 2, kStepLeaf = 3, kStepBvh = 4, kStepCap = -1;
+
+// One step of Algorithm 3 on the ray's current pair; returns its kind.
+template <bool STATS, int K, int MODE, int NC>
+CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, int L,
+                       const Scratch &scr, Counters &cnt, const ModeCtx &mc, const Grp &G)
 {
-    if (MODE == kModeLearned && s.phase == kPhasePropose) return;   // waits for the warp's network round
+    if (MODE == kModeLearned && s.phase == kPhasePropose) return kStepNone;   // waits for the network round
     if (s.gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level)
         float u0, u1, v0, v1;
         node_domain(s.path, s.level, L, u0, u1, v0, v1);
-        gregory_node(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, g, s.dx, s.dy, s.dz);
+        gregory_node<NC>(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, G, g, s.d);
         s.gpend = false;
-        return;
+        return kStepGregory;
     }
     const bool redesc = s.rd_target >= 0;
     const bool directed = MODE == kModeLearned && s.phase == kPhaseDirected;
@@ -646,8 +746,8 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
             s.best.pid = s.pid;
             s.best.cell = cell;
         }
-        backtrack<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
-        return;
+        backtrack<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
+        return kStepLeaf;
     }
     const int force = redesc ? (int)((s.path >> s.level) & 1u) : directed ? (int)((s.prop >> s.level) & 1u) : -1;
     const int slot = (!redesc && !directed && K > 0 && !s.greg) ? (s.ctop % (K > 0 ? K : 1)) : -1;
@@ -656,11 +756,11 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         if ((s.skip_path >> s.level) & 1u) allowR = false; else allowL = false;
     }
     if (STATS && !redesc) cnt.v[s.greg ? 2 : 1]++;
-    const StepOut o = split_step<K>(g, s.pr, s.dx, s.dy, s.dz, s.c0, s.c1, s.best.t, redesc || !s.greg, scr, slot,
-                                    allowL, allowR, force);
+    const StepOut o = split_step<K, NC>(g, s.pr, s.d, s.c0, s.c1, s.best.t, redesc || !s.greg, scr, slot, allowL,
+                                        allowR, force, G);
     if (redesc) {
         if (++s.level == s.rd_target) s.rd_target = -1;
-        return;
+        return kStepSplit;
     }
     if (directed) {   // straight descent to the proposed cell; abandon it if the ray misses a box on the way
         const bool up = force == 1;
@@ -672,9 +772,9 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
             s.gpend = s.greg;
             if (s.level == kProposalLevel) s.phase = kPhaseSubtree;
         } else {
-            restart_pair(s, g, sc, false);
+            restart_pair<NC>(s, g, sc, false, G);
         }
-        return;
+        return kStepSplit;
     }
     if (o.hitL || o.hitR) {
         const uint32_t bit = 1u << s.level;
@@ -692,38 +792,48 @@ CCS_DEV void pair_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &s
         s.c1 = o.goR ? o.r1 : o.l1;
         ++s.level;
         s.gpend = s.greg && s.level < 2 * L;
-        return;
+        return kStepSplit;
     }
-    backtrack<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
+    backtrack<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
+    return kStepSplit;
 }
 
 // One BVH step: expand an internal node (nearer child first), or start the pair of a leaf.
-template <bool STATS, int MODE>
-CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, Counters &cnt, const Scratch &scr)
+template <bool STATS, int MODE, int NC>
+CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, Counters &cnt,
+                      const Scratch &scr, const Grp &G)
 {
     if (s.node == kDone) return;
     if (s.node < 0) {
         const uint32_t pid = (uint32_t)(~s.node);
         if (s.n0 <= s.best.t) {
             if (STATS) cnt.v[7]++;
-            start_pair<MODE>(s, g, sc, pid, s.n0, s.n1);
+            start_pair<MODE, NC>(s, g, sc, pid, s.n0, s.n1, G);
         } else {
-            pop_next(s, stk);
+            pop_next<NC>(s, stk);
         }
         return;
     }
     if (STATS) cnt.v[0]++;
-    float4 q0, q1, q2, q3;
+    float4 q[NC];
+    int c0, c1;
     if (s.pf == s.node) {   // fetched during the previous iteration
         cp_async_wait_all();
-        q0 = scr.node[0]; q1 = scr.node[scr.stride]; q2 = scr.node[2 * scr.stride]; q3 = scr.node[3 * scr.stride];
+#pragma unroll
+        for (int k = 0; k < NC; ++k) q[k] = scr.node[k * scr.stride];
+        const float4 ch = scr.node[NC * scr.stride];
+        c0 = __float_as_int(ch.x);
+        c1 = __float_as_int(ch.y);
     } else {
         const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
-        q0 = __ldg(nd); q1 = __ldg(nd + 1); q2 = __ldg(nd + 2); q3 = __ldg(nd + 3);
+#pragma unroll
+        for (int k = 0; k < NC; ++k) q[k] = __ldg(nd + comp<NC>(G, k));
+        const int2 ch = __ldg(reinterpret_cast<const int2 *>(nd + 3));
+        c0 = ch.x;
+        c1 = ch.y;
     }
     float a0, a1, b0, b1;
-    int c0, c1;
-    node_child_boxes(q0, q1, q2, q3, s.r, s.tmin, s.tmax, a0, a1, b0, b1, c0, c1);
+    node_child_boxes<NC>(q, s.r, s.tmin, s.tmax, G, a0, a1, b0, b1);
     const bool ha = a0 <= a1 && a0 <= s.best.t && c0 != kEmptyChild;
     const bool hb = b0 <= b1 && b0 <= s.best.t && c1 != kEmptyChild;
     if (ha && hb) {
@@ -741,41 +851,49 @@ CCS_DEV void bvh_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc
         s.n0 = ha ? a0 : b0;
         s.n1 = ha ? a1 : b1;
     } else {
-        pop_next(s, stk);
+        pop_next<NC>(s, stk);
     }
 }
 
-// One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
-// so lanes that traverse catch up while the others subdivide).  Returns false on the iteration cap.
-// The data of the next BVH node goes to the lane's shared-memory slot asynchronously, so its latency
-// overlaps the other lanes' subdivision step of the next warp iteration.
-CCS_DEV void prefetch_node(Lane &s, const DevScene &sc, const Scratch &scr)
+// The data of the next BVH node goes to the lane's shared-memory slot asynchronously (the lane's
+// components and the child word), so its latency overlaps the other lanes' subdivision step of the
+// next warp iteration.
+template <int NC>
+CCS_DEV void prefetch_node(Lane<NC> &s, const DevScene &sc, const Scratch &scr, const Grp &G)
 {
     if (s.in_pair || s.node < 0 || s.node == s.pf) return;
     const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) cp_async16(scr.node + k * scr.stride, nd + k);
+    for (int k = 0; k < NC; ++k) cp_async16(scr.node + k * scr.stride, nd + comp<NC>(G, k));
+    cp_async16(scr.node + NC * scr.stride, nd + 3);
     cp_async_commit();
     s.pf = s.node;
 }
 
-template <bool STATS, int K, int MODE>
-CCS_DEV bool lane_step(Lane &s, float (&g)[48], BvhStack &stk, const DevScene &sc, int L, const Scratch &scr,
-                       Counters &cnt, int burst, const ModeCtx &mc)
+// One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
+// so rays that traverse catch up while the others subdivide).  Returns the kind of the step (kStepCap
+// on the iteration cap); bsteps receives the number of BVH steps taken.
+template <bool STATS, int K, int MODE, int NC>
+CCS_DEV int lane_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, int L,
+                      const Scratch &scr, Counters &cnt, int burst, const ModeCtx &mc, const Grp &G, int &bsteps)
 {
+    int kind;
+    bsteps = 0;
     if (s.in_pair) {
-        if (s.iters == 0) return false;
+        if (s.iters == 0) return kStepCap;
         --s.iters;
-        pair_step<STATS, K, MODE>(s, g, stk, sc, L, scr, cnt, mc);
+        kind = pair_step<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
     } else {
+        kind = kStepBvh;
         for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
-            if (s.iters == 0) return false;
+            if (s.iters == 0) return kStepCap;
             --s.iters;
-            bvh_step<STATS, MODE>(s, g, stk, sc, cnt, scr);
+            ++bsteps;
+            bvh_step<STATS, MODE, NC>(s, g, stk, sc, cnt, scr, G);
         }
     }
-    prefetch_node(s, sc, scr);
-    return true;
+    prefetch_node<NC>(s, sc, scr, G);
+    return kind;
 }
 
 }  // namespace ccs
