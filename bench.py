@@ -115,6 +115,46 @@ def build_workload(width, height, seed=1):
     return s, r
 
 
+def schedule_summary(c: dict, lanes_per_ray: int) -> dict:
+    """Warp schedule from the kernel's schedule counters: rays resident per warp iteration, and for each step
+    kind the share of iterations that run it and the rays taking part when it runs."""
+    it = max(1, c["warp_iters"])
+    rpw = 10 if lanes_per_ray == 3 else 32
+    out = {"warp_iters": c["warp_iters"], "rays_per_warp": rpw, "resident_per_iter": c["resident_rays"] / it}
+    for k in ("split", "gregory", "leaf", "bvh"):
+        runs = c[k + "_iters"]
+        out[k + "_iter_frac"] = runs / it
+        out[k + "_rays_per_run"] = c[k + "_rays"] / runs if runs else 0.0
+    out["bvh_steps_per_run"] = c["bvh_burst_steps"] / max(1, c["bvh_iters"])
+    return out
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("traverse.cuh", "intersect.cu", "learned.cuh", "ccs_internal.h"):
+        with open(os.path.join(ROOT, "paper_1811_03510_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic() -> tuple:
+    """DRAM bytes per primary and diffuse launch from the committed ncu summary, if it was taken on the current
+    kernel sources (else None: the counters describe another kernel)."""
+    path = os.path.join(ROOT, "profiles", "k_intersect_cfg2_dram.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    import re
+    m_hash = re.search(r"kernel sources sha256\[:16\]: ([0-9a-f]{16})", text)
+    m_p = re.search(r"primary launch: dram bytes (\d+)", text)
+    m_d = re.search(r"diffuse launch: dram bytes (\d+)", text)
+    if not (m_hash and m_p and m_d) or m_hash.group(1) != kernel_source_hash():
+        return None, path
+    return (int(m_p.group(1)), int(m_d.group(1))), path
+
+
 def fp32_peak_ops(n_sm: int, mhz: float) -> float:
     """FP32 issue peak: SMs x 128 FP32 lanes x SM clock (one FMA, add, mul or min/max = one op)."""
     return n_sm * 128 * mhz * 1e6
@@ -423,6 +463,13 @@ def main():
         counts[name] = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
     alg_ops = {k: v["bvh_nodes"] * OPS_BVH_NODE + v["bezier_splits"] * OPS_SPLIT_BEZIER
                + v["gregory_splits"] * OPS_SPLIT_GREGORY for k, v in counts.items()}
+    # schedule of the warps under the chosen options (counting launches of the same configuration)
+    sched = {}
+    for name, rays, n, h, o in (("primary", prim, n_prim, hits_p, opts_p), ("diffuse", diff, n_diff, hits_d, opts_d)):
+        c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        ccs.ccs_intersect(scene.handle, rays, n, h, ccs.make_opts(**ccs.opts_dict(o), counters=c), stream)
+        torch.cuda.synchronize()
+        sched[name] = schedule_summary(dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist())), o.lanes_per_ray)
 
     for _ in range(args.warmup):
         step()
@@ -478,6 +525,7 @@ def main():
         te.append(time.perf_counter() - t0)
     e2e_value = rays_per_step * world * args.steps / sum(te) / 1e6
 
+    traffic, traffic_src = measured_traffic()
     peak_max = fp32_peak_ops(n_sm, 2070.0)
     ops_step = alg_ops["primary"] + alg_ops["diffuse"]
     achieved = ops_step * args.steps / T
@@ -494,11 +542,18 @@ def main():
         "primary_mrays_s": n_prim * args.steps / t_prim / 1e6,
         "diffuse_mrays_s": n_diff * args.steps / t_diff / 1e6,
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_max / 1e12, "unit": "Top/s (FP32)",
-                     "frac": achieved / peak_max, "traffic": None,
+                     "frac": achieved / peak_max,
+                     "traffic": (traffic[0] + traffic[1]) / 2 if traffic else None,
+                     "per": "launch (mean of the step's primary and diffuse k_intersect launches)",
                      "note": "algorithmic FP32 ops (BVH node 34, Bezier split 360, Gregory split 1490) from the "
-                             "kernel's traversal counters / event-timed launch time; peak = SMs x 128 lanes x 2070 MHz",
+                             "kernel's traversal counters / event-timed launch time; peak = SMs x 128 lanes x 2070 MHz "
+                             "(nominal FP32 issue; no FP32 figure in the measured peaks); traffic = DRAM bytes per "
+                             "launch from " + (os.path.relpath(traffic_src, ROOT) if traffic_src else "no capture") +
+                             ("" if traffic else " (null: no capture of the current kernel sources)"),
+                     "algorithmic_bytes_per_launch": 48 * rays_per_step / 2,
                      "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None},
         "counters": counts,
+        "schedule": sched,
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
                    "samples": ck["samples"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * rays_per_step,
