@@ -166,6 +166,22 @@ ccs_status ccs_scene_info(const ccs_scene *scene, uint32_t *n_patches, uint32_t 
 ccs_status ccs_gen_diffuse(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
                            uint64_t seed, uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
 
+/* Any-hit query for shadow rays (Sec. 4 traces one shadow ray per path): occluded[i] = 1 if ray i enters
+ * a leaf box of some patch within [tmin, tmax] (the condition under which ccs_intersect reports a hit),
+ * else 0.  The traversal is the closest-hit one with the best distance held at tmax; it stops at the
+ * first leaf it records, so occluded[i] equals (ccs_intersect's patch_id[i] != 0xFFFFFFFF) exactly,
+ * whatever the launch options.  Invalid rays and rays that reach opts->iter_cap give 0 (the latter also
+ * latch CCS_ERR_TRAVERSAL_LIMIT).  rays: device planes of n elements; occluded: a device array of n
+ * bytes, written.  One lane per ray (lanes_per_ray is ignored).  Asynchronous on `stream`. */
+ccs_status ccs_occluded(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, uint8_t *occluded,
+                        const ccs_trace_opts *opts, void *stream);
+
+/* Shadow rays, as ccs_gen_diffuse but aimed at the point light light[0..2]: unit direction toward the
+ * light, tmin = 0, tmax = the distance to it.  Slots without a hit, and slots whose light lies behind the
+ * surface (normal flipped against the incoming direction), get the empty interval tmin = 1, tmax = 0. */
+ccs_status ccs_gen_shadow(const ccs_scene *scene, const ccs_rays *in_rays, const ccs_hits *hits, uint32_t n,
+                          const float *light, uint32_t leaf_depth, float offset_abs, ccs_rays *out_rays, void *stream);
+
 /* ---- Batched scenes (many scenes and their rays per launch; CUDA-graph capturable) ---------------- */
 typedef struct ccs_batch ccs_batch;   /* opaque; created and freed by the library */
 

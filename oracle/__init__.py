@@ -93,6 +93,18 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | in
     return out
 
 
+def occluded(P, types, rays_soa, L: int = 8, flags: bool | int = False) -> dict:
+    """Any-hit query of shadow rays (Sec. 4): a ray is occluded iff some leaf box of some patch has a
+    non-empty nested interval inside [tmin, tmax] (the leaf condition of Algorithm 3), which is exactly when
+    the closest-hit answer exists.  Returns occluded (u8) and, with flags, the FP32 error-model flags of the
+    closest-hit query (bit 2: hit/miss may flip)."""
+    o = intersect(P, types, rays_soa, L=L, flags=flags)
+    out = {"occluded": (o["pid"] != 0xFFFFFFFF).astype(np.uint8)}
+    if flags:
+        out["flags"] = o["flags"]
+    return out
+
+
 def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False):
     """Single (ray, patch) query; g [20, 3] f64, ray8 = (ox, oy, oz, dx, dy, dz, tmin, tmax).
     Returns (hit, t, cell, stats5)."""

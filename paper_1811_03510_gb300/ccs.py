@@ -117,6 +117,11 @@ _SIGS = {
     "ccs_gen_mirror": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
                        ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays), ctypes.c_void_p],
     "ccs_scene_info": [ctypes.c_void_p, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint32)],
+    "ccs_occluded": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.c_void_p,
+                     ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_gen_shadow": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
+                       ctypes.POINTER(ctypes.c_float), ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays),
+                       ctypes.c_void_p],
 }
 
 
@@ -274,6 +279,45 @@ def gen_mirror(scene: "Scene", rays_dev, hits, leaf_depth: int = 8, offset_abs: 
     planes = [o[:n], o[n:2 * n], o[2 * n:], d[:n], d[n:2 * n], d[2 * n:], tmin, tmax]
     ccs_gen_mirror(scene.handle, rays_dev, hits, n, leaf_depth, offset_abs, planes, stream)
     return planes
+
+
+def ccs_occluded(scene: int, rays, n: int, occluded, opts: ccs_trace_opts | None = None, stream=None):
+    """Any-hit query: occluded (n device bytes) = 1 where the ray enters a leaf box within [tmin, tmax]."""
+    r = rays if isinstance(rays, ccs_rays) else rays_struct(rays)
+    _check(lib().ccs_occluded(scene, ctypes.byref(r), n, _ptr(occluded), ctypes.byref(opts) if opts else None,
+                              _stream(stream)))
+
+
+def ccs_gen_shadow(scene: int, in_rays, hits, n: int, light, leaf_depth: int, offset_abs: float, out_rays,
+                   stream=None):
+    r = in_rays if isinstance(in_rays, ccs_rays) else rays_struct(in_rays)
+    h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
+    o = out_rays if isinstance(out_rays, ccs_rays) else rays_struct(out_rays)
+    lp = (ctypes.c_float * 3)(*[float(x) for x in light])
+    _check(lib().ccs_gen_shadow(scene, ctypes.byref(r), ctypes.byref(h), n, lp, leaf_depth, offset_abs,
+                                ctypes.byref(o), _stream(stream)))
+
+
+def gen_shadow(scene: "Scene", rays_dev, hits, light, leaf_depth: int = 8, offset_abs: float = 1e-4, stream=None):
+    """Shadow rays toward the point light for every slot (inactive slots have tmin > tmax)."""
+    import torch
+    n = int(rays_dev[0].numel())
+    o = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    d = torch.empty(3 * n, dtype=torch.float32, device=rays_dev[0].device)
+    tmin = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    tmax = torch.empty(n, dtype=torch.float32, device=rays_dev[0].device)
+    planes = [o[:n], o[n:2 * n], o[2 * n:], d[:n], d[n:2 * n], d[2 * n:], tmin, tmax]
+    ccs_gen_shadow(scene.handle, rays_dev, hits, n, light, leaf_depth, offset_abs, planes, stream)
+    return planes
+
+
+def occluded(scene: "Scene", rays_dev, opts: ccs_trace_opts | None = None, stream=None):
+    """Allocate the byte plane and run the any-hit query; returns a uint8 device tensor."""
+    import torch
+    n = int(rays_dev[0].numel())
+    out = torch.empty(n, dtype=torch.uint8, device=rays_dev[0].device)
+    ccs_occluded(scene.handle, rays_dev, n, out, opts, stream)
+    return out
 
 
 def gen_diffuse(scene: "Scene", rays_dev, hits, seed: int, leaf_depth: int = 8, offset_abs: float = 1e-4,

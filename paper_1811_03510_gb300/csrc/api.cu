@@ -1,6 +1,8 @@
 // C ABI of libccs (declared in include/ccs.h): scene store, BVH build/refit, intersect launches.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <cstring>
 #include <new>
@@ -343,7 +345,8 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
 }
 
 static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
-                                uint32_t leaf_depth, float offset_abs, ccs_rays *out, int mirror, void *stream)
+                                uint32_t leaf_depth, float offset_abs, ccs_rays *out, int kind, const float *light,
+                                void *stream)
 {
     CCS_ARG(sc && out, "scene and out_rays must not be NULL");
     ccs_status st = check_rays(in, hits);
@@ -358,7 +361,7 @@ static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const c
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_gen_diffuse(sc->d_rec, sc->d_leaf_box, sc->n, dr, dh, n, seed, (int)leaf_depth, offset_abs,
                                 const_cast<float *>(out->ox), const_cast<float *>(out->dx),
-                                const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), mirror,
+                                const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), kind, light,
                                 (cudaStream_t)stream));
     return CCS_OK;
 }
@@ -366,13 +369,44 @@ static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const c
 ccs_status ccs_gen_diffuse(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,
                            uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
 {
-    return gen_secondary(sc, in, hits, n, seed, leaf_depth, offset_abs, out, 0, stream);
+    return gen_secondary(sc, in, hits, n, seed, leaf_depth, offset_abs, out, 0, nullptr, stream);
 }
 
 ccs_status ccs_gen_mirror(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n,
                           uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
 {
-    return gen_secondary(sc, in, hits, n, 0, leaf_depth, offset_abs, out, 1, stream);
+    return gen_secondary(sc, in, hits, n, 0, leaf_depth, offset_abs, out, 1, nullptr, stream);
+}
+
+ccs_status ccs_gen_shadow(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, const float *light,
+                          uint32_t leaf_depth, float offset_abs, ccs_rays *out, void *stream)
+{
+    CCS_ARG(light, "light must not be NULL");
+    CCS_ARG(std::isfinite(light[0]) && std::isfinite(light[1]) && std::isfinite(light[2]), "light must be finite");
+    return gen_secondary(sc, in, hits, n, 0, leaf_depth, offset_abs, out, 2, light, stream);
+}
+
+ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, uint8_t *occluded,
+                        const ccs_trace_opts *opts, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    CCS_ARG(rays && rays->ox && rays->oy && rays->oz && rays->dx && rays->dy && rays->dz && rays->tmin && rays->tmax,
+            "a ray plane is NULL");
+    CCS_ARG(occluded || n == 0, "occluded must not be NULL");
+    if (!sc->built) {
+        set_error("ccs_occluded before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    ccs_status st;
+    LaunchCfg cfg;
+    if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    cfg.mode = 3;
+    cfg.mc.occluded = occluded;
+    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
+    DevHits dh{nullptr, nullptr, nullptr, nullptr};
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    return CCS_OK;
 }
 
 ccs_status ccs_scene_sync_status(ccs_scene *sc, void *stream)

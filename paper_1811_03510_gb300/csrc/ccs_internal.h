@@ -37,13 +37,14 @@ struct ModeCtx {
     uint8_t *ex_labels;
     uint32_t *ex_count;
     uint32_t ex_capacity;
+    uint8_t *occluded;   // any-hit mode: one byte per ray
 };
 
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
         lanes_per_ray, iter_cap, flags;
     unsigned long long *counters;
-    int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal
+    int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit
     ModeCtx mc{};
     const MlpWeights *mlp = nullptr;
     float min_conf = 0.0f;
@@ -96,7 +97,7 @@ const MlpWeights *proposal_weights(const ccs_proposal *p);
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, int mirror, cudaStream_t s);
+                               float *tmin, float *tmax, int kind, const float *light, cudaStream_t s);
 
 void set_error(const std::string &msg);
 

@@ -164,7 +164,9 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
                     if (lead) atomicOr(status, 1u);
                     s.best.pid = kMissId;
                 }
-                if (lead) {
+                if (MODE == kModeAnyHit && lead) {
+                    mc.occluded[ray_local] = s.best.pid != kMissId ? 1 : 0;
+                } else if (lead) {
                     const DevHits &hh = src.hits_of(ray_scene);
                     const uint32_t i = ray_local;
                     if (s.best.pid != kMissId) {
@@ -294,6 +296,13 @@ static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queu
     if (cfg.mode == kModeExport)
         return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s)
                                     : launch_one<false, 2, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s);
+    if (cfg.mode == kModeAnyHit) {
+        if (stats)
+            return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
+                                        : launch_one<true, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
+        return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
+                                    : launch_one<false, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
+    }
     if (cfg.mode == kModeLearned)   // the network's shared memory leaves no room for the sibling cache
         return stats ? launch_one<true, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s)
                      : launch_one<false, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s);

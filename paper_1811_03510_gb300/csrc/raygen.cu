@@ -1,5 +1,5 @@
-// Secondary-ray generation for a wavefront tracer (test input of the diffuse workloads, not part of
-// the intersection path): cosine-weighted diffuse rays leaving the surface point of each hit.
+// Secondary-ray generation for a wavefront tracer (test input of the diffuse, mirror and shadow
+// workloads, not part of the intersection path): rays leaving the surface point of each hit.
 #include "ccs_internal.h"
 
 namespace ccs {
@@ -73,9 +73,10 @@ __device__ void patch_frame(const float4 *__restrict__ rec, float u, float v, fl
     }
 }
 
+// kind 0: cosine-weighted diffuse, 1: mirror reflection, 2: shadow ray toward the point light
 __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__restrict__ leaf_box, uint32_t n_patches,
                               DevRays in, DevHits hits, uint32_t n, unsigned long long seed, int L, float offset_abs,
-                              float *out_o, float *out_d, float *out_tmin, float *out_tmax, int mirror)
+                              float *out_o, float *out_d, float *out_tmin, float *out_tmax, int kind, float3 light)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -98,10 +99,23 @@ __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__re
     const float4 lo = leaf_box[2 * (size_t)pid], hi = leaf_box[2 * (size_t)pid + 1];
     const float l1 = (hi.x - lo.x) + (hi.y - lo.y) + (hi.z - lo.z);
     const float off = offset_abs + 2.0f * l1 * __int_as_float((127 - L) << 23);
-    out_o[i] = f[0] + off * nx;
-    out_o[(size_t)n + i] = f[1] + off * ny;
-    out_o[2 * (size_t)n + i] = f[2] + off * nz;
-    if (mirror) {   // reflection of the incoming direction about the normal
+    const float ox = f[0] + off * nx, oy = f[1] + off * ny, oz = f[2] + off * nz;
+    out_o[i] = ox;
+    out_o[(size_t)n + i] = oy;
+    out_o[2 * (size_t)n + i] = oz;
+    if (kind == 2) {   // toward the light; none when the light is behind the surface (self-shadowed)
+        const float lx = light.x - ox, ly = light.y - oy, lz = light.z - oz;
+        const float dist = sqrtf(lx * lx + ly * ly + lz * lz);
+        const bool lit = dist > 0.0f && lx * nx + ly * ny + lz * nz > 0.0f;
+        const float id = lit ? 1.0f / dist : 0.0f;
+        out_d[i] = lit ? lx * id : 0.0f;
+        out_d[(size_t)n + i] = lit ? ly * id : 0.0f;
+        out_d[2 * (size_t)n + i] = lit ? lz * id : 1.0f;
+        out_tmin[i] = lit ? 0.0f : 1.0f;
+        out_tmax[i] = lit ? dist : 0.0f;
+        return;
+    }
+    if (kind == 1) {   // reflection of the incoming direction about the normal
         const float ix = in.dx[i], iy = in.dy[i], iz = in.dz[i];
         const float k = 2.0f * (ix * nx + iy * ny + iz * nz);
         out_d[i] = ix - k * nx;
@@ -128,11 +142,12 @@ __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__re
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, int mirror, cudaStream_t s)
+                               float *tmin, float *tmax, int kind, const float *light, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
+    const float3 lp = light ? make_float3(light[0], light[1], light[2]) : make_float3(0.0f, 0.0f, 0.0f);
     k_gen_diffuse<<<(n + 255) / 256, 256, 0, s>>>(rec, leaf_box, n_patches, in, hits, n, seed, L, offset_abs, o, d, tmin, tmax,
-                                                   mirror);
+                                                   kind, lp);
     return cudaGetLastError();
 }
 

@@ -528,9 +528,9 @@ struct Lane {
     float rc0, rc1;                 // root interval of the current pair
 };
 
-// Kernel modes: plain traversal, trace export (features + depth-3 cell of each pair's best leaf), and
-// traversal with the learned proposal.
-constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2;
+// Kernel modes: plain traversal, trace export (features + depth-3 cell of each pair's best leaf),
+// traversal with the learned proposal, and any hit (the ray ends at the first leaf it records).
+constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2, kModeAnyHit = 3;
 // Phases of a pair with the learned proposal: waiting for the network, descending straight to the
 // proposed depth-3 cell, searching that cell's subtree, then the full search with the cell skipped.
 constexpr int kPhaseNormal = 0, kPhasePropose = 1, kPhaseDirected = 2, kPhaseSubtree = 3;
@@ -670,6 +670,12 @@ template <bool STATS, int K, int MODE, int NC>
 CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, int L,
                        const Scratch &scr, Counters &cnt, const ModeCtx &mc, const Grp &G)
 {
+    if (MODE == kModeAnyHit && s.best.pid != kMissId) {   // any leaf answers the query: the ray is done
+        s.in_pair = false;
+        s.node = kDone;
+        s.sp = 0;
+        return;
+    }
     while (s.trail != 0u) {
         const int l = 31 - __clz(s.trail);
         const uint32_t bit = 1u << l;
