@@ -292,6 +292,57 @@ def run_batched(args, dev, stream, world):
             "launches_per_frame": {"batched": 1, "plain": 3 * len(handles)}}
 
 
+LIGHT = (2.0, 3.0, 4.0)
+
+
+def run_shadow(args, dev, stream, flush):
+    """Shadow rays (Sec. 4: one per path) from the primary hits toward a point light, traced as an any-hit
+    query and, for comparison, as a closest-hit query.  The scene is the benchmark sphere plus a 96-patch
+    sphere of radius 0.35 between it and the light, so that some rays are occluded."""
+    import torch
+    from paper_1811_03510_gb300 import ccs, scenegen as sg
+    big, small = sg.config_scene(2), sg.config_scene(1)
+    ldir = np.array(LIGHT) / np.linalg.norm(LIGHT)
+    P = np.concatenate([big.P, (small.P.astype(np.float64) * 0.35 + 1.6 * ldir).astype(np.float32)])
+    T = np.concatenate([big.types, small.types])
+    sc = ccs.Scene(P, T)
+    cam = sg.pinhole_rays(args.width, args.height)
+    prim = ccs.rays_to_device(cam.soa(), dev)
+    hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
+    planes = ccs.gen_shadow(sc, prim, hp, LIGHT, stream=stream)
+    torch.cuda.synchronize()
+    act = (planes[7] >= planes[6]).nonzero().squeeze(1)
+    rays = [p.index_select(0, act).contiguous() for p in planes]
+    n = int(act.numel())
+    occ = torch.empty(n, dtype=torch.uint8, device=dev)
+    hits = ccs.alloc_hits(n, dev)
+    out = {"scene": "1536-patch sphere + 96-patch occluder sphere (r 0.35) toward the light", "light": LIGHT,
+           "rays": n}
+    for name, call in (("any_hit", lambda o: ccs.ccs_occluded(sc.handle, rays, n, occ, o, stream)),
+                       ("closest_hit", lambda o: ccs.ccs_intersect(sc.handle, rays, n, hits, o, stream))):
+        opts = ccs.make_opts()
+        for _ in range(max(3, args.warmup)):
+            call(opts)
+        tot = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call(opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        out[name + "_mrays_s"] = n * args.steps / tot / 1e3
+    torch.cuda.synchronize()
+    g = ccs.hits_to_numpy(hits)
+    o = occ.cpu().numpy()
+    out["occluded_frac"] = float(o.mean())
+    out["identical_to_closest_hit"] = bool(np.array_equal(o.astype(bool), g["pid"] != 0xFFFFFFFF))
+    out["speedup"] = out["any_hit_mrays_s"] / out["closest_hit_mrays_s"]
+    sc.close()
+    return out
+
+
 def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     """Train the proposal on traces of scenes with other seeds (GPU export + GPU training), then time the
     learned traversal against the plain one on this workload's primary and diffuse batches."""
@@ -565,6 +616,7 @@ def main():
     if args.variant == "all":
         b = run_batched(args, dev, stream, world)
         res["batched"] = b
+        res["shadow"] = run_shadow(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
