@@ -55,14 +55,18 @@ def num_cores() -> int:
 
 
 def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | int = False, rel_t: float = 1e-4,
-              eps: float = 5e-7, perturb: float = 1e-4, stats: bool = False) -> dict:
+              eps: float = 5e-7, perturb: float = 1e-4, stats: bool = False, spread: float = 0.0) -> dict:
     """Closest hit of every ray.  P: [n, 20, 3] float32 patch points, types [n] uint8, rays_soa: eight
     float32 arrays (ox, oy, oz, dx, dy, dz, tmin, tmax).  Returns t (f64, inf on miss), u, v (f32 cell
     centre), pid (u32, 0xFFFFFFFF on miss), cell (u64, v_cell * 2^L + u_cell); with flags 'flags' and 't2'
     under the FP32 error model (boxes within eps, far distances within 1 + 1e-6; bit0 another patch may
     win, bit1 a far cell of the patch may win, bit2 hit/miss may flip, bit3 t may leave rel_t; flags=2
     adds bit4, the origin perturbation test by +-perturb); with stats=True 'stats' [n, 5]
-    (bvh nodes, Bezier expansions, Gregory expansions, leaves, pops) and 'threads'."""
+    (bvh nodes, Bezier expansions, Gregory expansions, leaves, pops) and 'threads'.
+    spread > 0: screen-space termination (Sec. 3.3): a node made by a split is a leaf once the L1 length of
+    its box diagonal is below spread / 2 times its entry distance (spread = radians per pixel of the ray);
+    'level' gives the recorded leaf's tree level (2L at full depth), u, v the centre of its domain, and
+    the flags also cover a termination test within FP32 error of its threshold."""
     P = np.ascontiguousarray(P, dtype=np.float32)
     n = P.shape[0]
     x = np.ascontiguousarray(P[..., 0]).reshape(-1)
@@ -76,15 +80,18 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | in
     fl = np.zeros(m, np.uint8) if flags else None
     t2 = np.empty(m, np.float64) if flags else None
     st = np.zeros((m, 5), np.uint64) if stats else None
+    level = np.zeros(m, np.uint8)
     nt = lib().orc_intersect(
         _p(x, _F), _p(y, _F), _p(z, _F), _p(types, _U8), ctypes.c_uint32(n),
         *[_p(a, _F) for a in planes], ctypes.c_uint32(m), ctypes.c_int(L), ctypes.c_int(threads),
         ctypes.c_int(int(flags)), ctypes.c_double(rel_t), ctypes.c_double(eps), ctypes.c_double(perturb),
         _p(out["t"], _D), _p(out["u"], _F), _p(out["v"], _F), _p(out["pid"], _U32), _p(out["cell"], _U64),
-        _p(fl, _U8) if flags else None, _p(t2, _D) if flags else None, _p(st, _U64) if stats else None)
+        _p(fl, _U8) if flags else None, _p(t2, _D) if flags else None, _p(st, _U64) if stats else None,
+        ctypes.c_double(spread), _p(level, _U8))
     if nt < 0:
         raise ValueError("oracle rejected arguments (leaf depth out of range?)")
     out["threads"] = nt
+    out["level"] = level
     if flags:
         out["flags"] = fl
         out["t2"] = t2
@@ -105,18 +112,22 @@ def occluded(P, types, rays_soa, L: int = 8, flags: bool | int = False) -> dict:
     return out
 
 
-def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False):
+def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False, spread: float = 0.0, with_level: bool = False):
     """Single (ray, patch) query; g [20, 3] f64, ray8 = (ox, oy, oz, dx, dy, dz, tmin, tmax).
-    Returns (hit, t, cell, stats5)."""
+    Returns (hit, t, cell, stats5), and the leaf level with with_level (spread: as in intersect)."""
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
     r = np.ascontiguousarray(ray8, dtype=np.float64)
     t = ctypes.c_double()
     c = ctypes.c_uint64()
     st = np.zeros(5, np.uint64)
+    lv = ctypes.c_int()
     h = lib().orc_intersect_patch(_p(g, _D), ctypes.c_int(int(greg)), _p(r, _D), ctypes.c_int(L),
-                                  ctypes.c_int(int(brute)), ctypes.byref(t), ctypes.byref(c), _p(st, _U64))
+                                  ctypes.c_int(int(brute)), ctypes.byref(t), ctypes.byref(c), _p(st, _U64),
+                                  ctypes.c_double(spread), ctypes.byref(lv))
     if h < 0:
         raise ValueError("bad leaf depth")
+    if with_level:
+        return bool(h), t.value, c.value, st, lv.value
     return bool(h), t.value, c.value, st
 
 

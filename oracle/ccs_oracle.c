@@ -272,6 +272,7 @@ typedef struct {
     uint32_t pid;
     uint64_t cell;
     int hit;
+    int level;        /* tree level of the recorded leaf (2L unless a screen-space leaf) */
 } best_t;
 
 typedef struct {
@@ -283,7 +284,19 @@ typedef struct {
     int level;
     uint64_t pu, pv;  /* lower domain corner, scale 2^52 */
     double t0, t1;    /* effective ray interval */
+    double diag;      /* L1 length of the node box's diagonal */
 } node_t;
+
+/* Screen-space termination (Sec. 3.3): partitioning stops at a node whose box diagonal, seen from the ray
+ * at the node's entry distance, spans less than half a pixel.  A ray of a pinhole camera covers `spread`
+ * radians per pixel, so the test is L1(diagonal) < spread / 2 * t_entry.  Only nodes made by a split are
+ * tested (the patch root never is); spread = 0 keeps the fixed depth 2L. */
+static int screen_leaf(double spread, int level, double diag, double t_entry)
+{
+    return spread > 0.0 && level > 0 && diag < 0.5 * spread * t_entry;
+}
+
+static double box_diag_l1(v3 lo, v3 hi) { return (hi.x - lo.x) + (hi.y - lo.y) + (hi.z - lo.z); }
 
 static int key_less(double t, uint32_t pid, uint64_t cell, const best_t *b)
 {
@@ -314,14 +327,14 @@ static uint64_t leaf_cell(uint64_t pu, uint64_t pv, int L)
  *         under the loose boxes and enters before a fixed bound, calling back for each. */
 typedef void (*leaf_cb)(void *ctx, uint32_t pid, uint64_t cell, double t_loose, int strict, double t_strict);
 
-static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double bound, double eps, leaf_cb cb,
-                            void *ctx);
+static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spread, double bound, double eps,
+                            leaf_cb cb, void *ctx);
 
-static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *best, stats_t *st,
+static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spread, best_t *best, stats_t *st,
                             int mode, double bound, leaf_cb cb, void *ctx, double eps)
 {
     if (mode == 1) {
-        enumerate_patch(P, r, L, bound, eps, cb, ctx);
+        enumerate_patch(P, r, L, spread, bound, eps, cb, ctx);
         return;
     }
     node_t stack[2 * ORC_MAX_L + 4];
@@ -336,13 +349,14 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
     root->pu = root->pv = 0;
     root->t0 = t0;
     root->t1 = t1;
+    root->diag = box_diag_l1(P->lo, P->hi);
     while (sp > 0) {
         node_t N = stack[--sp];
         if (st) st->pops++;
         lim = mode == 0 ? best->t : bound;
         if (N.t0 > lim) continue;
-        if (N.level == 2 * L) {
-            uint64_t cell = leaf_cell(N.pu, N.pv, L);
+        if (N.level == 2 * L || screen_leaf(spread, N.level, N.diag, N.t0)) {
+            uint64_t cell = leaf_cell(N.pu, N.pv, L);   /* lowest leaf cell of the node */
             if (st) st->leaves++;
             if (mode == 0) {
                 if (key_less(N.t0, P->id, cell, best)) {
@@ -350,6 +364,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
                     best->pid = P->id;
                     best->cell = cell;
                     best->hit = 1;
+                    best->level = N.level;
                 }
             }
             continue;
@@ -368,12 +383,13 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
         }
         v3 H[2][16];
         subdivideDeCasteljau(q, axis, H[0], H[1]);
-        double c0[2], c1[2];
+        double c0[2], c1[2], diag[2];
         int hit[2];
         for (int s = 0; s < 2; ++s) {
             v3 lo = H[s][0], hi = H[s][0];
             for (int k = 1; k < 16; ++k) { lo = vmin(lo, H[s][k]); hi = vmax(hi, H[s][k]); }
             hi = add(hi, d);
+            diag[s] = box_diag_l1(lo, hi);
             hit[s] = slab(r, lo, hi, N.t0, N.t1, &c0[s], &c1[s]) && c0[s] <= lim;
         }
         int su = (N.level + 1) / 2, sv = N.level / 2;   /* splits already taken along u, v */
@@ -389,6 +405,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, best_t *bes
             C->pv = N.pv + (axis == 1 && s == 1 ? half : 0);
             C->t0 = c0[s];
             C->t1 = c1[s];
+            C->diag = diag[s];
         }
     }
 }
@@ -410,7 +427,12 @@ typedef struct {
     double l0, l1;    /* loose interval */
     double s0, s1;    /* strict interval (valid if strict) */
     int strict;
+    double diag;      /* L1 diagonal of the exact box */
 } enode_t;
+
+/* relative slack of the screen-space test under FP32 (the product and the comparison round; the
+ * entry distance and the box extents carry the box error model's eps and far scale) */
+static const double ORC_SS_MARGIN = 1e-5;
 
 static void grow_box(v3 *lo, v3 *hi, double eps, int deflate)
 {
@@ -430,8 +452,8 @@ static void grow_box(v3 *lo, v3 *hi, double eps, int deflate)
 
 static const double ORC_FAR_SCALE = 1.0 + 1e-6;
 
-static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double bound, double eps, leaf_cb cb,
-                            void *ctx)
+static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spread, double bound, double eps,
+                            leaf_cb cb, void *ctx)
 {
     enode_t stack[2 * ORC_MAX_L + 4];
     int sp = 0;
@@ -451,11 +473,25 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double boun
     hi = P->hi;
     grow_box(&lo, &hi, eps, 1);
     root->strict = slab(r, lo, hi, r->tmin, r->tmax, &root->s0, &root->s1);
+    root->diag = box_diag_l1(P->lo, P->hi);
     while (sp > 0) {
         enode_t N = stack[--sp];
         if (N.level == 2 * L) {
             cb(ctx, P->id, leaf_cell(N.pu, N.pv, L), N.l0, N.strict, N.s0);
             continue;
+        }
+        if (spread > 0.0 && N.level > 0) {
+            /* screen-space test under the error model: certainly a leaf, certainly split, or either (then
+             * the node is a possible, not a certain, leaf and its subtree stays possible too) */
+            const double ta = N.strict ? fmin(N.l0, N.s0) : N.l0, tb = N.strict ? fmax(N.l0, N.s0) : N.l0;
+            const double thr_lo = 0.5 * spread * ta * (1.0 - ORC_SS_MARGIN);
+            const double thr_hi = 0.5 * spread * tb * (1.0 + ORC_SS_MARGIN);
+            const double dlo = fmax(0.0, N.diag - 6.0 * eps), dhi = N.diag + 6.0 * eps;
+            if (dhi < thr_lo) {
+                cb(ctx, P->id, leaf_cell(N.pu, N.pv, L), N.l0, N.strict, N.s0);
+                continue;
+            }
+            if (!(dlo >= thr_hi)) cb(ctx, P->id, leaf_cell(N.pu, N.pv, L), N.l0, 0, N.s0);
         }
         int axis = N.level & 1;
         v3 q[16], d;
@@ -490,6 +526,7 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double boun
             C->pv = N.pv + (axis == 1 && s == 1 ? half : 0);
             C->l0 = c0;
             C->l1 = c1;
+            C->diag = box_diag_l1(blo, bhi);
             C->strict = 0;
             if (N.strict) {
                 v3 slo = blo, shi = bhi;
@@ -504,13 +541,13 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double boun
  * Brute force definition for tiny inputs: every leaf whose whole ancestor chain has a non-empty
  * interval is a candidate; the answer is the smallest key.  No pruning, no ordering.
  * ---------------------------------------------------------------------------------------------- */
-static void brute_rec(const patch_t *P, const ray_t *r, int L, const v3 q_in[16], int level, uint64_t pu,
-                      uint64_t pv, double t0, double t1, best_t *best)
+static void brute_rec(const patch_t *P, const ray_t *r, int L, double spread, const v3 q_in[16], int level,
+                      uint64_t pu, uint64_t pv, double t0, double t1, double diag, best_t *best)
 {
-    if (level == 2 * L) {
+    if (level == 2 * L || screen_leaf(spread, level, diag, t0)) {
         uint64_t cell = leaf_cell(pu, pv, L);
         if (t0 <= r->tmax && key_less(t0, P->id, cell, best)) {
-            best->t = t0; best->pid = P->id; best->cell = cell; best->hit = 1;
+            best->t = t0; best->pid = P->id; best->cell = cell; best->hit = 1; best->level = level;
         }
         return;
     }
@@ -534,8 +571,8 @@ static void brute_rec(const patch_t *P, const ray_t *r, int L, const v3 q_in[16]
         hi = add(hi, d);
         double a, b;
         if (!slab(r, lo, hi, t0, t1, &a, &b)) continue;
-        brute_rec(P, r, L, H[s], level + 1, pu + (axis == 0 && s ? half : 0), pv + (axis == 1 && s ? half : 0),
-                  a, b, best);
+        brute_rec(P, r, L, spread, H[s], level + 1, pu + (axis == 0 && s ? half : 0),
+                  pv + (axis == 1 && s ? half : 0), a, b, box_diag_l1(lo, hi), best);
     }
 }
 
@@ -619,8 +656,8 @@ static void scene_free(scene_t *S)
 }
 
 /* closest hit over the scene (mode 0), or leaf enumeration below a fixed bound (mode 1) */
-static void trace(const scene_t *S, const ray_t *r, int L, best_t *best, stats_t *st, int mode, double bound,
-                  leaf_cb cb, void *ctx, double eps)
+static void trace(const scene_t *S, const ray_t *r, int L, double spread, best_t *best, stats_t *st, int mode,
+                  double bound, leaf_cb cb, void *ctx, double eps)
 {
     if (S->nnodes == 0) return;
     int stack[256];
@@ -636,7 +673,7 @@ static void trace(const scene_t *S, const ray_t *r, int L, best_t *best, stats_t
         if (!slab(r, lo, hi, r->tmin, r->tmax, &t0, &t1) || t0 > lim) continue;
         if (nd->left < 0) {
             for (int i = 0; i < nd->count; ++i)
-                intersect_patch(&S->P[S->order[nd->first + i]], r, L, best, st, mode, bound, cb, ctx, eps);
+                intersect_patch(&S->P[S->order[nd->first + i]], r, L, spread, best, st, mode, bound, cb, ctx, eps);
             continue;
         }
         stack[sp++] = nd->right;
@@ -703,25 +740,25 @@ static double min_strict(const leaf_list *l)
     return R;
 }
 
-static uint8_t fp32_flags(const scene_t *S, const ray_t *r, int L, const best_t *b, double rel_t, double eps,
-                          double *t2)
+static uint8_t fp32_flags(const scene_t *S, const ray_t *r, int L, double spread, const best_t *b, double rel_t,
+                          double eps, double *t2)
 {
     leaf_list l = {NULL, 0, 0};
     best_t dummy = {0, 0, 0, 0};
     uint8_t flags = 0;
     *t2 = INFINITY;
     if (!b->hit) {
-        trace(S, r, L, &dummy, NULL, 1, r->tmax, list_cb, &l, eps);
+        trace(S, r, L, spread, &dummy, NULL, 1, r->tmax, list_cb, &l, eps);
         if (l.n) flags |= 4;
         free(l.v);
         return flags;
     }
     const double B = b->t + fabs(b->t) * rel_t;
-    trace(S, r, L, &dummy, NULL, 1, B, list_cb, &l, eps);
+    trace(S, r, L, spread, &dummy, NULL, 1, B, list_cb, &l, eps);
     double R = min_strict(&l);
     if (R > B) {
         leaf_list all = {NULL, 0, 0};
-        trace(S, r, L, &dummy, NULL, 1, r->tmax, list_cb, &all, eps);
+        trace(S, r, L, spread, &dummy, NULL, 1, r->tmax, list_cb, &all, eps);
         double Ra = min_strict(&all);
         flags |= isinf(Ra) ? 4 : 8;
         free(all.v);
@@ -773,6 +810,8 @@ typedef struct {
     uint8_t *flag_out;
     double *t2_out;
     uint64_t *stats_out;   /* per ray: bvh_nodes, expand_bez, expand_greg, leaves, pops */
+    double spread;         /* screen-space termination (0: fixed depth) */
+    uint8_t *level_out;    /* per ray: tree level of the recorded leaf */
     uint32_t next;
     pthread_mutex_t mu;
 } job_t;
@@ -785,12 +824,14 @@ static void run_one(job_t *J, uint32_t i)
     stats_t st = {0, 0, 0, 0, 0};
     int valid = !(isnan(r.o.x) || isnan(r.o.y) || isnan(r.o.z) || isnan(r.d.x) || isnan(r.d.y) || isnan(r.d.z) ||
                   isnan(r.tmin) || isnan(r.tmax) || r.tmin > r.tmax);
-    if (valid) trace(J->S, &r, J->L, &b, &st, 0, 0.0, NULL, NULL, 0.0);
+    if (valid) trace(J->S, &r, J->L, J->spread, &b, &st, 0, 0.0, NULL, NULL, 0.0);
     double cells = ldexp(1.0, J->L);
     if (b.hit) {
+        /* u, v: centre of the leaf's domain (a cell at level 2L, a larger block for a screen-space leaf) */
+        const int su = (b.level + 1) / 2, sv = b.level / 2;
         J->t_out[i] = b.t;
-        J->u_out[i] = (float)(((double)(b.cell & ((1ull << J->L) - 1)) + 0.5) / cells);
-        J->v_out[i] = (float)(((double)(b.cell >> J->L) + 0.5) / cells);
+        J->u_out[i] = (float)((double)(b.cell & ((1ull << J->L) - 1)) / cells + ldexp(0.5, -su));
+        J->v_out[i] = (float)((double)(b.cell >> J->L) / cells + ldexp(0.5, -sv));
         J->pid_out[i] = b.pid;
         J->cell_out[i] = b.cell;
     } else {
@@ -800,6 +841,7 @@ static void run_one(job_t *J, uint32_t i)
         J->pid_out[i] = 0xFFFFFFFFu;
         J->cell_out[i] = ~0ull;
     }
+    if (J->level_out) J->level_out[i] = (uint8_t)(b.hit ? b.level : 0);
     if (J->stats_out) {
         uint64_t *s = J->stats_out + 5 * (size_t)i;
         s[0] = st.bvh_nodes; s[1] = st.expand_bez; s[2] = st.expand_greg; s[3] = st.leaves; s[4] = st.pops;
@@ -810,7 +852,7 @@ static void run_one(job_t *J, uint32_t i)
         return;
     }
     double t2 = INFINITY;
-    uint8_t flags = fp32_flags(J->S, &r, J->L, &b, J->rel_t, J->eps, &t2);
+    uint8_t flags = fp32_flags(J->S, &r, J->L, J->spread, &b, J->rel_t, J->eps, &t2);
     if (J->flags_mode == 2) {
         v3 e1, e2;
         ortho_basis(r.d, &e1, &e2);
@@ -819,7 +861,7 @@ static void run_one(job_t *J, uint32_t i)
             v3 off = scl(k < 2 ? e1 : e2, (k & 1) ? -J->perturb : J->perturb);
             rp.o = add(r.o, off);
             best_t bp = {rp.tmax, 0xFFFFFFFFu, ~0ull, 0};
-            trace(J->S, &rp, J->L, &bp, NULL, 0, 0.0, NULL, NULL, 0.0);
+            trace(J->S, &rp, J->L, J->spread, &bp, NULL, 0, 0.0, NULL, NULL, 0.0);
             if (bp.hit != b.hit) flags |= 16;
         }
     }
@@ -857,7 +899,8 @@ int orc_intersect(const float *x, const float *y, const float *z, const uint8_t 
                   const float *ox, const float *oy, const float *oz, const float *dx, const float *dy,
                   const float *dz, const float *tmin, const float *tmax, uint32_t n_rays, int L, int n_threads,
                   int flags_mode, double rel_t, double eps, double perturb, double *t_out, float *u_out, float *v_out,
-                  uint32_t *pid_out, uint64_t *cell_out, uint8_t *flag_out, double *t2_out, uint64_t *stats_out)
+                  uint32_t *pid_out, uint64_t *cell_out, uint8_t *flag_out, double *t2_out, uint64_t *stats_out,
+                  double spread, uint8_t *level_out)
 {
     if (L < 1 || L > ORC_MAX_L) return -1;
     scene_t S;
@@ -870,6 +913,7 @@ int orc_intersect(const float *x, const float *y, const float *z, const uint8_t 
     J.n_rays = n_rays; J.L = L; J.flags_mode = flags_mode; J.rel_t = rel_t; J.eps = eps; J.perturb = perturb;
     J.t_out = t_out; J.u_out = u_out; J.v_out = v_out; J.pid_out = pid_out; J.cell_out = cell_out;
     J.flag_out = flag_out; J.t2_out = t2_out; J.stats_out = stats_out;
+    J.spread = spread; J.level_out = level_out;
     pthread_mutex_init(&J.mu, NULL);
     if (n_threads <= 0) n_threads = orc_num_cores();
     if (n_threads > 256) n_threads = 256;
@@ -905,7 +949,7 @@ static void load_ray(ray_t *r, const double *r8)
 /* Single (ray, patch) query.  g60: 20 points xyz-interleaved; r8: ox oy oz dx dy dz tmin tmax.
  * brute != 0 uses the all-leaves definition.  Returns 1 on hit with *t and *cell. */
 int orc_intersect_patch(const double *g60, int greg, const double *r8, int L, int brute, double *t, uint64_t *cell,
-                        uint64_t *stats5)
+                        uint64_t *stats5, double spread, int *level)
 {
     if (L < 1 || L > ORC_MAX_L) return -1;
     patch_t P;
@@ -916,10 +960,12 @@ int orc_intersect_patch(const double *g60, int greg, const double *r8, int L, in
     stats_t st = {0, 0, 0, 0, 0};
     if (brute) {
         double t0, t1;
-        if (slab(&r, P.lo, P.hi, r.tmin, r.tmax, &t0, &t1)) brute_rec(&P, &r, L, P.g, 0, 0, 0, t0, t1, &b);
+        if (slab(&r, P.lo, P.hi, r.tmin, r.tmax, &t0, &t1))
+            brute_rec(&P, &r, L, spread, P.g, 0, 0, 0, t0, t1, box_diag_l1(P.lo, P.hi), &b);
     } else {
-        intersect_patch(&P, &r, L, &b, &st, 0, 0.0, NULL, NULL, 0.0);
+        intersect_patch(&P, &r, L, spread, &b, &st, 0, 0.0, NULL, NULL, 0.0);
     }
+    if (level) *level = b.hit ? b.level : -1;
     if (stats5) { stats5[0] = st.bvh_nodes; stats5[1] = st.expand_bez; stats5[2] = st.expand_greg; stats5[3] = st.leaves; stats5[4] = st.pops; }
     *t = b.hit ? b.t : INFINITY;
     *cell = b.hit ? b.cell : ~0ull;
