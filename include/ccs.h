@@ -59,8 +59,9 @@ typedef struct {
 } ccs_hits;
 
 /* Launch and method options.  Zero-initialised fields take the defaults given in brackets (except
- * cache_slots, whose 0 is meaningful: pass CCS_CACHE_DEFAULT for the default).  None of them changes
- * the answer: hits are bit-identical for every launch configuration. */
+ * cache_slots, whose 0 is meaningful: pass CCS_CACHE_DEFAULT for the default).  Apart from leaf_depth and
+ * pixel_spread, which define the hierarchy, none of them changes the answer: hits are bit-identical for
+ * every launch configuration. */
 typedef struct {
     uint32_t leaf_depth;      /* L, splits per axis of the (u,v) domain, 1..15 [8] */
     uint32_t block_threads;   /* threads per block, multiple of 32, 32..1024 [128] */
@@ -84,6 +85,13 @@ typedef struct {
                                  warp; refill and vote then count rays, not lanes.  The trace export and
                                  learned entry points use 1 [1] */
     uint32_t iter_cap;        /* per-ray cap on traversal iterations [1 << 22] */
+    float pixel_spread;       /* ccs_intersect / ccs_intersect_host: screen-space termination (Sec. 3.3).
+                                 0: fixed depth (every leaf at level 2L).  > 0: the rays' angular size of
+                                 one pixel in radians (pinhole camera: 2 tan(fov/2) / height); a node made
+                                 by a split whose box has an L1 diagonal below pixel_spread / 2 times its
+                                 entry distance is a leaf, reported with u, v at its domain's centre and
+                                 the cell index of its lowest leaf cell.  Changes the answer (it is a
+                                 method parameter, not a launch option); one lane per ray.  [0] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
 } ccs_trace_opts;

@@ -50,6 +50,7 @@ class ccs_trace_opts(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_uint32), ("refill", ctypes.c_uint32), ("chunk", ctypes.c_uint32),
                 ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("min_blocks", ctypes.c_uint32),
                 ("vote", ctypes.c_uint32), ("lanes_per_ray", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
+                ("pixel_spread", ctypes.c_float),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
 
 
@@ -185,7 +186,7 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
-              counters=None) -> ccs_trace_opts:
+              counters=None, pixel_spread=0.0) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -198,6 +199,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.lanes_per_ray = lanes_per_ray
     o.cache_slots = cache_slots
     o.iter_cap = iter_cap
+    o.pixel_spread = pixel_spread
     o.flags = CCS_TRACE_COUNT if counters is not None else 0
     o.counters = _ptr(counters) if counters is not None else None
     return o

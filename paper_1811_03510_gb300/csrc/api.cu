@@ -70,6 +70,8 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.min_blocks = o ? o->min_blocks : 0;
     c.vote = o ? o->vote : 0;
     c.lanes_per_ray = o && o->lanes_per_ray ? o->lanes_per_ray : 1;
+    c.pixel_spread = o ? o->pixel_spread : 0.0f;
+    c.mc.spread = c.pixel_spread;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
@@ -84,6 +86,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.min_blocks == 0 || c.min_blocks == 4, "min_blocks must be 0 or 4");
     CCS_ARG(c.vote <= 32, "vote must be in 0..32");
     CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
+    CCS_ARG(c.pixel_spread >= 0.0f && c.pixel_spread < 1.0f, "pixel_spread must be in [0, 1) radians per pixel");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     return CCS_OK;
 }
@@ -255,6 +258,7 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     }
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    if (cfg.pixel_spread > 0.0f) cfg.mode = 4;   // screen-space termination (one lane per ray)
     DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};

@@ -38,13 +38,15 @@ struct ModeCtx {
     uint32_t *ex_count;
     uint32_t ex_capacity;
     uint8_t *occluded;   // any-hit mode: one byte per ray
+    float spread;        // screen-space termination: radians per pixel of the ray (0: fixed depth)
 };
 
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
         lanes_per_ray, iter_cap, flags;
+    float pixel_spread;
     unsigned long long *counters;
-    int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit
+    int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit, 4 screen-space
     ModeCtx mc{};
     const MlpWeights *mlp = nullptr;
     float min_conf = 0.0f;

@@ -172,8 +172,14 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
                     if (s.best.pid != kMissId) {
                         const uint32_t cu = s.best.cell & ((1u << L) - 1u), cv = s.best.cell >> L;
                         hh.t[i] = s.best.t;
-                        hh.u[i] = ((float)cu + 0.5f) * cellw;
-                        hh.v[i] = ((float)cv + 0.5f) * cellw;
+                        if (MODE == kModeScreen) {   // centre of the leaf node's domain (exact powers of two)
+                            const int su = (s.best.lvl + 1) >> 1, sv = s.best.lvl >> 1;
+                            hh.u[i] = (float)cu * cellw + __int_as_float((126 - su) << 23);
+                            hh.v[i] = (float)cv * cellw + __int_as_float((126 - sv) << 23);
+                        } else {
+                            hh.u[i] = ((float)cu + 0.5f) * cellw;
+                            hh.v[i] = ((float)cv + 0.5f) * cellw;
+                        }
                         hh.pid[i] = s.best.pid;
                     } else {
                         hh.t[i] = __int_as_float(0x7f800000);
@@ -293,19 +299,26 @@ static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queu
     if (e != cudaSuccess) return e;
     const bool stats = (cfg.flags & CCS_TRACE_COUNT) != 0;
     if constexpr (std::is_same<Src, SingleSource>::value) {
-    if (cfg.mode == kModeExport)
-        return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s)
-                                    : launch_one<false, 2, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s);
-    if (cfg.mode == kModeAnyHit) {
-        if (stats)
-            return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
-                                        : launch_one<true, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
-        return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
-                                    : launch_one<false, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
-    }
-    if (cfg.mode == kModeLearned)   // the network's shared memory leaves no room for the sibling cache
-        return stats ? launch_one<true, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s)
-                     : launch_one<false, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s);
+        if (cfg.mode == kModeExport)
+            return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s)
+                                        : launch_one<false, 2, 3, Src, kModeExport>(src, cfg, queue, status, num_sms, s);
+        if (cfg.mode == kModeScreen) {
+            if (stats)
+                return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModeScreen>(src, cfg, queue, status, num_sms, s)
+                                            : launch_one<true, 2, 3, Src, kModeScreen>(src, cfg, queue, status, num_sms, s);
+            return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeScreen>(src, cfg, queue, status, num_sms, s)
+                                        : launch_one<false, 2, 3, Src, kModeScreen>(src, cfg, queue, status, num_sms, s);
+        }
+        if (cfg.mode == kModeAnyHit) {
+            if (stats)
+                return cfg.cache_slots == 0 ? launch_one<true, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
+                                            : launch_one<true, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
+            return cfg.cache_slots == 0 ? launch_one<false, 0, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s)
+                                        : launch_one<false, 2, 3, Src, kModeAnyHit>(src, cfg, queue, status, num_sms, s);
+        }
+        if (cfg.mode == kModeLearned)   // the network's shared memory leaves no room for the sibling cache
+            return stats ? launch_one<true, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s)
+                         : launch_one<false, 0, 3, Src, kModeLearned>(src, cfg, queue, status, num_sms, s);
     }
     if (cfg.lanes_per_ray == 3) {   // groups of three lanes per ray (plain traversal)
         if (stats)

@@ -344,6 +344,7 @@ CCS_DEV void gregory_node(const float4 *__restrict__ rec, float u0, float u1, fl
 struct Best {
     float t;
     uint32_t pid, cell;
+    int lvl;   // tree level of the recorded leaf (screen-space termination)
 };
 
 CCS_DEV bool key_less(float t, uint32_t pid, uint32_t cell, const Best &b)
@@ -388,6 +389,7 @@ CCS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "me
 struct StepOut {
     bool hitL, hitR, goR;
     float l0, l1, r0, r1;
+    float dL, dR;   // L1 diagonals of the child boxes (the lane's components; screen-space termination)
 };
 
 template <int K, int NC>
@@ -424,6 +426,13 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
         rmax[c] = __fadd_rn(fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]), d[c]);
     }
     StepOut o;
+    o.dL = 0.0f;
+    o.dR = 0.0f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        o.dL = __fadd_rn(o.dL, __fsub_rn(lmax[c], lmin[c]));
+        o.dR = __fadd_rn(o.dR, __fsub_rn(rmax[c], rmin[c]));
+    }
     slab<NC>(r, lmin, lmax, c0, c1, G, o.l0, o.l1);
     slab<NC>(r, rmin, rmax, c0, c1, G, o.r0, o.r1);
     o.hitL = allowL && o.l0 <= o.l1 && o.l0 <= tb;
@@ -526,11 +535,14 @@ struct Lane {
     int phase;                      // learned proposal: kPhase*
     uint32_t prop;                  // path bits (levels 0..5) of the proposed depth-3 cell
     float rc0, rc1;                 // root interval of the current pair
+    bool sleaf;                     // screen-space termination: the current node is a leaf
+    uint32_t sleaf_trail;           // bit l: the pending sibling at level l+1 is a screen-space leaf
 };
 
 // Kernel modes: plain traversal, trace export (features + depth-3 cell of each pair's best leaf),
-// traversal with the learned proposal, and any hit (the ray ends at the first leaf it records).
-constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2, kModeAnyHit = 3;
+// traversal with the learned proposal, any hit (the ray ends at the first leaf it records), and plain
+// traversal with screen-space termination (Sec. 3.3).
+constexpr int kModePlain = 0, kModeExport = 1, kModeLearned = 2, kModeAnyHit = 3, kModeScreen = 4;
 // Phases of a pair with the learned proposal: waiting for the network, descending straight to the
 // proposed depth-3 cell, searching that cell's subtree, then the full search with the cell skipped.
 constexpr int kPhaseNormal = 0, kPhasePropose = 1, kPhaseDirected = 2, kPhaseSubtree = 3;
@@ -616,7 +628,11 @@ CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, ui
     s.c0 = c0;
     s.c1 = c1;
     s.ctop = s.cvalid = 0;
-    if (MODE != kModePlain) {
+    if (MODE == kModeScreen) {
+        s.sleaf = false;
+        s.sleaf_trail = 0u;
+    }
+    if (MODE != kModePlain && MODE != kModeScreen) {
         s.rc0 = c0;
         s.rc1 = c1;
     }
@@ -693,12 +709,22 @@ CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const De
         const float2 sb = scr.sib[l * scr.stride];
         if (sb.x > s.best.t) {
             if (STATS) cnt.v[6]++;
+            if (MODE == kModeScreen) s.sleaf_trail &= ~bit;
             continue;
         }
         s.path = (s.path & (bit - 1u)) | (~s.path & bit);
         s.c0 = sb.x;
         s.c1 = sb.y;
         if (STATS) cnt.v[4]++;
+        if (MODE == kModeScreen) {
+            s.sleaf = (s.sleaf_trail & bit) != 0u;
+            s.sleaf_trail &= ~bit;
+            if (s.sleaf) {   // a screen-space leaf: recorded by the next step, no points needed
+                s.level = l + 1;
+                s.gpend = false;
+                return;
+            }
+        }
         if (s.greg) {
             s.level = l + 1;
             s.gpend = s.level < 2 * L;   // a leaf needs no bound
@@ -742,16 +768,18 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     }
     const bool redesc = s.rd_target >= 0;
     const bool directed = MODE == kModeLearned && s.phase == kPhaseDirected;
-    if (!redesc && s.level == 2 * L) {
+    if (!redesc && (s.level == 2 * L || (MODE == kModeScreen && s.sleaf))) {
         uint32_t cu, cv;
-        path_cells(s.path, L, cu, cv);
+        path_cells(s.path, L, cu, cv);   // lowest leaf cell of the node (path bits below its level are 0)
         const uint32_t cell = (cv << L) | cu;
         if (STATS) cnt.v[3]++;
         if (key_less(s.c0, s.pid, cell, s.best)) {
             s.best.t = s.c0;
             s.best.pid = s.pid;
             s.best.cell = cell;
+            if (MODE == kModeScreen) s.best.lvl = s.level;
         }
+        if (MODE == kModeScreen) s.sleaf = false;
         backtrack<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
         return kStepLeaf;
     }
@@ -784,6 +812,11 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     }
     if (o.hitL || o.hitR) {
         const uint32_t bit = 1u << s.level;
+        if (MODE == kModeScreen) {   // Sec. 3.3: a box under half a pixel at its entry distance is a leaf
+            const float h = 0.5f * mc.spread;
+            s.sleaf = (o.goR ? o.dR : o.dL) < h * (o.goR ? o.r0 : o.l0);
+            if (o.hitL && o.hitR && (o.goR ? o.dL : o.dR) < h * (o.goR ? o.l0 : o.r0)) s.sleaf_trail |= bit;
+        }
         if (o.hitL && o.hitR) {
             s.trail |= bit;
             scr.sib[s.level * scr.stride] = o.goR ? make_float2(o.l0, o.l1) : make_float2(o.r0, o.r1);
@@ -797,7 +830,7 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         s.c0 = o.goR ? o.r0 : o.l0;
         s.c1 = o.goR ? o.r1 : o.l1;
         ++s.level;
-        s.gpend = s.greg && s.level < 2 * L;
+        s.gpend = s.greg && s.level < 2 * L && !(MODE == kModeScreen && s.sleaf);
         return kStepSplit;
     }
     backtrack<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
