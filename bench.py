@@ -343,6 +343,38 @@ def run_shadow(args, dev, stream, flush):
     return out
 
 
+def run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p):
+    """Primary rays with screen-space termination (Sec. 3.3) at the camera's pixel size, against the fixed
+    leaf depth of the benchmark, on the same rays and launch options."""
+    import torch
+    from paper_1811_03510_gb300 import ccs
+    spread = 2.0 * np.tan(np.radians(30.0)) / args.height   # 60 degree vertical field of view
+    base = ccs.opts_dict(opts_p)
+    out = {"pixel_spread": spread}
+    hits = ccs.alloc_hits(n_prim, dev)
+    for name, sp in (("fixed_depth", 0.0), ("screen_space", spread)):
+        opts = ccs.make_opts(**base, pixel_spread=sp)
+        for _ in range(max(3, args.warmup)):
+            ccs.ccs_intersect(scene.handle, prim, n_prim, hits, opts, stream)
+        tot = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ccs.ccs_intersect(scene.handle, prim, n_prim, hits, opts, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        ccs.ccs_intersect(scene.handle, prim, n_prim, hits, ccs.make_opts(**base, pixel_spread=sp, counters=c), stream)
+        torch.cuda.synchronize()
+        v = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
+        out[name + "_mrays_s"] = n_prim * args.steps / tot / 1e3
+        out[name + "_splits"] = v["bezier_splits"] + v["gregory_splits"]
+    out["speedup"] = out["screen_space_mrays_s"] / out["fixed_depth_mrays_s"]
+    return out
+
+
 def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     """Train the proposal on traces of scenes with other seeds (GPU export + GPU training), then time the
     learned traversal against the plain one on this workload's primary and diffuse batches."""
@@ -617,6 +649,7 @@ def main():
         b = run_batched(args, dev, stream, world)
         res["batched"] = b
         res["shadow"] = run_shadow(args, dev, stream, flush)
+        res["screen_space"] = run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
