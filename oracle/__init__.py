@@ -55,7 +55,8 @@ def num_cores() -> int:
 
 
 def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | int = False, rel_t: float = 1e-4,
-              eps: float = 5e-7, perturb: float = 1e-4, stats: bool = False, spread: float = 0.0) -> dict:
+              eps: float = 5e-7, perturb: float = 1e-4, stats: bool = False, spread: float = 0.0,
+              local: bool = False) -> dict:
     """Closest hit of every ray.  P: [n, 20, 3] float32 patch points, types [n] uint8, rays_soa: eight
     float32 arrays (ox, oy, oz, dx, dy, dz, tmin, tmax).  Returns t (f64, inf on miss), u, v (f32 cell
     centre), pid (u32, 0xFFFFFFFF on miss), cell (u64, v_cell * 2^L + u_cell); with flags 'flags' and 't2'
@@ -66,7 +67,9 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | in
     spread > 0: screen-space termination (Sec. 3.3): a node made by a split is a leaf once the L1 length of
     its box diagonal is below spread / 2 times its entry distance (spread = radians per pixel of the ray);
     'level' gives the recorded leaf's tree level (2L at full depth), u, v the centre of its domain, and
-    the flags also cover a termination test within FP32 error of its threshold."""
+    the flags also cover a termination test within FP32 error of its threshold.
+    local=True: below the root, boxes are taken in each patch's local frame (Sec. 3.4; see local_frame);
+    the root interval is still the world box's."""
     P = np.ascontiguousarray(P, dtype=np.float32)
     n = P.shape[0]
     x = np.ascontiguousarray(P[..., 0]).reshape(-1)
@@ -87,7 +90,7 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | in
         ctypes.c_int(int(flags)), ctypes.c_double(rel_t), ctypes.c_double(eps), ctypes.c_double(perturb),
         _p(out["t"], _D), _p(out["u"], _F), _p(out["v"], _F), _p(out["pid"], _U32), _p(out["cell"], _U64),
         _p(fl, _U8) if flags else None, _p(t2, _D) if flags else None, _p(st, _U64) if stats else None,
-        ctypes.c_double(spread), _p(level, _U8))
+        ctypes.c_double(spread), _p(level, _U8), ctypes.c_int(int(local)))
     if nt < 0:
         raise ValueError("oracle rejected arguments (leaf depth out of range?)")
     out["threads"] = nt
@@ -100,19 +103,20 @@ def intersect(P, types, rays_soa, L: int = 8, threads: int = 0, flags: bool | in
     return out
 
 
-def occluded(P, types, rays_soa, L: int = 8, flags: bool | int = False) -> dict:
+def occluded(P, types, rays_soa, L: int = 8, flags: bool | int = False, local: bool = False) -> dict:
     """Any-hit query of shadow rays (Sec. 4): a ray is occluded iff some leaf box of some patch has a
     non-empty nested interval inside [tmin, tmax] (the leaf condition of Algorithm 3), which is exactly when
     the closest-hit answer exists.  Returns occluded (u8) and, with flags, the FP32 error-model flags of the
     closest-hit query (bit 2: hit/miss may flip)."""
-    o = intersect(P, types, rays_soa, L=L, flags=flags)
+    o = intersect(P, types, rays_soa, L=L, flags=flags, local=local)
     out = {"occluded": (o["pid"] != 0xFFFFFFFF).astype(np.uint8)}
     if flags:
         out["flags"] = o["flags"]
     return out
 
 
-def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False, spread: float = 0.0, with_level: bool = False):
+def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False, spread: float = 0.0, with_level: bool = False,
+                    local: bool = False):
     """Single (ray, patch) query; g [20, 3] f64, ray8 = (ox, oy, oz, dx, dy, dz, tmin, tmax).
     Returns (hit, t, cell, stats5), and the leaf level with with_level (spread: as in intersect)."""
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
@@ -123,12 +127,21 @@ def intersect_patch(g, greg: bool, ray8, L: int, brute: bool = False, spread: fl
     lv = ctypes.c_int()
     h = lib().orc_intersect_patch(_p(g, _D), ctypes.c_int(int(greg)), _p(r, _D), ctypes.c_int(L),
                                   ctypes.c_int(int(brute)), ctypes.byref(t), ctypes.byref(c), _p(st, _U64),
-                                  ctypes.c_double(spread), ctypes.byref(lv))
+                                  ctypes.c_double(spread), ctypes.byref(lv), ctypes.c_int(int(local)))
     if h < 0:
         raise ValueError("bad leaf depth")
     if with_level:
         return bool(h), t.value, c.value, st, lv.value
     return bool(h), t.value, c.value, st
+
+
+def local_frame(g20):
+    """Rows (x, y, z) of a patch's local frame (Sec. 3.4): z along the normal of the corner quad (the
+    cross product of its diagonals), x along its u edge made orthogonal to z, y = z x x."""
+    g = np.ascontiguousarray(g20, dtype=np.float64).reshape(-1)
+    out = np.zeros(9)
+    lib().orc_local_frame(_p(g, _D), _p(out, _D))
+    return out.reshape(3, 3)
 
 
 def bezier_eval(p16, u: float, v: float):

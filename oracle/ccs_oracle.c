@@ -265,7 +265,54 @@ typedef struct {
     int greg;
     uint32_t id;
     v3 lo, hi;        /* root box: AABB of the 16 (Bezier) or 20 (Gregory) points */
+    int local;        /* boxes below the root are taken in the patch's own frame (Sec. 3.4) */
+    v3 R[3];          /* rows of that frame */
+    v3 gl[20];        /* the control points in it: R p */
 } patch_t;
+
+static double dot3(v3 a, v3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static v3 cross3(v3 a, v3 b) { return v3make(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x); }
+
+/* Local frame of a patch (Sec. 3.4 intersects patches in local frames to shrink the boxes' overlap):
+ * z along the normal of the corner quad (the cross product of its diagonals p33 - p00 and p03 - p30),
+ * x along its u edge p30 - p00 made orthogonal to z, y = z x x.  The world frame where that is
+ * degenerate.  Rows of R; a point p has local coordinates R p. */
+static void local_frame(const v3 g[20], v3 R[3])
+{
+    R[0] = v3make(1, 0, 0);
+    R[1] = v3make(0, 1, 0);
+    R[2] = v3make(0, 0, 1);
+    v3 z = cross3(sub(g[15], g[0]), sub(g[12], g[3]));
+    const double nz = sqrt(dot3(z, z));
+    if (!(nz > 0.0)) return;
+    z = scl(z, 1.0 / nz);
+    const v3 e = sub(g[3], g[0]);
+    v3 x = sub(e, scl(z, dot3(e, z)));
+    const double nx = sqrt(dot3(x, x));
+    if (!(nx > 0.0)) return;
+    x = scl(x, 1.0 / nx);
+    R[0] = x;
+    R[1] = cross3(z, x);
+    R[2] = z;
+}
+
+static v3 rotate(const v3 R[3], v3 p) { return v3make(dot3(R[0], p), dot3(R[1], p), dot3(R[2], p)); }
+
+static void patch_set_frame(patch_t *P, int local)
+{
+    P->local = local;
+    if (local) local_frame(P->g, P->R);
+    else { P->R[0] = v3make(1, 0, 0); P->R[1] = v3make(0, 1, 0); P->R[2] = v3make(0, 0, 1); }
+    for (int k = 0; k < 20; ++k) P->gl[k] = local ? rotate(P->R, P->g[k]) : P->g[k];
+}
+
+/* the ray in the frame of the patch's boxes below the root */
+static ray_t local_ray(const patch_t *P, const ray_t *r)
+{
+    ray_t l = *r;
+    if (P->local) { l.o = rotate(P->R, r->o); l.d = rotate(P->R, r->d); }
+    return l;
+}
 
 typedef struct {
     double t;
@@ -341,10 +388,11 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spre
     int sp = 0;
     double lim = mode == 0 ? best->t : bound;
     double t0, t1;
-    if (!slab(r, P->lo, P->hi, r->tmin, r->tmax, &t0, &t1)) return;
+    if (!slab(r, P->lo, P->hi, r->tmin, r->tmax, &t0, &t1)) return;   /* the root box is the world one */
     if (t0 > lim) return;
+    const ray_t rl = local_ray(P, r);
     node_t *root = &stack[sp++];
-    memcpy(root->q, P->g, sizeof(root->q));
+    memcpy(root->q, P->gl, sizeof(root->q));
     root->level = 0;
     root->pu = root->pv = 0;
     root->t0 = t0;
@@ -374,7 +422,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spre
         if (P->greg) {
             double u0, u1, v0, v1;
             node_domain(N.level, N.pu, N.pv, &u0, &u1, &v0, &v1);
-            calcPointsAndD(P->g, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
+            calcPointsAndD(P->gl, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
             if (st) st->expand_greg++;
         } else {
             memcpy(q, N.q, sizeof(q));
@@ -390,7 +438,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spre
             for (int k = 1; k < 16; ++k) { lo = vmin(lo, H[s][k]); hi = vmax(hi, H[s][k]); }
             hi = add(hi, d);
             diag[s] = box_diag_l1(lo, hi);
-            hit[s] = slab(r, lo, hi, N.t0, N.t1, &c0[s], &c1[s]) && c0[s] <= lim;
+            hit[s] = slab(&rl, lo, hi, N.t0, N.t1, &c0[s], &c1[s]) && c0[s] <= lim;
         }
         int su = (N.level + 1) / 2, sv = N.level / 2;   /* splits already taken along u, v */
         uint64_t half = axis == 0 ? (1ull << (ORC_SCALE_BITS - su - 1)) : (1ull << (ORC_SCALE_BITS - sv - 1));
@@ -463,8 +511,14 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
     if (!slab(r, lo, hi, r->tmin, r->tmax, &a, &b)) return;
     b *= ORC_FAR_SCALE;
     if (a > bound || a > b) return;
+    /* below the root the boxes are compared with the ray in the patch frame: the FP32 transform of the
+     * ray adds an error that grows with the distance of the origin from the patch */
+    const ray_t rl = local_ray(P, r);
+    const v3 cen = scl(add(P->lo, P->hi), 0.5);
+    const v3 oc = sub(r->o, cen);
+    const double eps_in = P->local ? eps + 6e-7 * sqrt(dot3(oc, oc)) : eps;
     enode_t *root = &stack[sp++];
-    memcpy(root->q, P->g, sizeof(root->q));
+    memcpy(root->q, P->gl, sizeof(root->q));
     root->level = 0;
     root->pu = root->pv = 0;
     root->l0 = a;
@@ -486,7 +540,7 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
             const double ta = N.strict ? fmin(N.l0, N.s0) : N.l0, tb = N.strict ? fmax(N.l0, N.s0) : N.l0;
             const double thr_lo = 0.5 * spread * ta * (1.0 - ORC_SS_MARGIN);
             const double thr_hi = 0.5 * spread * tb * (1.0 + ORC_SS_MARGIN);
-            const double dlo = fmax(0.0, N.diag - 6.0 * eps), dhi = N.diag + 6.0 * eps;
+            const double dlo = fmax(0.0, N.diag - 6.0 * eps_in), dhi = N.diag + 6.0 * eps_in;
             if (dhi < thr_lo) {
                 cb(ctx, P->id, leaf_cell(N.pu, N.pv, L), N.l0, N.strict, N.s0);
                 continue;
@@ -498,7 +552,7 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
         if (P->greg) {
             double u0, u1, v0, v1;
             node_domain(N.level, N.pu, N.pv, &u0, &u1, &v0, &v1);
-            calcPointsAndD(P->g, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
+            calcPointsAndD(P->gl, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
         } else {
             memcpy(q, N.q, sizeof(q));
             d = v3make(0, 0, 0);
@@ -512,9 +566,9 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
             for (int k = 1; k < 16; ++k) { blo = vmin(blo, H[s][k]); bhi = vmax(bhi, H[s][k]); }
             bhi = add(bhi, d);
             v3 llo = blo, lhi = bhi;
-            grow_box(&llo, &lhi, eps, 0);
+            grow_box(&llo, &lhi, eps_in, 0);
             double c0, c1;
-            if (!slab(r, llo, lhi, -INFINITY, INFINITY, &c0, &c1)) continue;
+            if (!slab(&rl, llo, lhi, -INFINITY, INFINITY, &c0, &c1)) continue;
             c1 *= ORC_FAR_SCALE;
             c0 = fmax(c0, N.l0);
             c1 = fmin(c1, N.l1);
@@ -530,8 +584,8 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
             C->strict = 0;
             if (N.strict) {
                 v3 slo = blo, shi = bhi;
-                grow_box(&slo, &shi, eps, 1);
-                C->strict = slab(r, slo, shi, N.s0, N.s1, &C->s0, &C->s1);
+                grow_box(&slo, &shi, eps_in, 1);
+                C->strict = slab(&rl, slo, shi, N.s0, N.s1, &C->s0, &C->s1);
             }
         }
     }
@@ -553,10 +607,11 @@ static void brute_rec(const patch_t *P, const ray_t *r, int L, double spread, co
     }
     int axis = level & 1;
     v3 q[16], d;
+    const ray_t rl = local_ray(P, r);
     if (P->greg) {
         double u0, u1, v0, v1;
         node_domain(level, pu, pv, &u0, &u1, &v0, &v1);
-        calcPointsAndD(P->g, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
+        calcPointsAndD(P->gl, 1, u0, u1, v0, v1, q, &d, NULL, NULL);
     } else {
         memcpy(q, q_in, sizeof(q));
         d = v3make(0, 0, 0);
@@ -570,7 +625,7 @@ static void brute_rec(const patch_t *P, const ray_t *r, int L, double spread, co
         for (int k = 1; k < 16; ++k) { lo = vmin(lo, H[s][k]); hi = vmax(hi, H[s][k]); }
         hi = add(hi, d);
         double a, b;
-        if (!slab(r, lo, hi, t0, t1, &a, &b)) continue;
+        if (!slab(&rl, lo, hi, t0, t1, &a, &b)) continue;
         brute_rec(P, r, L, spread, H[s], level + 1, pu + (axis == 0 && s ? half : 0),
                   pv + (axis == 1 && s ? half : 0), a, b, box_diag_l1(lo, hi), best);
     }
@@ -627,7 +682,8 @@ static int bvh_build_rec(scene_t *S, int first, int count)
     return idx;
 }
 
-static void scene_init(scene_t *S, const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n)
+static void scene_init(scene_t *S, const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
+                       int local)
 {
     S->n = n;
     S->P = (patch_t *)malloc(sizeof(patch_t) * (n ? n : 1));
@@ -640,6 +696,7 @@ static void scene_init(scene_t *S, const float *x, const float *y, const float *
         int np = P->greg ? 20 : 16;
         P->lo = P->hi = P->g[0];
         for (int k = 1; k < np; ++k) { P->lo = vmin(P->lo, P->g[k]); P->hi = vmax(P->hi, P->g[k]); }
+        patch_set_frame(P, local);
     }
     S->nodes = (bnode_t *)malloc(sizeof(bnode_t) * (2 * (size_t)n + 2));
     S->order = (uint32_t *)malloc(sizeof(uint32_t) * (n ? n : 1));
@@ -900,11 +957,11 @@ int orc_intersect(const float *x, const float *y, const float *z, const uint8_t 
                   const float *dz, const float *tmin, const float *tmax, uint32_t n_rays, int L, int n_threads,
                   int flags_mode, double rel_t, double eps, double perturb, double *t_out, float *u_out, float *v_out,
                   uint32_t *pid_out, uint64_t *cell_out, uint8_t *flag_out, double *t2_out, uint64_t *stats_out,
-                  double spread, uint8_t *level_out)
+                  double spread, uint8_t *level_out, int local)
 {
     if (L < 1 || L > ORC_MAX_L) return -1;
     scene_t S;
-    scene_init(&S, x, y, z, types, n_patches);
+    scene_init(&S, x, y, z, types, n_patches, local);
     job_t J;
     memset(&J, 0, sizeof(J));
     J.S = &S;
@@ -928,7 +985,7 @@ int orc_intersect(const float *x, const float *y, const float *z, const uint8_t 
     return n_threads;
 }
 
-static void load_patch(patch_t *P, const double *g60, int greg)
+static void load_patch(patch_t *P, const double *g60, int greg, int local)
 {
     P->greg = greg;
     P->id = 0;
@@ -936,6 +993,7 @@ static void load_patch(patch_t *P, const double *g60, int greg)
     int np = greg ? 20 : 16;
     P->lo = P->hi = P->g[0];
     for (int k = 1; k < np; ++k) { P->lo = vmin(P->lo, P->g[k]); P->hi = vmax(P->hi, P->g[k]); }
+    patch_set_frame(P, local);
 }
 
 static void load_ray(ray_t *r, const double *r8)
@@ -949,11 +1007,11 @@ static void load_ray(ray_t *r, const double *r8)
 /* Single (ray, patch) query.  g60: 20 points xyz-interleaved; r8: ox oy oz dx dy dz tmin tmax.
  * brute != 0 uses the all-leaves definition.  Returns 1 on hit with *t and *cell. */
 int orc_intersect_patch(const double *g60, int greg, const double *r8, int L, int brute, double *t, uint64_t *cell,
-                        uint64_t *stats5, double spread, int *level)
+                        uint64_t *stats5, double spread, int *level, int local)
 {
     if (L < 1 || L > ORC_MAX_L) return -1;
     patch_t P;
-    load_patch(&P, g60, greg);
+    load_patch(&P, g60, greg, local);
     ray_t r;
     load_ray(&r, r8);
     best_t b = {r.tmax, 0xFFFFFFFFu, ~0ull, 0};
@@ -961,7 +1019,7 @@ int orc_intersect_patch(const double *g60, int greg, const double *r8, int L, in
     if (brute) {
         double t0, t1;
         if (slab(&r, P.lo, P.hi, r.tmin, r.tmax, &t0, &t1))
-            brute_rec(&P, &r, L, spread, P.g, 0, 0, 0, t0, t1, box_diag_l1(P.lo, P.hi), &b);
+            brute_rec(&P, &r, L, spread, P.gl, 0, 0, 0, t0, t1, box_diag_l1(P.lo, P.hi), &b);
     } else {
         intersect_patch(&P, &r, L, spread, &b, &st, 0, 0.0, NULL, NULL, 0.0);
     }
@@ -1074,4 +1132,13 @@ void orc_child_boxes(const double *g60, int greg, int level, uint64_t pu, uint64
         box12[6 * s + 0] = lo.x; box12[6 * s + 1] = lo.y; box12[6 * s + 2] = lo.z;
         box12[6 * s + 3] = hi.x; box12[6 * s + 4] = hi.y; box12[6 * s + 5] = hi.z;
     }
+}
+
+/* Rows of the local frame of a patch (Sec. 3.4), for tests. */
+void orc_local_frame(const double *g60, double *out9)
+{
+    v3 g[20], R[3];
+    for (int k = 0; k < 20; ++k) g[k] = v3make(g60[3 * k], g60[3 * k + 1], g60[3 * k + 2]);
+    local_frame(g, R);
+    for (int i = 0; i < 3; ++i) { out9[3 * i] = R[i].x; out9[3 * i + 1] = R[i].y; out9[3 * i + 2] = R[i].z; }
 }

@@ -1,0 +1,119 @@
+"""Local frames (Sec. 3.4) in the oracle: below the patch root, boxes are taken in each patch's own frame.
+Pinned to closed forms (the frame of a plane, the exact distance to a tilted flat patch), to brute force,
+and to watertightness at the shared boundaries of the closed cube-sphere."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_03510_gb300 import scenegen as sg
+
+MISS = 0xFFFFFFFF
+RNG = np.random.default_rng(2024)
+
+
+def rotation(axis, ang):
+    a = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+    return np.eye(3) + np.sin(ang) * K + (1 - np.cos(ang)) * K @ K
+
+
+def flat_square(a, Q=np.eye(3), c=np.zeros(3)):
+    """Degree-elevated affine patch: the square [-a/2, a/2]^2 of the plane z = 0 (u along x, v along y),
+    rotated by Q and moved to c."""
+    g = np.zeros((20, 3))
+    for j in range(4):
+        for i in range(4):
+            g[4 * j + i] = Q @ np.array([a * (i / 3 - 0.5), a * (j / 3 - 0.5), 0.0]) + c
+    g[16:20] = g[[5, 6, 9, 10]]
+    return g
+
+
+def test_frame_of_a_plane_is_its_tangent_frame():
+    Q = rotation([1.0, 2.0, 0.5], 0.7)
+    R = oracle.local_frame(flat_square(1.0, Q, np.array([0.3, -0.2, 1.0])))
+    # rows: u direction, v direction, normal of the plane (the columns of Q)
+    np.testing.assert_allclose(R, Q.T, atol=1e-12)
+    np.testing.assert_allclose(oracle.local_frame(flat_square(2.0)), np.eye(3), atol=1e-12)
+
+
+@pytest.mark.parametrize("L", [4, 8, 12])
+def test_tilted_flat_patch_is_hit_at_the_plane_distance(L):
+    """In its own frame a flat patch has boxes of zero thickness, so the leaf is entered exactly where the
+    ray meets the plane; in world axes the tilted leaf boxes are entered earlier."""
+    Q = rotation([1.0, 0.3, 0.0], np.pi / 4)
+    c = np.array([0.1, -0.2, 0.3])
+    g = flat_square(1.0, Q, c)
+    nrm = Q[:, 2]
+    for k in range(30):
+        x, y = RNG.uniform(-0.45, 0.45, 2)
+        target = Q @ np.array([x, y, 0.0]) + c
+        o = target + 3.0 * (nrm + 0.3 * RNG.normal(size=3))
+        d = target - o
+        ray = np.array([*o, *d, 0.0, np.inf])
+        t_plane = ((c - o) @ nrm) / (d @ nrm)
+        hit, t, _, _ = oracle.intersect_patch(g, False, ray, L, local=True)
+        assert hit and abs(t - t_plane) <= 1e-12 * abs(t_plane)
+        hw, tw, _, _ = oracle.intersect_patch(g, False, ray, L, local=False)
+        assert hw and tw < t_plane - 1e-9
+
+
+@pytest.mark.parametrize("greg", [False, True])
+@pytest.mark.parametrize("spread", [0.0, 3e-2])
+def test_pruned_search_equals_brute_force_in_local_frames(greg, spread):
+    s = sg.config_scene(1)
+    p = int(np.nonzero(s.types == (1 if greg else 0))[0][0])
+    g = s.P[p].astype(np.float64)
+    c = g.mean(0)
+    n_hit = 0
+    for k in range(120):
+        o = c + RNG.normal(size=3) * 1.5
+        f = oracle.patch_frame(g, greg, *RNG.uniform(0.02, 0.98, 2))[0]
+        d = f + 0.01 * RNG.normal(size=3) - o
+        ray = np.array([*o, *d, 0.0, np.inf])
+        a = oracle.intersect_patch(g, greg, ray, 4, spread=spread, with_level=True, local=True)
+        b = oracle.intersect_patch(g, greg, ray, 4, brute=True, spread=spread, with_level=True, local=True)
+        assert a[0] == b[0]
+        if a[0]:
+            n_hit += 1
+            assert a[1] == b[1] and a[2] == b[2] and a[4] == b[4], (k, a, b)
+    assert n_hit > 40
+
+
+def test_local_frames_keep_shared_boundaries_watertight():
+    """Rays through points on shared patch boundaries of the closed cube-sphere always hit in local
+    frames too (Sec. 3.4: false positives only)."""
+    s = sg.config_scene(1)
+    P = s.P.astype(float)
+    targets = []
+    for f in range(s.n):
+        for slots in [(0, 1, 2, 3), (3, 7, 11, 15), (15, 14, 13, 12), (12, 8, 4, 0)]:
+            b = P[f, list(slots)]
+            for t in (0.0, 0.25, 0.5, 0.75):
+                w = np.array([(1 - t) ** 3, 3 * t * (1 - t) ** 2, 3 * t * t * (1 - t), t ** 3])
+                targets.append(w @ b)
+    targets = np.array(targets)
+    o = RNG.normal(size=targets.shape)
+    o *= 3.0 / np.linalg.norm(o, axis=1, keepdims=True)
+    flip = np.einsum("ij,ij->i", o, targets) < 0
+    o[flip] *= -1
+    d = targets - o
+    n = len(targets)
+    rays = [np.ascontiguousarray(a, dtype=np.float32)
+            for a in (o[:, 0], o[:, 1], o[:, 2], d[:, 0], d[:, 1], d[:, 2], np.zeros(n), np.full(n, np.inf))]
+    out = oracle.intersect(s.P, s.types, rays, L=8, local=True)
+    assert (out["pid"] != MISS).all()
+
+
+def test_local_frames_agree_with_world_frames_away_from_edges():
+    """Both frames bound the same surface with boxes around each leaf cell, so away from patch edges they
+    report the same patch, at distances a few leaf-box sizes apart at most."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(160, 90)
+    w = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
+    l = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True, local=True)
+    both = (w["pid"] != MISS) & (l["pid"] != MISS) & (w["flags"] == 0) & (l["flags"] == 0)
+    assert both.sum() > 2000
+    same = both & (w["pid"] == l["pid"])
+    assert same.mean() / both.mean() > 0.97
+    dt = np.abs(l["t"][same] - w["t"][same])
+    assert dt.max() < 1e-2 and np.median(dt) < 1e-3
