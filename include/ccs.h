@@ -120,13 +120,21 @@ typedef struct {
  *   point is p^v + h (p^u - p^v) with h_11 = u/(u+v), h_21 = (1-u)/((1-u)+v), h_12 = u/(u+1-v),
  *   h_22 = (1-u)/((1-u)+(1-v)) (the convention of Algorithm 2).  Bezier patches ignore slots 16..19.
  * types: n_patches bytes, CCS_BEZIER or CCS_GREGORY.
- * device_ptrs: 0 if x, y, z, types are host addresses, 1 if device addresses.
+ * flags: CCS_SCENE_DEVICE_PTRS if x, y, z, types are device addresses (else host addresses);
+ *   CCS_SCENE_LOCAL_FRAMES to take the boxes below each patch root in the patch's own frame (Sec. 3.4:
+ *   local frames shrink the overlap of the sub-domain boxes): z along the normal of the corner quad (the
+ *   cross product of its diagonals p33 - p00 and p03 - p30), x along its u edge p30 - p00 made orthogonal
+ *   to z, y = z x x (the world axes where that is degenerate).  The BVH and the patch root interval stay
+ *   in world space.  The hits are those of the same method with boxes in these frames.
  * The library copies the data into its own device store (patch records anchored at their box centre,
  * Sec. 3.4); the caller keeps ownership of its arrays.  n_patches may be 0 (every ray misses).
  * Blocks until the copy has finished.  Errors: INVALID_ARG (null pointers, n_patches > 2^26),
  * OOM, CUDA. */
 ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, const float *z, const uint8_t *types,
-                            uint32_t n_patches, int device_ptrs, void *stream);
+                            uint32_t n_patches, int flags, void *stream);
+
+#define CCS_SCENE_DEVICE_PTRS 1
+#define CCS_SCENE_LOCAL_FRAMES 2
 
 /* Replace the control points (same layout, same patch count and types) from device addresses,
  * asynchronously on `stream`; a following ccs_bvh_refit updates the hierarchy.  Graph-capturable. */

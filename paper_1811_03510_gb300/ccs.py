@@ -215,10 +215,15 @@ def hits_struct(planes) -> ccs_hits:
 
 # ------------------------------------------------------------------ entry points (same names as the C ABI)
 
-def ccs_scene_create(x, y, z, types, n_patches: int, device_ptrs: bool, stream=None) -> int:
+CCS_SCENE_DEVICE_PTRS = 1
+CCS_SCENE_LOCAL_FRAMES = 2
+
+
+def ccs_scene_create(x, y, z, types, n_patches: int, device_ptrs: bool, stream=None, local: bool = False) -> int:
     h = ctypes.c_void_p()
-    _check(lib().ccs_scene_create(ctypes.byref(h), _ptr(x), _ptr(y), _ptr(z), _ptr(types), n_patches,
-                                  1 if device_ptrs else 0, _stream(stream)))
+    flags = (CCS_SCENE_DEVICE_PTRS if device_ptrs else 0) | (CCS_SCENE_LOCAL_FRAMES if local else 0)
+    _check(lib().ccs_scene_create(ctypes.byref(h), _ptr(x), _ptr(y), _ptr(z), _ptr(types), n_patches, flags,
+                                  _stream(stream)))
     return h.value
 
 
@@ -509,9 +514,10 @@ def ccs_last_error() -> str:
 # ------------------------------------------------------------------ small conveniences over the entry points
 
 class Scene:
-    """Owns a ccs_scene handle built from host arrays P [n, 20, 3] float32 and types [n] uint8."""
+    """Owns a ccs_scene handle built from host arrays P [n, 20, 3] float32 and types [n] uint8; local=True
+    takes the sub-domain boxes in each patch's own frame (CCS_SCENE_LOCAL_FRAMES)."""
 
-    def __init__(self, P, types, bins: int = 16, stream=None):
+    def __init__(self, P, types, bins: int = 16, stream=None, local: bool = False):
         import numpy as np
         P = np.ascontiguousarray(P, dtype=np.float32)
         self.n = int(P.shape[0])
@@ -519,8 +525,9 @@ class Scene:
         y = np.ascontiguousarray(P[..., 1]).reshape(-1)
         z = np.ascontiguousarray(P[..., 2]).reshape(-1)
         t = np.ascontiguousarray(types, dtype=np.uint8)
+        self.local = bool(local)
         self.handle = ccs_scene_create(x.ctypes.data, y.ctypes.data, z.ctypes.data, t.ctypes.data, self.n, False,
-                                       stream)
+                                       stream, local=self.local)
         ccs_bvh_build(self.handle, bins)
 
     def close(self):

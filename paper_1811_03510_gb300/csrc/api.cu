@@ -108,10 +108,12 @@ extern "C" {
 const char *ccs_last_error(void) { return g_err.c_str(); }
 
 ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, const float *z, const uint8_t *types,
-                            uint32_t n_patches, int device_ptrs, void *stream)
+                            uint32_t n_patches, int flags, void *stream)
 {
     CCS_ARG(out, "out must not be NULL");
     *out = nullptr;
+    CCS_ARG((flags & ~(CCS_SCENE_DEVICE_PTRS | CCS_SCENE_LOCAL_FRAMES)) == 0, "unknown scene flags");
+    const bool device_ptrs = (flags & CCS_SCENE_DEVICE_PTRS) != 0;
     CCS_ARG(n_patches <= kMaxPatches, "n_patches above 2^26");
     CCS_ARG(n_patches == 0 || (x && y && z && types), "point or type array is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -121,6 +123,7 @@ ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, con
         return CCS_ERR_OOM;
     }
     sc->n = n_patches;
+    sc->local = (flags & CCS_SCENE_LOCAL_FRAMES) != 0;
     ccs_status st = CCS_OK;
     do {
         cudaError_t e;
@@ -149,7 +152,8 @@ ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, con
             cudaMemcpyAsync(tmp + np, sc->hy.data(), np * 4, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(tmp + 2 * np, sc->hz.data(), np * 4, cudaMemcpyHostToDevice, s);
             cudaMemcpyAsync(sc->d_types, sc->htypes.data(), n_patches, cudaMemcpyHostToDevice, s);
-            e = launch_repack(tmp, tmp + np, tmp + 2 * np, sc->d_types, n_patches, sc->d_rec, sc->d_leaf_box, s);
+            e = launch_repack(tmp, tmp + np, tmp + 2 * np, sc->d_types, n_patches, sc->local ? 1 : 0, sc->d_rec,
+                              sc->d_leaf_box, s);
             cudaError_t e2 = cudaStreamSynchronize(s);
             cudaFree(tmp);
             if (e == cudaSuccess) e = e2;
@@ -230,7 +234,8 @@ ccs_status ccs_scene_update_points(ccs_scene *sc, const float *x, const float *y
 {
     CCS_ARG(sc, "scene is NULL");
     CCS_ARG(sc->n == 0 || (x && y && z), "point array is NULL");
-    CCS_CUDA(launch_repack(x, y, z, sc->d_types, sc->n, sc->d_rec, sc->d_leaf_box, (cudaStream_t)stream));
+    CCS_CUDA(launch_repack(x, y, z, sc->d_types, sc->n, sc->local ? 1 : 0, sc->d_rec, sc->d_leaf_box,
+                           (cudaStream_t)stream));
     return CCS_OK;
 }
 
@@ -259,7 +264,7 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
     if (cfg.pixel_spread > 0.0f) cfg.mode = 4;   // screen-space termination (one lane per ray)
-    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
@@ -285,7 +290,7 @@ ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t 
     cfg.mode = 1;
     cfg.mc = ModeCtx{features, labels, count, capacity};
     CCS_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), (cudaStream_t)stream));
-    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
@@ -310,7 +315,7 @@ ccs_status ccs_intersect_learned(const ccs_scene *sc, const ccs_proposal *prop, 
     cfg.cache_slots = 0;
     cfg.mlp = proposal_weights(prop);
     cfg.min_conf = min_confidence;
-    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
@@ -366,7 +371,7 @@ static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const c
     CCS_CUDA(launch_gen_diffuse(sc->d_rec, sc->d_leaf_box, sc->n, dr, dh, n, seed, (int)leaf_depth, offset_abs,
                                 const_cast<float *>(out->ox), const_cast<float *>(out->dx),
                                 const_cast<float *>(out->tmin), const_cast<float *>(out->tmax), kind, light,
-                                (cudaStream_t)stream));
+                                sc->local ? 1 : 0, (cudaStream_t)stream));
     return CCS_OK;
 }
 
@@ -406,7 +411,7 @@ ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, u
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
     cfg.mode = 3;
     cfg.mc.occluded = occluded;
-    DevScene ds{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+    DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{nullptr, nullptr, nullptr, nullptr};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));

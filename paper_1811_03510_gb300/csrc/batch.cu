@@ -31,7 +31,7 @@ __global__ void k_batch_repack(const BatchEntry *__restrict__ entries, const uin
     const uint32_t s = find_scene(patch_prefix, n_scenes, gp);
     const BatchEntry &e = entries[s];
     if (!e.px) return;
-    repack_one(e.px, e.py, e.pz, e.types, gp - patch_prefix[s], e.rec, e.leaf_box);
+    repack_one(e.px, e.py, e.pz, e.types, gp - patch_prefix[s], e.rec, e.leaf_box, (int)e.sc.local);
 }
 
 __global__ void k_batch_refit(const BatchEntry *__restrict__ entries, const uint32_t *__restrict__ patch_prefix,
@@ -160,7 +160,7 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
             ccs_scene *sc = scenes[s];
             BatchEntry &t = b->h_table[s];
             std::memset(&t, 0, sizeof(t));
-            t.sc = DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+            t.sc = dev_scene(sc);
             t.rays = DevRays{rays[s].ox, rays[s].oy, rays[s].oz, rays[s].dx, rays[s].dy, rays[s].dz, rays[s].tmin,
                              rays[s].tmax};
             t.hits = DevHits{hits[s].t, hits[s].u, hits[s].v, hits[s].patch_id};

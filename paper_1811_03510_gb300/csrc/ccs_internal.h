@@ -11,11 +11,13 @@
 
 namespace ccs {
 
-// One patch record = 16 float4 = 256 bytes, control points relative to the record's anchor:
+// One patch record = 20 float4 = 320 bytes, control points relative to the record's anchor and, in a
+// scene with local frames, rotated into the patch's frame (Sec. 3.4):
 //   [0..3] x of the 16 grid slots (slot 4*j + i), [4..7] y, [8..11] z,
 //   [12] x of p^v (inner slots (1,1),(2,1),(1,2),(2,2)), [13] y, [14] z,
-//   [15] anchor xyz (box centre), w = 1 for Gregory, 0 for Bezier.
-constexpr int kRecF4 = 16;
+//   [15] anchor xyz (world box centre), w = 1 for Gregory, 0 for Bezier,
+//   [16..18] rows of the frame (identity without local frames), [19] unused.
+constexpr int kRecF4 = 20;
 
 // BVH node = 4 float4 = 64 bytes (both children's boxes stored in the parent), one float4 per axis so
 // that the lane of a component loads one vector:
@@ -56,6 +58,7 @@ struct DevScene {
     const float4 *rec;       // n_patches records
     const float4 *nodes;     // n_nodes nodes
     uint32_t n_patches, n_nodes;
+    uint32_t local;          // records hold points in local frames (Sec. 3.4)
 };
 
 struct DevRays {
@@ -81,7 +84,7 @@ struct BatchEntry {
 
 // kernels (intersect.cu, scene.cu)
 size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K, uint32_t NC);
-cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
+cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n, int local,
                           float4 *rec, float4 *leaf_box, cudaStream_t s);
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,
                          uint32_t n_patches, uint32_t n_nodes, cudaStream_t s);
@@ -99,7 +102,7 @@ const MlpWeights *proposal_weights(const ccs_proposal *p);
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, int kind, const float *light, cudaStream_t s);
+                               float *tmin, float *tmax, int kind, const float *light, int local, cudaStream_t s);
 
 void set_error(const std::string &msg);
 
@@ -119,8 +122,16 @@ struct ccs_scene {
     uint32_t *d_refit_flags = nullptr; // per node arrival counters of the refit
     uint32_t n_nodes = 0;
     bool built = false;
+    bool local = false;                // CCS_SCENE_LOCAL_FRAMES
     uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word
     // host-buffer path staging
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
 };
+
+namespace ccs {
+inline DevScene dev_scene(const ccs_scene *sc)
+{
+    return DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes, sc->local ? 1u : 0u};
+}
+}  // namespace ccs

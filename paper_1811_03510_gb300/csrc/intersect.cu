@@ -98,6 +98,7 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     G.mask = NC == 3 ? FULL : (7u << (3 * grp)) & FULL;
     G.l1 = 3 * grp + (G.c + 1) % 3;
     G.l2 = 3 * grp + (G.c + 2) % 3;
+    G.l0 = 3 * grp;
     const bool valid = grp < kRaysPerWarp;
     const bool lead = valid && G.c == 0;
     const unsigned lead_mask = NC == 3 ? FULL : 0x09249249u;                 // lanes 0, 3, ..., 27
@@ -219,8 +220,8 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
             if (need && (__popc(need) >= 8 || need == active)) {
                 if (mine) {
                     float f[kFeat];
-                    pair_features(rec_of(src.scene(lsc), s.pid), s.o[0], s.o[1], s.o[2], s.r.inv[0], s.r.inv[1],
-                                  s.r.inv[2], s.rc0, s.rc1, f);
+                    pair_features(rec_of(src.scene(lsc), s.pid), s.pr.org[0], s.pr.org[1], s.pr.org[2], s.pr.inv[0],
+                                  s.pr.inv[1], s.pr.inv[2], s.rc0, s.rc1, f);
 #pragma unroll
                     for (int k = 0; k < 32; k += 2)
                         st_bf16x2(mt->x + lane * kXStride + k, k < kFeat ? f[k] : 0.0f,

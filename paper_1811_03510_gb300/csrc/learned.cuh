@@ -145,11 +145,12 @@ __device__ __forceinline__ void load_weights(MlpWeights &dst, const MlpWeights *
     for (int i = threadIdx.x; i < n4; i += blockDim.x) d[i] = __ldg(s + i);
 }
 
-// The 24 features of a (ray, patch) pair at the start of Algorithm 3, in the patch's frame scaled by
-// the size S of its corner points: entry point of the ray into the patch box (3), unit direction (3),
-// the 4 corners (12), unit normal of the corner quad (3), length of the ray inside the box (1, <= 4),
-// cosine of direction and normal (1), Gregory flag (1).
-__device__ __forceinline__ void pair_features(const float4 *__restrict__ rec, float ox, float oy, float oz, float ix,
+// The 24 features of a (ray, patch) pair at the start of Algorithm 3, in the frame of the patch record
+// (anchored; rotated with local frames) scaled by the size S of its corner points: entry point of the
+// ray into the patch box (3), unit direction (3), the 4 corners (12), unit normal of the corner quad (3),
+// length of the ray inside the box (1, <= 4), cosine of direction and normal (1), Gregory flag (1).
+// (lx, ly, lz) is the ray origin and (ix, iy, iz) its inverse direction in that frame.
+__device__ __forceinline__ void pair_features(const float4 *__restrict__ rec, float lx, float ly, float lz, float ix,
                                               float iy, float iz, float t0, float t1, float (&f)[kFeat])
 {
     const float4 X0 = __ldg(rec + 0), X3 = __ldg(rec + 3), Y0 = __ldg(rec + 4), Y3 = __ldg(rec + 7);
@@ -163,7 +164,6 @@ __device__ __forceinline__ void pair_features(const float4 *__restrict__ rec, fl
     float dx = 1.0f / ix, dy = 1.0f / iy, dz = 1.0f / iz;
     const float dn = rsqrtf(fmaxf(dx * dx + dy * dy + dz * dz, 1e-30f));
     dx *= dn; dy *= dn; dz *= dn;
-    const float lx = ox - an.x, ly = oy - an.y, lz = oz - an.z;   // anchored origin
     const float te = t0 / dn;                                      // entry along the unit direction
     f[0] = (lx + te * dx) * inv;
     f[1] = (ly + te * dy) * inv;

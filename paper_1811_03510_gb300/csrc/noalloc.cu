@@ -107,7 +107,7 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
             const ccs_hits &h = hits_per_scene[b + k];
             BatchEntry &t = chunk[k];
             std::memset(&t, 0, sizeof(t));
-            t.sc = DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes};
+            t.sc = dev_scene(sc);
             t.rays = DevRays{r.ox, r.oy, r.oz, r.dx, r.dy, r.dz, r.tmin, r.tmax};
             t.hits = DevHits{h.t, h.u, h.v, h.patch_id};
             prefix[k] = r0;

@@ -27,8 +27,10 @@ struct Pcg32 {
 
 __device__ __forceinline__ float unit24(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
 
-// Surface point and partial derivatives of the (Gregory-reduced) patch record at (u, v), world space.
-__device__ void patch_frame(const float4 *__restrict__ rec, float u, float v, float f[3], float fu[3], float fv[3])
+// Surface point and partial derivatives of the (Gregory-reduced) patch record at (u, v), world space
+// (records of a scene with local frames are rotated back with the frame rows [16..18]).
+__device__ void patch_frame(const float4 *__restrict__ rec, float u, float v, float f[3], float fu[3], float fv[3],
+                            bool local)
 {
     const float4 an = rec[15];
     const bool greg = an.w != 0.0f;
@@ -67,16 +69,32 @@ __device__ void patch_frame(const float4 *__restrict__ rec, float u, float v, fl
                 b += Du[i] * Bv[j] * pij;
                 e += Bu[i] * Dv[j] * pij;
             }
-        f[c] = a + anc[c];
+        f[c] = local ? a : a + anc[c];
         fu[c] = b;
         fv[c] = e;
+    }
+    if (local) {   // world = R^T local + anchor
+        const float4 R0 = rec[16], R1 = rec[17], R2 = rec[18];
+        const float Rm[3][3] = {{R0.x, R0.y, R0.z}, {R1.x, R1.y, R1.z}, {R2.x, R2.y, R2.z}};
+        float wf[3], wu[3], wv[3];
+        for (int c = 0; c < 3; ++c) {
+            wf[c] = Rm[0][c] * f[0] + Rm[1][c] * f[1] + Rm[2][c] * f[2] + anc[c];
+            wu[c] = Rm[0][c] * fu[0] + Rm[1][c] * fu[1] + Rm[2][c] * fu[2];
+            wv[c] = Rm[0][c] * fv[0] + Rm[1][c] * fv[1] + Rm[2][c] * fv[2];
+        }
+        for (int c = 0; c < 3; ++c) {
+            f[c] = wf[c];
+            fu[c] = wu[c];
+            fv[c] = wv[c];
+        }
     }
 }
 
 // kind 0: cosine-weighted diffuse, 1: mirror reflection, 2: shadow ray toward the point light
 __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__restrict__ leaf_box, uint32_t n_patches,
                               DevRays in, DevHits hits, uint32_t n, unsigned long long seed, int L, float offset_abs,
-                              float *out_o, float *out_d, float *out_tmin, float *out_tmax, int kind, float3 light)
+                              float *out_o, float *out_d, float *out_tmin, float *out_tmax, int kind, float3 light,
+                              int local)
 {
     const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -90,7 +108,7 @@ __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__re
     }
     const float4 *r = rec + (size_t)pid * kRecF4;
     float f[3], fu[3], fv[3];
-    patch_frame(r, hits.u[i], hits.v[i], f, fu, fv);
+    patch_frame(r, hits.u[i], hits.v[i], f, fu, fv, local != 0);
     float nx = fu[1] * fv[2] - fu[2] * fv[1], ny = fu[2] * fv[0] - fu[0] * fv[2], nz = fu[0] * fv[1] - fu[1] * fv[0];
     const float inv = rsqrtf(fmaxf(nx * nx + ny * ny + nz * nz, 1e-30f));
     nx *= inv; ny *= inv; nz *= inv;
@@ -142,12 +160,12 @@ __global__ void k_gen_diffuse(const float4 *__restrict__ rec, const float4 *__re
 
 cudaError_t launch_gen_diffuse(const float4 *rec, const float4 *leaf_box, uint32_t n_patches, const DevRays &in,
                                const DevHits &hits, uint32_t n, unsigned long long seed, int L, float offset_abs, float *o, float *d,
-                               float *tmin, float *tmax, int kind, const float *light, cudaStream_t s)
+                               float *tmin, float *tmax, int kind, const float *light, int local, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const float3 lp = light ? make_float3(light[0], light[1], light[2]) : make_float3(0.0f, 0.0f, 0.0f);
     k_gen_diffuse<<<(n + 255) / 256, 256, 0, s>>>(rec, leaf_box, n_patches, in, hits, n, seed, L, offset_abs, o, d, tmin, tmax,
-                                                   kind, lp);
+                                                   kind, lp, local);
     return cudaGetLastError();
 }
 

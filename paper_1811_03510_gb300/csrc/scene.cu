@@ -1,23 +1,23 @@
-// Scene-store kernels: repacking of the caller's SoA control points into anchored 256-byte patch
-// records with leaf boxes, and bottom-up BVH refit.
+// Scene-store kernels: repacking of the caller's SoA control points into anchored 320-byte patch
+// records (in local frames if the scene has them) with world leaf boxes, and bottom-up BVH refit.
 #include "scene_dev.cuh"
 
 namespace ccs {
 
 __global__ void k_repack(const float *__restrict__ x, const float *__restrict__ y, const float *__restrict__ z,
-                         const uint8_t *__restrict__ types, uint32_t n, float4 *__restrict__ rec,
+                         const uint8_t *__restrict__ types, uint32_t n, int local, float4 *__restrict__ rec,
                          float4 *__restrict__ leaf_box)
 {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    repack_one(x, y, z, types, p, rec, leaf_box);
+    repack_one(x, y, z, types, p, rec, leaf_box, local);
 }
 
-cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n,
+cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n, int local,
                           float4 *rec, float4 *leaf_box, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_repack<<<(n + 127) / 128, 128, 0, s>>>(x, y, z, types, n, rec, leaf_box);
+    k_repack<<<(n + 127) / 128, 128, 0, s>>>(x, y, z, types, n, local, rec, leaf_box);
     return cudaGetLastError();
 }
 

@@ -7,9 +7,39 @@ namespace ccs {
 
 // Patch p of SoA points (20 slots per patch) -> 256-byte record anchored at its box centre
 // (Sec. 3.4, anchoring), plus its leaf box (AABB of 16 or 20 points: convex hull, Sec. 3.1/3.2).
+// Rows of the local frame of a patch (Sec. 3.4): z along the normal of the corner quad (the cross product
+// of its diagonals p33 - p00 and p03 - p30), x along its u edge p30 - p00 made orthogonal to z, y = z x x;
+// the world axes where that is degenerate.
+__device__ __forceinline__ void local_frame(const float *const pl[3], float (&R)[3][3])
+{
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = i == j ? 1.0f : 0.0f;
+    float a[3], b[3], e[3];
+    for (int c = 0; c < 3; ++c) {
+        a[c] = pl[c][15] - pl[c][0];
+        b[c] = pl[c][12] - pl[c][3];
+        e[c] = pl[c][3] - pl[c][0];
+    }
+    float z[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    const float nz = sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+    if (!(nz > 0.0f)) return;
+    for (int c = 0; c < 3; ++c) z[c] /= nz;
+    const float ez = e[0] * z[0] + e[1] * z[1] + e[2] * z[2];
+    float x[3] = {e[0] - ez * z[0], e[1] - ez * z[1], e[2] - ez * z[2]};
+    const float nx = sqrtf(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    if (!(nx > 0.0f)) return;
+    for (int c = 0; c < 3; ++c) x[c] /= nx;
+    const float y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+    for (int c = 0; c < 3; ++c) {
+        R[0][c] = x[c];
+        R[1][c] = y[c];
+        R[2][c] = z[c];
+    }
+}
+
 __device__ __forceinline__ void repack_one(const float *__restrict__ x, const float *__restrict__ y,
                                            const float *__restrict__ z, const uint8_t *__restrict__ types, uint32_t p,
-                                           float4 *__restrict__ rec, float4 *__restrict__ leaf_box)
+                                           float4 *__restrict__ rec, float4 *__restrict__ leaf_box, int local)
 {
     const bool greg = types[p] != 0;
     const float *pl[3] = {x + (size_t)20 * p, y + (size_t)20 * p, z + (size_t)20 * p};
@@ -25,17 +55,27 @@ __device__ __forceinline__ void repack_one(const float *__restrict__ x, const fl
         an[c] = __fmul_rn(__fadd_rn(a, b), 0.5f);
     }
     float4 *r = rec + (size_t)p * kRecF4;
+    float R[3][3];
+    local_frame(pl, R);
+    // component c of slot k: anchored, and rotated into the patch frame with local frames
+    auto comp = [&](int c, int k) -> float {
+        if (!local) return pl[c][k] - an[c];
+        const float dx = pl[0][k] - an[0], dy = pl[1][k] - an[1], dz = pl[2][k] - an[2];
+        return fmaf(R[c][0], dx, fmaf(R[c][1], dy, R[c][2] * dz));
+    };
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         for (int q = 0; q < 4; ++q)
-            r[c * 4 + q] = make_float4(pl[c][4 * q] - an[c], pl[c][4 * q + 1] - an[c], pl[c][4 * q + 2] - an[c],
-                                       pl[c][4 * q + 3] - an[c]);
+            r[c * 4 + q] = make_float4(comp(c, 4 * q), comp(c, 4 * q + 1), comp(c, 4 * q + 2), comp(c, 4 * q + 3));
         if (greg)
-            r[12 + c] = make_float4(pl[c][16] - an[c], pl[c][17] - an[c], pl[c][18] - an[c], pl[c][19] - an[c]);
+            r[12 + c] = make_float4(comp(c, 16), comp(c, 17), comp(c, 18), comp(c, 19));
         else
-            r[12 + c] = make_float4(pl[c][5] - an[c], pl[c][6] - an[c], pl[c][9] - an[c], pl[c][10] - an[c]);
+            r[12 + c] = make_float4(comp(c, 5), comp(c, 6), comp(c, 9), comp(c, 10));
+        r[16 + c] = local ? make_float4(R[c][0], R[c][1], R[c][2], 0.0f)
+                          : make_float4(c == 0 ? 1.0f : 0.0f, c == 1 ? 1.0f : 0.0f, c == 2 ? 1.0f : 0.0f, 0.0f);
     }
     r[15] = make_float4(an[0], an[1], an[2], greg ? 1.0f : 0.0f);
+    r[19] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     leaf_box[2 * (size_t)p] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     leaf_box[2 * (size_t)p + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
 }

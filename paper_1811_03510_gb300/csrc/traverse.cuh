@@ -49,6 +49,7 @@ struct Grp {
     int c;           // first component held by this lane
     unsigned mask;   // the group's lanes (NC = 1)
     int l1, l2;      // the group's other two lanes (NC = 1)
+    int l0;          // the group's lane of component 0 (NC = 1)
 };
 
 template <int NC>
@@ -617,11 +618,34 @@ CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, ui
     s.greg = an.w != 0.0f;
     s.pid = pid;
     s.pr = s.r;
+    if (!sc.local) {
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-        s.pr.org[k] = s.o[k] - pick(comp<NC>(G, k), an.x, an.y, an.z);
-        s.d[k] = 0.0f;
+        for (int k = 0; k < NC; ++k) s.pr.org[k] = s.o[k] - pick(comp<NC>(G, k), an.x, an.y, an.z);
+    } else {   // the ray in the patch's frame (Sec. 3.4): R (o - anchor), R d
+        float o3[3], d3[3];
+        if constexpr (NC == 3) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o3[c] = s.o[c] - pick(c, an.x, an.y, an.z);
+                d3[c] = 1.0f / s.r.inv[c];
+            }
+        } else {   // gather the three components from the group
+            const float oc = s.o[0] - pick(G.c, an.x, an.y, an.z), dc = 1.0f / s.r.inv[0];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                o3[c] = __shfl_sync(G.mask, oc, G.l0 + c);
+                d3[c] = __shfl_sync(G.mask, dc, G.l0 + c);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const float4 Rk = __ldg(rec + 16 + comp<NC>(G, k));
+            s.pr.org[k] = fmaf(Rk.x, o3[0], fmaf(Rk.y, o3[1], Rk.z * o3[2]));
+            s.pr.inv[k] = safe_inv(fmaf(Rk.x, d3[0], fmaf(Rk.y, d3[1], Rk.z * d3[2])));
+        }
     }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s.d[k] = 0.0f;
     s.level = 0;
     s.rd_target = -1;
     s.path = s.trail = 0u;
@@ -673,8 +697,8 @@ CCS_DEV void export_pair(const Lane<NC> &s, const DevScene &sc, int L, const Mod
         const uint32_t slot = atomicAdd(mc.ex_count, 1u);
         if (slot >= mc.ex_capacity) return;
         float f[kFeat];
-        pair_features(rec_of(sc, s.pid), s.o[0], s.o[1], s.o[2], s.r.inv[0], s.r.inv[1], s.r.inv[2], s.rc0, s.rc1,
-                      f);
+        pair_features(rec_of(sc, s.pid), s.pr.org[0], s.pr.org[1], s.pr.org[2], s.pr.inv[0], s.pr.inv[1],
+                      s.pr.inv[2], s.rc0, s.rc1, f);
 #pragma unroll
         for (int k = 0; k < kFeat; ++k) mc.ex_features[(size_t)slot * kFeat + k] = f[k];
         mc.ex_labels[slot] = (uint8_t)label;
