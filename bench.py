@@ -33,6 +33,7 @@ WORKLOAD = "cfg2: 1536-patch cube-sphere (8x8/face, noise 0.05, 3 oct, seed 1), 
 OPS_BVH_NODE = 34        # two slab tests
 OPS_SPLIT_BEZIER = 360   # de Casteljau split 144 + two 16-point boxes 180 + two slabs 34 + order 2
 OPS_SPLIT_GREGORY = 360 + 1130   # + Algorithm 2 bounds and Algorithm 1 crop of the lower patch
+OPS_PAIR_FRAME = 24              # local frames: the ray rotated into the patch frame (2 x 9 + 3 inverses + 3)
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="default launch options (profiling runs)")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
+    ap.add_argument("--boxes", default="local", choices=["local", "world"],
+                    help="sub-domain boxes in each patch's frame (Sec. 3.4) or in world axes")
     return ap.parse_args()
 
 
@@ -171,7 +174,7 @@ def run_reference(args, rank, world):
     from oracle.raygen import diffuse_rays
     stride = 8
     sub = r.subset(np.arange(0, r.n, stride))
-    o = oracle.intersect(s.P, s.types, sub.soa(), L=8)
+    o = oracle.intersect(s.P, s.types, sub.soa(), L=8, local=args.boxes == "local")
     d = diffuse_rays(s.P, s.types, sub.soa(), o, seed=1)
     act = d[7] >= d[6]
     dsub = [a[act] for a in d]
@@ -180,8 +183,8 @@ def run_reference(args, rank, world):
     threads = 0
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        a = oracle.intersect(s.P, s.types, sub.soa(), L=8)
-        b = oracle.intersect(s.P, s.types, dsub, L=8)
+        a = oracle.intersect(s.P, s.types, sub.soa(), L=8, local=args.boxes == "local")
+        b = oracle.intersect(s.P, s.types, dsub, L=8, local=args.boxes == "local")
         dt = time.perf_counter() - t0
         threads = a["threads"]
         if k >= args.warmup:
@@ -190,7 +193,8 @@ def run_reference(args, rank, world):
     value = n_step * args.steps / T / 1e6
     out.update(value=value, n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                ms_per_step=1e3 * T / args.steps, scaling="weak", vs_baseline=None, dtype="f64",
-               data="synthetic", config={"workload": WORKLOAD, "sample": f"every {stride}th primary ray "
+               data="synthetic", config={"workload": WORKLOAD, "boxes": args.boxes,
+                                         "sample": f"every {stride}th primary ray "
                                          f"({sub.n}) + its {int(act.sum())} diffuse rays per step"},
                cpu_baseline={"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"every {stride}th primary ray + its diffuse rays, {n_step} rays per step"},
@@ -209,7 +213,7 @@ def run_batched(args, dev, stream, world):
     from paper_1811_03510_gb300 import ccs, scenegen as sg
     sizes = sg.batched_sizes()
     scenes = [sg.make_scene(n, 0.0, name=f"n={n}") for n in sizes]
-    handles = [ccs.Scene(s.P, s.types) for s in scenes]
+    handles = [ccs.Scene(s.P, s.types, local=args.boxes == "local") for s in scenes]
     cam = sg.pinhole_rays(512, 512)
     prim = ccs.rays_to_device(cam.soa(), dev)
     opts = ccs.make_opts(leaf_depth=8)
@@ -305,7 +309,7 @@ def run_shadow(args, dev, stream, flush):
     ldir = np.array(LIGHT) / np.linalg.norm(LIGHT)
     P = np.concatenate([big.P, (small.P.astype(np.float64) * 0.35 + 1.6 * ldir).astype(np.float32)])
     T = np.concatenate([big.types, small.types])
-    sc = ccs.Scene(P, T)
+    sc = ccs.Scene(P, T, local=args.boxes == "local")
     cam = sg.pinhole_rays(args.width, args.height)
     prim = ccs.rays_to_device(cam.soa(), dev)
     hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
@@ -375,6 +379,43 @@ def run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p):
     return out
 
 
+def run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush):
+    """The same rays with sub-domain boxes in world axes and in each patch's frame (Sec. 3.4), default
+    launch options for both: MRays/s and subdivision steps."""
+    import torch
+    from paper_1811_03510_gb300 import ccs
+    out = {}
+    for name, local in (("world", False), ("local", True)):
+        sc = ccs.Scene(s.P, s.types, local=local)
+        res = {}
+        for kind, rays, n in (("primary", prim, n_prim), ("diffuse", diff, n_diff)):
+            hits = ccs.alloc_hits(n, dev)
+            opts = ccs.make_opts()
+            for _ in range(max(3, args.warmup)):
+                ccs.ccs_intersect(sc.handle, rays, n, hits, opts, stream)
+            tot = 0.0
+            for k in range(args.steps):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ccs.ccs_intersect(sc.handle, rays, n, hits, opts, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1)
+            c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+            ccs.ccs_intersect(sc.handle, rays, n, hits, ccs.make_opts(counters=c), stream)
+            torch.cuda.synchronize()
+            v = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
+            res[kind + "_mrays_s"] = n * args.steps / tot / 1e3
+            res[kind + "_splits"] = v["bezier_splits"] + v["gregory_splits"]
+            res[kind + "_backtracks"] = v["backtracks"]
+        out[name] = res
+        sc.close()
+    out["speedup_primary"] = out["local"]["primary_mrays_s"] / out["world"]["primary_mrays_s"]
+    out["speedup_diffuse"] = out["local"]["diffuse_mrays_s"] / out["world"]["diffuse_mrays_s"]
+    return out
+
+
 def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     """Train the proposal on traces of scenes with other seeds (GPU export + GPU training), then time the
     learned traversal against the plain one on this workload's primary and diffuse batches."""
@@ -390,7 +431,7 @@ def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     cam_d = ccs.rays_to_device(cam.soa(), dev)
     for seed in range(2, 2 + args.train_seeds):
         st = sg.config_scene(2, seed=seed)
-        sct = ccs.Scene(st.P, st.types)
+        sct = ccs.Scene(st.P, st.types, local=args.boxes == "local")
         hp = ccs.alloc_hits(cam.n, dev)
         room = cap - n_tr
         if room <= 0:
@@ -509,7 +550,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
     s, r = build_workload(args.width, args.height)
-    scene = ccs.Scene(s.P, s.types)
+    scene = ccs.Scene(s.P, s.types, local=args.boxes == "local")
     prim = ccs.rays_to_device(r.soa(), dev)
     n_prim = r.n
     opts = ccs.make_opts(leaf_depth=8)
@@ -545,7 +586,8 @@ def main():
         torch.cuda.synchronize()
         counts[name] = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
     alg_ops = {k: v["bvh_nodes"] * OPS_BVH_NODE + v["bezier_splits"] * OPS_SPLIT_BEZIER
-               + v["gregory_splits"] * OPS_SPLIT_GREGORY for k, v in counts.items()}
+               + v["gregory_splits"] * OPS_SPLIT_GREGORY + (v["pairs"] * OPS_PAIR_FRAME if scene.local else 0)
+               for k, v in counts.items()}
     # schedule of the warps under the chosen options (counting launches of the same configuration)
     sched = {}
     for name, rays, n, h, o in (("primary", prim, n_prim, hits_p, opts_p), ("diffuse", diff, n_diff, hits_d, opts_d)):
@@ -617,6 +659,7 @@ def main():
         "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "primary_rays": n_prim, "diffuse_rays": n_diff, "leaf_depth": 8,
+                   "boxes": ("local frames (Sec. 3.4)" if scene.local else "world axes"),
                    "variant": args.variant, "l2": "flushed (256 MB write) before every timed step",
                    "launch_opts": {"primary": ccs.opts_dict(opts_p), "diffuse": ccs.opts_dict(opts_d),
                                    "chosen_by": "defaults" if args.no_autotune else
@@ -650,12 +693,13 @@ def main():
         res["batched"] = b
         res["shadow"] = run_shadow(args, dev, stream, flush)
         res["screen_space"] = run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p)
+        res["frames"] = run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush)
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
-        o = oracle.intersect(s.P, s.types, r.soa(), L=8)
+        o = oracle.intersect(s.P, s.types, r.soa(), L=8, local=args.boxes == "local")
         dh = [p.cpu().numpy() for p in diff]
-        o2 = oracle.intersect(s.P, s.types, dh, L=8)
+        o2 = oracle.intersect(s.P, s.types, dh, L=8, local=args.boxes == "local")
         dt = time.perf_counter() - t0
         res["cpu_baseline"] = {"value": rays_per_step / dt / 1e6, "unit": UNIT, "cores": o["threads"],
                                "kind": "oracle", "sample": f"the full step: {n_prim} primary + {n_diff} diffuse rays, "
