@@ -67,3 +67,33 @@ def test_full_size_primary_sampled_and_secondaries(big):
         g2 = ccs.hits_to_numpy(h2)
         inactive = g["pid"] == MISS
         assert (g2["pid"][inactive] == MISS).all()
+
+
+def test_full_size_local_frames_sampled(big):
+    """The same launch with the sub-domain boxes in the patches' local frames (Sec. 3.4), sampled against
+    the oracle under the same frames, with its secondary rays."""
+    s, _ = big
+    sc = ccs.Scene(s.P, s.types, local=True)
+    cam = sg.pinhole_rays(3840, 2160)
+    rays = ccs.rays_to_device(cam.soa())
+    hits = ccs.alloc_hits(cam.n)
+    ccs.ccs_intersect(sc.handle, rays, cam.n, hits, ccs.make_opts())
+    torch.cuda.synchronize()
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    g = ccs.hits_to_numpy(hits)
+    hit_idx = np.nonzero(g["pid"] != MISS)[0]
+    rng = np.random.default_rng(4)
+    pick = np.unique(np.concatenate([rng.choice(cam.n, 1500, replace=False), rng.choice(hit_idx, 1500, replace=False)]))
+    sub = cam.subset(pick)
+    o = oracle.intersect(s.P, s.types, sub.soa(), L=8, flags=True, local=True)
+    compare({k: v[pick] for k, v in g.items()}, o, 8, max_flagged_frac=0.05)
+    sec = diffuse_rays(s.P, s.types, sub.soa(), o, seed=2)
+    act = sec[7] >= sec[6]
+    sr = [a[act] for a in sec]
+    n = int(act.sum())
+    hs = ccs.alloc_hits(n)
+    ccs.ccs_intersect(sc.handle, ccs.rays_to_device(sr), n, hs, ccs.make_opts())
+    torch.cuda.synchronize()
+    compare(ccs.hits_to_numpy(hs), oracle.intersect(s.P, s.types, sr, L=8, flags=True, local=True), 8,
+            max_flagged_frac=0.05)
+    sc.close()
