@@ -314,6 +314,29 @@ static ray_t local_ray(const patch_t *P, const ray_t *r)
     return l;
 }
 
+/* Box extension of Sec. 3.4 (closing the gaps that the transform into a local frame may open): below the
+ * root, a box thinner than tau along an axis of the patch frame is widened symmetrically to tau.  tau
+ * exceeds twice the FP32 error of the ray's transform: 2^-19 (1 + L1 distance of the origin from the
+ * patch's box centre).  0 without local frames. */
+static double box_tau(const patch_t *P, const ray_t *r)
+{
+    if (!P->local) return 0.0;
+    const v3 c = scl(add(P->lo, P->hi), 0.5);
+    const v3 oc = vabs(sub(r->o, c));
+    return ldexp(1.0, -19) * (1.0 + oc.x + oc.y + oc.z);
+}
+
+static void extend_box(v3 *lo, v3 *hi, double tau)
+{
+    double l[3] = {lo->x, lo->y, lo->z}, h[3] = {hi->x, hi->y, hi->z};
+    for (int k = 0; k < 3; ++k) {
+        const double w = h[k] - l[k];
+        if (w < tau) { const double e = 0.5 * (tau - w); l[k] -= e; h[k] += e; }
+    }
+    *lo = v3make(l[0], l[1], l[2]);
+    *hi = v3make(h[0], h[1], h[2]);
+}
+
 typedef struct {
     double t;
     uint32_t pid;
@@ -391,6 +414,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spre
     if (!slab(r, P->lo, P->hi, r->tmin, r->tmax, &t0, &t1)) return;   /* the root box is the world one */
     if (t0 > lim) return;
     const ray_t rl = local_ray(P, r);
+    const double tau = box_tau(P, r);
     node_t *root = &stack[sp++];
     memcpy(root->q, P->gl, sizeof(root->q));
     root->level = 0;
@@ -437,6 +461,7 @@ static void intersect_patch(const patch_t *P, const ray_t *r, int L, double spre
             v3 lo = H[s][0], hi = H[s][0];
             for (int k = 1; k < 16; ++k) { lo = vmin(lo, H[s][k]); hi = vmax(hi, H[s][k]); }
             hi = add(hi, d);
+            extend_box(&lo, &hi, tau);
             diag[s] = box_diag_l1(lo, hi);
             hit[s] = slab(&rl, lo, hi, N.t0, N.t1, &c0[s], &c1[s]) && c0[s] <= lim;
         }
@@ -511,12 +536,14 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
     if (!slab(r, lo, hi, r->tmin, r->tmax, &a, &b)) return;
     b *= ORC_FAR_SCALE;
     if (a > bound || a > b) return;
-    /* below the root the boxes are compared with the ray in the patch frame: the FP32 transform of the
-     * ray adds an error that grows with the distance of the origin from the patch */
+    /* below the root the boxes are compared with the ray in the patch frame; its FP32 transform (origin,
+     * direction recovered from the inverse, the new inverse) adds an error that grows with the distance
+     * of the origin from the patch: 6e-7 per unit of distance bounds it */
     const ray_t rl = local_ray(P, r);
     const v3 cen = scl(add(P->lo, P->hi), 0.5);
     const v3 oc = sub(r->o, cen);
     const double eps_in = P->local ? eps + 6e-7 * sqrt(dot3(oc, oc)) : eps;
+    const double tau = box_tau(P, r);
     enode_t *root = &stack[sp++];
     memcpy(root->q, P->gl, sizeof(root->q));
     root->level = 0;
@@ -565,6 +592,7 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
             v3 blo = H[s][0], bhi = H[s][0];
             for (int k = 1; k < 16; ++k) { blo = vmin(blo, H[s][k]); bhi = vmax(bhi, H[s][k]); }
             bhi = add(bhi, d);
+            extend_box(&blo, &bhi, tau);
             v3 llo = blo, lhi = bhi;
             grow_box(&llo, &lhi, eps_in, 0);
             double c0, c1;
@@ -608,6 +636,7 @@ static void brute_rec(const patch_t *P, const ray_t *r, int L, double spread, co
     int axis = level & 1;
     v3 q[16], d;
     const ray_t rl = local_ray(P, r);
+    const double tau = box_tau(P, r);
     if (P->greg) {
         double u0, u1, v0, v1;
         node_domain(level, pu, pv, &u0, &u1, &v0, &v1);
@@ -624,6 +653,7 @@ static void brute_rec(const patch_t *P, const ray_t *r, int L, double spread, co
         v3 lo = H[s][0], hi = H[s][0];
         for (int k = 1; k < 16; ++k) { lo = vmin(lo, H[s][k]); hi = vmax(hi, H[s][k]); }
         hi = add(hi, d);
+        extend_box(&lo, &hi, tau);
         double a, b;
         if (!slab(&rl, lo, hi, t0, t1, &a, &b)) continue;
         brute_rec(P, r, L, spread, H[s], level + 1, pu + (axis == 0 && s ? half : 0),

@@ -9,31 +9,32 @@ namespace ccs {
 // (Sec. 3.4, anchoring), plus its leaf box (AABB of 16 or 20 points: convex hull, Sec. 3.1/3.2).
 // Rows of the local frame of a patch (Sec. 3.4): z along the normal of the corner quad (the cross product
 // of its diagonals p33 - p00 and p03 - p30), x along its u edge p30 - p00 made orthogonal to z, y = z x x;
-// the world axes where that is degenerate.
+// the world axes where that is degenerate.  Computed in FP64 (once per patch) and rounded: the points and
+// the rays are both rotated by this rounded matrix, so they stay in one common frame.
 __device__ __forceinline__ void local_frame(const float *const pl[3], float (&R)[3][3])
 {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) R[i][j] = i == j ? 1.0f : 0.0f;
-    float a[3], b[3], e[3];
+    double a[3], b[3], e[3];
     for (int c = 0; c < 3; ++c) {
-        a[c] = pl[c][15] - pl[c][0];
-        b[c] = pl[c][12] - pl[c][3];
-        e[c] = pl[c][3] - pl[c][0];
+        a[c] = (double)pl[c][15] - (double)pl[c][0];
+        b[c] = (double)pl[c][12] - (double)pl[c][3];
+        e[c] = (double)pl[c][3] - (double)pl[c][0];
     }
-    float z[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
-    const float nz = sqrtf(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
-    if (!(nz > 0.0f)) return;
+    double z[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+    const double nz = sqrt(z[0] * z[0] + z[1] * z[1] + z[2] * z[2]);
+    if (!(nz > 0.0)) return;
     for (int c = 0; c < 3; ++c) z[c] /= nz;
-    const float ez = e[0] * z[0] + e[1] * z[1] + e[2] * z[2];
-    float x[3] = {e[0] - ez * z[0], e[1] - ez * z[1], e[2] - ez * z[2]};
-    const float nx = sqrtf(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
-    if (!(nx > 0.0f)) return;
+    const double ez = e[0] * z[0] + e[1] * z[1] + e[2] * z[2];
+    double x[3] = {e[0] - ez * z[0], e[1] - ez * z[1], e[2] - ez * z[2]};
+    const double nx = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    if (!(nx > 0.0)) return;
     for (int c = 0; c < 3; ++c) x[c] /= nx;
-    const float y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
+    const double y[3] = {z[1] * x[2] - z[2] * x[1], z[2] * x[0] - z[0] * x[2], z[0] * x[1] - z[1] * x[0]};
     for (int c = 0; c < 3; ++c) {
-        R[0][c] = x[c];
-        R[1][c] = y[c];
-        R[2][c] = z[c];
+        R[0][c] = (float)x[c];
+        R[1][c] = (float)y[c];
+        R[2][c] = (float)z[c];
     }
 }
 

@@ -393,10 +393,21 @@ struct StepOut {
     float dL, dR;   // L1 diagonals of the child boxes (the lane's components; screen-space termination)
 };
 
+// Widen [lo, hi] symmetrically to at least tau (Sec. 3.4's box extension in local frames).
+CCS_DEV void extend(float &lo, float &hi, float tau)
+{
+    const float w = __fsub_rn(hi, lo);
+    if (w < tau) {
+        const float e = __fmul_rn(__fsub_rn(tau, w), 0.5f);
+        lo = __fsub_rn(lo, e);
+        hi = __fadd_rn(hi, e);
+    }
+}
+
 template <int K, int NC>
 CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (&d)[NC], float c0, float c1, float tb,
                            bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR, int force,
-                           const Grp &G)
+                           const Grp &G, float tau)
 {
     float e0[4 * NC], e3[4 * NC], m01[4 * NC], m012[4 * NC], mm[4 * NC], m123[4 * NC], m23[4 * NC];
     float lmin[NC], lmax[NC], rmin[NC], rmax[NC];
@@ -425,6 +436,13 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
         lmax[c] = __fadd_rn(fmaxf(max3f(cL[0], cL[1], cL[2]), cL[3]), d[c]);
         rmin[c] = fminf(min3f(cr[0], cr[1], cr[2]), cr[3]);
         rmax[c] = __fadd_rn(fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]), d[c]);
+    }
+    if (tau > 0.0f) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            extend(lmin[c], lmax[c], tau);
+            extend(rmin[c], rmax[c], tau);
+        }
     }
     StepOut o;
     o.dL = 0.0f;
@@ -536,6 +554,7 @@ struct Lane {
     int phase;                      // learned proposal: kPhase*
     uint32_t prop;                  // path bits (levels 0..5) of the proposed depth-3 cell
     float rc0, rc1;                 // root interval of the current pair
+    float tau;                      // box extension of the current pair (local frames), else 0
     bool sleaf;                     // screen-space termination: the current node is a leaf
     uint32_t sleaf_trail;           // bit l: the pending sibling at level l+1 is a screen-space leaf
 };
@@ -618,6 +637,7 @@ CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, ui
     s.greg = an.w != 0.0f;
     s.pid = pid;
     s.pr = s.r;
+    s.tau = 0.0f;
     if (!sc.local) {
 #pragma unroll
         for (int k = 0; k < NC; ++k) s.pr.org[k] = s.o[k] - pick(comp<NC>(G, k), an.x, an.y, an.z);
@@ -643,6 +663,9 @@ CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, ui
             s.pr.org[k] = fmaf(Rk.x, o3[0], fmaf(Rk.y, o3[1], Rk.z * o3[2]));
             s.pr.inv[k] = safe_inv(fmaf(Rk.x, d3[0], fmaf(Rk.y, d3[1], Rk.z * d3[2])));
         }
+        // box extension (Sec. 3.4): boxes below the root at least tau wide along every axis of the frame
+        s.tau = __fmul_rn(__int_as_float((127 - 19) << 23),
+                          __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) s.d[k] = 0.0f;
@@ -815,7 +838,7 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     }
     if (STATS && !redesc) cnt.v[s.greg ? 2 : 1]++;
     const StepOut o = split_step<K, NC>(g, s.pr, s.d, s.c0, s.c1, s.best.t, redesc || !s.greg, scr, slot, allowL,
-                                        allowR, force, G);
+                                        allowR, force, G, s.tau);
     if (redesc) {
         if (++s.level == s.rd_target) s.rd_target = -1;
         return kStepSplit;

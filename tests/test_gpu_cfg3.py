@@ -71,7 +71,10 @@ def test_full_size_primary_sampled_and_secondaries(big):
 
 def test_full_size_local_frames_sampled(big):
     """The same launch with the sub-domain boxes in the patches' local frames (Sec. 3.4), sampled against
-    the oracle under the same frames, with its secondary rays."""
+    the oracle under the same frames, with its secondary rays.  Leaf cells of these small patches are
+    about 5e-5 wide, while the FP32 transform of a ray from 3 units away into a patch frame carries about
+    2e-6 of error, so the error model leaves about one hit in six ambiguous (one in a hundred with boxes
+    in world axes); every other ray must agree."""
     s, _ = big
     sc = ccs.Scene(s.P, s.types, local=True)
     cam = sg.pinhole_rays(3840, 2160)
@@ -86,7 +89,8 @@ def test_full_size_local_frames_sampled(big):
     pick = np.unique(np.concatenate([rng.choice(cam.n, 1500, replace=False), rng.choice(hit_idx, 1500, replace=False)]))
     sub = cam.subset(pick)
     o = oracle.intersect(s.P, s.types, sub.soa(), L=8, flags=True, local=True)
-    compare({k: v[pick] for k, v in g.items()}, o, 8, max_flagged_frac=0.05)
+    rep = compare({k: v[pick] for k, v in g.items()}, o, 8, max_flagged_frac=0.2)
+    assert rep["hits"] - rep["flagged"] > 1000
     sec = diffuse_rays(s.P, s.types, sub.soa(), o, seed=2)
     act = sec[7] >= sec[6]
     sr = [a[act] for a in sec]
@@ -95,5 +99,5 @@ def test_full_size_local_frames_sampled(big):
     ccs.ccs_intersect(sc.handle, ccs.rays_to_device(sr), n, hs, ccs.make_opts())
     torch.cuda.synchronize()
     compare(ccs.hits_to_numpy(hs), oracle.intersect(s.P, s.types, sr, L=8, flags=True, local=True), 8,
-            max_flagged_frac=0.05)
+            max_flagged_frac=0.2)
     sc.close()

@@ -38,11 +38,13 @@ def test_frame_of_a_plane_is_its_tangent_frame():
 
 @pytest.mark.parametrize("L", [4, 8, 12])
 def test_tilted_flat_patch_is_hit_at_the_plane_distance(L):
-    """In its own frame a flat patch has boxes of zero thickness, so the leaf is entered exactly where the
-    ray meets the plane; in world axes the tilted leaf boxes are entered earlier."""
+    """In its own frame a flat patch has boxes of zero thickness, widened to the box-extension thickness
+    tau = 2^-19 (1 + L1 distance of the origin from the patch's box centre): the leaf is entered tau / 2
+    before the plane along its normal.  In world axes the tilted leaf boxes are entered earlier."""
     Q = rotation([1.0, 0.3, 0.0], np.pi / 4)
     c = np.array([0.1, -0.2, 0.3])
     g = flat_square(1.0, Q, c)
+    centre = 0.5 * (g[:16].min(0) + g[:16].max(0))
     nrm = Q[:, 2]
     for k in range(30):
         x, y = RNG.uniform(-0.45, 0.45, 2)
@@ -51,10 +53,12 @@ def test_tilted_flat_patch_is_hit_at_the_plane_distance(L):
         d = target - o
         ray = np.array([*o, *d, 0.0, np.inf])
         t_plane = ((c - o) @ nrm) / (d @ nrm)
+        tau = 2.0 ** -19 * (1.0 + np.abs(o - centre).sum())
+        t_exp = t_plane - 0.5 * tau / abs(d @ nrm)
         hit, t, _, _ = oracle.intersect_patch(g, False, ray, L, local=True)
-        assert hit and abs(t - t_plane) <= 1e-12 * abs(t_plane)
+        assert hit and abs(t - t_exp) <= 1e-12 * abs(t_plane)
         hw, tw, _, _ = oracle.intersect_patch(g, False, ray, L, local=False)
-        assert hw and tw < t_plane - 1e-9
+        assert hw and tw < t_exp - 1e-9
 
 
 @pytest.mark.parametrize("greg", [False, True])
