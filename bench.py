@@ -118,6 +118,23 @@ def build_workload(width, height, seed=1):
     return s, r
 
 
+def max_over_ranks(t: float, device=None) -> float:
+    """The slowest rank's time: the whole job ends when its last replica does (barrier-bracketed timing).
+    Works with gloo (CPU tensor) and nccl (device tensor); a single process returns t."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(t)
+    x = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(x, op=dist.ReduceOp.MAX)
+    return float(x.item())
+
+
+def whole_job_rate(rays_per_step: int, steps: int, t_slowest: float, world: int) -> float:
+    """MRays/s of the whole job: every rank traces its own replica of the step (weak scaling)."""
+    return rays_per_step * world * steps / t_slowest / 1e6
+
+
 def schedule_summary(c: dict, lanes_per_ray: int) -> dict:
     """Warp schedule from the kernel's schedule counters: rays resident per warp iteration, and for each step
     kind the share of iterations that run it and the rays taking part when it runs."""
@@ -623,15 +640,13 @@ def main():
     T = t_prim + t_diff
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([T], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        T = float(t.item())
+        T = max_over_ranks(T, dev)
         dist.barrier()
     st = ccs.ccs_scene_sync_status(scene.handle, stream)
     assert st == ccs.CCS_OK, "traversal limit reached"
 
     rays_per_step = n_prim + n_diff
-    value = rays_per_step * world * args.steps / T / 1e6
+    value = whole_job_rate(rays_per_step, args.steps, T, world)
 
     # end to end through the host-buffer entry point: pinned host rays in, hits out, every step
     host_p = [p.cpu().pin_memory() for p in prim]
