@@ -146,6 +146,8 @@ def schedule_summary(c: dict, lanes_per_ray: int) -> dict:
         out[k + "_iter_frac"] = runs / it
         out[k + "_rays_per_run"] = c[k + "_rays"] / runs if runs else 0.0
     out["bvh_steps_per_run"] = c["bvh_burst_steps"] / max(1, c["bvh_iters"])
+    from paper_1811_03510_gb300 import ccs
+    out.update(ccs.timeline(c))   # of the counting launch, which runs slower than the timed one
     return out
 
 
@@ -588,10 +590,12 @@ def main():
 
     # launch options from the autotuner (answer-preserving knobs), separately for each batch
     tuned = {"primary": opts, "diffuse": opts}
-    for name, rays, n, h in (("primary", prim, n_prim, hits_p), ("diffuse", diff, n_diff, hits_d)):
+    # the primary batch is an image (the work order may rank its 8 x 8 pixel tiles), the diffuse one is not
+    for name, rays, n, h, width in (("primary", prim, n_prim, hits_p, args.width), ("diffuse", diff, n_diff, hits_d, 0)):
         if args.no_autotune:
             break
-        best, ms, _ = ccs.ccs_autotune(scene.handle, rays, n, h, ccs.make_opts(leaf_depth=8), reps=2, stream=stream)
+        best, ms, _ = ccs.ccs_autotune(scene.handle, rays, n, h, ccs.make_opts(leaf_depth=8, image_width=width), reps=2,
+                                       stream=stream)
         tuned[name] = best
     opts_p, opts_d = tuned["primary"], tuned["diffuse"]
 
@@ -649,10 +653,11 @@ def main():
     value = whole_job_rate(rays_per_step, args.steps, T, world)
 
     # end to end through the host-buffer entry point: pinned host rays in, hits out, every step
-    host_p = [p.cpu().pin_memory() for p in prim]
-    host_d = [p.cpu().pin_memory() for p in diff]
-    out_p = [torch.empty(n_prim, dtype=torch.float32).pin_memory() for _ in range(4)]
-    out_d = [torch.empty(n_diff, dtype=torch.float32).pin_memory() for _ in range(4)]
+    # each batch's ray planes are the rows of one pinned block, and so are its hit planes
+    host_p = list(torch.stack([p.cpu() for p in prim]).pin_memory())
+    host_d = list(torch.stack([p.cpu() for p in diff]).pin_memory())
+    out_p = list(torch.empty(4, n_prim, dtype=torch.float32).pin_memory())
+    out_d = list(torch.empty(4, n_diff, dtype=torch.float32).pin_memory())
     for _ in range(2):
         ccs.ccs_intersect_host(scene.handle, host_p, n_prim, out_p, opts_p, stream)
     te = []
@@ -687,7 +692,8 @@ def main():
                      "traffic": (traffic[0] + traffic[1]) / 2 if traffic else None,
                      "per": "launch (mean of the step's primary and diffuse k_intersect launches)",
                      "note": "algorithmic FP32 ops (BVH node 34, Bezier split 360, Gregory split 1490) from the "
-                             "kernel's traversal counters / event-timed launch time; peak = SMs x 128 lanes x 2070 MHz "
+                             "kernel's traversal counters / event-timed launch time (with the work-order kernels "
+                             "where the launch uses them); peak = SMs x 128 lanes x 2070 MHz "
                              "(nominal FP32 issue; no FP32 figure in the measured peaks); traffic = DRAM bytes per "
                              "launch from " + (os.path.relpath(traffic_src, ROOT) if traffic_src else "no capture") +
                              ("" if traffic else " (null: no capture of the current kernel sources)"),
@@ -699,7 +705,8 @@ def main():
                    "samples": ck["samples"]},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 32 * rays_per_step,
                 "d2h_bytes_per_step": 16 * rays_per_step},
-        "gpu_launches": 2 * args.steps,
+        # k_intersect per batch, plus the three kernels of the work order where the tuner chose it
+        "gpu_launches": args.steps * sum(1 + 3 * ccs.opts_dict(o)["order"] for o in (opts_p, opts_d)),
     }
     if args.variant in ("all", "learned"):
         res["learned"] = run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d)

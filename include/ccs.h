@@ -94,11 +94,25 @@ typedef struct {
                                  method parameter, not a launch option); one lane per ray.  [0] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
+    uint32_t image_width;     /* CCS_TRACE_ORDER: the rays are an image of this width, ray y * width + x
+                                 (the last row may be partial), ordered in tiles of 8 x 8 pixels with
+                                 every 4th pixel in x and y sampled; 0: tiles of 32 consecutive rays,
+                                 every 4th ray sampled [0] */
 } ccs_trace_opts;
 
 #define CCS_CACHE_DEFAULT 0xFFFFFFFFu
 #define CCS_TRACE_COUNT 1u          /* accumulate traversal counters into opts->counters */
-#define CCS_NUM_COUNTERS 20         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
+#define CCS_TRACE_ORDER 2u          /* work order: before the launch, count for sampled rays the BVH leaf
+                                       boxes (candidate patches) they enter within [tmin, tmax]; the work
+                                       queue then hands out tiles in descending order of their largest
+                                       count (stable within a count, counts clamped to 15), so that the
+                                       rays that subdivide most start first and the launch does not end
+                                       on a few late, long rays.  Never changes an answer.  Three small
+                                       kernels and a permutation of 4 bytes per ray in scratch owned by
+                                       the scene (allocated on first use and on growth, which synchronises
+                                       the stream).  Used by ccs_intersect, ccs_intersect_host and
+                                       ccs_occluded; the other entry points ignore it. */
+#define CCS_NUM_COUNTERS 23         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
                                        splits, leaves, backtracks, re-descent levels, pruned siblings, pairs;
                                        schedule of the warps, summed over warp iterations (8..19): warp
                                        iterations, resident rays, then for each step kind (subdivision,
@@ -106,7 +120,10 @@ typedef struct {
                                        iterations in which any ray does it (the BVH pair is followed by
                                        the longest burst of the iteration), then warp refills.  The
                                        schedule counts depend on the launch options, the work counts do
-                                       not. */
+                                       not.  Timeline of the launch in device-clock nanoseconds, kept as
+                                       maxima (20..22): bitwise NOT of the first warp's start, bitwise
+                                       NOT of the time a warp first found the work queue empty, the last
+                                       warp's exit; meaningful for one launch per zeroed array. */
 
 typedef struct {
     uint32_t bins;            /* SAH bins per axis, 4..64 [16] */
@@ -158,8 +175,12 @@ ccs_status ccs_intersect(const ccs_scene *scene, const ccs_rays *rays, uint32_t 
                          const ccs_trace_opts *opts, void *stream);
 
 /* Same answer as ccs_intersect, for rays and hits in host memory (pinned memory gives full copy
- * bandwidth): copies the rays to a device staging buffer owned by the scene, intersects, copies the
- * hits back, and synchronises `stream` before returning. */
+ * bandwidth and lets the copies overlap the traversal).  The rays are copied to a device staging buffer
+ * owned by the scene in chunks of about 2^20 rays (at most 8 chunks).  Chunk k is traced while chunk
+ * k+1 is copied in and chunk k-1's hits are copied out, on streams the scene owns and orders after the
+ * work already on `stream`.  Planes that are rows of one host block (equally spaced, in the order of the
+ * struct) move as one 2D copy per chunk; other planes take one copy each.  Synchronises `stream` before returning.  Not thread-safe per scene (one
+ * staging buffer); not graph-capturable.  Errors: INVALID_ARG, NOT_BUILT, OOM, CUDA. */
 ccs_status ccs_intersect_host(ccs_scene *scene, const ccs_rays *host_rays, uint32_t n, ccs_hits *host_hits,
                               const ccs_trace_opts *opts, void *stream);
 
@@ -322,8 +343,9 @@ typedef struct {
     float ms;                 /* mean time of one ccs_intersect launch */
 } ccs_autotune_trial;
 
-/* Autotuner: coordinate descent (two passes) over lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
- * threads per block {64, 96, 128}, blocks per SM {1..6}, refill {1, 2, 4, 8}, chunk {32..1024},
+/* Autotuner: coordinate descent (two passes) over the work order (CCS_TRACE_ORDER off / on, with the
+ * base's image_width), lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
+ * threads per block {64, 96, 128}, blocks per SM {1..6}, refill {1, 2, 4, 8, 16}, chunk {32..1024},
  * bvh_burst {1..16}, cache_slots {0, 2} and min_blocks {0, 4}, starting from
  * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so
  * tuning is safe.  Each candidate is timed with CUDA events over `reps` launches (after one warm-up)

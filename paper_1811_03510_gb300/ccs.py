@@ -18,13 +18,26 @@ CCS_ERR_NOT_BUILT = 5
 CCS_BEZIER = 0
 CCS_GREGORY = 1
 CCS_TRACE_COUNT = 1
-CCS_NUM_COUNTERS = 20
+CCS_TRACE_ORDER = 2
+CCS_NUM_COUNTERS = 23
 COUNTER_NAMES = ("bvh_nodes", "bezier_splits", "gregory_splits", "leaves", "backtracks", "redescent_levels",
                  "pruned_siblings", "pairs",
                  # schedule of the warps (depends on the launch options)
                  "warp_iters", "resident_rays", "split_rays", "split_iters", "gregory_rays", "gregory_iters",
-                 "leaf_rays", "leaf_iters", "bvh_rays", "bvh_iters", "bvh_burst_steps", "refills")
+                 "leaf_rays", "leaf_iters", "bvh_rays", "bvh_iters", "bvh_burst_steps", "refills",
+                 # timeline of one launch (device-clock ns; the first two bitwise inverted, see timeline())
+                 "start_ns_inv", "queue_empty_ns_inv", "end_ns")
 NUM_WORK_COUNTERS = 8
+
+
+def timeline(c: dict) -> dict:
+    """Launch timeline from the counters of one counting launch: total time, and the drain (from the moment
+    a warp first found the work queue empty to the last warp's exit), in microseconds."""
+    m = (1 << 64) - 1
+    start = ~(c["start_ns_inv"] & m) & m
+    empty = ~(c["queue_empty_ns_inv"] & m) & m
+    end = c["end_ns"] & m
+    return {"launch_us": (end - start) / 1e3, "drain_us": (end - empty) / 1e3}
 MISS = 0xFFFFFFFF
 
 _STATUS = {0: "CCS_OK", 1: "CCS_ERR_INVALID_ARG", 2: "CCS_ERR_CUDA", 3: "CCS_ERR_OOM",
@@ -51,7 +64,7 @@ class ccs_trace_opts(ctypes.Structure):
                 ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("min_blocks", ctypes.c_uint32),
                 ("vote", ctypes.c_uint32), ("lanes_per_ray", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("pixel_spread", ctypes.c_float),
-                ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p)]
+                ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p), ("image_width", ctypes.c_uint32)]
 
 
 class ccs_autotune_trial(ctypes.Structure):
@@ -186,7 +199,7 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
-              counters=None, pixel_spread=0.0) -> ccs_trace_opts:
+              counters=None, pixel_spread=0.0, order=False, image_width=0) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -200,8 +213,9 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.cache_slots = cache_slots
     o.iter_cap = iter_cap
     o.pixel_spread = pixel_spread
-    o.flags = CCS_TRACE_COUNT if counters is not None else 0
+    o.flags = (CCS_TRACE_COUNT if counters is not None else 0) | (CCS_TRACE_ORDER if order else 0)
     o.counters = _ptr(counters) if counters is not None else None
+    o.image_width = image_width
     return o
 
 
@@ -489,8 +503,11 @@ def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=No
 
 
 def opts_dict(o: ccs_trace_opts) -> dict:
-    return {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
-                                             "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray")}
+    d = {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
+                                          "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray",
+                                          "image_width")}
+    d["order"] = bool(o.flags & CCS_TRACE_ORDER)
+    return d
 
 
 def ccs_scene_sync_status(scene: int, stream=None) -> int:

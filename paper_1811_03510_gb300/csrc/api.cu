@@ -53,6 +53,11 @@ void free_scene(ccs_scene *s)
     cudaFree(s->d_refit_flags);
     cudaFree(s->d_work);
     cudaFree(s->d_stage);
+    for (cudaEvent_t e : s->pipe_ev)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t q : {s->pipe_h2d, s->pipe_d2h, s->pipe_comp})
+        if (q) cudaStreamDestroy(q);
+    for (uint32_t *o : s->d_order) cudaFree(o);
     delete s;
 }
 
@@ -74,6 +79,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.mc.spread = c.pixel_spread;
     c.iter_cap = o && o->iter_cap ? o->iter_cap : (1u << 22);
     c.flags = o ? o->flags : 0;
+    c.image_width = o ? o->image_width : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
     CCS_ARG(c.leaf_depth >= 1 && c.leaf_depth <= (uint32_t)kMaxLeafDepth, "leaf_depth must be in 1..15");
     CCS_ARG(c.block_threads % 32 == 0 && c.block_threads >= 32 && c.block_threads <= 128,
@@ -88,6 +94,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
     CCS_ARG(c.pixel_spread >= 0.0f && c.pixel_spread < 1.0f, "pixel_spread must be in [0, 1) radians per pixel");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
+    CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER)) == 0, "unknown trace flags");
     return CCS_OK;
 }
 
@@ -98,6 +105,28 @@ ccs_status check_rays(const ccs_rays *r, const ccs_hits *h)
     CCS_ARG(r && h, "rays and hits must not be NULL");
     CCS_ARG(r->ox && r->oy && r->oz && r->dx && r->dy && r->dz && r->tmin && r->tmax, "a ray plane is NULL");
     CCS_ARG(h->t && h->u && h->v && h->patch_id, "a hit plane is NULL");
+    return CCS_OK;
+}
+
+// With CCS_TRACE_ORDER: the permutation of the launch's rays in estimated-cost order, computed on
+// `stream` into the scene's order scratch `slot` (grown on demand, which synchronises the stream);
+// *perm stays null without the flag.
+ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRays &dr, uint32_t n, cudaStream_t s,
+                      const uint32_t **perm)
+{
+    *perm = nullptr;
+    if (!(cfg.flags & CCS_TRACE_ORDER) || n == 0) return CCS_OK;
+    const size_t words = order_scratch_words(n, cfg.image_width);
+    if (words > sc->order_words[slot]) {
+        CCS_CUDA(cudaStreamSynchronize(s));
+        cudaFree(sc->d_order[slot]);
+        sc->d_order[slot] = nullptr;
+        sc->order_words[slot] = 0;
+        CCS_CUDA(cudaMalloc(&sc->d_order[slot], words * sizeof(uint32_t)));
+        sc->order_words[slot] = words;
+    }
+    CCS_CUDA(launch_order(dev_scene(sc), dr, n, cfg.image_width, sc->d_order[slot], s));
+    *perm = sc->d_order[slot];
     return CCS_OK;
 }
 
@@ -267,7 +296,9 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    const uint32_t *perm;
+    if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream, perm));
     return CCS_OK;
 }
 
@@ -328,6 +359,14 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     CCS_ARG(sc, "scene is NULL");
     ccs_status st = check_rays(hr, hh);
     if (st != CCS_OK) return st;
+    if (!sc->built) {
+        set_error("ccs_intersect_host before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
+    }
+    LaunchCfg cfg;
+    if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    if (cfg.pixel_spread > 0.0f) cfg.mode = 4;
+    if (n == 0) return CCS_OK;
     cudaStream_t s = (cudaStream_t)stream;
     const size_t need = (size_t)n * 12 * sizeof(float);
     if (need > sc->stage_bytes) {
@@ -338,17 +377,84 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
         CCS_CUDA(cudaMalloc(&sc->d_stage, need));
         sc->stage_bytes = need;
     }
+    if (!sc->pipe_h2d) {
+        for (cudaStream_t *q : {&sc->pipe_h2d, &sc->pipe_d2h, &sc->pipe_comp})
+            CCS_CUDA(cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : sc->pipe_ev) CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    // Pipeline over chunks of about 2^20 rays (at most 8): chunk k's rays are copied in while chunk k-1 is
+    // traced and chunk k-2's hits are copied out.  Consecutive chunks alternate between the caller's
+    // stream and a second compute stream, each with its own queue head, so that one chunk's launch
+    // fills the SMs that the previous one frees while its last rays finish.  Chunks stay large: every
+    // launch ends on its slowest rays, and smaller chunks pay that drain more often than they save in
+    // exposed copy time.
+    const uint32_t chunks = std::min<uint32_t>(8, (n + (1u << 20) - 1) >> 20);
+    // chunk boundaries of an image fall on rows of 8-pixel tiles, so that each chunk is an image too
+    const size_t align = (cfg.flags & CCS_TRACE_ORDER) && cfg.image_width ? (size_t)cfg.image_width * 8 : 1;
+    auto bound = [&](uint32_t k) -> size_t {
+        const size_t b = (size_t)n * k / chunks;
+        return k == chunks ? (size_t)n : b / align * align;
+    };
+    cudaEvent_t *ev_in = sc->pipe_ev, *ev_hit = sc->pipe_ev + 8, ev_start = sc->pipe_ev[16], ev_out = sc->pipe_ev[17];
+    CCS_CUDA(cudaEventRecord(ev_start, s));
+    for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));
     float *b = static_cast<float *>(sc->d_stage);
     const float *src[8] = {hr->ox, hr->oy, hr->oz, hr->dx, hr->dy, hr->dz, hr->tmin, hr->tmax};
-    for (int k = 0; k < 8; ++k) CCS_CUDA(cudaMemcpyAsync(b + (size_t)k * n, src[k], (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    ccs_rays dr = {b, b + n, b + 2 * (size_t)n, b + 3 * (size_t)n, b + 4 * (size_t)n, b + 5 * (size_t)n,
-                   b + 6 * (size_t)n, b + 7 * (size_t)n};
-    ccs_hits dh = {b + 8 * (size_t)n, b + 9 * (size_t)n, b + 10 * (size_t)n,
-                   reinterpret_cast<uint32_t *>(b + 11 * (size_t)n)};
-    if ((st = ccs_intersect(sc, &dr, n, &dh, opts, stream)) != CCS_OK) return st;
     void *dst[4] = {hh->t, hh->u, hh->v, hh->patch_id};
-    for (int k = 0; k < 4; ++k)
-        CCS_CUDA(cudaMemcpyAsync(dst[k], b + (size_t)(8 + k) * n, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
+    // planes at one constant stride (rows of one host block) move as one 2D copy per chunk
+    auto stride_of = [n](const void *const *pl, int k) -> size_t {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(pl[0]);
+        const uintptr_t a1 = reinterpret_cast<uintptr_t>(pl[1]);
+        if (a1 <= a0 || (a1 - a0) % 4 != 0 || a1 - a0 < (size_t)n * 4) return 0;
+        for (int c = 2; c < k; ++c)
+            if (reinterpret_cast<uintptr_t>(pl[c]) != a0 + (uintptr_t)c * (a1 - a0)) return 0;
+        return a1 - a0;
+    };
+    const void *srcv[8];
+    for (int c = 0; c < 8; ++c) srcv[c] = src[c];
+    // (equally spaced planes of separate allocations are refused by the runtime at the call, with nothing
+    // enqueued; the copies then go plane by plane)
+    size_t in_pitch = stride_of(srcv, 8), out_pitch = stride_of(dst, 4);
+    const DevScene ds = dev_scene(sc);
+    for (uint32_t k = 0; k < chunks; ++k) {
+        const size_t a = bound(k), m = bound(k + 1) - a;
+        if (m == 0) continue;
+        if (in_pitch && cudaMemcpy2DAsync(b + a, (size_t)n * 4, src[0] + a, in_pitch, m * 4, 8, cudaMemcpyHostToDevice,
+                                          sc->pipe_h2d) != cudaSuccess) {
+            (void)cudaGetLastError();
+            in_pitch = 0;
+        }
+        if (!in_pitch) {
+            for (int c = 0; c < 8; ++c)
+                CCS_CUDA(cudaMemcpyAsync(b + (size_t)c * n + a, src[c] + a, m * 4, cudaMemcpyHostToDevice,
+                                         sc->pipe_h2d));
+        }
+        CCS_CUDA(cudaEventRecord(ev_in[k], sc->pipe_h2d));
+        cudaStream_t cs = (k & 1) ? sc->pipe_comp : s;
+        CCS_CUDA(cudaStreamWaitEvent(cs, ev_in[k], 0));
+        const DevRays dr{b + a, b + n + a, b + 2 * (size_t)n + a, b + 3 * (size_t)n + a, b + 4 * (size_t)n + a,
+                         b + 5 * (size_t)n + a, b + 6 * (size_t)n + a, b + 7 * (size_t)n + a};
+        const DevHits dh{b + 8 * (size_t)n + a, b + 9 * (size_t)n + a, b + 10 * (size_t)n + a,
+                         reinterpret_cast<uint32_t *>(b + 11 * (size_t)n + a)};
+        const uint32_t *perm;
+        if ((st = work_order(sc, (int)(k & 1), cfg, dr, (uint32_t)m, cs, &perm)) != CCS_OK) return st;
+        CCS_CUDA(launch_intersect(ds, dr, dh, (uint32_t)m, cfg, sc->d_work + ((k & 1) ? 2 : 0), sc->d_work + 1,
+                                  sc->num_sms, cs, perm));
+        CCS_CUDA(cudaEventRecord(ev_hit[k], cs));
+        CCS_CUDA(cudaStreamWaitEvent(sc->pipe_d2h, ev_hit[k], 0));
+        if (out_pitch && cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + a * 4, out_pitch, b + (size_t)8 * n + a,
+                                           (size_t)n * 4, m * 4, 4, cudaMemcpyDeviceToHost, sc->pipe_d2h) != cudaSuccess) {
+            (void)cudaGetLastError();
+            out_pitch = 0;
+        }
+        if (!out_pitch) {
+            for (int c = 0; c < 4; ++c)
+                CCS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst[c]) + a * 4, b + (size_t)(8 + c) * n + a, m * 4,
+                                         cudaMemcpyDeviceToHost, sc->pipe_d2h));
+        }
+    }
+    CCS_CUDA(cudaEventRecord(ev_out, sc->pipe_d2h));
+    CCS_CUDA(cudaStreamWaitEvent(s, ev_out, 0));
     CCS_CUDA(cudaStreamSynchronize(s));
     return CCS_OK;
 }
@@ -414,7 +520,9 @@ ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, u
     DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{nullptr, nullptr, nullptr, nullptr};
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    const uint32_t *perm;
+    if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream, perm));
     return CCS_OK;
 }
 

@@ -1,6 +1,6 @@
 // Autotuner of the closest-hit launch: coordinate descent over options that cannot change the answer
-// (lanes per ray, phase vote, threads per block, blocks per SM, warp refill threshold, queue chunk, BVH
-// burst, sibling cache, register budget),
+// (work order, lanes per ray, phase vote, threads per block, blocks per SM, warp refill threshold, queue
+// chunk, BVH burst, sibling cache, register budget),
 // each candidate timed with CUDA events over `reps` launches on the caller's rays.
 #include <cuda_runtime.h>
 
@@ -26,7 +26,7 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     cudaStream_t s = (cudaStream_t)stream;
     ccs_trace_opts cur{};
     if (base) cur = *base;
-    cur.flags = 0;
+    cur.flags &= CCS_TRACE_ORDER;
     cur.counters = nullptr;
     if (!cur.leaf_depth) cur.leaf_depth = 8;
     if (!cur.block_threads) cur.block_threads = 128;
@@ -67,20 +67,21 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> threads_c = {64, 96, 128};
     const std::vector<uint32_t> lanes_c = {1, 3};
     const std::vector<uint32_t> bps_c = {1, 2, 3, 4, 5, 6};
-    const std::vector<uint32_t> refill_c = {1, 2, 4, 8};
+    const std::vector<uint32_t> refill_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> cache_c = {0, 2};
     const std::vector<uint32_t> minb_c = {0, 4};
     const std::vector<uint32_t> vote_c = {0, 4, 8, 12, 16, 20, 24};
-    const std::vector<uint32_t> *cands[9] = {&lanes_c, &vote_c, &threads_c, &bps_c, &refill_c, &chunk_c, &burst_c,
-                                             &cache_c, &minb_c};
+    const std::vector<uint32_t> order_c = {0, CCS_TRACE_ORDER};
+    const std::vector<uint32_t> *cands[10] = {&order_c, &lanes_c, &vote_c, &threads_c, &bps_c, &refill_c, &chunk_c,
+                                              &burst_c, &cache_c, &minb_c};
     for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
-        for (int knob = 0; knob < 9 && st == CCS_OK; ++knob) {
+        for (int knob = 0; knob < 10 && st == CCS_OK; ++knob) {
             for (uint32_t v : *cands[knob]) {
                 ccs_trace_opts o = cur;
-                uint32_t *fields[9] = {&o.lanes_per_ray, &o.vote, &o.block_threads, &o.blocks_per_sm, &o.refill,
-                                       &o.chunk, &o.bvh_burst, &o.cache_slots, &o.min_blocks};
+                uint32_t *fields[10] = {&o.flags, &o.lanes_per_ray, &o.vote, &o.block_threads, &o.blocks_per_sm,
+                                        &o.refill, &o.chunk, &o.bvh_burst, &o.cache_slots, &o.min_blocks};
                 uint32_t *field = fields[knob];
                 if (*field == v) continue;
                 *field = v;

@@ -27,9 +27,11 @@ constexpr int kRecF4 = 20;
 //   [3] (child0, child1, parent, slot in parent) as int bits; child >= 0 is a node index,
 //       child < 0 is the leaf of patch ~child.  Node 0 is the root (parent -1).
 constexpr int kNodeF4 = 4;
+constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
 
 constexpr int kMaxLeafDepth = 15;
 constexpr int kNumCounters = CCS_NUM_COUNTERS;
+constexpr int kNumSumCounters = 20;   // summed counters; the last three are the launch's timeline
 
 struct MlpWeights;
 
@@ -45,7 +47,7 @@ struct ModeCtx {
 
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
-        lanes_per_ray, iter_cap, flags;
+        lanes_per_ray, iter_cap, flags, image_width;
     float pixel_spread;
     unsigned long long *counters;
     int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit, 4 screen-space
@@ -89,7 +91,13 @@ cudaError_t launch_repack(const float *x, const float *y, const float *z, const 
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,
                          uint32_t n_patches, uint32_t n_nodes, cudaStream_t s);
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
-                             const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s);
+                             const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s,
+                             const uint32_t *perm = nullptr);
+// work order (order.cu): scratch of order_scratch_words(n, image_width) words; the permutation of ray
+// indices in the order the work queue hands them out is its first n words
+size_t order_scratch_words(uint32_t n, uint32_t image_width);
+cudaError_t launch_order(const DevScene &sc, const DevRays &r, uint32_t n, uint32_t image_width, uint32_t *scratch,
+                         cudaStream_t s);
 cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
                                    uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
                                    int num_sms, cudaStream_t s);
@@ -123,10 +131,16 @@ struct ccs_scene {
     uint32_t n_nodes = 0;
     bool built = false;
     bool local = false;                // CCS_SCENE_LOCAL_FRAMES
-    uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word
-    // host-buffer path staging
+    uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word, [2] second queue head
+    // host-buffer path: staging planes and the copy/compute pipeline (created on first use)
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
+    cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr, pipe_comp = nullptr;
+    cudaEvent_t pipe_ev[2 * 8 + 2] = {};   // per chunk: input copied, hits written; start; end of the copies out
+    // work-order scratch (CCS_TRACE_ORDER): [0] for launches on the caller's stream, [1] for the host
+    // path's second compute stream
+    uint32_t *d_order[2] = {};
+    size_t order_words[2] = {};
 };
 
 namespace ccs {

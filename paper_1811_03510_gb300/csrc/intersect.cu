@@ -9,19 +9,28 @@
 
 namespace ccs {
 
+// Device clock in nanoseconds (the timeline counters of a counting launch).
+CCS_DEV unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Rays of one scene (the scene descriptor stays in kernel-parameter space, uniform over lanes).
 struct SingleSource {
     DevScene sc;
     DevRays rays;
     DevHits hits;
     uint32_t n;
+    const uint32_t *perm;   // queue position -> ray index (work order), or null for the identity
     struct LaneScene {};
     CCS_DEV uint32_t total() const { return n; }
     CCS_DEV const DevScene &scene(const LaneScene &) const { return sc; }
     CCS_DEV void locate(uint32_t i, LaneScene &, uint32_t &scene, uint32_t &local) const
     {
         scene = 0;
-        local = i;
+        local = perm ? __ldg(perm + i) : i;
     }
     CCS_DEV const DevRays &rays_of(uint32_t) const { return rays; }
     CCS_DEV const DevHits &hits_of(uint32_t) const { return hits; }
@@ -88,7 +97,8 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     scr.node = reinterpret_cast<float4 *>(smem + sf * stride) + threadIdx.x;
     Counters cnt;
 #pragma unroll
-    for (int k = 0; k < kNumCounters; ++k) cnt.v[k] = 0;
+    for (int k = 0; k < kNumSumCounters; ++k) cnt.v[k] = 0;
+    if (STATS && (threadIdx.x & 31) == 0) atomicMax(counters + 20, ~global_ns());   // first warp start
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     constexpr int kRaysPerWarp = NC == 3 ? 32 : 10;
@@ -121,6 +131,7 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
                 base = __shfl_sync(FULL, base, 0);
                 if (base >= n) {
                     exhausted = true;
+                    if (STATS && lane == 0) atomicMax(counters + 21, ~global_ns());   // queue found empty
                 } else {
                     wnext = base;
                     wend = min(base + chunk, n);
@@ -245,11 +256,12 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     cp_async_wait_all();
     if (STATS) {   // every lane of a group holds the same counts: the leader reports them
 #pragma unroll
-        for (int k = 0; k < kNumCounters; ++k) {
+        for (int k = 0; k < kNumSumCounters; ++k) {
             unsigned long long v = lead ? cnt.v[k] : 0ull;
             for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
             if (lane == 0 && v) atomicAdd(counters + k, v);
         }
+        if (lane == 0) atomicMax(counters + 22, global_ns());   // last warp exit
     }
 }
 
@@ -272,9 +284,19 @@ static cudaError_t launch_one(const Src &src, const LaunchCfg &cfg, uint32_t *qu
         if (e != cudaSuccess) return e;
         configured = smem;
     }
-    int max_active = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_active, kern, (int)threads, smem);
-    if (e != cudaSuccess) return e;
+    // resident blocks per SM for this instantiation, block size and shared memory (queried once per shape)
+    static uint32_t occ_threads = 0;
+    static size_t occ_smem = 0;
+    static int occ_active = 0;
+    if (occ_threads != threads || occ_smem != smem) {
+        int max_active = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&max_active, kern, (int)threads, smem);
+        if (e != cudaSuccess) return e;
+        occ_threads = threads;
+        occ_smem = smem;
+        occ_active = max_active;
+    }
+    const int max_active = occ_active;
     if (max_active < 1) return cudaErrorInvalidConfiguration;
     uint32_t per_sm = cfg.blocks_per_sm < (uint32_t)max_active ? cfg.blocks_per_sm : (uint32_t)max_active;
     uint32_t blocks = (uint32_t)num_sms * per_sm;
@@ -339,9 +361,9 @@ static cudaError_t dispatch(const Src &src, const LaunchCfg &cfg, uint32_t *queu
 }
 
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
-                             uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
+                             uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s, const uint32_t *perm)
 {
-    SingleSource src{sc, r, h, n};
+    SingleSource src{sc, r, h, n, perm};
     return dispatch(src, cfg, queue, status, num_sms, s);
 }
 

@@ -356,7 +356,7 @@ CCS_DEV bool key_less(float t, uint32_t pid, uint32_t cell, const Best &b)
 }
 
 struct Counters {
-    unsigned long long v[kNumCounters];
+    unsigned long long v[kNumSumCounters];
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -504,7 +504,6 @@ CCS_DEV void node_child_boxes(const float4 (&q)[NC], const RayG<NC> &r, float c0
 }
 
 constexpr int kBvhStack = 64;
-constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
 constexpr int kDone = (int)0x80000000;    // traversal finished
 
 // BVH node stack of one thread (local memory): node index and its interval.

@@ -38,3 +38,39 @@ def test_binding_raises_with_message(L):
     with pytest.raises(ccs.CcsError) as e:
         ccs._check(ccs.CCS_ERR_INVALID_ARG)
     assert "CCS_ERR_INVALID_ARG" in str(e.value)
+
+
+def test_binding_structs_and_constants_match_the_header(tmp_path):
+    """The ctypes mirrors of the option, ray, hit and trial structs have the C layout of include/ccs.h,
+    and the binding's constants equal the header's (checked with the host C compiler)."""
+    import os
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    fields = [f[0] for f in ccs.ccs_trace_opts._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "ccs.h"', "int main(void) {",
+           'printf("opts %zu\\n", sizeof(ccs_trace_opts));',
+           'printf("rays %zu\\n", sizeof(ccs_rays));', 'printf("hits %zu\\n", sizeof(ccs_hits));',
+           'printf("trial %zu\\n", sizeof(ccs_autotune_trial));',
+           'printf("NUM_COUNTERS %d\\n", CCS_NUM_COUNTERS);', 'printf("TRACE_COUNT %u\\n", CCS_TRACE_COUNT);',
+           'printf("TRACE_ORDER %u\\n", CCS_TRACE_ORDER);', 'printf("CACHE_DEFAULT %u\\n", CCS_CACHE_DEFAULT);']
+    src += [f'printf("off_{f} %zu\\n", offsetof(ccs_trace_opts, {f}));' for f in fields]
+    src += ["return 0; }"]
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", inc, str(c), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    assert int(got["opts"]) == ctypes.sizeof(ccs.ccs_trace_opts)
+    assert int(got["rays"]) == ctypes.sizeof(ccs.ccs_rays)
+    assert int(got["hits"]) == ctypes.sizeof(ccs.ccs_hits)
+    assert int(got["trial"]) == ctypes.sizeof(ccs.ccs_autotune_trial)
+    for f in fields:
+        assert int(got["off_" + f]) == getattr(ccs.ccs_trace_opts, f).offset, f
+    assert int(got["NUM_COUNTERS"]) == ccs.CCS_NUM_COUNTERS == len(ccs.COUNTER_NAMES)
+    assert int(got["TRACE_COUNT"]) == ccs.CCS_TRACE_COUNT
+    assert int(got["TRACE_ORDER"]) == ccs.CCS_TRACE_ORDER
+    assert int(got["CACHE_DEFAULT"]) == ccs.CCS_CACHE_DEFAULT

@@ -194,19 +194,56 @@ def test_zero_rays_is_a_no_op():
     sc.close()
 
 
-def test_host_buffer_path_matches_device_path():
+@pytest.mark.parametrize("case", ["one_chunk", "two_ragged_chunks_local", "four_chunks", "screen_space"])
+def test_host_buffer_path_matches_device_path(case):
+    """The host-buffer entry (chunked copies overlapping the traversal) returns the device path's hits."""
     s = sg.config_scene(2)
-    r = sg.pinhole_rays(320, 180)
-    sc = ccs.Scene(s.P, s.types)
-    g = gpu_run(s.P, s.types, r, 8, scene=sc)
+    if case == "one_chunk":
+        r, local, kw = sg.pinhole_rays(320, 180), False, {}
+    elif case == "two_ragged_chunks_local":   # 2,000,001 rays: chunks of 1,000,000 and 1,000,001
+        r, local, kw = sg.pinhole_rays(1920, 1080).subset(np.arange(2000001)), True, {}
+    elif case == "four_chunks":               # 3 * 2^20 + 5 rays
+        r, local, kw = sg.random_rays(3 * (1 << 20) + 5, seed=77), True, {}
+    else:
+        r, local, kw = sg.pinhole_rays(640, 480), False, dict(pixel_spread=2.0 * np.tan(np.radians(30.0)) / 480)
+    sc = ccs.Scene(s.P, s.types, local=local)
+    g = ccs.hits_to_numpy(ccs.intersect(sc, ccs.rays_to_device(r.soa()), ccs.make_opts(**kw)))
+    torch.cuda.synchronize()
     planes = [np.ascontiguousarray(a) for a in r.soa()]
-    ht = np.empty(r.n, np.float32)
-    hu = np.empty(r.n, np.float32)
-    hv = np.empty(r.n, np.float32)
-    hp = np.empty(r.n, np.uint32)
-    ccs.ccs_intersect_host(sc.handle, [a.ctypes.data for a in planes], r.n,
-                           [ht.ctypes.data, hu.ctypes.data, hv.ctypes.data, hp.ctypes.data], ccs.make_opts())
-    assert np.array_equal(hp, g["pid"]) and np.array_equal(ht, g["t"]) and np.array_equal(hu, g["u"])
+    block = np.stack(planes)                               # rays as rows of one block (pitched copies)
+    for rep in range(2):   # the second call reuses the scene's staging buffer, streams and events
+        ht = np.empty(r.n, np.float32)
+        hu = np.empty(r.n, np.float32)
+        hv = np.empty(r.n, np.float32)
+        hp = np.empty(r.n, np.uint32)
+        ccs.ccs_intersect_host(sc.handle, [a.ctypes.data for a in planes], r.n,
+                               [ht.ctypes.data, hu.ctypes.data, hv.ctypes.data, hp.ctypes.data], ccs.make_opts(**kw))
+        assert np.array_equal(hp, g["pid"]) and np.array_equal(ht, g["t"])
+        assert np.array_equal(hu, g["u"]) and np.array_equal(hv, g["v"])
+        out = np.full((4, r.n + 3), -7, np.float32)      # hits as rows of one block with a wider pitch
+        ccs.ccs_intersect_host(sc.handle, [block[c].ctypes.data for c in range(8)], r.n,
+                               [out[c].ctypes.data for c in range(4)], ccs.make_opts(**kw))
+        assert np.array_equal(out[3, :r.n].view(np.uint32), g["pid"]) and np.array_equal(out[0, :r.n], g["t"])
+        assert np.array_equal(out[1, :r.n], g["u"]) and np.array_equal(out[2, :r.n], g["v"])
+        assert (out[:, r.n:] == -7).all()
+    assert (g["pid"] != MISS).sum() > 1000
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    sc.close()
+
+
+def test_launch_timeline_counters():
+    """Counters 20..22 of a counting launch: first warp start <= queue found empty <= last warp exit."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(480, 270)
+    sc = ccs.Scene(s.P, s.types)
+    cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    ccs.intersect(sc, ccs.rays_to_device(r.soa()), ccs.make_opts(counters=cnt))
+    ev[1].record()
+    torch.cuda.synchronize()
+    tl = ccs.timeline(dict(zip(ccs.COUNTER_NAMES, cnt.cpu().tolist())))
+    assert 0.0 < tl["drain_us"] < tl["launch_us"] <= 1e3 * ev[0].elapsed_time(ev[1]) + 5.0, tl
     sc.close()
 
 
