@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch options (profiling runs)")
+    ap.add_argument("--opts-primary", default=None,
+                    help='launch options of the primary batch as JSON (e.g. {"block_threads": 96, "order": true}), '
+                         "instead of the tuner's (profiling runs)")
+    ap.add_argument("--opts-diffuse", default=None, help="the same for the diffuse batch")
     ap.add_argument("--width", type=int, default=1920)
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--boxes", default="local", choices=["local", "world"],
@@ -259,6 +263,11 @@ def run_batched(args, dev, stream, world):
             Q = P + 0.02 * torch.sin(w * P + phi + 6.283185307179586 * f / args.frames)
             fr.append([Q[..., c].contiguous().reshape(-1) for c in range(3)])
         frames.append(fr)
+    if not args.no_autotune:   # launch options tuned on the largest scene's rays (the batch has no work order)
+        big = max(range(len(handles)), key=lambda i: scenes[i].n)
+        opts, _, _ = ccs.ccs_autotune(handles[big].handle, rays[big], int(rays[big][0].numel()), hits[big], opts,
+                                      reps=2, stream=stream)
+        opts.flags &= ~ccs.CCS_TRACE_ORDER
     b = ccs.ccs_batch_create(handles, rays, hits)
     stages = ccs.CCS_BATCH_UPDATE | ccs.CCS_BATCH_REFIT | ccs.CCS_BATCH_INTERSECT
     for i in range(len(handles)):
@@ -312,7 +321,8 @@ def run_batched(args, dev, stream, world):
             "batched_mrays_s": n_step * args.steps / T_b / 1e6, "plain_mrays_s": n_step * args.steps / T_p / 1e6,
             "batched_ms_per_frame": 1e3 * T_b / args.steps, "plain_ms_per_frame": 1e3 * T_p / args.steps,
             "speedup": T_p / T_b, "identical_hits": bool(identical),
-            "launches_per_frame": {"batched": 1, "plain": 3 * len(handles)}}
+            "launches_per_frame": {"batched": 1, "plain": 3 * len(handles)},
+            "launch_opts": ccs.opts_dict(opts)}
 
 
 LIGHT = (2.0, 3.0, 4.0)
@@ -594,9 +604,14 @@ def main():
     for name, rays, n, h, width in (("primary", prim, n_prim, hits_p, args.width), ("diffuse", diff, n_diff, hits_d, 0)):
         if args.no_autotune:
             break
+        if (args.opts_primary if name == "primary" else args.opts_diffuse):
+            continue
         best, ms, _ = ccs.ccs_autotune(scene.handle, rays, n, h, ccs.make_opts(leaf_depth=8, image_width=width), reps=2,
                                        stream=stream)
         tuned[name] = best
+    for name, arg in (("primary", args.opts_primary), ("diffuse", args.opts_diffuse)):
+        if arg:
+            tuned[name] = ccs.make_opts(**{"leaf_depth": 8, **json.loads(arg)})
     opts_p, opts_d = tuned["primary"], tuned["diffuse"]
 
     # algorithmic work per launch from the traversal counters (separate, untimed launches)
@@ -682,8 +697,8 @@ def main():
                    "boxes": ("local frames (Sec. 3.4)" if scene.local else "world axes"),
                    "variant": args.variant, "l2": "flushed (256 MB write) before every timed step",
                    "launch_opts": {"primary": ccs.opts_dict(opts_p), "diffuse": ccs.opts_dict(opts_d),
-                                   "chosen_by": "defaults" if args.no_autotune else
-                                   "ccs_autotune (answer-preserving knobs)"},
+                                   "chosen_by": "given" if (args.opts_primary or args.opts_diffuse) else
+                                   "defaults" if args.no_autotune else "ccs_autotune (answer-preserving knobs)"},
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "primary_mrays_s": n_prim * args.steps / t_prim / 1e6,
         "diffuse_mrays_s": n_diff * args.steps / t_diff / 1e6,
