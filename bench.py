@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--boxes", default="local", choices=["local", "world"],
                     help="sub-domain boxes in each patch's frame (Sec. 3.4) or in world axes")
+    ap.add_argument("--bvh-width", type=int, default=2, choices=[2, 4], help="children per BVH node")
     return ap.parse_args()
 
 
@@ -236,7 +237,7 @@ def run_batched(args, dev, stream, world):
     from paper_1811_03510_gb300 import ccs, scenegen as sg
     sizes = sg.batched_sizes()
     scenes = [sg.make_scene(n, 0.0, name=f"n={n}") for n in sizes]
-    handles = [ccs.Scene(s.P, s.types, local=args.boxes == "local") for s in scenes]
+    handles = [ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=args.bvh_width) for s in scenes]
     cam = sg.pinhole_rays(512, 512)
     prim = ccs.rays_to_device(cam.soa(), dev)
     opts = ccs.make_opts(leaf_depth=8)
@@ -338,7 +339,7 @@ def run_shadow(args, dev, stream, flush):
     ldir = np.array(LIGHT) / np.linalg.norm(LIGHT)
     P = np.concatenate([big.P, (small.P.astype(np.float64) * 0.35 + 1.6 * ldir).astype(np.float32)])
     T = np.concatenate([big.types, small.types])
-    sc = ccs.Scene(P, T, local=args.boxes == "local")
+    sc = ccs.Scene(P, T, local=args.boxes == "local", bvh_width=args.bvh_width)
     cam = sg.pinhole_rays(args.width, args.height)
     prim = ccs.rays_to_device(cam.soa(), dev)
     hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
@@ -415,7 +416,7 @@ def run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush):
     from paper_1811_03510_gb300 import ccs
     out = {}
     for name, local in (("world", False), ("local", True)):
-        sc = ccs.Scene(s.P, s.types, local=local)
+        sc = ccs.Scene(s.P, s.types, local=local, bvh_width=args.bvh_width)
         res = {}
         for kind, rays, n in (("primary", prim, n_prim), ("diffuse", diff, n_diff)):
             hits = ccs.alloc_hits(n, dev)
@@ -460,7 +461,7 @@ def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     cam_d = ccs.rays_to_device(cam.soa(), dev)
     for seed in range(2, 2 + args.train_seeds):
         st = sg.config_scene(2, seed=seed)
-        sct = ccs.Scene(st.P, st.types, local=args.boxes == "local")
+        sct = ccs.Scene(st.P, st.types, local=args.boxes == "local", bvh_width=args.bvh_width)
         hp = ccs.alloc_hits(cam.n, dev)
         room = cap - n_tr
         if room <= 0:
@@ -579,7 +580,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
     s, r = build_workload(args.width, args.height)
-    scene = ccs.Scene(s.P, s.types, local=args.boxes == "local")
+    scene = ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=args.bvh_width)
     prim = ccs.rays_to_device(r.soa(), dev)
     n_prim = r.n
     opts = ccs.make_opts(leaf_depth=8)
@@ -695,6 +696,7 @@ def main():
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "primary_rays": n_prim, "diffuse_rays": n_diff, "leaf_depth": 8,
                    "boxes": ("local frames (Sec. 3.4)" if scene.local else "world axes"),
+                   "bvh_width": args.bvh_width,
                    "variant": args.variant, "l2": "flushed (256 MB write) before every timed step",
                    "launch_opts": {"primary": ccs.opts_dict(opts_p), "diffuse": ccs.opts_dict(opts_d),
                                    "chosen_by": "given" if (args.opts_primary or args.opts_diffuse) else

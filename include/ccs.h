@@ -127,6 +127,11 @@ typedef struct {
 
 typedef struct {
     uint32_t bins;            /* SAH bins per axis, 4..64 [16] */
+    uint32_t width;           /* children per node: 2 (the binary BVH of Sec. 4) or 4 (the binary tree
+                                 collapsed, each node opening its largest child until it holds four
+                                 subtrees; a wider BVH is named as future work in Sec. 4).  Does not change
+                                 any answer.  A 4-wide tree deeper than 21 levels is refused (INVALID_ARG:
+                                 its traversal stack holds 64 entries) [2] */
 } ccs_bvh_params;
 
 /* Create a scene from n_patches patches.
@@ -159,9 +164,10 @@ ccs_status ccs_scene_update_points(ccs_scene *scene, const float *x, const float
 
 ccs_status ccs_scene_destroy(ccs_scene *scene);
 
-/* Binary BVH over whole-patch boxes (AABB of the 16 or 20 control points; convex hull property,
- * Sec. 3.1), built on the host with binned SAH (Sec. 4), one patch per leaf, and uploaded.  Uses the
- * points given at creation (or copied back after an update).  Blocks.  params may be NULL. */
+/* BVH over whole-patch boxes (AABB of the 16 or 20 control points; convex hull property, Sec. 3.1),
+ * built on the host with binned SAH (Sec. 4), one patch per leaf, binary or collapsed to 4-wide nodes
+ * (params->width), and uploaded.  Uses the points given at creation (or copied back after an update).
+ * Blocks.  params may be NULL.  Batches need every scene's BVH of one width. */
 ccs_status ccs_bvh_build(ccs_scene *scene, const ccs_bvh_params *params);
 
 /* Recompute every box of the hierarchy bottom-up from the current control points, keeping its

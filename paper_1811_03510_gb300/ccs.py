@@ -72,7 +72,7 @@ class ccs_autotune_trial(ctypes.Structure):
 
 
 class ccs_bvh_params(ctypes.Structure):
-    _fields_ = [("bins", ctypes.c_uint32)]
+    _fields_ = [("bins", ctypes.c_uint32), ("width", ctypes.c_uint32)]
 
 
 _lib = None
@@ -249,8 +249,8 @@ def ccs_scene_destroy(scene: int):
     _check(lib().ccs_scene_destroy(scene))
 
 
-def ccs_bvh_build(scene: int, bins: int = 16):
-    p = ccs_bvh_params(bins)
+def ccs_bvh_build(scene: int, bins: int = 16, width: int = 2):
+    p = ccs_bvh_params(bins, width)
     _check(lib().ccs_bvh_build(scene, ctypes.byref(p)))
 
 
@@ -532,9 +532,9 @@ def ccs_last_error() -> str:
 
 class Scene:
     """Owns a ccs_scene handle built from host arrays P [n, 20, 3] float32 and types [n] uint8; local=True
-    takes the sub-domain boxes in each patch's own frame (CCS_SCENE_LOCAL_FRAMES)."""
+    takes the sub-domain boxes in each patch's own frame (CCS_SCENE_LOCAL_FRAMES); bvh_width 2 or 4."""
 
-    def __init__(self, P, types, bins: int = 16, stream=None, local: bool = False):
+    def __init__(self, P, types, bins: int = 16, stream=None, local: bool = False, bvh_width: int = 2):
         import numpy as np
         P = np.ascontiguousarray(P, dtype=np.float32)
         self.n = int(P.shape[0])
@@ -545,7 +545,8 @@ class Scene:
         self.local = bool(local)
         self.handle = ccs_scene_create(x.ctypes.data, y.ctypes.data, z.ctypes.data, t.ctypes.data, self.n, False,
                                        stream, local=self.local)
-        ccs_bvh_build(self.handle, bins)
+        self.bvh_width = int(bvh_width)
+        ccs_bvh_build(self.handle, bins, self.bvh_width)
 
     def close(self):
         if self.handle:

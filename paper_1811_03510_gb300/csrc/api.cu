@@ -219,6 +219,8 @@ ccs_status ccs_bvh_build(ccs_scene *sc, const ccs_bvh_params *params)
     CCS_ARG(sc, "scene is NULL");
     int bins = params && params->bins ? (int)params->bins : 16;
     CCS_ARG(bins >= 4 && bins <= 64, "bins must be in 4..64");
+    const uint32_t width = params && params->width ? params->width : 2;
+    CCS_ARG(width == 2 || width == 4, "width must be 2 or 4");
     const uint32_t n = sc->n;
     std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n);
     for (uint32_t p = 0; p < n; ++p) {
@@ -240,13 +242,21 @@ ccs_status ccs_bvh_build(ccs_scene *sc, const ccs_bvh_params *params)
         set_error(err);
         return CCS_ERR_INVALID_ARG;
     }
+    if (width == 4) {
+        BvhHost bin = std::move(bvh);
+        if (!collapse_bvh4(bin, n, bvh, err)) {
+            set_error(err);
+            return CCS_ERR_INVALID_ARG;
+        }
+    }
     cudaFree(sc->d_nodes);
     cudaFree(sc->d_leaf_parent);
     cudaFree(sc->d_refit_flags);
     sc->d_nodes = nullptr;
     sc->d_leaf_parent = nullptr;
     sc->d_refit_flags = nullptr;
-    sc->n_nodes = (uint32_t)(bvh.nodes.size() / 16);
+    sc->n_nodes = (uint32_t)(bvh.nodes.size() / (width == 4 ? 32 : 16));
+    sc->bvh_width = width;
     sc->built = false;
     if (sc->n_nodes) {
         CCS_CUDA(cudaMalloc(&sc->d_nodes, bvh.nodes.size() * sizeof(float)));
@@ -276,7 +286,7 @@ ccs_status ccs_bvh_refit(ccs_scene *sc, void *stream)
         return CCS_ERR_NOT_BUILT;
     }
     CCS_CUDA(launch_refit(sc->d_nodes, sc->d_leaf_parent, sc->d_leaf_box, sc->d_refit_flags, sc->n, sc->n_nodes,
-                          (cudaStream_t)stream));
+                          sc->bvh_width, (cudaStream_t)stream));
     return CCS_OK;
 }
 

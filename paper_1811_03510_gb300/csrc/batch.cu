@@ -41,7 +41,7 @@ __global__ void k_batch_refit(const BatchEntry *__restrict__ entries, const uint
     if (gp >= n_patches) return;
     const uint32_t s = find_scene(patch_prefix, n_scenes, gp);
     const BatchEntry &e = entries[s];
-    refit_one(e.nodes, e.leaf_parent, e.leaf_box, e.refit_flags, gp - patch_prefix[s]);
+    refit_one(e.nodes, e.leaf_parent, e.leaf_box, e.refit_flags, gp - patch_prefix[s], e.sc.width);
 }
 
 cudaError_t launch_batch_repack(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
@@ -70,6 +70,7 @@ struct ccs_batch {
     uint32_t n = 0;                       // scenes
     uint32_t n_rays = 0, n_patches = 0, n_nodes = 0;
     int num_sms = 0;
+    uint32_t width = 2;                   // BVH node width of every scene
     BatchEntry *h_table = nullptr;        // pinned host copy, uploaded at the start of every run
     BatchEntry *d_table = nullptr;
     uint32_t *d_ray_prefix = nullptr, *d_patch_prefix = nullptr;
@@ -121,6 +122,10 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
             set_error("ccs_batch_create: every scene must exist and have a BVH (ccs_bvh_build)");
             return sc ? CCS_ERR_NOT_BUILT : CCS_ERR_INVALID_ARG;
         }
+        if (sc->bvh_width != scenes[0]->bvh_width) {
+            set_error("ccs_batch_create: every scene's BVH must have the same width");
+            return CCS_ERR_INVALID_ARG;
+        }
         if (n_rays[s] && (!rays[s].ox || !rays[s].oy || !rays[s].oz || !rays[s].dx || !rays[s].dy || !rays[s].dz ||
                           !rays[s].tmin || !rays[s].tmax || !hits[s].t || !hits[s].u || !hits[s].v ||
                           !hits[s].patch_id)) {
@@ -145,6 +150,7 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
     b->n_patches = (uint32_t)tot_p;
     b->n_nodes = (uint32_t)tot_n;
     b->num_sms = scenes[0]->num_sms;
+    b->width = scenes[0]->bvh_width;
     std::vector<uint32_t> rp(n_scenes + 1), pp(n_scenes + 1);
     cudaError_t e = cudaSuccess;
     do {
@@ -225,7 +231,7 @@ ccs_status ccs_batch_run(ccs_batch *b, uint32_t stages, const ccs_trace_opts *op
         BCK(launch_batch_refit(b->d_table, b->d_patch_prefix, b->n, b->n_patches, b->d_flags, b->n_nodes, s));
     if (stages & CCS_BATCH_INTERSECT)
         BCK(launch_intersect_batch(b->d_table, b->d_ray_prefix, b->n, b->n_rays, cfg, b->d_work, b->d_work + 1,
-                                   b->num_sms, s));
+                                   b->num_sms, s, b->width));
     return CCS_OK;
 }
 

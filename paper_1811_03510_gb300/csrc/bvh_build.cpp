@@ -176,4 +176,108 @@ bool build_bvh(const std::vector<float> &leaf_lo, const std::vector<float> &leaf
     return true;
 }
 
+namespace {
+
+// One subtree below a node of the binary BVH: its box and child word (node index, or ~patch).
+struct Sub {
+    Aabb box;
+    int child;
+};
+
+Sub binary_child(const std::vector<float> &nodes, int node, int slot)
+{
+    const float *nd = &nodes[(size_t)node * 16];
+    Sub s;
+    for (int a = 0; a < 3; ++a) {
+        s.box.lo[a] = nd[4 * a + 2 * slot];
+        s.box.hi[a] = nd[4 * a + 2 * slot + 1];
+    }
+    std::memcpy(&s.child, nd + 12 + slot, 4);
+    return s;
+}
+
+// 4-wide node = 32 floats: [8a .. 8a+3] lo of the four children along axis a, [8a+4 .. 8a+7] hi, then
+// the four child words, then (parent, slot in parent, children present, 0).
+void set_child4(std::vector<float> &nodes, int node, int slot, const Aabb &b, int child)
+{
+    float *nd = &nodes[(size_t)node * 32];
+    for (int a = 0; a < 3; ++a) {
+        nd[8 * a + slot] = b.lo[a];
+        nd[8 * a + 4 + slot] = b.hi[a];
+    }
+    std::memcpy(nd + 24 + slot, &child, 4);
+}
+
+}  // namespace
+
+bool collapse_bvh4(const BvhHost &bin, uint32_t n, BvhHost &out, std::string &err)
+{
+    out.nodes.clear();
+    out.leaf_parent.assign(n, 0);
+    out.max_depth = 0;
+    if (n == 0 || bin.nodes.empty()) return true;
+    const int kEmpty = 0x7FFFFFFF;
+    struct Task {
+        int bin_node, parent, slot, depth;
+    };
+    std::vector<Task> stack{{0, -1, 0, 1}};
+    while (!stack.empty()) {
+        const Task t = stack.back();
+        stack.pop_back();
+        const int id = (int)(out.nodes.size() / 32);
+        out.nodes.resize(out.nodes.size() + 32, 0.0f);
+        if (t.parent >= 0) std::memcpy(&out.nodes[(size_t)t.parent * 32 + 24 + t.slot], &id, 4);
+        out.max_depth = std::max(out.max_depth, t.depth);
+        std::vector<Sub> subs;
+        for (int s = 0; s < 2; ++s) {
+            Sub c = binary_child(bin.nodes, t.bin_node, s);
+            if (c.child != kEmpty) subs.push_back(c);
+        }
+        while (subs.size() < 4) {   // open the internal subtree of largest surface area
+            int pick = -1;
+            float best = -1.0f;
+            for (size_t i = 0; i < subs.size(); ++i)
+                if (subs[i].child >= 0 && subs[i].box.area() > best) {
+                    best = subs[i].box.area();
+                    pick = (int)i;
+                }
+            if (pick < 0) break;
+            const int b = subs[pick].child;
+            subs.erase(subs.begin() + pick);
+            for (int s = 0; s < 2; ++s) {
+                Sub c = binary_child(bin.nodes, b, s);
+                if (c.child != kEmpty) subs.insert(subs.begin() + pick + s, c);
+            }
+        }
+        float *nd = &out.nodes[(size_t)id * 32];
+        const int present = (int)subs.size();
+        std::memcpy(nd + 28, &t.parent, 4);
+        std::memcpy(nd + 29, &t.slot, 4);
+        std::memcpy(nd + 30, &present, 4);
+        Aabb empty;
+        empty.reset();
+        for (int s = 0; s < 4; ++s) {
+            if (s >= present) {
+                set_child4(out.nodes, id, s, empty, kEmpty);
+                continue;
+            }
+            const Sub &c = subs[s];
+            if (c.child < 0) {
+                set_child4(out.nodes, id, s, c.box, c.child);
+                out.leaf_parent[~c.child] = (id << 2) | s;
+                out.max_depth = std::max(out.max_depth, t.depth + 1);
+            } else {
+                set_child4(out.nodes, id, s, c.box, kEmpty);   // child word patched when the task runs
+                stack.push_back({c.child, id, s, t.depth + 1});
+            }
+        }
+    }
+    // a traversal path pushes at most three siblings per level onto a 64-entry stack
+    if (3 * out.max_depth > 64) {
+        err = "4-wide BVH deeper than the traversal stack (21 levels)";
+        return false;
+    }
+    return true;
+}
+
 }  // namespace ccs

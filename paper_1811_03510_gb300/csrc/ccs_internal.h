@@ -29,6 +29,12 @@ constexpr int kRecF4 = 20;
 constexpr int kNodeF4 = 4;
 constexpr int kEmptyChild = 0x7FFFFFFF;   // child slot without a subtree (single-patch scenes)
 
+// 4-wide BVH node = 8 float4 = 128 bytes, two float4 per axis so that the lane of a component loads two:
+//   [2a]   (c0.lo, c1.lo, c2.lo, c3.lo) along axis a,  [2a+1] (c0.hi, c1.hi, c2.hi, c3.hi)
+//   [6]    (child0, child1, child2, child3) as int bits (empty slot: kEmptyChild, box lo > hi)
+//   [7]    (parent, slot in parent, children present, 0) as int bits
+constexpr int kNode4F4 = 8;
+
 constexpr int kMaxLeafDepth = 15;
 constexpr int kNumCounters = CCS_NUM_COUNTERS;
 constexpr int kNumSumCounters = 20;   // summed counters; the last three are the launch's timeline
@@ -61,6 +67,7 @@ struct DevScene {
     const float4 *nodes;     // n_nodes nodes
     uint32_t n_patches, n_nodes;
     uint32_t local;          // records hold points in local frames (Sec. 3.4)
+    uint32_t width;          // BVH node width: 2 or 4
 };
 
 struct DevRays {
@@ -85,11 +92,10 @@ struct BatchEntry {
 };
 
 // kernels (intersect.cu, scene.cu)
-size_t intersect_smem_bytes(uint32_t threads, uint32_t L, uint32_t K, uint32_t NC);
 cudaError_t launch_repack(const float *x, const float *y, const float *z, const uint8_t *types, uint32_t n, int local,
                           float4 *rec, float4 *leaf_box, cudaStream_t s);
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,
-                         uint32_t n_patches, uint32_t n_nodes, cudaStream_t s);
+                         uint32_t n_patches, uint32_t n_nodes, uint32_t width, cudaStream_t s);
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
                              const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s,
                              const uint32_t *perm = nullptr);
@@ -100,7 +106,7 @@ cudaError_t launch_order(const DevScene &sc, const DevRays &r, uint32_t n, uint3
                          cudaStream_t s);
 cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
                                    uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
-                                   int num_sms, cudaStream_t s);
+                                   int num_sms, cudaStream_t s, uint32_t width);
 cudaError_t launch_batch_repack(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
                                 uint32_t n_patches, cudaStream_t s);
 cudaError_t launch_batch_refit(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
@@ -129,6 +135,7 @@ struct ccs_scene {
     int *d_leaf_parent = nullptr;      // per patch: (node << 1) | slot
     uint32_t *d_refit_flags = nullptr; // per node arrival counters of the refit
     uint32_t n_nodes = 0;
+    uint32_t bvh_width = 2;            // node width of the built BVH
     bool built = false;
     bool local = false;                // CCS_SCENE_LOCAL_FRAMES
     uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word, [2] second queue head
@@ -146,6 +153,6 @@ struct ccs_scene {
 namespace ccs {
 inline DevScene dev_scene(const ccs_scene *sc)
 {
-    return DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes, sc->local ? 1u : 0u};
+    return DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};
 }
 }  // namespace ccs

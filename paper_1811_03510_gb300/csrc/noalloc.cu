@@ -72,6 +72,10 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
             set_error("ccs_intersect_batched_noalloc: every scene must exist and have a BVH");
             return sc ? CCS_ERR_NOT_BUILT : CCS_ERR_INVALID_ARG;
         }
+        if (sc->bvh_width != scenes[0]->bvh_width) {
+            set_error("ccs_intersect_batched_noalloc: every scene's BVH must have the same width");
+            return CCS_ERR_INVALID_ARG;
+        }
         const ccs_rays &r = rays_per_scene[s];
         const ccs_hits &h = hits_per_scene[s];
         if (n_per_scene[s] && (!r.ox || !r.oy || !r.oz || !r.dx || !r.dy || !r.dz || !r.tmin || !r.tmax || !h.t ||
@@ -125,7 +129,7 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
     }
     if ((e = cudaMemsetAsync(&scr->status, 0, sizeof(uint32_t), s)) != cudaSuccess ||
         (e = launch_intersect_batch(scr->entries, scr->ray_prefix, n_scenes, (uint32_t)total, cfg, &scr->queue,
-                                    &scr->status, scenes[0]->num_sms, s)) != cudaSuccess ||
+                                    &scr->status, scenes[0]->num_sms, s, scenes[0]->bvh_width)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess) {
         set_error(std::string("ccs_intersect_batched_noalloc: ") + cudaGetErrorString(e));
         return CCS_ERR_CUDA;

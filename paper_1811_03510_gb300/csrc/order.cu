@@ -54,38 +54,30 @@ __device__ inline uint32_t tile_size(const OrderGeom &g, uint32_t x0, uint32_t y
 }
 
 // Candidate patches of one ray: the BVH leaves it enters within [t0, t1] (every one, with no pruning by
-// a closest hit; counting whole subtrees instead of their leaves ranks the tiles clearly worse).
-__device__ uint32_t count_candidates(const float4 *__restrict__ nodes, uint32_t n_nodes, float ox, float oy, float oz,
-                                     float dx, float dy, float dz, float t0, float t1)
+// a closest hit; counting whole subtrees instead of their leaves ranks the tiles clearly worse).  Binary
+// or 4-wide nodes (the stack bound of either tree holds: 62 levels, or three siblings on each of at
+// most 21 levels).
+__device__ uint32_t count_candidates(const float4 *__restrict__ nodes, uint32_t n_nodes, uint32_t width, float ox,
+                                     float oy, float oz, float dx, float dy, float dz, float t0, float t1)
 {
     if (n_nodes == 0 || !(t0 <= t1)) return 0;
     const float ix = 1.0f / dx, iy = 1.0f / dy, iz = 1.0f / dz;
     int stack[kOrderStack];
     int sp = 0, node = 0;
     uint32_t cnt = 0;
+    // fminf/fmaxf drop the NaN of 0 * inf, as in the traversal's slab test
+    auto enters = [&](float lx, float hx, float ly, float hy, float lz, float hz) {
+        const float ax = (lx - ox) * ix, bx = (hx - ox) * ix;
+        const float ay = (ly - oy) * iy, by = (hy - oy) * iy;
+        const float az = (lz - oz) * iz, bz = (hz - oz) * iz;
+        const float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
+        const float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
+        return tn <= tf;
+    };
     for (;;) {
-        const float4 *nd = nodes + (size_t)node * kNodeF4;
-        const float4 qx = __ldg(nd), qy = __ldg(nd + 1), qz = __ldg(nd + 2);
-        const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 3));
-        bool hit[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const float lx = c ? qx.z : qx.x, hx = c ? qx.w : qx.y;
-            const float ly = c ? qy.z : qy.x, hy = c ? qy.w : qy.y;
-            const float lz = c ? qz.z : qz.x, hz = c ? qz.w : qz.y;
-            const float ax = (lx - ox) * ix, bx = (hx - ox) * ix;
-            const float ay = (ly - oy) * iy, by = (hy - oy) * iy;
-            const float az = (lz - oz) * iz, bz = (hz - oz) * iz;
-            // fminf/fmaxf drop the NaN of 0 * inf, as in the traversal's slab test
-            const float tn = fmaxf(fmaxf(fminf(ax, bx), fminf(ay, by)), fmaxf(fminf(az, bz), t0));
-            const float tf = fminf(fminf(fmaxf(ax, bx), fmaxf(ay, by)), fminf(fmaxf(az, bz), t1));
-            hit[c] = tn <= tf;
-        }
         int next = -1;
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-            const int child = c ? ch.y : ch.x;
-            if (!hit[c] || child == kEmptyChild) continue;
+        auto take = [&](bool hit, int child) {
+            if (!hit || child == kEmptyChild) return;
             if (child < 0) {
                 ++cnt;
             } else if (next < 0) {
@@ -93,6 +85,22 @@ __device__ uint32_t count_candidates(const float4 *__restrict__ nodes, uint32_t 
             } else if (sp < kOrderStack) {
                 stack[sp++] = child;
             }
+        };
+        if (width == 4) {
+            const float4 *nd = nodes + (size_t)node * kNode4F4;
+            const float4 lx = __ldg(nd), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+            const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5);
+            const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+            take(enters(lx.x, hx.x, ly.x, hy.x, lz.x, hz.x), ch.x);
+            take(enters(lx.y, hx.y, ly.y, hy.y, lz.y, hz.y), ch.y);
+            take(enters(lx.z, hx.z, ly.z, hy.z, lz.z, hz.z), ch.z);
+            take(enters(lx.w, hx.w, ly.w, hy.w, lz.w, hz.w), ch.w);
+        } else {
+            const float4 *nd = nodes + (size_t)node * kNodeF4;
+            const float4 qx = __ldg(nd), qy = __ldg(nd + 1), qz = __ldg(nd + 2);
+            const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 3));
+            take(enters(qx.x, qx.y, qy.x, qy.y, qz.x, qz.y), ch.x);
+            take(enters(qx.z, qx.w, qy.z, qy.w, qz.z, qz.w), ch.y);
         }
         if (next >= 0) {
             node = next;
@@ -110,7 +118,7 @@ __device__ uint32_t count_candidates(const float4 *__restrict__ nodes, uint32_t 
 // key in hist[key * n_blocks + block] (zeroed before the launch).
 template <class S>
 __global__ void __launch_bounds__(kOrderThreads) k_order_estimate(OrderGeom g, const float4 *__restrict__ nodes,
-                                                                    uint32_t n_nodes, DevRays r,
+                                                                    uint32_t n_nodes, uint32_t width, DevRays r,
                                                                     uint32_t *__restrict__ tile_key,
                                                                     uint32_t *__restrict__ hist)
 {
@@ -122,8 +130,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_estimate(OrderGeom g, c
         const uint32_t y = ty * S::TH + S::SY / 2 + (smp / S::NX) * S::SY;
         if (y < g.h && x < row_len(g, y)) {
             const uint32_t j = y * g.w + x;
-            c = count_candidates(nodes, n_nodes, __ldg(r.ox + j), __ldg(r.oy + j), __ldg(r.oz + j), __ldg(r.dx + j),
-                                 __ldg(r.dy + j), __ldg(r.dz + j), __ldg(r.tmin + j), __ldg(r.tmax + j));
+            c = count_candidates(nodes, n_nodes, width, __ldg(r.ox + j), __ldg(r.oy + j), __ldg(r.oz + j),
+                                 __ldg(r.dx + j), __ldg(r.dy + j), __ldg(r.dz + j), __ldg(r.tmin + j),
+                                 __ldg(r.tmax + j));
         }
     }
 #pragma unroll
@@ -276,7 +285,7 @@ static cudaError_t order_with(const DevScene &sc, const DevRays &r, uint32_t n, 
     uint32_t *perm = scratch, *key = scratch + n, *hist = key + g.n_tiles, *base = hist + (size_t)nb * kOrderKeys;
     cudaError_t e = cudaMemsetAsync(hist, 0, (size_t)nb * kOrderKeys * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    k_order_estimate<S><<<nb, kOrderThreads, 0, s>>>(g, sc.nodes, sc.n_nodes, r, key, hist);
+    k_order_estimate<S><<<nb, kOrderThreads, 0, s>>>(g, sc.nodes, sc.n_nodes, sc.width, r, key, hist);
     k_order_scan<<<1, kOrderScan, 0, s>>>(hist, nb, base);
     k_order_place<S><<<nb, kOrderThreads, 0, s>>>(g, key, base, perm);
     return cudaGetLastError();

@@ -22,20 +22,20 @@ cudaError_t launch_repack(const float *x, const float *y, const float *z, const 
 }
 
 __global__ void k_refit(float4 *nodes, const int *__restrict__ leaf_parent, const float4 *__restrict__ leaf_box,
-                        uint32_t *flags, uint32_t n)
+                        uint32_t *flags, uint32_t n, uint32_t width)
 {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    refit_one(nodes, leaf_parent, leaf_box, flags, p);
+    refit_one(nodes, leaf_parent, leaf_box, flags, p, width);
 }
 
 cudaError_t launch_refit(float4 *nodes, const int *leaf_parent, const float4 *leaf_box, uint32_t *flags,
-                         uint32_t n_patches, uint32_t n_nodes, cudaStream_t s)
+                         uint32_t n_patches, uint32_t n_nodes, uint32_t width, cudaStream_t s)
 {
     if (n_patches == 0 || n_nodes == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(uint32_t) * n_nodes, s);
     if (e != cudaSuccess) return e;
-    k_refit<<<(n_patches + 127) / 128, 128, 0, s>>>(nodes, leaf_parent, leaf_box, flags, n_patches);
+    k_refit<<<(n_patches + 127) / 128, 128, 0, s>>>(nodes, leaf_parent, leaf_box, flags, n_patches, width);
     return cudaGetLastError();
 }
 

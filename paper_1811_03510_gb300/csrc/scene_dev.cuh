@@ -93,27 +93,61 @@ __device__ __forceinline__ void write_child_box(float4 *nodes, int node, int slo
     nd[9 + 2 * slot] = hi.z;
 }
 
-// Refit from leaf p: write its box into its parent's slot; the second thread to arrive at a node (per
-// node arrival counter) takes the union of both children up to the node's parent.  Sibling boxes are
-// read through L2 (.cg) after a fence; the climb is bounded by the tree depth.
+__device__ __forceinline__ void write_child_box4(float4 *nodes, int node, int slot, float4 lo, float4 hi)
+{
+    float *nd = reinterpret_cast<float *>(nodes + (size_t)node * kNode4F4);
+    // float4 2a = lo of the four children along axis a, 2a + 1 = their hi
+    nd[0 + slot] = lo.x;
+    nd[4 + slot] = hi.x;
+    nd[8 + slot] = lo.y;
+    nd[12 + slot] = hi.y;
+    nd[16 + slot] = lo.z;
+    nd[20 + slot] = hi.z;
+}
+
+// Refit from leaf p: write its box into its parent's slot; the last thread to arrive at a node (per
+// node arrival counter: two children in a binary node, the children present in a 4-wide one) takes the
+// union of the children up to the node's parent.  Sibling boxes are read through L2 (.cg) after a
+// fence; the climb is bounded by the tree depth.
 __device__ __forceinline__ void refit_one(float4 *nodes, const int *__restrict__ leaf_parent,
-                                          const float4 *__restrict__ leaf_box, uint32_t *flags, uint32_t p)
+                                          const float4 *__restrict__ leaf_box, uint32_t *flags, uint32_t p,
+                                          uint32_t width)
 {
     float4 lo = leaf_box[2 * (size_t)p], hi = leaf_box[2 * (size_t)p + 1];
     int link = leaf_parent[p];
+    const int shift = width == 4 ? 2 : 1;
     for (int guard = 0; guard < 128; ++guard) {
-        const int node = link >> 1, slot = link & 1;
-        write_child_box(nodes, node, slot, lo, hi);
-        __threadfence();
-        if (atomicAdd(flags + node, 1u) == 0u) return;
-        __threadfence();
-        const float4 *nd = nodes + (size_t)node * kNodeF4;
-        const float4 a = __ldcg(nd + 0), b = __ldcg(nd + 1), c = __ldcg(nd + 2), d = __ldcg(nd + 3);
-        lo = make_float4(fminf(a.x, a.z), fminf(b.x, b.z), fminf(c.x, c.z), 0.0f);
-        hi = make_float4(fmaxf(a.y, a.w), fmaxf(b.y, b.w), fmaxf(c.y, c.w), 0.0f);
-        const int parent = __float_as_int(d.z);
+        const int node = link >> shift, slot = link & ((1 << shift) - 1);
+        int parent;
+        if (width == 4) {
+            write_child_box4(nodes, node, slot, lo, hi);
+            __threadfence();
+            const float4 *nd = nodes + (size_t)node * kNode4F4;
+            const float4 meta = __ldcg(nd + 7);
+            if (atomicAdd(flags + node, 1u) + 1u < (uint32_t)__float_as_int(meta.z)) return;
+            __threadfence();
+            const float4 lx = __ldcg(nd + 0), hx = __ldcg(nd + 1), ly = __ldcg(nd + 2), hy = __ldcg(nd + 3);
+            const float4 lz = __ldcg(nd + 4), hz = __ldcg(nd + 5);
+            // empty slots hold lo = +max, hi = -max and drop out of the union
+            lo = make_float4(fminf(fminf(lx.x, lx.y), fminf(lx.z, lx.w)), fminf(fminf(ly.x, ly.y), fminf(ly.z, ly.w)),
+                             fminf(fminf(lz.x, lz.y), fminf(lz.z, lz.w)), 0.0f);
+            hi = make_float4(fmaxf(fmaxf(hx.x, hx.y), fmaxf(hx.z, hx.w)), fmaxf(fmaxf(hy.x, hy.y), fmaxf(hy.z, hy.w)),
+                             fmaxf(fmaxf(hz.x, hz.y), fmaxf(hz.z, hz.w)), 0.0f);
+            parent = __float_as_int(meta.x);
+            link = (parent << 2) | __float_as_int(meta.y);
+        } else {
+            write_child_box(nodes, node, slot, lo, hi);
+            __threadfence();
+            if (atomicAdd(flags + node, 1u) == 0u) return;
+            __threadfence();
+            const float4 *nd = nodes + (size_t)node * kNodeF4;
+            const float4 a = __ldcg(nd + 0), b = __ldcg(nd + 1), c = __ldcg(nd + 2), d = __ldcg(nd + 3);
+            lo = make_float4(fminf(a.x, a.z), fminf(b.x, b.z), fminf(c.x, c.z), 0.0f);
+            hi = make_float4(fmaxf(a.y, a.w), fmaxf(b.y, b.w), fmaxf(c.y, c.w), 0.0f);
+            parent = __float_as_int(d.z);
+            link = (parent << 1) | __float_as_int(d.w);
+        }
         if (parent < 0) return;
-        link = (parent << 1) | __float_as_int(d.w);
     }
 }
 

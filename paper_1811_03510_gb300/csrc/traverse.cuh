@@ -369,7 +369,7 @@ struct Scratch {
     float2 *sib;     // [level * stride]
     float *cache;    // [(slot * 16 * NC + k) * stride]
     int *tag;        // [slot * stride]
-    float4 *node;    // [k * stride], k <= NC: prefetched float4s of a BVH node
+    float4 *node;    // [k * stride], k < node_f4<BW, NC>(): prefetched float4s of a BVH node
     int stride;
 };
 
@@ -883,8 +883,28 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     return kStepSplit;
 }
 
-// One BVH step: expand an internal node (nearer child first), or start the pair of a leaf.
-template <bool STATS, int MODE, int NC>
+// Float4s of a BVH node that one lane reads: binary, the lane's component planes and the child word;
+// 4-wide, the lane's lo and hi planes and the child words.
+template <int BW, int NC>
+__host__ __device__ constexpr int node_f4() { return BW == 2 ? NC + 1 : 2 * NC + 1; }
+
+// Order a 4-wide node's hit children by entry distance (compare-exchange network; misses carry +inf).
+CCS_DEV void cx4(float (&k)[4], float (&e)[4], int (&c)[4], int a, int b)
+{
+    const bool sw = k[b] < k[a];
+    const float ka = k[a], ea = e[a];
+    const int ca = c[a];
+    k[a] = sw ? k[b] : ka;
+    e[a] = sw ? e[b] : ea;
+    c[a] = sw ? c[b] : ca;
+    k[b] = sw ? ka : k[b];
+    e[b] = sw ? ea : e[b];
+    c[b] = sw ? ca : c[b];
+}
+
+// One BVH step: expand an internal node (nearest child first, the others pushed), or start the pair of
+// a leaf.
+template <bool STATS, int MODE, int NC, int BW>
 CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, Counters &cnt,
                       const Scratch &scr, const Grp &G)
 {
@@ -900,6 +920,71 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         return;
     }
     if (STATS) cnt.v[0]++;
+    if constexpr (BW == 4) {
+        float4 lo4[NC], hi4[NC];
+        int c[4];
+        if (s.pf == s.node) {   // fetched during the previous iteration
+            cp_async_wait_all();
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                lo4[k] = scr.node[(2 * k) * scr.stride];
+                hi4[k] = scr.node[(2 * k + 1) * scr.stride];
+            }
+            const float4 ch = scr.node[(2 * NC) * scr.stride];
+            c[0] = __float_as_int(ch.x);
+            c[1] = __float_as_int(ch.y);
+            c[2] = __float_as_int(ch.z);
+            c[3] = __float_as_int(ch.w);
+        } else {
+            const float4 *nd = sc.nodes + (size_t)s.node * kNode4F4;
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                lo4[k] = __ldg(nd + 2 * comp<NC>(G, k));
+                hi4[k] = __ldg(nd + 2 * comp<NC>(G, k) + 1);
+            }
+            const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+            c[0] = ch.x;
+            c[1] = ch.y;
+            c[2] = ch.z;
+            c[3] = ch.w;
+        }
+        float key[4], ex[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            float lo[NC], hi[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                lo[k] = j == 0 ? lo4[k].x : j == 1 ? lo4[k].y : j == 2 ? lo4[k].z : lo4[k].w;
+                hi[k] = j == 0 ? hi4[k].x : j == 1 ? hi4[k].y : j == 2 ? hi4[k].z : hi4[k].w;
+            }
+            float t0, t1;
+            slab<NC>(s.r, lo, hi, s.tmin, s.tmax, G, t0, t1);
+            const bool h = t0 <= t1 && t0 <= s.best.t && c[j] != kEmptyChild;
+            key[j] = h ? t0 : __int_as_float(0x7f800000);
+            ex[j] = t1;
+        }
+        cx4(key, ex, c, 0, 1);
+        cx4(key, ex, c, 2, 3);
+        cx4(key, ex, c, 0, 2);
+        cx4(key, ex, c, 1, 3);
+        cx4(key, ex, c, 1, 2);
+        if (!(key[0] < __int_as_float(0x7f800000))) {
+            pop_next<NC>(s, stk);
+            return;
+        }
+#pragma unroll
+        for (int j = 3; j >= 1; --j) {   // farthest first, so that the nearer ones are popped first
+            if (key[j] < __int_as_float(0x7f800000) && s.sp < kBvhStack) {
+                stk.node[s.sp] = c[j];
+                stk.t[s.sp] = make_float2(key[j], ex[j]);
+                ++s.sp;
+            }
+        }
+        s.node = c[0];
+        s.n0 = key[0];
+        s.n1 = ex[0];
+        return;
+    }
     float4 q[NC];
     int c0, c1;
     if (s.pf == s.node) {   // fetched during the previous iteration
@@ -941,16 +1026,26 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
 }
 
 // The data of the next BVH node goes to the lane's shared-memory slot asynchronously (the lane's
-// components and the child word), so its latency overlaps the other lanes' subdivision step of the
+// components and the child words), so its latency overlaps the other lanes' subdivision step of the
 // next warp iteration.
-template <int NC>
+template <int NC, int BW>
 CCS_DEV void prefetch_node(Lane<NC> &s, const DevScene &sc, const Scratch &scr, const Grp &G)
 {
     if (s.in_pair || s.node < 0 || s.node == s.pf) return;
-    const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
+    if constexpr (BW == 4) {
+        const float4 *nd = sc.nodes + (size_t)s.node * kNode4F4;
 #pragma unroll
-    for (int k = 0; k < NC; ++k) cp_async16(scr.node + k * scr.stride, nd + comp<NC>(G, k));
-    cp_async16(scr.node + NC * scr.stride, nd + 3);
+        for (int k = 0; k < NC; ++k) {
+            cp_async16(scr.node + (2 * k) * scr.stride, nd + 2 * comp<NC>(G, k));
+            cp_async16(scr.node + (2 * k + 1) * scr.stride, nd + 2 * comp<NC>(G, k) + 1);
+        }
+        cp_async16(scr.node + (2 * NC) * scr.stride, nd + 6);
+    } else {
+        const float4 *nd = sc.nodes + (size_t)s.node * kNodeF4;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) cp_async16(scr.node + k * scr.stride, nd + comp<NC>(G, k));
+        cp_async16(scr.node + NC * scr.stride, nd + 3);
+    }
     cp_async_commit();
     s.pf = s.node;
 }
@@ -958,7 +1053,7 @@ CCS_DEV void prefetch_node(Lane<NC> &s, const DevScene &sc, const Scratch &scr, 
 // One unit of work: a subdivision step, or up to `burst` BVH steps (cheap next to a subdivision step,
 // so rays that traverse catch up while the others subdivide).  Returns the kind of the step (kStepCap
 // on the iteration cap); bsteps receives the number of BVH steps taken.
-template <bool STATS, int K, int MODE, int NC>
+template <bool STATS, int K, int MODE, int NC, int BW>
 CCS_DEV int lane_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const DevScene &sc, int L,
                       const Scratch &scr, Counters &cnt, int burst, const ModeCtx &mc, const Grp &G, int &bsteps)
 {
@@ -974,10 +1069,10 @@ CCS_DEV int lane_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
             if (s.iters == 0) return kStepCap;
             --s.iters;
             ++bsteps;
-            bvh_step<STATS, MODE, NC>(s, g, stk, sc, cnt, scr, G);
+            bvh_step<STATS, MODE, NC, BW>(s, g, stk, sc, cnt, scr, G);
         }
     }
-    prefetch_node<NC>(s, sc, scr, G);
+    prefetch_node<NC, BW>(s, sc, scr, G);
     return kind;
 }
 
