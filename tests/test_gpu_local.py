@@ -158,3 +158,44 @@ def test_batched_any_hit_learned_and_screen_space_on_local_frame_scenes():
     assert (np.abs(g["t"][hit] - o["t"][hit]) <= 1e-4 * np.abs(o["t"][hit])).all()
     for h in handles:
         h.close()
+
+
+def test_benchmark_step_in_its_tuned_configuration_sampled():
+    """The benchmark's step as bench.py times it: the 1920 x 1080 primary batch and its compacted diffuse
+    batch on the local-frame scene, each with the options the autotuner picks (the primary batch as an
+    image, so the work order may rank its tiles).  Sampled rays against the oracle under the same frames,
+    and every hit identical to the default launch."""
+    s = sg.config_scene(2)
+    cam = sg.pinhole_rays(1920, 1080)
+    sc = ccs.Scene(s.P, s.types, local=True)
+    prim = ccs.rays_to_device(cam.soa())
+    ref_p = ccs.hits_to_numpy(ccs.intersect(sc, prim, ccs.make_opts()))
+    hp = ccs.intersect(sc, prim, ccs.make_opts())
+    planes = ccs.gen_diffuse(sc, prim, hp, seed=1, leaf_depth=8, offset_abs=1e-4)
+    torch.cuda.synchronize()
+    act = (planes[7] >= planes[6]).nonzero().squeeze(1)
+    diff = [p.index_select(0, act).contiguous() for p in planes]
+    nd = int(act.numel())
+    ref_d = ccs.hits_to_numpy(ccs.intersect(sc, diff, ccs.make_opts()))
+    got = {}
+    for name, rays, n, width in (("primary", prim, cam.n, 1920), ("diffuse", diff, nd, 0)):
+        h = ccs.alloc_hits(n)
+        best, _, _ = ccs.ccs_autotune(sc.handle, rays, n, h, ccs.make_opts(image_width=width), reps=1)
+        out = ccs.alloc_hits(n)
+        for t in out:
+            t.fill_(-7)
+        ccs.ccs_intersect(sc.handle, rays, n, out, best)
+        torch.cuda.synchronize()
+        assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+        got[name] = ccs.hits_to_numpy(out)
+    same(got["primary"], ref_p, "primary, tuned")
+    same(got["diffuse"], ref_d, "diffuse, tuned")
+    hit_idx = np.nonzero(ref_p["pid"] != MISS)[0]
+    pick = np.unique(np.concatenate([RNG.choice(cam.n, 1500, replace=False), RNG.choice(hit_idx, 1500, replace=False)]))
+    o = oracle.intersect(s.P, s.types, cam.subset(pick).soa(), L=8, flags=True, local=True)
+    compare({k: v[pick] for k, v in got["primary"].items()}, o, 8, max_flagged_frac=0.03)
+    dsoa = [p.cpu().numpy() for p in diff]
+    dpick = RNG.choice(nd, 3000, replace=False)
+    o = oracle.intersect(s.P, s.types, [a[dpick] for a in dsoa], L=8, flags=True, local=True)
+    compare({k: v[dpick] for k, v in got["diffuse"].items()}, o, 8, max_flagged_frac=0.05)
+    sc.close()
