@@ -98,6 +98,9 @@ typedef struct {
                                  (the last row may be partial), ordered in tiles of 8 x 8 pixels with
                                  every 4th pixel in x and y sampled; 0: tiles of 32 consecutive rays,
                                  every 4th ray sampled [0] */
+    uint32_t host_chunk;      /* ccs_intersect_host: rays per chunk of its copy/trace pipeline, at most 8
+                                 chunks (larger chunks then); 0: chunks of 2^20 rays, at least two from
+                                 2^17 rays on [0] */
 } ccs_trace_opts;
 
 #define CCS_CACHE_DEFAULT 0xFFFFFFFFu
@@ -182,7 +185,7 @@ ccs_status ccs_intersect(const ccs_scene *scene, const ccs_rays *rays, uint32_t 
 
 /* Same answer as ccs_intersect, for rays and hits in host memory (pinned memory gives full copy
  * bandwidth and lets the copies overlap the traversal).  The rays are copied to a device staging buffer
- * owned by the scene in chunks of about 2^20 rays (at most 8 chunks).  Chunk k is traced while chunk
+ * owned by the scene in chunks (opts->host_chunk; at most 8).  Chunk k is traced while chunk
  * k+1 is copied in and chunk k-1's hits are copied out, on streams the scene owns and orders after the
  * work already on `stream`.  Planes that are rows of one host block (equally spaced, in the order of the
  * struct) move as one 2D copy per chunk; other planes take one copy each.  Synchronises `stream` before returning.  Not thread-safe per scene (one

@@ -64,7 +64,8 @@ class ccs_trace_opts(ctypes.Structure):
                 ("bvh_burst", ctypes.c_uint32), ("cache_slots", ctypes.c_uint32), ("min_blocks", ctypes.c_uint32),
                 ("vote", ctypes.c_uint32), ("lanes_per_ray", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("pixel_spread", ctypes.c_float),
-                ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p), ("image_width", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p), ("image_width", ctypes.c_uint32),
+                ("host_chunk", ctypes.c_uint32)]
 
 
 class ccs_autotune_trial(ctypes.Structure):
@@ -199,7 +200,7 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
-              counters=None, pixel_spread=0.0, order=False, image_width=0) -> ccs_trace_opts:
+              counters=None, pixel_spread=0.0, order=False, image_width=0, host_chunk=0) -> ccs_trace_opts:
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -216,6 +217,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.flags = (CCS_TRACE_COUNT if counters is not None else 0) | (CCS_TRACE_ORDER if order else 0)
     o.counters = _ptr(counters) if counters is not None else None
     o.image_width = image_width
+    o.host_chunk = host_chunk
     return o
 
 
@@ -505,7 +507,7 @@ def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=No
 def opts_dict(o: ccs_trace_opts) -> dict:
     d = {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
                                           "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray",
-                                          "image_width")}
+                                          "image_width", "host_chunk")}
     d["order"] = bool(o.flags & CCS_TRACE_ORDER)
     return d
 

@@ -53,7 +53,7 @@ struct ModeCtx {
 
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
-        lanes_per_ray, iter_cap, flags, image_width;
+        lanes_per_ray, iter_cap, flags, image_width, host_chunk;
     float pixel_spread;
     unsigned long long *counters;
     int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit, 4 screen-space

@@ -194,7 +194,8 @@ def test_zero_rays_is_a_no_op():
     sc.close()
 
 
-@pytest.mark.parametrize("case", ["one_chunk", "two_ragged_chunks_local", "four_chunks", "screen_space"])
+@pytest.mark.parametrize("case", ["one_chunk", "two_ragged_chunks_local", "four_chunks", "seven_given_chunks",
+                                  "screen_space"])
 def test_host_buffer_path_matches_device_path(case):
     """The host-buffer entry (chunked copies overlapping the traversal) returns the device path's hits."""
     s = sg.config_scene(2)
@@ -204,6 +205,8 @@ def test_host_buffer_path_matches_device_path(case):
         r, local, kw = sg.pinhole_rays(1920, 1080).subset(np.arange(2000001)), True, {}
     elif case == "four_chunks":               # 3 * 2^20 + 5 rays
         r, local, kw = sg.random_rays(3 * (1 << 20) + 5, seed=77), True, {}
+    elif case == "seven_given_chunks":        # 700,001 rays in chunks of 100,003 (the last one short)
+        r, local, kw = sg.random_rays(700001, seed=78), False, dict(host_chunk=100003)
     else:
         r, local, kw = sg.pinhole_rays(640, 480), False, dict(pixel_spread=2.0 * np.tan(np.radians(30.0)) / 480)
     sc = ccs.Scene(s.P, s.types, local=local)
