@@ -29,7 +29,7 @@ METRIC = "closest-hit MRays/s (primary, diffuse) & % FP32 roofline, learned/batc
 UNIT = "MRays/s"
 WORKLOAD = "cfg2: 1536-patch cube-sphere (8x8/face, noise 0.05, 3 oct, seed 1), 1920x1080 primary + diffuse, L=8"
 
-# FP32 operations per unit of work that the method itself performs (roofline):
+# FP32 operations per unit of work that the method itself performs (the roofline of the traversal):
 OPS_BVH_NODE = 34        # two slab tests
 OPS_SPLIT_BEZIER = 360   # de Casteljau split 144 + two 16-point boxes 180 + two slabs 34 + order 2
 OPS_SPLIT_GREGORY = 360 + 1130   # + Algorithm 2 bounds and Algorithm 1 crop of the lower patch
