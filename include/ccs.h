@@ -162,7 +162,9 @@ ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, con
 #define CCS_SCENE_LOCAL_FRAMES 2
 
 /* Replace the control points (same layout, same patch count and types) from device addresses,
- * asynchronously on `stream`; a following ccs_bvh_refit updates the hierarchy.  Graph-capturable. */
+ * asynchronously on `stream`; a following ccs_bvh_refit updates the hierarchy, and intersections must
+ * wait for it (before the refit, hits are undefined: the patch boxes are new, the BVH's are old).
+ * Graph-capturable. */
 ccs_status ccs_scene_update_points(ccs_scene *scene, const float *x, const float *y, const float *z, void *stream);
 
 ccs_status ccs_scene_destroy(ccs_scene *scene);

@@ -65,6 +65,7 @@ struct LaunchCfg {
 struct DevScene {
     const float4 *rec;       // n_patches records
     const float4 *nodes;     // n_nodes nodes
+    const float4 *leaf_box;  // 2 float4 per patch: (lo.xyz, 0), (hi.xyz, 0), the exact patch AABB
     uint32_t n_patches, n_nodes;
     uint32_t local;          // records hold points in local frames (Sec. 3.4)
     uint32_t width;          // BVH node width: 2 or 4
@@ -153,6 +154,6 @@ struct ccs_scene {
 namespace ccs {
 inline DevScene dev_scene(const ccs_scene *sc)
 {
-    return DevScene{sc->d_rec, sc->d_nodes, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};
+    return DevScene{sc->d_rec, sc->d_nodes, sc->d_leaf_box, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};
 }
 }  // namespace ccs

@@ -506,10 +506,11 @@ CCS_DEV void node_child_boxes(const float4 (&q)[NC], const RayG<NC> &r, float c0
 constexpr int kBvhStack = 64;
 constexpr int kDone = (int)0x80000000;    // traversal finished
 
-// BVH node stack of one thread (local memory): node index and its interval.
+// BVH node stack of one thread (local memory): node index and entry distance, one 8-byte word per
+// entry.  A patch leaf's exit distance is not kept: its pair recomputes the root interval from the
+// patch box.
 struct BvhStack {
-    int node[kBvhStack];
-    float2 t[kBvhStack];
+    int2 e[kBvhStack];
 };
 
 // ------------------------------------------------------------------------------------------------
@@ -536,7 +537,7 @@ struct Lane {
     Best best;
     uint32_t iters;
     int node;                       // BVH: >= 0 internal node, kDone, else leaf of patch ~node
-    float n0, n1;                   // interval of `node`
+    float n0;                       // entry distance of `node`
     int sp;
     bool in_pair, greg;             // Algorithm 3 on patch `pid`
     bool gpend;                     // Gregory node (path, level) still needs its (q, d): next step computes it
@@ -580,7 +581,6 @@ CCS_DEV void begin_ray(Lane<NC> &s, const DevScene &sc, float ox, float oy, floa
     s.tmax = tmax;
     s.node = 0;
     s.n0 = tmin;
-    s.n1 = tmax;
     s.in_pair = false;
     s.gpend = false;
     s.skip_level = -1;
@@ -613,11 +613,11 @@ CCS_DEV void pop_next(Lane<NC> &s, BvhStack &stk)
 {
     while (s.sp > 0) {
         --s.sp;
-        const float2 t = stk.t[s.sp];
-        if (t.x > s.best.t) continue;
-        s.node = stk.node[s.sp];
-        s.n0 = t.x;
-        s.n1 = t.y;
+        const int2 e = stk.e[s.sp];
+        const float t0 = __int_as_float(e.y);
+        if (t0 > s.best.t) continue;
+        s.node = e.x;
+        s.n0 = t0;
         return;
     }
     s.node = kDone;
@@ -889,16 +889,14 @@ template <int BW, int NC>
 __host__ __device__ constexpr int node_f4() { return BW == 2 ? NC + 1 : 2 * NC + 1; }
 
 // Order a 4-wide node's hit children by entry distance (compare-exchange network; misses carry +inf).
-CCS_DEV void cx4(float (&k)[4], float (&e)[4], int (&c)[4], int a, int b)
+CCS_DEV void cx4(float (&k)[4], int (&c)[4], int a, int b)
 {
     const bool sw = k[b] < k[a];
-    const float ka = k[a], ea = e[a];
+    const float ka = k[a];
     const int ca = c[a];
     k[a] = sw ? k[b] : ka;
-    e[a] = sw ? e[b] : ea;
     c[a] = sw ? c[b] : ca;
     k[b] = sw ? ka : k[b];
-    e[b] = sw ? ea : e[b];
     c[b] = sw ? ca : c[b];
 }
 
@@ -913,7 +911,17 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         const uint32_t pid = (uint32_t)(~s.node);
         if (s.n0 <= s.best.t) {
             if (STATS) cnt.v[7]++;
-            start_pair<MODE, NC>(s, g, sc, pid, s.n0, s.n1, G);
+            // the root interval: the slab of the patch box, as its parent's step computed it
+            float lo[NC], hi[NC], c0, c1;
+            const float4 blo = __ldg(sc.leaf_box + 2 * (size_t)pid), bhi = __ldg(sc.leaf_box + 2 * (size_t)pid + 1);
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                const int c = comp<NC>(G, k);
+                lo[k] = pick(c, blo.x, blo.y, blo.z);
+                hi[k] = pick(c, bhi.x, bhi.y, bhi.z);
+            }
+            slab<NC>(s.r, lo, hi, s.tmin, s.tmax, G, c0, c1);
+            start_pair<MODE, NC>(s, g, sc, pid, c0, c1, G);
         } else {
             pop_next<NC>(s, stk);
         }
@@ -948,7 +956,7 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
             c[2] = ch.z;
             c[3] = ch.w;
         }
-        float key[4], ex[4];
+        float key[4];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             float lo[NC], hi[NC];
@@ -961,13 +969,12 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
             slab<NC>(s.r, lo, hi, s.tmin, s.tmax, G, t0, t1);
             const bool h = t0 <= t1 && t0 <= s.best.t && c[j] != kEmptyChild;
             key[j] = h ? t0 : __int_as_float(0x7f800000);
-            ex[j] = t1;
         }
-        cx4(key, ex, c, 0, 1);
-        cx4(key, ex, c, 2, 3);
-        cx4(key, ex, c, 0, 2);
-        cx4(key, ex, c, 1, 3);
-        cx4(key, ex, c, 1, 2);
+        cx4(key, c, 0, 1);
+        cx4(key, c, 2, 3);
+        cx4(key, c, 0, 2);
+        cx4(key, c, 1, 3);
+        cx4(key, c, 1, 2);
         if (!(key[0] < __int_as_float(0x7f800000))) {
             pop_next<NC>(s, stk);
             return;
@@ -975,14 +982,12 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
 #pragma unroll
         for (int j = 3; j >= 1; --j) {   // farthest first, so that the nearer ones are popped first
             if (key[j] < __int_as_float(0x7f800000) && s.sp < kBvhStack) {
-                stk.node[s.sp] = c[j];
-                stk.t[s.sp] = make_float2(key[j], ex[j]);
+                stk.e[s.sp] = make_int2(c[j], __float_as_int(key[j]));
                 ++s.sp;
             }
         }
         s.node = c[0];
         s.n0 = key[0];
-        s.n1 = ex[0];
         return;
     }
     float4 q[NC];
@@ -1009,17 +1014,14 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     if (ha && hb) {
         const bool bfirst = b0 < a0;
         if (s.sp < kBvhStack) {
-            stk.node[s.sp] = bfirst ? c0 : c1;
-            stk.t[s.sp] = bfirst ? make_float2(a0, a1) : make_float2(b0, b1);
+            stk.e[s.sp] = make_int2(bfirst ? c0 : c1, __float_as_int(bfirst ? a0 : b0));
             ++s.sp;
         }
         s.node = bfirst ? c1 : c0;
         s.n0 = bfirst ? b0 : a0;
-        s.n1 = bfirst ? b1 : a1;
     } else if (ha || hb) {
         s.node = ha ? c0 : c1;
         s.n0 = ha ? a0 : b0;
-        s.n1 = ha ? a1 : b1;
     } else {
         pop_next<NC>(s, stk);
     }
