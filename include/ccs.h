@@ -105,6 +105,9 @@ typedef struct {
 
 #define CCS_CACHE_DEFAULT 0xFFFFFFFFu
 #define CCS_TRACE_COUNT 1u          /* accumulate traversal counters into opts->counters */
+#define CCS_TRACE_HOST_MAPPED 4u    /* ccs_intersect_host: when every plane is mapped page-locked memory,
+                                       read rays and write hits through the mapping instead of staging
+                                       copies */
 #define CCS_TRACE_ORDER 2u          /* work order: before the launch, count for sampled rays the BVH leaf
                                        boxes (candidate patches) they enter within [tmin, tmax]; the work
                                        queue then hands out tiles in descending order of their largest
@@ -185,13 +188,16 @@ ccs_status ccs_bvh_refit(ccs_scene *scene, void *stream);
 ccs_status ccs_intersect(const ccs_scene *scene, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
                          const ccs_trace_opts *opts, void *stream);
 
-/* Same answer as ccs_intersect, for rays and hits in host memory (pinned memory gives full copy
- * bandwidth and lets the copies overlap the traversal).  The rays are copied to a device staging buffer
- * owned by the scene in chunks (opts->host_chunk; at most 8).  Chunk k is traced while chunk
- * k+1 is copied in and chunk k-1's hits are copied out, on streams the scene owns and orders after the
- * work already on `stream`.  Planes that are rows of one host block (equally spaced, in the order of the
- * struct) move as one 2D copy per chunk; other planes take one copy each.  Synchronises `stream` before returning.  Not thread-safe per scene (one
- * staging buffer); not graph-capturable.  Errors: INVALID_ARG, NOT_BUILT, OOM, CUDA. */
+/* Same answer as ccs_intersect, for rays and hits in host memory.  The rays are copied to a device
+ * staging buffer owned by the scene in chunks (opts->host_chunk; at most 8).  Chunk k is traced while chunk k+1 is copied in and chunk k-1's hits are copied out, on
+ * streams the scene owns and orders after the work already on `stream`.  Planes that are rows of one
+ * host block (equally spaced, in the order of the struct) move as one 2D copy per chunk; other planes
+ * take one copy each.  With CCS_TRACE_HOST_MAPPED, when every plane is page-locked memory mapped into the
+ * device (cudaHostAlloc / cudaHostRegister; both ends of each plane are checked with
+ * cudaPointerGetAttributes), the launch instead reads the rays and writes the hits through that
+ * mapping: one launch, no staging (on Grace systems over NVLink-C2C).  Synchronises `stream` before
+ * returning.  Not thread-safe per scene (one staging
+ * buffer); not graph-capturable.  Errors: INVALID_ARG, NOT_BUILT, OOM, CUDA. */
 ccs_status ccs_intersect_host(ccs_scene *scene, const ccs_rays *host_rays, uint32_t n, ccs_hits *host_hits,
                               const ccs_trace_opts *opts, void *stream);
 

@@ -95,7 +95,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
     CCS_ARG(c.pixel_spread >= 0.0f && c.pixel_spread < 1.0f, "pixel_spread must be in [0, 1) radians per pixel");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
-    CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER)) == 0, "unknown trace flags");
+    CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER | CCS_TRACE_HOST_MAPPED)) == 0, "unknown trace flags");
     return CCS_OK;
 }
 
@@ -379,6 +379,47 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     if (cfg.pixel_spread > 0.0f) cfg.mode = 4;
     if (n == 0) return CCS_OK;
     cudaStream_t s = (cudaStream_t)stream;
+    // CCS_TRACE_HOST_MAPPED with mapped page-locked planes: the launch reads the rays and writes the hits
+    // through the host memory's device mapping (NVLink-C2C on Grace systems), as one launch with no
+    // staging copies.  Both ends of every plane must lie in one mapped allocation; anything else takes
+    // the copies.
+    auto mapped = [n](const void *p, void **dev) -> bool {
+        const size_t last = (size_t)n * 4 - 1;
+        cudaPointerAttributes a, z;
+        if (cudaPointerGetAttributes(&a, p) != cudaSuccess ||
+            cudaPointerGetAttributes(&z, static_cast<const char *>(p) + last) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return false;
+        }
+        if (a.type != cudaMemoryTypeHost || z.type != cudaMemoryTypeHost || !a.devicePointer || !z.devicePointer)
+            return false;
+        if (static_cast<char *>(z.devicePointer) - static_cast<char *>(a.devicePointer) != (ptrdiff_t)last)
+            return false;
+        *dev = a.devicePointer;
+        return true;
+    };
+    if (cfg.flags & CCS_TRACE_HOST_MAPPED) {
+        const void *in[8] = {hr->ox, hr->oy, hr->oz, hr->dx, hr->dy, hr->dz, hr->tmin, hr->tmax};
+        const void *out[4] = {hh->t, hh->u, hh->v, hh->patch_id};
+        void *din[8], *dout[4];
+        bool zc = true;
+        for (int c = 0; c < 8 && zc; ++c) zc = mapped(in[c], &din[c]);
+        for (int c = 0; c < 4 && zc; ++c) zc = mapped(out[c], &dout[c]);
+        if (zc) {
+            const DevRays dr{static_cast<const float *>(din[0]), static_cast<const float *>(din[1]),
+                             static_cast<const float *>(din[2]), static_cast<const float *>(din[3]),
+                             static_cast<const float *>(din[4]), static_cast<const float *>(din[5]),
+                             static_cast<const float *>(din[6]), static_cast<const float *>(din[7])};
+            const DevHits dh{static_cast<float *>(dout[0]), static_cast<float *>(dout[1]),
+                             static_cast<float *>(dout[2]), static_cast<uint32_t *>(dout[3])};
+            const uint32_t *perm;
+            if ((st = work_order(sc, 0, cfg, dr, n, s, &perm)) != CCS_OK) return st;
+            CCS_CUDA(launch_intersect(dev_scene(sc), dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, s,
+                                      perm));
+            CCS_CUDA(cudaStreamSynchronize(s));
+            return CCS_OK;
+        }
+    }
     const size_t need = (size_t)n * 12 * sizeof(float);
     if (need > sc->stage_bytes) {
         CCS_CUDA(cudaStreamSynchronize(s));
@@ -393,23 +434,31 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
             CCS_CUDA(cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
         for (cudaEvent_t &e : sc->pipe_ev) CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    // Pipeline over chunks of about host_chunk rays (at most 8): chunk k's rays are copied in while
-    // chunk k-1 is traced and chunk k-2's hits are copied out.  Consecutive chunks alternate between the
-    // caller's stream and a second compute stream, each with its own queue head, so that one chunk's
-    // launch fills the SMs that the previous one frees while its last rays finish.  Chunks stay large:
-    // every launch ends on its slowest rays, and smaller chunks pay that drain more often than they
-    // save in exposed copy time.
-    // default: chunks of 2^20 rays, and at least two once there are 2^17 rays (measured on the 1080p
-    // primary batch and its 0.33 M diffuse rays: two chunks beat one by 7% and 10%)
-    const uint64_t per = cfg.host_chunk ? cfg.host_chunk : (1u << 20);
-    uint32_t chunks = (uint32_t)std::min<uint64_t>(8, ((uint64_t)n + per - 1) / per);
-    if (!cfg.host_chunk && n >= (1u << 17) && chunks < 2) chunks = 2;
+    // Pipeline over chunks: chunk k's rays are copied in while chunk k-1 is traced and chunk k-2's hits
+    // are copied out.  Consecutive chunks alternate between the caller's stream and a second compute
+    // stream, each with its own queue head, so that one chunk's launch fills the SMs that the previous
+    // one frees while its last rays finish.  Chunks stay large: every launch ends on its slowest rays,
+    // and many small chunks pay that drain more often than they save in exposed copy time.
+    // Chunk boundaries (at most 8 chunks).  Given host_chunk: equal chunks of that size.  Default: a short
+    // first and last chunk (n/8, at most 2^18 rays), so that little copy time is exposed before the first
+    // launch and after the last one, and middle chunks of about 2^20 rays; below 2^17 rays, one chunk.
+    size_t cut[9];
+    uint32_t chunks;
+    if (cfg.host_chunk || n < (1u << 17)) {
+        const uint64_t per = cfg.host_chunk ? cfg.host_chunk : (uint64_t)n;
+        chunks = (uint32_t)std::min<uint64_t>(8, ((uint64_t)n + per - 1) / per);
+        for (uint32_t k = 0; k <= chunks; ++k) cut[k] = (size_t)n * k / chunks;
+    } else {
+        const size_t ramp = std::min<size_t>(n / 8, 1u << 18), middle = n - 2 * ramp;
+        const uint32_t mid = (uint32_t)std::min<size_t>(6, std::max<size_t>(1, (middle + (1u << 20) - 1) >> 20));
+        chunks = mid + 2;
+        cut[0] = 0;
+        for (uint32_t k = 0; k <= mid; ++k) cut[k + 1] = ramp + middle * k / mid;
+        cut[chunks] = n;
+    }
     // chunk boundaries of an image fall on rows of 8-pixel tiles, so that each chunk is an image too
     const size_t align = (cfg.flags & CCS_TRACE_ORDER) && cfg.image_width ? (size_t)cfg.image_width * 8 : 1;
-    auto bound = [&](uint32_t k) -> size_t {
-        const size_t b = (size_t)n * k / chunks;
-        return k == chunks ? (size_t)n : b / align * align;
-    };
+    auto bound = [&](uint32_t k) -> size_t { return k == chunks ? (size_t)n : cut[k] / align * align; };
     cudaEvent_t *ev_in = sc->pipe_ev, *ev_hit = sc->pipe_ev + 8, ev_start = sc->pipe_ev[16], ev_out = sc->pipe_ev[17];
     CCS_CUDA(cudaEventRecord(ev_start, s));
     for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));

@@ -55,7 +55,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
            'printf("rays %zu\\n", sizeof(ccs_rays));', 'printf("hits %zu\\n", sizeof(ccs_hits));',
            'printf("trial %zu\\n", sizeof(ccs_autotune_trial));',
            'printf("NUM_COUNTERS %d\\n", CCS_NUM_COUNTERS);', 'printf("TRACE_COUNT %u\\n", CCS_TRACE_COUNT);',
-           'printf("TRACE_ORDER %u\\n", CCS_TRACE_ORDER);', 'printf("CACHE_DEFAULT %u\\n", CCS_CACHE_DEFAULT);']
+           'printf("TRACE_ORDER %u\\n", CCS_TRACE_ORDER);', 'printf("CACHE_DEFAULT %u\\n", CCS_CACHE_DEFAULT);',
+           'printf("TRACE_HOST_MAPPED %u\\n", CCS_TRACE_HOST_MAPPED);']
     src += [f'printf("off_{f} %zu\\n", offsetof(ccs_trace_opts, {f}));' for f in fields]
     src += ["return 0; }"]
     c = tmp_path / "layout.c"
@@ -73,4 +74,5 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     assert int(got["NUM_COUNTERS"]) == ccs.CCS_NUM_COUNTERS == len(ccs.COUNTER_NAMES)
     assert int(got["TRACE_COUNT"]) == ccs.CCS_TRACE_COUNT
     assert int(got["TRACE_ORDER"]) == ccs.CCS_TRACE_ORDER
+    assert int(got["TRACE_HOST_MAPPED"]) == ccs.CCS_TRACE_HOST_MAPPED
     assert int(got["CACHE_DEFAULT"]) == ccs.CCS_CACHE_DEFAULT

@@ -323,3 +323,28 @@ def test_counters_count_the_work():
         assert c["pairs"] > 1000 and c["leaves"] > 500
         assert abs(c[key] - exp) <= 0.01 * exp, (p, c, exp)
         sc.close()
+
+
+@pytest.mark.parametrize("layout", ["mapped", "page_locked_copies", "one_plane_pageable"])
+def test_host_path_on_page_locked_memory(layout):
+    """With CCS_TRACE_HOST_MAPPED, page-locked planes are read and written by the launch through their
+    device mapping; without it, or with one pageable plane among them, the copy pipeline runs.  All give
+    the device path's hits."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(1920, 1080).subset(np.arange(1920 * 900 + 11))
+    sc = ccs.Scene(s.P, s.types, local=True)
+    kw = dict(order=True, image_width=1920)
+    g = ccs.hits_to_numpy(ccs.intersect(sc, ccs.rays_to_device(r.soa()), ccs.make_opts(**kw)))
+    torch.cuda.synchronize()
+    rays = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in r.soa()]
+    out = [torch.full((r.n,), -7.0).pin_memory() for _ in range(4)]
+    if layout == "one_plane_pageable":
+        rays[3] = torch.from_numpy(np.ascontiguousarray(r.soa()[3]))
+    opts = ccs.make_opts(host_mapped=layout != "page_locked_copies", **kw)
+    for _ in range(2):
+        ccs.ccs_intersect_host(sc.handle, rays, r.n, out, opts)
+        got = dict(t=out[0].numpy(), u=out[1].numpy(), v=out[2].numpy(), pid=out[3].numpy().view(np.uint32))
+        for k in ("t", "u", "v", "pid"):
+            assert np.array_equal(got[k], g[k]), (layout, k)
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    sc.close()
