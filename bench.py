@@ -410,6 +410,48 @@ def run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p):
     return out
 
 
+def run_large(args, dev, stream, flush):
+    """The 393,216-patch cube-sphere (128 x 128 quads per face, noise 0.1, 5 octaves) with 3840 x 2160
+    primary rays and their diffuse rays, tuned, on binary and on 4-wide BVHs: MRays/s and BVH nodes per
+    ray (Sec. 4: larger models are dominated by the traversal of the hierarchy)."""
+    import torch
+    from paper_1811_03510_gb300 import ccs, scenegen as sg
+    s = sg.config_scene(3)
+    cam = sg.pinhole_rays(3840, 2160)
+    prim = ccs.rays_to_device(cam.soa(), dev)
+    out = {"patches": int(s.n), "primary_rays": cam.n}
+    for width in (2, 4):
+        sc = ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=width)
+        hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
+        d = ccs.gen_diffuse(sc, prim, hp, seed=1, leaf_depth=8, offset_abs=1e-4, stream=stream)
+        torch.cuda.synchronize()
+        act = (d[7] >= d[6]).nonzero().squeeze(1)
+        diff = [p.index_select(0, act).contiguous() for p in d]
+        res = {}
+        for name, rays, n, iw in (("primary", prim, cam.n, 3840), ("diffuse", diff, int(act.numel()), 0)):
+            h = ccs.alloc_hits(n, dev)
+            best, _, _ = ccs.ccs_autotune(sc.handle, rays, n, h, ccs.make_opts(image_width=iw), reps=1, stream=stream)
+            tot = 0.0
+            for k in range(max(3, args.steps // 4)):
+                flush.fill_(float(k))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ccs.ccs_intersect(sc.handle, rays, n, h, best, stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                tot += e0.elapsed_time(e1) / 1e3
+            c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+            ccs.ccs_intersect(sc.handle, rays, n, h, ccs.make_opts(counters=c), stream)
+            torch.cuda.synchronize()
+            cc = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
+            res[name + "_mrays_s"] = n * max(3, args.steps // 4) / tot / 1e6
+            res[name + "_bvh_nodes_per_ray"] = cc["bvh_nodes"] / n
+        res["diffuse_rays"] = int(act.numel())
+        out[f"bvh{width}"] = res
+        sc.close()
+    return out
+
+
 def run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush):
     """The same rays with sub-domain boxes in world axes and in each patch's frame (Sec. 3.4), default
     launch options for both: MRays/s and subdivision steps."""
@@ -745,6 +787,7 @@ def main():
         res["shadow"] = run_shadow(args, dev, stream, flush)
         res["screen_space"] = run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p)
         res["frames"] = run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush)
+        res["large_scene"] = run_large(args, dev, stream, flush)
     if rank == 0 and not args.no_cpu_baseline:
         # the FP64 oracle on all host cores over the same step, repeated until about 10 s of CPU work
         import oracle
