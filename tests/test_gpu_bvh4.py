@@ -121,3 +121,26 @@ def test_four_wide_batches_and_mixed_widths():
                                   ccs.make_opts())
     for h in two + four:
         h.close()
+
+
+def test_four_wide_trace_export_runs_and_keeps_the_hits():
+    """The trace export (a pair's features and its best leaf's depth-3 cell) on a 4-wide BVH: same hits as
+    the binary tree, one exported row per pair that found a leaf, labels within the 64 depth-3 cells."""
+    s = sg.config_scene(2)
+    r = sg.random_rays(20000, seed=64)
+    two = ccs.Scene(s.P, s.types)
+    four = ccs.Scene(s.P, s.types, bvh_width=4)
+    rays = ccs.rays_to_device(r.soa())
+    hits = ccs.alloc_hits(r.n)
+    cap = 4 * r.n
+    feat = torch.zeros(cap, 24, device="cuda")
+    lab = torch.zeros(cap, dtype=torch.uint8, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ccs.ccs_trace_export(four.handle, rays, r.n, hits, ccs.make_opts(), feat, lab, cap, cnt)
+    torch.cuda.synchronize()
+    same(ccs.hits_to_numpy(hits), run(two, r), "export")
+    k = int(cnt.item())
+    assert k >= int((ccs.hits_to_numpy(hits)["pid"] != MISS).sum()) > 500
+    assert (lab[:k].cpu().numpy() < 64).all() and torch.isfinite(feat[:k]).all()
+    two.close()
+    four.close()
