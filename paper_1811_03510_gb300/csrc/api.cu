@@ -164,8 +164,8 @@ ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, con
         sc->hy.resize(np);
         sc->hz.resize(np);
         sc->htypes.resize(n_patches);
-        if ((e = cudaMalloc(&sc->d_work, 64)) != cudaSuccess) break;
-        if ((e = cudaMemsetAsync(sc->d_work, 0, 64, s)) != cudaSuccess) break;
+        if ((e = cudaMalloc(&sc->d_work, kWorkWords * sizeof(uint32_t))) != cudaSuccess) break;
+        if ((e = cudaMemsetAsync(sc->d_work, 0, kWorkWords * sizeof(uint32_t), s)) != cudaSuccess) break;
         if (n_patches) {
             const cudaMemcpyKind k = device_ptrs ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
             if ((e = cudaMemcpy(sc->hx.data(), x, np * 4, k)) != cudaSuccess) break;
@@ -309,7 +309,8 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     const uint32_t *perm;
     if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream, perm));
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
+                              (cudaStream_t)stream, perm));
     return CCS_OK;
 }
 
@@ -335,7 +336,8 @@ ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t 
     DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
+                              (cudaStream_t)stream));
     return CCS_OK;
 }
 
@@ -360,7 +362,8 @@ ccs_status ccs_intersect_learned(const ccs_scene *sc, const ccs_proposal *prop, 
     DevScene ds = dev_scene(sc);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream));
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
+                              (cudaStream_t)stream));
     return CCS_OK;
 }
 
@@ -414,7 +417,7 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
                              static_cast<float *>(dout[2]), static_cast<uint32_t *>(dout[3])};
             const uint32_t *perm;
             if ((st = work_order(sc, 0, cfg, dr, n, s, &perm)) != CCS_OK) return st;
-            CCS_CUDA(launch_intersect(dev_scene(sc), dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, s,
+            CCS_CUDA(launch_intersect(dev_scene(sc), dr, dh, n, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, s,
                                       perm));
             CCS_CUDA(cudaStreamSynchronize(s));
             return CCS_OK;
@@ -502,8 +505,8 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
                          reinterpret_cast<uint32_t *>(b + 11 * (size_t)n + a)};
         const uint32_t *perm;
         if ((st = work_order(sc, (int)(k & 1), cfg, dr, (uint32_t)m, cs, &perm)) != CCS_OK) return st;
-        CCS_CUDA(launch_intersect(ds, dr, dh, (uint32_t)m, cfg, sc->d_work + ((k & 1) ? 2 : 0), sc->d_work + 1,
-                                  sc->num_sms, cs, perm));
+        CCS_CUDA(launch_intersect(ds, dr, dh, (uint32_t)m, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, cs,
+                                  perm));
         CCS_CUDA(cudaEventRecord(ev_hit[k], cs));
         CCS_CUDA(cudaStreamWaitEvent(sc->pipe_d2h, ev_hit[k], 0));
         if (out_pitch && cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + a * 4, out_pitch, b + (size_t)8 * n + a,
@@ -586,7 +589,8 @@ ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, u
     DevHits dh{nullptr, nullptr, nullptr, nullptr};
     const uint32_t *perm;
     if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
-    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, sc->d_work, sc->d_work + 1, sc->num_sms, (cudaStream_t)stream, perm));
+    CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
+                              (cudaStream_t)stream, perm));
     return CCS_OK;
 }
 

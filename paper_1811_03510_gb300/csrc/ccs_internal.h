@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -139,7 +140,8 @@ struct ccs_scene {
     uint32_t bvh_width = 2;            // node width of the built BVH
     bool built = false;
     bool local = false;                // CCS_SCENE_LOCAL_FRAMES
-    uint32_t *d_work = nullptr;        // [0] work queue head, [1] device status word, [2] second queue head
+    uint32_t *d_work = nullptr;        // [1] device status word; [kQueueBase + k] ring of work-queue heads
+    std::atomic<uint32_t> next_queue{0};   // next ring slot: launches in flight at once use different heads
     // host-buffer path: staging planes and the copy/compute pipeline (created on first use)
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
@@ -152,6 +154,14 @@ struct ccs_scene {
 };
 
 namespace ccs {
+// The scene's work words: the status word, then a ring of queue heads.  Every launch takes the next
+// head, so launches on different streams (or the host path's two compute streams) do not share one.
+constexpr int kQueueBase = 16, kQueueRing = 48, kWorkWords = kQueueBase + kQueueRing;
+inline uint32_t *take_queue(ccs_scene *sc)
+{
+    return sc->d_work + kQueueBase + sc->next_queue.fetch_add(1, std::memory_order_relaxed) % kQueueRing;
+}
+
 inline DevScene dev_scene(const ccs_scene *sc)
 {
     return DevScene{sc->d_rec, sc->d_nodes, sc->d_leaf_box, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};

@@ -348,3 +348,27 @@ def test_host_path_on_page_locked_memory(layout):
             assert np.array_equal(got[k], g[k]), (layout, k)
     assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
     sc.close()
+
+
+def test_concurrent_launches_on_one_scene_use_separate_queues():
+    """Two launches on one scene at the same time on two streams (each takes its own work-queue head)
+    give the hits each gives alone."""
+    s = sg.config_scene(2)
+    sc = ccs.Scene(s.P, s.types, local=True)
+    ra, rb = sg.pinhole_rays(960, 540), sg.random_rays(200000, seed=91)
+    da, db = ccs.rays_to_device(ra.soa()), ccs.rays_to_device(rb.soa())
+    ref_a = ccs.hits_to_numpy(ccs.intersect(sc, da, ccs.make_opts()))
+    ref_b = ccs.hits_to_numpy(ccs.intersect(sc, db, ccs.make_opts()))
+    torch.cuda.synchronize()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    for _ in range(3):
+        ha, hb = ccs.alloc_hits(ra.n), ccs.alloc_hits(rb.n)
+        torch.cuda.synchronize()
+        ccs.ccs_intersect(sc.handle, da, ra.n, ha, ccs.make_opts(), s1)
+        ccs.ccs_intersect(sc.handle, db, rb.n, hb, ccs.make_opts(), s2)
+        torch.cuda.synchronize()
+        for got, ref in ((ccs.hits_to_numpy(ha), ref_a), (ccs.hits_to_numpy(hb), ref_b)):
+            for k in ("t", "u", "v", "pid"):
+                assert np.array_equal(got[k], ref[k]), k
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    sc.close()
