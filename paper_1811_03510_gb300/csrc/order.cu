@@ -257,9 +257,9 @@ static OrderGeom order_geom(uint32_t n, uint32_t w)
 {
     OrderGeom g{};
     g.n = n;
-    g.w = w;
-    g.h = (uint32_t)(((uint64_t)n + w - 1) / w);
-    g.tiles_x = (w + S::TW - 1) / S::TW;
+    g.w = w < n ? w : n;   // a width beyond the batch is one partial row of n rays
+    g.h = (uint32_t)(((uint64_t)n + g.w - 1) / g.w);
+    g.tiles_x = (g.w + S::TW - 1) / S::TW;
     g.n_tiles = (uint32_t)((uint64_t)g.tiles_x * ((g.h + S::TH - 1) / S::TH));
     return g;
 }

@@ -51,10 +51,10 @@ def test_image_order_keeps_every_hit(local):
     sc.close()
 
 
-@pytest.mark.parametrize("w,n", [(333, 333 * 77 + 100), (37, 37 * 5), (1, 1000), (4096, 5000), (64, 63)])
+@pytest.mark.parametrize("w,n", [(333, 333 * 77 + 100), (37, 37 * 5), (1, 1000), (4096, 5000), (64, 63), (1 << 30, 1000)])
 def test_ragged_images_and_tiny_batches(w, n):
     """Widths not a multiple of the tile, a partial last row, one-pixel-wide images, fewer rays than one
-    row or one tile."""
+    row or one tile, and a width far beyond the batch (one partial row)."""
     s = sg.make_scene(8, 0.05, 3, 1, gregory_ring=True)
     r = sg.random_rays(n, seed=w + n, target=1.0)
     sc = ccs.Scene(s.P, s.types, local=True)
