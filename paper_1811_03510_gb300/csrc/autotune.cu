@@ -67,7 +67,7 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> threads_c = {64, 96, 128};
     const std::vector<uint32_t> lanes_c = {1, 3};
     const std::vector<uint32_t> bps_c = {1, 2, 3, 4, 5, 6};
-    const std::vector<uint32_t> refill_c = {1, 2, 4, 8, 16};
+    const std::vector<uint32_t> refill_c = {1, 2, 4, 8, 16, 24};
     const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
     const std::vector<uint32_t> cache_c = {0, 2};
