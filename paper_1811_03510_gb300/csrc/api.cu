@@ -10,6 +10,7 @@
 
 #include "bvh_build.h"
 #include "ccs_internal.h"
+#include "host_plan.h"
 
 namespace ccs {
 
@@ -441,27 +442,12 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     // are copied out.  Consecutive chunks alternate between the caller's stream and a second compute
     // stream, each with its own queue head, so that one chunk's launch fills the SMs that the previous
     // one frees while its last rays finish.  Chunks stay large: every launch ends on its slowest rays,
-    // and many small chunks pay that drain more often than they save in exposed copy time.
-    // Chunk boundaries (at most 8 chunks).  Given host_chunk: equal chunks of that size.  Default: a short
-    // first and last chunk (n/8, at most 2^18 rays), so that little copy time is exposed before the first
-    // launch and after the last one, and middle chunks of about 2^20 rays; below 2^17 rays, one chunk.
-    size_t cut[9];
-    uint32_t chunks;
-    if (cfg.host_chunk || n < (1u << 17)) {
-        const uint64_t per = cfg.host_chunk ? cfg.host_chunk : (uint64_t)n;
-        chunks = (uint32_t)std::min<uint64_t>(8, ((uint64_t)n + per - 1) / per);
-        for (uint32_t k = 0; k <= chunks; ++k) cut[k] = (size_t)n * k / chunks;
-    } else {
-        const size_t ramp = std::min<size_t>(n / 8, 1u << 18), middle = n - 2 * ramp;
-        const uint32_t mid = (uint32_t)std::min<size_t>(6, std::max<size_t>(1, (middle + (1u << 20) - 1) >> 20));
-        chunks = mid + 2;
-        cut[0] = 0;
-        for (uint32_t k = 0; k <= mid; ++k) cut[k + 1] = ramp + middle * k / mid;
-        cut[chunks] = n;
-    }
-    // chunk boundaries of an image fall on rows of 8-pixel tiles, so that each chunk is an image too
+    // and many small chunks pay that drain more often than they save in exposed copy time.  An image's
+    // chunk boundaries fall on rows of 8-pixel tiles, so that each chunk is an image too.
     const size_t align = (cfg.flags & CCS_TRACE_ORDER) && cfg.image_width ? (size_t)cfg.image_width * 8 : 1;
-    auto bound = [&](uint32_t k) -> size_t { return k == chunks ? (size_t)n : cut[k] / align * align; };
+    size_t cut[kHostMaxChunks + 1];
+    const uint32_t chunks = host_chunk_plan(n, cfg.host_chunk, align, cut);
+    auto bound = [&](uint32_t k) -> size_t { return cut[k]; };
     cudaEvent_t *ev_in = sc->pipe_ev, *ev_hit = sc->pipe_ev + 8, ev_start = sc->pipe_ev[16], ev_out = sc->pipe_ev[17];
     CCS_CUDA(cudaEventRecord(ev_start, s));
     for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));
