@@ -159,8 +159,8 @@ def schedule_summary(c: dict, lanes_per_ray: int) -> dict:
 def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("traverse.cuh", "intersect_impl.cuh", "intersect.cu", "intersect4.cu", "order.cu", "learned.cuh",
-              "ccs_internal.h"):
+    for f in ("traverse.cuh", "intersect_impl.cuh", "intersect.cu", "intersect4.cu", "order.cu", "order_plan.h",
+              "learned.cuh", "ccs_internal.h"):
         with open(os.path.join(ROOT, "paper_1811_03510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -11,47 +11,11 @@
 #include <cuda_runtime.h>
 
 #include "ccs_internal.h"
+#include "order_plan.h"
 
 namespace ccs {
 
-constexpr int kOrderKeys = 16;     // cost classes: candidate patches, clamped to 15
-constexpr int kOrderThreads = 256; // threads per block of the estimate and placement kernels
 constexpr int kOrderStack = 64;
-
-struct OrderGeom {
-    uint32_t n, w, h, tiles_x, n_tiles;
-};
-
-// Tile shape and samples: TW x TH rays, every SX-th ray in x from SX / 2 and every SY-th in y from SY / 2.
-template <int TW_, int TH_, int SX_, int SY_>
-struct Shape {
-    static constexpr uint32_t TW = TW_, TH = TH_, SX = SX_, SY = SY_;
-    static constexpr uint32_t NX = (TW + SX - 1 - SX / 2) / SX, NY = (TH + SY - 1 - SY / 2) / SY;
-    static constexpr uint32_t SPT = NX * NY;                  // samples per tile, a divisor of 32
-    static constexpr uint32_t TPB = kOrderThreads / SPT;      // tiles per block
-    static_assert(32 % SPT == 0, "a tile's samples share a warp");
-};
-using ImageShape = Shape<8, 8, 4, 4>;
-using RunShape = Shape<32, 1, 4, 1>;
-
-__host__ __device__ inline uint32_t row_len(const OrderGeom &g, uint32_t y) { return y + 1 < g.h ? g.w : g.n - y * g.w; }
-
-// Rays of the tile at (x0, y0): its rows are full (min(TW, w - x0)) except the image's last row.
-template <class S>
-__device__ inline uint32_t tile_size(const OrderGeom &g, uint32_t x0, uint32_t y0)
-{
-    const uint32_t row = g.w - x0 < S::TW ? g.w - x0 : S::TW;
-    uint32_t s = 0;
-#pragma unroll
-    for (uint32_t dy = 0; dy < S::TH; ++dy) {
-        const uint32_t y = y0 + dy;
-        if (y < g.h) {
-            const uint32_t len = row_len(g, y);
-            s += x0 >= len ? 0u : (len - x0 < row ? len - x0 : row);
-        }
-    }
-    return s;
-}
 
 // Candidate patches of one ray: the BVH leaves it enters within [t0, t1] (every one, with no pruning by
 // a closest hit; counting whole subtrees instead of their leaves ranks the tiles clearly worse).  Binary
@@ -124,12 +88,9 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_estimate(OrderGeom g, c
 {
     const uint32_t tile = blockIdx.x * S::TPB + threadIdx.x / S::SPT, smp = threadIdx.x % S::SPT;
     const uint32_t tx = tile % g.tiles_x, ty = tile / g.tiles_x;
-    uint32_t c = 0;
+    uint32_t c = 0, j;
     if (tile < g.n_tiles) {
-        const uint32_t x = tx * S::TW + S::SX / 2 + (smp % S::NX) * S::SX;
-        const uint32_t y = ty * S::TH + S::SY / 2 + (smp / S::NX) * S::SY;
-        if (y < g.h && x < row_len(g, y)) {
-            const uint32_t j = y * g.w + x;
+        if (tile_sample<S>(g, tile, smp, &j)) {
             c = count_candidates(nodes, n_nodes, width, __ldg(r.ox + j), __ldg(r.oy + j), __ldg(r.oz + j),
                                  __ldg(r.dx + j), __ldg(r.dy + j), __ldg(r.dz + j), __ldg(r.tmin + j),
                                  __ldg(r.tmax + j));
@@ -243,29 +204,11 @@ __global__ void __launch_bounds__(kOrderThreads) k_order_place(OrderGeom g, cons
     const uint32_t first = blockIdx.x * S::TPB;
     const uint32_t tiles = g.n_tiles - first < S::TPB ? g.n_tiles - first : S::TPB;
     for (uint32_t e = t; e < tiles * kPerTile; e += kOrderThreads) {
-        const uint32_t lt = e / kPerTile, l = e % kPerTile;
-        const uint32_t ly = l / S::TW, lx = l % S::TW;
-        const uint32_t x0 = tx0[lt], y = ty0[lt] + ly, x = x0 + lx;
-        if (y >= g.h || x >= row_len(g, y)) continue;
-        const uint32_t row = g.w - x0 < S::TW ? g.w - x0 : S::TW;
-        perm[tpos[lt] + ly * row + lx] = y * g.w + x;
+        const uint32_t lt = e / kPerTile;
+        uint32_t j, off;
+        if (tile_entry<S>(g, tx0[lt], ty0[lt], e % kPerTile, &j, &off)) perm[tpos[lt] + off] = j;
     }
 }
-
-template <class S>
-static OrderGeom order_geom(uint32_t n, uint32_t w)
-{
-    OrderGeom g{};
-    g.n = n;
-    g.w = w < n ? w : n;   // a width beyond the batch is one partial row of n rays
-    g.h = (uint32_t)(((uint64_t)n + g.w - 1) / g.w);
-    g.tiles_x = (g.w + S::TW - 1) / S::TW;
-    g.n_tiles = (uint32_t)((uint64_t)g.tiles_x * ((g.h + S::TH - 1) / S::TH));
-    return g;
-}
-
-template <class S>
-static uint32_t order_blocks(const OrderGeom &g) { return (g.n_tiles + S::TPB - 1) / S::TPB; }
 
 size_t order_scratch_words(uint32_t n, uint32_t image_width)
 {
