@@ -805,12 +805,12 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
                        const Scratch &scr, Counters &cnt, const ModeCtx &mc, const Grp &G)
 {
     if (MODE == kModeLearned && s.phase == kPhasePropose) return kStepNone;   // waits for the network round
-    if (s.gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level)
+    if (s.gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level), then
+                     // its split in the same step: a Gregory ray advances one level per warp iteration
         float u0, u1, v0, v1;
         node_domain(s.path, s.level, L, u0, u1, v0, v1);
         gregory_node<NC>(rec_of(sc, s.pid), u0, u1, v0, v1, s.level, G, g, s.d);
         s.gpend = false;
-        return kStepGregory;
     }
     const bool redesc = s.rd_target >= 0;
     const bool directed = MODE == kModeLearned && s.phase == kPhaseDirected;
@@ -1064,7 +1064,9 @@ CCS_DEV int lane_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
     if (s.in_pair) {
         if (s.iters == 0) return kStepCap;
         --s.iters;
+        const bool bound = s.gpend;
         kind = pair_step<STATS, K, MODE, NC>(s, g, stk, sc, L, scr, cnt, mc, G);
+        if (bound && kind == kStepSplit) kind = kStepGregory;   // a Gregory bound and its split
     } else {
         kind = kStepBvh;
         for (int k = 0; k < burst && !s.in_pair && s.node != kDone; ++k) {
