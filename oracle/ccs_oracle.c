@@ -10,14 +10,14 @@
  *
  * What it computes.  The method does not solve the ray/surface equation; it returns the entry
  * distance of the closest hit leaf bounding box of the hierarchy of (u,v) sub-domains (Sec. 3,
- * Sec. 3.3: "intersecting only bounding boxes is sufficient").  This oracle computes exactly that
+ * Sec. 3.3: testing bounding boxes alone suffices).  This oracle computes exactly that
  * answer in FP64, with an explicit stack in place of the paper's bit trails:
  *   - domains split alternately along u and v, starting with u (Sec. 3.3; Algorithm 3), leaf depth L
  *     splits per axis, i.e. 2L tree levels;
  *   - Bezier node control points are the de Casteljau halves of the parent's (Sec. 3.1);
  *   - Gregory nodes recompute (q, d) = calcPointsAndD(p_org, D) on their own domain D (Algorithm 2,
  *     with Algorithm 1 for the crop), and their children are the de Casteljau halves of q with the
- *     upper corner raised by d (Sec. 3.3, "maximum displacement determined on the coarser scale");
+ *     upper corner raised by d (Sec. 3.3: the displacement bound comes from the coarser level);
  *   - the ray interval of a node is its box's slab interval intersected with its parent's interval,
  *     which makes the boxes nested, so the answer does not depend on traversal order;
  *   - both children are tested, the nearer one is descended first, ties go to the lower half
