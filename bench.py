@@ -728,7 +728,7 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ov.append(e0.elapsed_time(e1) / 1e3)
-    overlapped = rays_per_step * args.steps / sum(ov) / 1e6
+    overlapped = whole_job_rate(rays_per_step, args.steps, max_over_ranks(sum(ov), dev), world)
 
     # end to end through the host-buffer entry point: pinned host rays in, hits out, every step
     # each batch's ray planes are the rows of one pinned block, and so are its hit planes
@@ -752,7 +752,7 @@ def main():
             ccs.ccs_intersect_host(scene.handle, host_p, n_prim, out_p, op, stream)
             ccs.ccs_intersect_host(scene.handle, host_d, n_diff, out_d, od, stream)
             te.append(time.perf_counter() - t0)
-        e2e[name] = rays_per_step * world * args.steps / sum(te) / 1e6
+        e2e[name] = whole_job_rate(rays_per_step, args.steps, max_over_ranks(sum(te), dev), world)
     e2e_value = e2e["staged_copies"]
 
     traffic, traffic_src = measured_traffic()
