@@ -203,6 +203,9 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
               counters=None, pixel_spread=0.0, order=False, image_width=0, host_chunk=0,
               host_mapped=False) -> ccs_trace_opts:
+    """ccs_trace_opts with the fields of include/ccs.h (0: the library's default).  counters: a device
+    int64 tensor of CCS_NUM_COUNTERS entries (sets CCS_TRACE_COUNT); order: CCS_TRACE_ORDER over tiles of
+    an image of width image_width (0: runs of 32 rays); host_mapped: CCS_TRACE_HOST_MAPPED."""
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
