@@ -101,3 +101,27 @@ def test_full_size_local_frames_sampled(big):
     compare(ccs.hits_to_numpy(hs), oracle.intersect(s.P, s.types, sr, L=8, flags=True, local=True), 8,
             max_flagged_frac=0.2)
     sc.close()
+
+
+def test_full_size_four_wide_bvh_and_work_order_equal_binary(big):
+    """The 3840 x 2160 primary launch on the 393,216-patch scene, local frames: a 4-wide BVH (19-level
+    binary tree collapsed) and the work order over the image's tiles give the binary launch's hits bit
+    for bit."""
+    s, _ = big
+    cam = sg.pinhole_rays(3840, 2160)
+    rays = ccs.rays_to_device(cam.soa())
+    out = {}
+    for width in (2, 4):
+        sc = ccs.Scene(s.P, s.types, local=True, bvh_width=width)
+        for order in (False, True):
+            hits = ccs.alloc_hits(cam.n)
+            ccs.ccs_intersect(sc.handle, rays, cam.n, hits, ccs.make_opts(order=order, image_width=3840))
+            torch.cuda.synchronize()
+            assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+            out[(width, order)] = ccs.hits_to_numpy(hits)
+        sc.close()
+    ref = out[(2, False)]
+    assert (ref["pid"] != MISS).mean() > 0.1
+    for key, g in out.items():
+        for k in ("t", "u", "v", "pid"):
+            assert np.array_equal(g[k], ref[k]), (key, k)
