@@ -55,8 +55,13 @@ def parse():
     ap.add_argument("--height", type=int, default=1080)
     ap.add_argument("--boxes", default="local", choices=["local", "world"],
                     help="sub-domain boxes in each patch's frame (Sec. 3.4) or in world axes")
-    ap.add_argument("--bvh-width", type=int, default=2, choices=[2, 4], help="children per BVH node")
+    ap.add_argument("--bvh-width", default="both", choices=["2", "4", "both"],
+                    help="children per BVH node; both: the binary and the 4-wide tree, the tuner picks per batch")
     return ap.parse_args()
+
+
+def bvh_arg(args):
+    return "both" if args.bvh_width == "both" else int(args.bvh_width)
 
 
 def dist_env():
@@ -238,7 +243,8 @@ def run_batched(args, dev, stream, world):
     from paper_1811_03510_gb300 import ccs, scenegen as sg
     sizes = sg.batched_sizes()
     scenes = [sg.make_scene(n, 0.0, name=f"n={n}") for n in sizes]
-    handles = [ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=args.bvh_width) for s in scenes]
+    one = 2 if args.bvh_width == "both" else int(args.bvh_width)   # batches need one tree per scene
+    handles = [ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=one) for s in scenes]
     cam = sg.pinhole_rays(512, 512)
     prim = ccs.rays_to_device(cam.soa(), dev)
     opts = ccs.make_opts(leaf_depth=8)
@@ -340,7 +346,7 @@ def run_shadow(args, dev, stream, flush):
     ldir = np.array(LIGHT) / np.linalg.norm(LIGHT)
     P = np.concatenate([big.P, (small.P.astype(np.float64) * 0.35 + 1.6 * ldir).astype(np.float32)])
     T = np.concatenate([big.types, small.types])
-    sc = ccs.Scene(P, T, local=args.boxes == "local", bvh_width=args.bvh_width)
+    sc = ccs.Scene(P, T, local=args.boxes == "local", bvh_width=bvh_arg(args))
     cam = sg.pinhole_rays(args.width, args.height)
     prim = ccs.rays_to_device(cam.soa(), dev)
     hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
@@ -459,7 +465,7 @@ def run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush):
     from paper_1811_03510_gb300 import ccs
     out = {}
     for name, local in (("world", False), ("local", True)):
-        sc = ccs.Scene(s.P, s.types, local=local, bvh_width=args.bvh_width)
+        sc = ccs.Scene(s.P, s.types, local=local, bvh_width=bvh_arg(args))
         res = {}
         for kind, rays, n in (("primary", prim, n_prim), ("diffuse", diff, n_diff)):
             hits = ccs.alloc_hits(n, dev)
@@ -504,7 +510,7 @@ def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     cam_d = ccs.rays_to_device(cam.soa(), dev)
     for seed in range(2, 2 + args.train_seeds):
         st = sg.config_scene(2, seed=seed)
-        sct = ccs.Scene(st.P, st.types, local=args.boxes == "local", bvh_width=args.bvh_width)
+        sct = ccs.Scene(st.P, st.types, local=args.boxes == "local", bvh_width=bvh_arg(args))
         hp = ccs.alloc_hits(cam.n, dev)
         room = cap - n_tr
         if room <= 0:
@@ -623,7 +629,7 @@ def main():
             print(json.dumps(res), flush=True)
         return
     s, r = build_workload(args.width, args.height)
-    scene = ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=args.bvh_width)
+    scene = ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=bvh_arg(args))
     prim = ccs.rays_to_device(r.soa(), dev)
     n_prim = r.n
     opts = ccs.make_opts(leaf_depth=8)

@@ -101,6 +101,8 @@ typedef struct {
                                  (the last row may be partial), ordered in tiles of 8 x 8 pixels with
                                  every 4th pixel in x and y sampled; 0: tiles of 32 consecutive rays,
                                  every 4th ray sampled [0] */
+    uint32_t bvh_width;       /* the scene's BVH to traverse: 0 its default, 2 or 4 (INVALID_ARG when the
+                                 scene was not built with that width) [0] */
     uint32_t host_chunk;      /* ccs_intersect_host: rays per chunk of its copy/trace pipeline, at most 8
                                  chunks (larger chunks then); 0: chunks of 2^20 rays, at least two from
                                  2^17 rays on [0] */
@@ -136,12 +138,16 @@ typedef struct {
 
 typedef struct {
     uint32_t bins;            /* SAH bins per axis, 4..64 [16] */
-    uint32_t width;           /* children per node: 2 (the binary BVH of Sec. 4) or 4 (the binary tree
+    uint32_t width;           /* children per node: 2 (the binary BVH of Sec. 4), 4 (the binary tree
                                  collapsed, each node opening its largest child until it holds four
-                                 subtrees; a wider BVH is named as future work in Sec. 4).  Does not change
+                                 subtrees; a wider BVH is named as future work in Sec. 4), or
+                                 CCS_BVH_BOTH (both trees: launches use the binary one unless
+                                 opts->bvh_width asks for the other; refits update both).  Does not change
                                  any answer.  A 4-wide tree deeper than 21 levels is refused (INVALID_ARG:
                                  its traversal stack holds 64 entries) [2] */
 } ccs_bvh_params;
+
+#define CCS_BVH_BOTH 6u
 
 /* Create a scene from n_patches patches.
  * x, y, z: control points, 20 float32 slots per patch, patch-major: x[20*p + s].  Slots 0..15 are the
@@ -178,7 +184,7 @@ ccs_status ccs_scene_destroy(ccs_scene *scene);
 /* BVH over whole-patch boxes (AABB of the 16 or 20 control points; convex hull property, Sec. 3.1),
  * built on the host with binned SAH (Sec. 4), one patch per leaf, binary or collapsed to 4-wide nodes
  * (params->width), and uploaded.  Uses the points given at creation (or copied back after an update).
- * Blocks.  params may be NULL.  Batches need every scene's BVH of one width. */
+ * Blocks.  params may be NULL.  Batches need every scene built with one width (not CCS_BVH_BOTH). */
 ccs_status ccs_bvh_build(ccs_scene *scene, const ccs_bvh_params *params);
 
 /* Recompute every box of the hierarchy bottom-up from the current control points, keeping its
@@ -363,8 +369,8 @@ typedef struct {
     float ms;                 /* mean time of one ccs_intersect launch */
 } ccs_autotune_trial;
 
-/* Autotuner: coordinate descent (two passes) over the work order (CCS_TRACE_ORDER off / on, with the
- * base's image_width), lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
+/* Autotuner: coordinate descent (two passes) over the BVH width (when the scene was built with
+ * CCS_BVH_BOTH), the work order (CCS_TRACE_ORDER off / on, with the base's image_width), lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
  * threads per block {64, 96, 128}, blocks per SM {1..6}, refill {1, 2, 4, 8, 16, 24}, chunk {32..1024},
  * bvh_burst {1..16}, cache_slots {0, 2} and min_blocks {0, 4}, starting from
  * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so

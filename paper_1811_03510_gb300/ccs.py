@@ -20,6 +20,7 @@ CCS_GREGORY = 1
 CCS_TRACE_COUNT = 1
 CCS_TRACE_ORDER = 2
 CCS_TRACE_HOST_MAPPED = 4
+CCS_BVH_BOTH = 6
 CCS_NUM_COUNTERS = 23
 COUNTER_NAMES = ("bvh_nodes", "bezier_splits", "gregory_splits", "leaves", "backtracks", "redescent_levels",
                  "pruned_siblings", "pairs",
@@ -66,7 +67,7 @@ class ccs_trace_opts(ctypes.Structure):
                 ("vote", ctypes.c_uint32), ("lanes_per_ray", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("pixel_spread", ctypes.c_float),
                 ("flags", ctypes.c_uint32), ("counters", ctypes.c_void_p), ("image_width", ctypes.c_uint32),
-                ("host_chunk", ctypes.c_uint32)]
+                ("bvh_width", ctypes.c_uint32), ("host_chunk", ctypes.c_uint32)]
 
 
 class ccs_autotune_trial(ctypes.Structure):
@@ -202,7 +203,7 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
               counters=None, pixel_spread=0.0, order=False, image_width=0, host_chunk=0,
-              host_mapped=False) -> ccs_trace_opts:
+              host_mapped=False, bvh_width=0) -> ccs_trace_opts:
     """ccs_trace_opts with the fields of include/ccs.h (0: the library's default).  counters: a device
     int64 tensor of CCS_NUM_COUNTERS entries (sets CCS_TRACE_COUNT); order: CCS_TRACE_ORDER over tiles of
     an image of width image_width (0: runs of 32 rays); host_mapped: CCS_TRACE_HOST_MAPPED."""
@@ -224,6 +225,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.counters = _ptr(counters) if counters is not None else None
     o.image_width = image_width
     o.host_chunk = host_chunk
+    o.bvh_width = bvh_width
     return o
 
 
@@ -513,7 +515,7 @@ def ccs_intersect_learned(scene: int, proposal: int, rays, n: int, hits, opts=No
 def opts_dict(o: ccs_trace_opts) -> dict:
     d = {k: int(getattr(o, k)) for k in ("leaf_depth", "block_threads", "blocks_per_sm", "refill", "chunk",
                                           "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray",
-                                          "image_width", "host_chunk")}
+                                          "image_width", "host_chunk", "bvh_width")}
     d["order"] = bool(o.flags & CCS_TRACE_ORDER)
     return d
 
@@ -540,7 +542,8 @@ def ccs_last_error() -> str:
 
 class Scene:
     """Owns a ccs_scene handle built from host arrays P [n, 20, 3] float32 and types [n] uint8; local=True
-    takes the sub-domain boxes in each patch's own frame (CCS_SCENE_LOCAL_FRAMES); bvh_width 2 or 4."""
+    takes the sub-domain boxes in each patch's own frame (CCS_SCENE_LOCAL_FRAMES); bvh_width 2, 4 or
+    "both" (CCS_BVH_BOTH: launches choose with make_opts(bvh_width=...))."""
 
     def __init__(self, P, types, bins: int = 16, stream=None, local: bool = False, bvh_width: int = 2):
         import numpy as np
@@ -553,7 +556,7 @@ class Scene:
         self.local = bool(local)
         self.handle = ccs_scene_create(x.ctypes.data, y.ctypes.data, z.ctypes.data, t.ctypes.data, self.n, False,
                                        stream, local=self.local)
-        self.bvh_width = int(bvh_width)
+        self.bvh_width = CCS_BVH_BOTH if bvh_width == "both" else int(bvh_width)
         ccs_bvh_build(self.handle, bins, self.bvh_width)
 
     def close(self):

@@ -52,6 +52,9 @@ void free_scene(ccs_scene *s)
     cudaFree(s->d_nodes);
     cudaFree(s->d_leaf_parent);
     cudaFree(s->d_refit_flags);
+    cudaFree(s->d_nodes_alt);
+    cudaFree(s->d_leaf_parent_alt);
+    cudaFree(s->d_refit_flags_alt);
     cudaFree(s->d_work);
     cudaFree(s->d_stage);
     for (cudaEvent_t e : s->pipe_ev)
@@ -82,6 +85,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     c.flags = o ? o->flags : 0;
     c.image_width = o ? o->image_width : 0;
     c.host_chunk = o ? o->host_chunk : 0;
+    c.bvh_width = o ? o->bvh_width : 0;
     c.counters = o ? reinterpret_cast<unsigned long long *>(o->counters) : nullptr;
     CCS_ARG(c.leaf_depth >= 1 && c.leaf_depth <= (uint32_t)kMaxLeafDepth, "leaf_depth must be in 1..15");
     CCS_ARG(c.block_threads % 32 == 0 && c.block_threads >= 32 && c.block_threads <= 128,
@@ -95,6 +99,7 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.vote <= 32, "vote must be in 0..32");
     CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
     CCS_ARG(c.pixel_spread >= 0.0f && c.pixel_spread < 1.0f, "pixel_spread must be in [0, 1) radians per pixel");
+    CCS_ARG(c.bvh_width == 0 || c.bvh_width == 2 || c.bvh_width == 4, "bvh_width must be 0, 2 or 4");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
     CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER | CCS_TRACE_HOST_MAPPED)) == 0, "unknown trace flags");
     return CCS_OK;
@@ -127,7 +132,7 @@ ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRa
         CCS_CUDA(cudaMalloc(&sc->d_order[slot], words * sizeof(uint32_t)));
         sc->order_words[slot] = words;
     }
-    CCS_CUDA(launch_order(dev_scene(sc), dr, n, cfg.image_width, sc->d_order[slot], s));
+    CCS_CUDA(launch_order(dev_scene(sc, cfg.bvh_width), dr, n, cfg.image_width, sc->d_order[slot], s));
     *perm = sc->d_order[slot];
     return CCS_OK;
 }
@@ -222,7 +227,7 @@ ccs_status ccs_bvh_build(ccs_scene *sc, const ccs_bvh_params *params)
     int bins = params && params->bins ? (int)params->bins : 16;
     CCS_ARG(bins >= 4 && bins <= 64, "bins must be in 4..64");
     const uint32_t width = params && params->width ? params->width : 2;
-    CCS_ARG(width == 2 || width == 4, "width must be 2 or 4");
+    CCS_ARG(width == 2 || width == 4 || width == CCS_BVH_BOTH, "width must be 2, 4 or CCS_BVH_BOTH");
     const uint32_t n = sc->n;
     std::vector<float> lo(3 * (size_t)n), hi(3 * (size_t)n);
     for (uint32_t p = 0; p < n; ++p) {
@@ -238,34 +243,55 @@ ccs_status ccs_bvh_build(ccs_scene *sc, const ccs_bvh_params *params)
             hi[3 * (size_t)p + c] = b;
         }
     }
-    BvhHost bvh;
+    BvhHost bin, wide;
     std::string err;
-    if (!build_bvh(lo, hi, n, bins, bvh, err)) {
+    if (!build_bvh(lo, hi, n, bins, bin, err)) {
         set_error(err);
         return CCS_ERR_INVALID_ARG;
     }
-    if (width == 4) {
-        BvhHost bin = std::move(bvh);
-        if (!collapse_bvh4(bin, n, bvh, err)) {
-            set_error(err);
-            return CCS_ERR_INVALID_ARG;
-        }
+    if (width != 2 && !collapse_bvh4(bin, n, wide, err)) {
+        set_error(err);
+        return CCS_ERR_INVALID_ARG;
     }
-    cudaFree(sc->d_nodes);
-    cudaFree(sc->d_leaf_parent);
-    cudaFree(sc->d_refit_flags);
-    sc->d_nodes = nullptr;
-    sc->d_leaf_parent = nullptr;
-    sc->d_refit_flags = nullptr;
-    sc->n_nodes = (uint32_t)(bvh.nodes.size() / (width == 4 ? 32 : 16));
-    sc->bvh_width = width;
+    for (float4 **p : {&sc->d_nodes, &sc->d_nodes_alt}) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    for (int **p : {&sc->d_leaf_parent, &sc->d_leaf_parent_alt}) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    for (uint32_t **p : {&sc->d_refit_flags, &sc->d_refit_flags_alt}) {
+        cudaFree(*p);
+        *p = nullptr;
+    }
+    sc->n_nodes = sc->n_nodes_alt = 0;
+    sc->alt_width = 0;
     sc->built = false;
-    if (sc->n_nodes) {
-        CCS_CUDA(cudaMalloc(&sc->d_nodes, bvh.nodes.size() * sizeof(float)));
-        CCS_CUDA(cudaMemcpy(sc->d_nodes, bvh.nodes.data(), bvh.nodes.size() * sizeof(float), cudaMemcpyHostToDevice));
-        CCS_CUDA(cudaMalloc(&sc->d_leaf_parent, (size_t)n * sizeof(int)));
-        CCS_CUDA(cudaMemcpy(sc->d_leaf_parent, bvh.leaf_parent.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice));
-        CCS_CUDA(cudaMalloc(&sc->d_refit_flags, (size_t)sc->n_nodes * sizeof(uint32_t)));
+    // upload one tree: nodes, leaf back-links and refit arrival counters
+    auto upload = [n](const BvhHost &t, uint32_t per_node, float4 **nodes, int **parent, uint32_t **flags,
+                      uint32_t *n_nodes) -> cudaError_t {
+        *n_nodes = (uint32_t)(t.nodes.size() / per_node);
+        if (*n_nodes == 0) return cudaSuccess;
+        cudaError_t e;
+        if ((e = cudaMalloc(nodes, t.nodes.size() * sizeof(float))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(*nodes, t.nodes.data(), t.nodes.size() * sizeof(float), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        if ((e = cudaMalloc(parent, (size_t)n * sizeof(int))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(*parent, t.leaf_parent.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+        return cudaMalloc(flags, (size_t)*n_nodes * sizeof(uint32_t));
+    };
+    if (width == 4) {
+        CCS_CUDA(upload(wide, 32, &sc->d_nodes, &sc->d_leaf_parent, &sc->d_refit_flags, &sc->n_nodes));
+        sc->bvh_width = 4;
+    } else {
+        CCS_CUDA(upload(bin, 16, &sc->d_nodes, &sc->d_leaf_parent, &sc->d_refit_flags, &sc->n_nodes));
+        sc->bvh_width = 2;
+    }
+    if (width == CCS_BVH_BOTH) {
+        CCS_CUDA(upload(wide, 32, &sc->d_nodes_alt, &sc->d_leaf_parent_alt, &sc->d_refit_flags_alt, &sc->n_nodes_alt));
+        sc->alt_width = 4;
     }
     sc->built = true;
     return CCS_OK;
@@ -289,6 +315,9 @@ ccs_status ccs_bvh_refit(ccs_scene *sc, void *stream)
     }
     CCS_CUDA(launch_refit(sc->d_nodes, sc->d_leaf_parent, sc->d_leaf_box, sc->d_refit_flags, sc->n, sc->n_nodes,
                           sc->bvh_width, (cudaStream_t)stream));
+    if (sc->alt_width)
+        CCS_CUDA(launch_refit(sc->d_nodes_alt, sc->d_leaf_parent_alt, sc->d_leaf_box, sc->d_refit_flags_alt, sc->n,
+                              sc->n_nodes_alt, sc->alt_width, (cudaStream_t)stream));
     return CCS_OK;
 }
 
@@ -304,8 +333,9 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     }
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
     if (cfg.pixel_spread > 0.0f) cfg.mode = 4;   // screen-space termination (one lane per ray)
-    DevScene ds = dev_scene(sc);
+    DevScene ds = dev_scene(sc, cfg.bvh_width);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     const uint32_t *perm;
@@ -329,12 +359,13 @@ ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t 
     }
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
     CCS_ARG(cfg.leaf_depth >= 3, "trace export needs leaf_depth >= 3 (labels are depth-3 cells)");
     cfg.flags &= ~CCS_TRACE_COUNT;
     cfg.mode = 1;
     cfg.mc = ModeCtx{features, labels, count, capacity};
     CCS_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), (cudaStream_t)stream));
-    DevScene ds = dev_scene(sc);
+    DevScene ds = dev_scene(sc, cfg.bvh_width);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
@@ -354,13 +385,14 @@ ccs_status ccs_intersect_learned(const ccs_scene *sc, const ccs_proposal *prop, 
     }
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
     CCS_ARG(cfg.leaf_depth >= 3, "the learned proposal needs leaf_depth >= 3 (it proposes depth-3 cells)");
     CCS_ARG(cfg.block_threads == 128, "the learned proposal runs with 128 threads per block");
     cfg.mode = 2;
     cfg.cache_slots = 0;
     cfg.mlp = proposal_weights(prop);
     cfg.min_conf = min_confidence;
-    DevScene ds = dev_scene(sc);
+    DevScene ds = dev_scene(sc, cfg.bvh_width);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
@@ -380,6 +412,7 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     }
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
     if (cfg.pixel_spread > 0.0f) cfg.mode = 4;
     if (n == 0) return CCS_OK;
     cudaStream_t s = (cudaStream_t)stream;
@@ -418,7 +451,7 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
                              static_cast<float *>(dout[2]), static_cast<uint32_t *>(dout[3])};
             const uint32_t *perm;
             if ((st = work_order(sc, 0, cfg, dr, n, s, &perm)) != CCS_OK) return st;
-            CCS_CUDA(launch_intersect(dev_scene(sc), dr, dh, n, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, s,
+            CCS_CUDA(launch_intersect(dev_scene(sc, cfg.bvh_width), dr, dh, n, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, s,
                                       perm));
             CCS_CUDA(cudaStreamSynchronize(s));
             return CCS_OK;
@@ -468,7 +501,7 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
     // (equally spaced planes of separate allocations are refused by the runtime at the call, with nothing
     // enqueued; the copies then go plane by plane)
     size_t in_pitch = stride_of(srcv, 8), out_pitch = stride_of(dst, 4);
-    const DevScene ds = dev_scene(sc);
+    const DevScene ds = dev_scene(sc, cfg.bvh_width);
     for (uint32_t k = 0; k < chunks; ++k) {
         const size_t a = bound(k), m = bound(k + 1) - a;
         if (m == 0) continue;
@@ -568,9 +601,10 @@ ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, u
     ccs_status st;
     LaunchCfg cfg;
     if ((st = fill_launch_cfg(opts, cfg)) != CCS_OK) return st;
+    CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
     cfg.mode = 3;
     cfg.mc.occluded = occluded;
-    DevScene ds = dev_scene(sc);
+    DevScene ds = dev_scene(sc, cfg.bvh_width);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{nullptr, nullptr, nullptr, nullptr};
     const uint32_t *perm;

@@ -1,6 +1,6 @@
 // Autotuner of the closest-hit launch: coordinate descent over options that cannot change the answer
-// (work order, lanes per ray, phase vote, threads per block, blocks per SM, warp refill threshold, queue
-// chunk, BVH burst, sibling cache, register budget),
+// (BVH width when the scene holds two, work order, lanes per ray, phase vote, threads per block, blocks
+// per SM, warp refill threshold, queue chunk, BVH burst, sibling cache, register budget),
 // each candidate timed with CUDA events over `reps` launches on the caller's rays.
 #include <cuda_runtime.h>
 
@@ -74,14 +74,17 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> minb_c = {0, 4};
     const std::vector<uint32_t> vote_c = {0, 4, 8, 12, 16, 20, 24};
     const std::vector<uint32_t> order_c = {0, CCS_TRACE_ORDER};
-    const std::vector<uint32_t> *cands[10] = {&order_c, &lanes_c, &vote_c, &threads_c, &bps_c, &refill_c, &chunk_c,
-                                              &burst_c, &cache_c, &minb_c};
+    std::vector<uint32_t> width_c = {0};   // the scene's default BVH, and its second one if it has one
+    if (scene->alt_width) width_c.push_back(scene->alt_width);
+    const std::vector<uint32_t> *cands[11] = {&width_c, &order_c, &lanes_c, &vote_c, &threads_c, &bps_c, &refill_c,
+                                              &chunk_c, &burst_c, &cache_c, &minb_c};
     for (int pass = 0; pass < 2 && st == CCS_OK; ++pass) {
-        for (int knob = 0; knob < 10 && st == CCS_OK; ++knob) {
+        for (int knob = 0; knob < 11 && st == CCS_OK; ++knob) {
             for (uint32_t v : *cands[knob]) {
                 ccs_trace_opts o = cur;
-                uint32_t *fields[10] = {&o.flags, &o.lanes_per_ray, &o.vote, &o.block_threads, &o.blocks_per_sm,
-                                        &o.refill, &o.chunk, &o.bvh_burst, &o.cache_slots, &o.min_blocks};
+                uint32_t *fields[11] = {&o.bvh_width, &o.flags, &o.lanes_per_ray, &o.vote, &o.block_threads,
+                                        &o.blocks_per_sm, &o.refill, &o.chunk, &o.bvh_burst, &o.cache_slots,
+                                        &o.min_blocks};
                 uint32_t *field = fields[knob];
                 if (*field == v) continue;
                 *field = v;

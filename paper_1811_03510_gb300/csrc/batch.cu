@@ -122,8 +122,8 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
             set_error("ccs_batch_create: every scene must exist and have a BVH (ccs_bvh_build)");
             return sc ? CCS_ERR_NOT_BUILT : CCS_ERR_INVALID_ARG;
         }
-        if (sc->bvh_width != scenes[0]->bvh_width) {
-            set_error("ccs_batch_create: every scene's BVH must have the same width");
+        if (sc->bvh_width != scenes[0]->bvh_width || sc->alt_width) {
+            set_error("ccs_batch_create: every scene needs one BVH, all of the same width");
             return CCS_ERR_INVALID_ARG;
         }
         if (n_rays[s] && (!rays[s].ox || !rays[s].oy || !rays[s].oz || !rays[s].dx || !rays[s].dy || !rays[s].dz ||

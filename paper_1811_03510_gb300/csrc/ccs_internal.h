@@ -54,7 +54,7 @@ struct ModeCtx {
 
 struct LaunchCfg {
     uint32_t leaf_depth, block_threads, blocks_per_sm, refill, chunk, bvh_burst, cache_slots, min_blocks, vote,
-        lanes_per_ray, iter_cap, flags, image_width, host_chunk;
+        lanes_per_ray, iter_cap, flags, image_width, host_chunk, bvh_width;
     float pixel_spread;
     unsigned long long *counters;
     int mode = 0;                         // 0 plain, 1 trace export, 2 learned proposal, 3 any hit, 4 screen-space
@@ -137,7 +137,13 @@ struct ccs_scene {
     int *d_leaf_parent = nullptr;      // per patch: (node << 1) | slot
     uint32_t *d_refit_flags = nullptr; // per node arrival counters of the refit
     uint32_t n_nodes = 0;
-    uint32_t bvh_width = 2;            // node width of the built BVH
+    uint32_t bvh_width = 2;            // node width of the built BVH (the default of launches)
+    // a second BVH of the other width, built with CCS_BVH_BOTH (launches pick it by opts->bvh_width)
+    float4 *d_nodes_alt = nullptr;
+    int *d_leaf_parent_alt = nullptr;
+    uint32_t *d_refit_flags_alt = nullptr;
+    uint32_t n_nodes_alt = 0;
+    uint32_t alt_width = 0;            // 0: none
     bool built = false;
     bool local = false;                // CCS_SCENE_LOCAL_FRAMES
     uint32_t *d_work = nullptr;        // [1] device status word; [kQueueBase + k] ring of work-queue heads
@@ -165,5 +171,18 @@ inline uint32_t *take_queue(ccs_scene *sc)
 inline DevScene dev_scene(const ccs_scene *sc)
 {
     return DevScene{sc->d_rec, sc->d_nodes, sc->d_leaf_box, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};
+}
+
+// The scene seen through its BVH of the given width (0: the default one); the caller has checked that
+// the scene holds it (has_width).
+inline bool has_width(const ccs_scene *sc, uint32_t width)
+{
+    return width == 0 || width == sc->bvh_width || (sc->alt_width != 0 && width == sc->alt_width);
+}
+inline DevScene dev_scene(const ccs_scene *sc, uint32_t width)
+{
+    if (width == 0 || width == sc->bvh_width) return dev_scene(sc);
+    return DevScene{sc->d_rec, sc->d_nodes_alt, sc->d_leaf_box, sc->n, sc->n_nodes_alt, sc->local ? 1u : 0u,
+                    sc->alt_width};
 }
 }  // namespace ccs

@@ -72,8 +72,8 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
             set_error("ccs_intersect_batched_noalloc: every scene must exist and have a BVH");
             return sc ? CCS_ERR_NOT_BUILT : CCS_ERR_INVALID_ARG;
         }
-        if (sc->bvh_width != scenes[0]->bvh_width) {
-            set_error("ccs_intersect_batched_noalloc: every scene's BVH must have the same width");
+        if (sc->bvh_width != scenes[0]->bvh_width || sc->alt_width) {
+            set_error("ccs_intersect_batched_noalloc: every scene needs one BVH, all of the same width");
             return CCS_ERR_INVALID_ARG;
         }
         const ccs_rays &r = rays_per_scene[s];

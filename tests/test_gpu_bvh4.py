@@ -144,3 +144,37 @@ def test_four_wide_trace_export_runs_and_keeps_the_hits():
     assert (lab[:k].cpu().numpy() < 64).all() and torch.isfinite(feat[:k]).all()
     two.close()
     four.close()
+
+
+def test_scene_with_both_trees_and_per_launch_width():
+    """CCS_BVH_BOTH: one scene holds the binary and the 4-wide tree; each launch picks one (bvh_width), the
+    tuner may pick either, a refit updates both, and asking a one-tree scene for the other width fails."""
+    s = sg.make_scene(8, 0.05, 3, 1, gregory_ring=True)
+    r = sg.random_rays(30000, seed=65)
+    both = ccs.Scene(s.P, s.types, local=True, bvh_width="both")
+    two = ccs.Scene(s.P, s.types, local=True)
+    ref = run(two, r)
+    for w in (0, 2, 4):
+        same(run(both, r, bvh_width=w), ref, ("width", w))
+    same(run(both, r, bvh_width=4, order=True, lanes_per_ray=3), ref, "width 4, order, groups")
+    rays = ccs.rays_to_device(r.soa())
+    h = ccs.alloc_hits(r.n)
+    best, _, trials = ccs.ccs_autotune(both.handle, rays, r.n, h, ccs.make_opts(), reps=1)
+    assert {o.bvh_width for o, _ in trials} >= {0, 4}
+    same(run(both, r, **ccs.opts_dict(best)), ref, "tuned")
+    # a deformation and one refit: both trees follow
+    Q = s.P + 0.03 * np.sin(3.0 * s.P + 1.0).astype(np.float32)
+    q = [torch.from_numpy(np.ascontiguousarray(Q[..., c]).reshape(-1)).cuda() for c in range(3)]
+    ccs.ccs_scene_update_points(both.handle, *q)
+    ccs.ccs_bvh_refit(both.handle)
+    torch.cuda.synchronize()
+    fresh = ccs.Scene(Q, s.types, local=True)
+    ref2 = run(fresh, r)
+    for w in (2, 4):
+        same(run(both, r, bvh_width=w), ref2, ("refit", w))
+    with pytest.raises(ccs.CcsError):
+        run(two, r, bvh_width=4)
+    with pytest.raises(ccs.CcsError):   # batches need one tree per scene
+        ccs.ccs_intersect_batched([both], [rays], [ccs.alloc_hits(r.n)], ccs.make_opts())
+    for sc in (both, two, fresh):
+        sc.close()
