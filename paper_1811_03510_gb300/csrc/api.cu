@@ -132,7 +132,10 @@ ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRa
         CCS_CUDA(cudaMalloc(&sc->d_order[slot], words * sizeof(uint32_t)));
         sc->order_words[slot] = words;
     }
-    CCS_CUDA(launch_order(dev_scene(sc, cfg.bvh_width), dr, n, cfg.image_width, sc->d_order[slot], s));
+    // the estimate counts the patch boxes a ray enters, the same in either tree: it walks the 4-wide one
+    // when the scene has it (fewer dependent node loads)
+    const uint32_t est_width = (sc->bvh_width == 4 || sc->alt_width == 4) ? 4u : 0u;
+    CCS_CUDA(launch_order(dev_scene(sc, est_width), dr, n, cfg.image_width, sc->d_order[slot], s));
     *perm = sc->d_order[slot];
     return CCS_OK;
 }
