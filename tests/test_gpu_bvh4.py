@@ -157,6 +157,8 @@ def test_scene_with_both_trees_and_per_launch_width():
     for w in (0, 2, 4):
         same(run(both, r, bvh_width=w), ref, ("width", w))
     same(run(both, r, bvh_width=4, order=True, lanes_per_ray=3), ref, "width 4, order, groups")
+    # a binary launch whose work-order estimate walks the scene's 4-wide tree
+    same(run(both, r, bvh_width=2, order=True), ref, "width 2, order")
     rays = ccs.rays_to_device(r.soa())
     h = ccs.alloc_hits(r.n)
     best, _, trials = ccs.ccs_autotune(both.handle, rays, r.n, h, ccs.make_opts(), reps=1)
@@ -172,6 +174,7 @@ def test_scene_with_both_trees_and_per_launch_width():
     ref2 = run(fresh, r)
     for w in (2, 4):
         same(run(both, r, bvh_width=w), ref2, ("refit", w))
+        same(run(both, r, bvh_width=w, order=True), ref2, ("refit, order", w))
     with pytest.raises(ccs.CcsError):
         run(two, r, bvh_width=4)
     with pytest.raises(ccs.CcsError):   # batches need one tree per scene
