@@ -188,6 +188,22 @@ def measured_traffic() -> tuple:
     return (int(m_p.group(1)), int(m_d.group(1))), path
 
 
+def measured_issue() -> tuple:
+    """Thread-instruction issue of the primary launch over the FP32 lane peak (all instructions, and FADD/FMUL/FFMA
+    alone) from the committed full ncu capture, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_intersect_cfg2_960x540_ncu.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    import re
+    m_hash = re.search(r"kernel sources sha256\[:16\]: ([0-9a-f]{16})", text)
+    m = re.search(r"thread instruction issue / FP32 lanes: ([0-9.]+) \(FADD, FMUL, FFMA: ([0-9.]+)\)", text)
+    if not (m_hash and m) or m_hash.group(1) != kernel_source_hash():
+        return None, path
+    return (float(m.group(1)), float(m.group(2))), path
+
+
 def fp32_peak_ops(n_sm: int, mhz: float) -> float:
     """FP32 issue peak: SMs x 128 FP32 lanes x SM clock (one FMA, add, mul or min/max = one op)."""
     return n_sm * 128 * mhz * 1e6
@@ -762,6 +778,7 @@ def main():
     e2e_value = e2e["staged_copies"]
 
     traffic, traffic_src = measured_traffic()
+    issue, issue_src = measured_issue()
     peak_max = fp32_peak_ops(n_sm, 2070.0)
     ops_step = alg_ops["primary"] + alg_ops["diffuse"]
     achieved = ops_step * args.steps / T
@@ -791,7 +808,11 @@ def main():
                              "launch from " + (os.path.relpath(traffic_src, ROOT) if traffic_src else "no capture") +
                              ("" if traffic else " (null: no capture of the current kernel sources)"),
                      "algorithmic_bytes_per_launch": 48 * rays_per_step / 2,
-                     "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None},
+                     "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None,
+                     "issue_frac_ncu": ({"all_instructions": issue[0], "fadd_fmul_ffma": issue[1],
+                                         "source": os.path.relpath(issue_src, ROOT),
+                                         "per": "thread instructions per cycle / (SMs x 128 lanes), one 960x540 "
+                                                "primary launch under ncu"} if issue else None)},
         "counters": counts,
         "schedule": sched,
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
