@@ -37,9 +37,11 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The compiled oracle.  CCS_ORACLE_LIB names another build of ccs_oracle.c to load instead: the
+    planted-mistake test points it at copies of the source with one mistake each."""
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
+        _lib = ctypes.CDLL(os.environ.get("CCS_ORACLE_LIB") or build())
         _lib.orc_intersect.restype = ctypes.c_int
         _lib.orc_intersect_patch.restype = ctypes.c_int
         _lib.orc_num_cores.restype = ctypes.c_int

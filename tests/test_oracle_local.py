@@ -121,3 +121,18 @@ def test_local_frames_agree_with_world_frames_away_from_edges():
     assert same.mean() / both.mean() > 0.97
     dt = np.abs(l["t"][same] - w["t"][same])
     assert dt.max() < 1e-2 and np.median(dt) < 1e-3
+
+
+def test_frame_of_a_curved_patch_is_a_rotation():
+    """The frame of a curved patch: orthonormal rows with determinant +1, z along the normal of the
+    corner quad (the cross product of the diagonals p33 - p00 and p03 - p30), x in the plane of z and the
+    u edge p30 - p00 on that edge's side (so y is orthogonal to the edge)."""
+    for _ in range(40):
+        g = RNG.normal(size=(20, 3))
+        R = oracle.local_frame(g)
+        np.testing.assert_allclose(R @ R.T, np.eye(3), atol=1e-12)
+        assert np.linalg.det(R) == pytest.approx(1.0, abs=1e-12)
+        n = np.cross(g[15] - g[0], g[12] - g[3])
+        np.testing.assert_allclose(R[2], n / np.linalg.norm(n), atol=1e-12)
+        e = g[3] - g[0]
+        assert abs(R[1] @ e) <= 1e-12 * np.linalg.norm(e) and R[0] @ e > 0

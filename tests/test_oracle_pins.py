@@ -230,7 +230,7 @@ def _frac(s):
 
 def test_bernstein_maxima_golden():
     """Bernstein maxima used by the weight bounds (golden values from Sec. 3.2 / Algorithm 2), read back
-    through d(D) of a Gregory patch whose only differing pair is (1,1) or (2,1)."""
+    through d(D) of Gregory patches whose only differing pair is one of the four inner pairs."""
     rows = []
     with open(os.path.join(GOLDEN, "bernstein_maxima.txt")) as f:
         for line in f:
@@ -254,6 +254,15 @@ def test_bernstein_maxima_golden():
         g = base.copy()
         g[9] = [1.0, 0, 0]
         hs = [greg_h(2, u, v) for u in (0.0, 1.0) for v in (t0, t1)]
+        _, d, _, _ = oracle.calc_points_and_d(g, True, 0.0, 1.0, t0, t1)
+        assert d[0] == pytest.approx((4 / 9) * b2 * (max(hs) - min(hs)), rel=1e-12)
+        # pair (2,2): weights wbar2(u) * wbar2(v), once with u over [t0,t1] and once with v over it
+        g = base.copy()
+        g[10] = [1.0, 0, 0]
+        hs = [greg_h(3, u, v) for u in (t0, t1) for v in (0.0, 1.0)]
+        _, d, _, _ = oracle.calc_points_and_d(g, True, t0, t1, 0.0, 1.0)
+        assert d[0] == pytest.approx(b2 * (4 / 9) * (max(hs) - min(hs)), rel=1e-12)
+        hs = [greg_h(3, u, v) for u in (0.0, 1.0) for v in (t0, t1)]
         _, d, _, _ = oracle.calc_points_and_d(g, True, 0.0, 1.0, t0, t1)
         assert d[0] == pytest.approx((4 / 9) * b2 * (max(hs) - min(hs)), rel=1e-12)
         # sampled check that the golden maxima are maxima
@@ -426,3 +435,41 @@ def test_scene_closest_hit_is_min_over_patches():
         assert out["t"][i] == best[0]
         assert out["pid"][i] == best[1]
         assert out["cell"][i] == best[2]
+
+
+def _square_grid():
+    """The square [0,3]^2 of the plane z = 0 as a degree-elevated affine patch, p_ij = (i, j, 0): every
+    de Casteljau midpoint of it is a dyadic rational, so the leaf boundaries fall exactly on u, v = k / 2^L."""
+    g = np.zeros((20, 3))
+    for j in range(4):
+        for i in range(4):
+            g[4 * j + i] = [i, j, 0.0]
+    g[16:] = g[[5, 6, 9, 10]]
+    return g
+
+
+def test_equal_entry_distances_take_the_lowest_cell():
+    """Sec. 3.3 records the closest leaf; where several leaves are entered at the same distance the key
+    (t, patch, cell) takes the lowest cell index (v_cell 2^L + u_cell).  A ray along -z onto a leaf
+    boundary of the flat square enters the two (or four) leaves that share it at exactly t = 2."""
+    g = _square_grid()
+    L = 8
+    v_mid = 3 * 37.5 / 256        # inside v cell 37
+    for greg in (False, True):
+        hit, t, cell, _ = oracle.intersect_patch(g, greg, _ray([1.5, v_mid, 2.0], [0.0, 0.0, -1.0]), L)
+        assert hit and t == 2.0 and cell == (37 << L) | 127          # u = 1/2: cells 127 and 128
+        hit, t, cell, _ = oracle.intersect_patch(g, greg, _ray([1.5, 1.5, 2.0], [0.0, 0.0, -1.0]), L)
+        assert hit and t == 2.0 and cell == (127 << L) | 127         # u = v = 1/2: four cells
+        hit, t, cell, _ = oracle.intersect_patch(g, greg, _ray([0.75, 2.25, 2.0], [0.0, 0.0, -1.0]), L)
+        assert hit and t == 2.0 and cell == (191 << L) | 63          # u = 1/4, v = 3/4
+
+
+def test_equal_keys_across_patches_take_the_lowest_patch():
+    """Copies of one patch are entered at the same distance in the same cell: the scene's answer is the
+    copy with the lowest index (key order t, patch, cell)."""
+    g = _square_grid().astype(np.float32)
+    far = g + np.float32(10.0)                                          # a patch off the ray
+    rays = [np.array([x], np.float32) for x in (1.5, 1.5, 2.0, 0.0, 0.0, -1.0, 0.0, np.inf)]
+    for P, want in (([g, g], 0), ([far, g, g, g], 1), ([g, far, g], 0)):
+        out = oracle.intersect(np.stack(P), np.zeros(len(P), np.uint8), rays, L=6)
+        assert out["pid"][0] == want and out["t"][0] == 2.0

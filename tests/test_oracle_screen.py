@@ -54,6 +54,34 @@ def test_flat_patch_terminates_at_the_closed_form_level(spread):
         assert cu == int(u * 2 ** su) << (L - su) and cv == int(v * 2 ** sv) << (L - sv)
 
 
+def test_coarse_leaf_reports_the_centre_of_its_domain():
+    """A screen-space leaf above the fixed depth is a block of 2^-su x 2^-sv in (u, v), su = ceil(level/2)
+    splits along u and sv = floor(level/2) along v; the hit reports the centre of that block.  Odd and even
+    termination levels both occur below."""
+    a, D, L = 1.0, 5.0, 8
+    g = flat_square(a).astype(np.float32)
+    rng = np.random.default_rng(77)
+    levels = set()
+    for spread in (1e-3, 4e-3, 2e-2, 0.09):
+        lev = expected_level(a, spread, D, L)
+        levels.add(lev % 2)
+        su, sv = (lev + 1) // 2, lev // 2
+        xy = rng.uniform(-0.49, 0.49, size=(50, 2)) * a
+        n = len(xy)
+        rays = [xy[:, 0], xy[:, 1], np.full(n, D), np.zeros(n), np.zeros(n), -np.ones(n), np.zeros(n),
+                np.full(n, np.inf)]
+        rays = [np.ascontiguousarray(r, np.float32) for r in rays]
+        out = oracle.intersect(g[None], np.zeros(1, np.uint8), rays, L=L, spread=spread)
+        u = rays[0].astype(np.float64) / a + 0.5
+        v = rays[1].astype(np.float64) / a + 0.5
+        want_u = (np.floor(u * 2 ** su) + 0.5) / 2 ** su
+        want_v = (np.floor(v * 2 ** sv) + 0.5) / 2 ** sv
+        assert (out["pid"] == 0).all()
+        np.testing.assert_array_equal(out["u"], want_u.astype(np.float32))
+        np.testing.assert_array_equal(out["v"], want_v.astype(np.float32))
+    assert levels == {0, 1}
+
+
 @pytest.mark.parametrize("greg", [False, True])
 @pytest.mark.parametrize("L", [3, 5])
 def test_pruned_search_equals_brute_force_with_screen_leaves(greg, L):
