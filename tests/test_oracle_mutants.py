@@ -117,3 +117,66 @@ def test_every_planted_mistake_fails_a_pin(tmp_path):
     assert ok, f"the unchanged oracle fails its pins under the mutant harness: {tail}"
     survivors = [n for n, (passed, _) in results.items() if passed]
     assert not survivors, f"planted mistakes that no pin catches: {survivors}"
+
+
+# Planted mistakes in the network oracle (oracle/mlp.py): each is a list of (text, replacement) applied
+# together, so that a mistake made consistently in the forward and the backward pass is covered too.
+MLP_MUTANTS = [
+    ("second ReLU dropped", [("    h2 = np.maximum(z2, 0.0)\n", "    h2 = z2\n"),
+                             ("    dz2 = dh2 * (z2 > 0)\n", "    dz2 = dh2\n")]),
+    ("first ReLU dropped", [("    h1 = np.maximum(z1, 0.0)\n", "    h1 = z1\n"),
+                            ("    dz1 = dh1 * (z1 > 0)\n", "    dz1 = dh1\n")]),
+    ("second layer transposed", [("    z2 = h1 @ W2.T + b2\n", "    z2 = h1 @ W2 + b2\n"),
+                                 ("    dW2 = dz2.T @ h1\n", "    dW2 = (dz2.T @ h1).T\n"),
+                                 ("    dh1 = dz2 @ W2\n", "    dh1 = dz2 @ W2.T\n")]),
+    ("column-major parameters", [("        out.append(theta[k:k + n].reshape(s))\n",
+                                  "        out.append(theta[k:k + n].reshape(s[::-1]).T)\n"),
+                                 ("dtype=np.float64).reshape(-1) for p in parts])",
+                                  "dtype=np.float64).T.reshape(-1) for p in parts])")]),
+    ("cross-entropy gradient sign", [("    dz3[np.arange(B), y] -= 1.0\n", "    dz3[np.arange(B), y] += 1.0\n")]),
+    ("batch mean dropped from the gradient", [("    dz3 /= B\n", "")]),
+    ("bias gradient", [("    db2 = dz2.sum(0)\n", "    db2 = dz2.mean(0)\n")]),
+    ("bf16 ties away from even", [("(u + 0x7FFF + ((u >> 16) & 1)) >> 16 << 16", "(u + 0x8000) >> 16 << 16")]),
+    ("bf16 forward: second ReLU dropped", [("    h2 = bf16(np.maximum(z2, 0.0)).astype(np.float64)\n",
+                                            "    h2 = bf16(z2).astype(np.float64)\n")]),
+    ("bf16 forward: second layer transposed", [("    z2 = h1 @ bf16(W2).astype(np.float64).T + b2",
+                                                "    z2 = h1 @ bf16(W2).astype(np.float64) + b2")]),
+    ("bf16 forward: first bias dropped", [(".T + b1.astype(np.float32)\n", ".T\n")]),
+]
+
+
+def _mlp_pins_pass(mlp_module) -> bool:
+    """Run every test of tests/test_oracle_mlp.py with `mlp` bound to the given module (fresh copy of the
+    test module, so its seeded generator starts over)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_mlp_pins", os.path.join(ROOT, "tests", "test_oracle_mlp.py"))
+    pins = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(pins)
+    pins.mlp = mlp_module
+    for name in sorted(n for n in dir(pins) if n.startswith("test_")):
+        try:
+            getattr(pins, name)()
+        except Exception:
+            return False
+    return True
+
+
+def _mlp_module(src_text: str):
+    import types
+    m = types.ModuleType("_mlp_mutant")
+    exec(compile(src_text, "mlp_mutant.py", "exec"), m.__dict__)
+    return m
+
+
+def test_every_planted_mistake_in_the_network_oracle_fails_a_pin():
+    src = open(os.path.join(ROOT, "oracle", "mlp.py")).read()
+    assert _mlp_pins_pass(_mlp_module(src)), "the unchanged network oracle fails its pins in the harness"
+    survivors = []
+    for name, edits in MLP_MUTANTS:
+        m = src
+        for find, repl in edits:
+            assert m.count(find) == 1, f"mutant site of '{name}' is not unique in mlp.py: {find!r}"
+            m = m.replace(find, repl)
+        if _mlp_pins_pass(_mlp_module(m)):
+            survivors.append(name)
+    assert not survivors, f"planted mistakes in the network oracle that no pin catches: {survivors}"
