@@ -145,14 +145,16 @@ MLP_MUTANTS = [
 ]
 
 
-def _mlp_pins_pass(mlp_module) -> bool:
-    """Run every test of tests/test_oracle_mlp.py with `mlp` bound to the given module (fresh copy of the
-    test module, so its seeded generator starts over)."""
+def _py_pins_pass(test_file: str, bindings: dict) -> bool:
+    """Run every test of tests/<test_file> with the given module attributes rebound (a fresh copy of the
+    test module, so its seeded generators start over)."""
     import importlib.util
-    spec = importlib.util.spec_from_file_location("_mlp_pins", os.path.join(ROOT, "tests", "test_oracle_mlp.py"))
+    spec = importlib.util.spec_from_file_location("_pins_" + test_file[:-3], os.path.join(ROOT, "tests", test_file))
     pins = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(pins)
-    pins.mlp = mlp_module
+    for k, v in bindings.items():
+        if hasattr(pins, k):
+            setattr(pins, k, v)
     for name in sorted(n for n in dir(pins) if n.startswith("test_")):
         try:
             getattr(pins, name)()
@@ -161,22 +163,62 @@ def _mlp_pins_pass(mlp_module) -> bool:
     return True
 
 
-def _mlp_module(src_text: str):
+def _py_module(src_text: str, package: str = None):
     import types
-    m = types.ModuleType("_mlp_mutant")
-    exec(compile(src_text, "mlp_mutant.py", "exec"), m.__dict__)
+    m = types.ModuleType("_mutant")
+    if package:   # a module of the oracle package (relative imports resolve against it)
+        m.__package__ = package
+        m.__name__ = package + "._mutant"
+    exec(compile(src_text, "mutant.py", "exec"), m.__dict__)
     return m
+
+
+def _survivors(src: str, mutants, passes) -> list:
+    survivors = []
+    for name, edits in mutants:
+        m = src
+        for find, repl in edits:
+            assert m.count(find) == 1, f"mutant site of '{name}' is not unique: {find!r}"
+            m = m.replace(find, repl)
+        if passes(m):
+            survivors.append(name)
+    return survivors
 
 
 def test_every_planted_mistake_in_the_network_oracle_fails_a_pin():
     src = open(os.path.join(ROOT, "oracle", "mlp.py")).read()
-    assert _mlp_pins_pass(_mlp_module(src)), "the unchanged network oracle fails its pins in the harness"
-    survivors = []
-    for name, edits in MLP_MUTANTS:
-        m = src
-        for find, repl in edits:
-            assert m.count(find) == 1, f"mutant site of '{name}' is not unique in mlp.py: {find!r}"
-            m = m.replace(find, repl)
-        if _mlp_pins_pass(_mlp_module(m)):
-            survivors.append(name)
+    passes = lambda text: _py_pins_pass("test_oracle_mlp.py", {"mlp": _py_module(text)})
+    assert passes(src), "the unchanged network oracle fails its pins in the harness"
+    survivors = _survivors(src, MLP_MUTANTS, passes)
     assert not survivors, f"planted mistakes in the network oracle that no pin catches: {survivors}"
+
+
+# Planted mistakes in the oracle's secondary-ray generator (oracle/raygen.py).
+RAYGEN_MUTANTS = [
+    ("disk radius not square-rooted", [("rr, phi = np.sqrt(u1), 2 * np.pi * u2", "rr, phi = u1, 2 * np.pi * u2")]),
+    ("uniform instead of cosine-weighted",
+     [("        lx, ly, lz = rr * np.cos(phi), rr * np.sin(phi), np.sqrt(max(0.0, 1 - u1))\n",
+       "        rr = np.sqrt(max(0.0, 1 - u1 * u1))\n        lx, ly, lz = rr * np.cos(phi), rr * np.sin(phi), u1\n")]),
+    ("tangent basis sign", [("b2 = np.array([bb, sg_ + nrm[1] ** 2 * aa, -nrm[1]])",
+                             "b2 = np.array([bb, sg_ + nrm[1] ** 2 * aa, nrm[1]])")]),
+    ("normal not turned toward the ray", [("        if nrm @ din[i] > 0:\n", "        if nrm @ din[i] < 0:\n")]),
+    ("offset without its factor 2", [("        off = offset_abs + 2.0 * l1 * 2.0 ** -L\n",
+                                      "        off = offset_abs + l1 * 2.0 ** -L\n")]),
+    ("pcg output shift", [("xs = (((old >> 18) ^ old) >> 27) & 0xFFFFFFFF", "xs = (((old >> 18) ^ old) >> 28) & 0xFFFFFFFF")]),
+    ("pcg seed and sequence swapped", [("    state = (state + seed) & _MASK\n", "    state = (state + seq) & _MASK\n")]),
+    ("mirror sign", [("d[i] = din[i] - 2.0 * (din[i] @ nrm) * nrm", "d[i] = din[i] + 2.0 * (din[i] @ nrm) * nrm")]),
+    ("shadow ray not ended at the light", [("            tmax[i] = dist\n", "            tmax[i] = np.inf\n")]),
+    ("shadow ray kept with the light behind", [("if dist > 0 and to_light @ nrm > 0:", "if dist > 0:")]),
+]
+
+
+def test_every_planted_mistake_in_the_ray_generator_fails_a_pin():
+    src = open(os.path.join(ROOT, "oracle", "raygen.py")).read()
+
+    def passes(text):
+        m = _py_module(text, package="oracle")
+        b = {"raygen": m, "shadow_rays": m.shadow_rays}
+        return _py_pins_pass("test_oracle_raygen.py", b) and _py_pins_pass("test_oracle_shadow.py", b)
+    assert passes(src), "the unchanged ray generator fails its pins in the harness"
+    survivors = _survivors(src, RAYGEN_MUTANTS, passes)
+    assert not survivors, f"planted mistakes in the ray generator that no pin catches: {survivors}"
