@@ -5,7 +5,8 @@ weight convention of the Gregory patch (Sec. 3.2), wrong corners or a dropped te
 Algorithm 2, a missing slab swap, a transposed leaf cell, the other split axis order, pruning on the exit
 distance, the tie rules of the leaf key, a non-orthonormal local frame (Sec. 3.4), the screen-space
 threshold (Sec. 3.3) and the centre of a coarser leaf, the box extension and the ray's transform
-(Sec. 3.4), a dropped BVH child.  Each copy is compiled on the CPU and the quick pin files are
+(Sec. 3.4), a dropped BVH child, and each part of the FP32 error model that flags rays for the parity
+tests (a flag never set, boxes not inflated or deflated, neighbouring cells taken as far apart).  Each copy is compiled on the CPU and the quick pin files are
 run against it (CCS_ORACLE_LIB); every run must fail, while the unchanged source passes the same way.
 Mutants that cannot change an answer (the order in which children are visited, the 0/0 reading of a
 weight whose Bernstein factor vanishes) are left out: the pins are right to let them through."""
@@ -19,7 +20,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "ccs_oracle.c")
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_local.py", "tests/test_oracle_screen.py",
-             "tests/test_oracle_shadow.py", "tests/test_oracle_scene.py"]
+             "tests/test_oracle_shadow.py", "tests/test_oracle_flags.py", "tests/test_oracle_scene.py"]
 SLOW = "tests/test_oracle_scene.py::test_agrees_with_dense_tessellation"
 
 # (name, text in ccs_oracle.c (exactly once), replacement)
@@ -74,6 +75,17 @@ MUTANTS = [
     ("box extension scale", "return ldexp(1.0, -19) * (1.0 + oc.x + oc.y + oc.z);",
      "return ldexp(1.0, -18) * (1.0 + oc.x + oc.y + oc.z);"),
     ("ray direction not rotated", "l.d = rotate(P->R, r->d); }", "l.d = r->d; }"),
+    ("flag: another patch never reported", "            flags |= 1;\n", ""),
+    ("flag: far cell never reported", "            flags |= 2;\n", ""),
+    ("flag: near misses not reported", "        if (l.n) flags |= 4;\n", ""),
+    ("flag: hits without a strict leaf not reported", "    if (R > B) {", "    if (0) {"),
+    ("flag: loose boxes not inflated",
+     "        *lo = sub(*lo, v3make(eps, eps, eps));\n        *hi = add(*hi, v3make(eps, eps, eps));\n", ""),
+    ("flag: strict boxes not deflated", "if (h[k] - l[k] > 2.0 * eps) { l[k] += eps; h[k] -= eps; }",
+     "if (h[k] - l[k] > 2.0 * eps) { }"),
+    ("flag: early loose leaves not reported", "        if (e->tl < b->t - fabs(b->t) * rel_t) flags |= 8;\n", ""),
+    ("flag: neighbouring cells taken as far", "return du < -1 || du > 1 || dv < -1 || dv > 1;",
+     "return du != 0 || dv != 0;"),
     ("screen leaf centre axis", "J->u_out[i] = (float)((double)(b.cell & ((1ull << J->L) - 1)) / cells + ldexp(0.5, -su));",
      "J->u_out[i] = (float)((double)(b.cell & ((1ull << J->L) - 1)) / cells + ldexp(0.5, -sv));"),
 ]
