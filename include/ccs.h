@@ -211,6 +211,19 @@ ccs_status ccs_intersect(const ccs_scene *scene, const ccs_rays *rays, uint32_t 
 ccs_status ccs_intersect_host(ccs_scene *scene, const ccs_rays *host_rays, uint32_t n, ccs_hits *host_hits,
                               const ccs_trace_opts *opts, void *stream);
 
+/* Several batches of host rays through one copy/trace pipeline: batch j has n[j] rays in host_rays[j],
+ * its hits go to host_hits[j], traced with opts[j] (opts or opts[j] may be NULL: defaults; each batch
+ * may have its own work order, BVH width or chunk size).  The answers are those of ccs_intersect_host
+ * called for each batch in turn; the difference is that batch j+1's copies and launches start while
+ * batch j's last chunks are traced and copied out, instead of after the call returns.  Every batch is
+ * checked before anything is queued.  Batches always take the staged copies (CCS_TRACE_HOST_MAPPED is
+ * ignored here); the staging buffer holds all batches at once (12 floats per ray).  Synchronises
+ * `stream` before returning.  Not thread-safe per scene; not graph-capturable.  n_batches may be 0, and
+ * any n[j] may be 0.  Errors: INVALID_ARG, NOT_BUILT, OOM, CUDA. */
+ccs_status ccs_intersect_host_batches(ccs_scene *scene, uint32_t n_batches, const ccs_rays *host_rays,
+                                      const uint32_t *n, ccs_hits *host_hits, const ccs_trace_opts *const *opts,
+                                      void *stream);
+
 /* Wait for `stream`, then return and clear the scene's latched device status (CCS_OK or
  * CCS_ERR_TRAVERSAL_LIMIT). */
 ccs_status ccs_scene_sync_status(ccs_scene *scene, void *stream);

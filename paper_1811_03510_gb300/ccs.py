@@ -92,6 +92,9 @@ _SIGS = {
                       ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
     "ccs_intersect_host": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.c_uint32, ctypes.POINTER(ccs_hits),
                            ctypes.POINTER(ccs_trace_opts), ctypes.c_void_p],
+    "ccs_intersect_host_batches": [ctypes.c_void_p, ctypes.c_uint32, ctypes.POINTER(ccs_rays),
+                                   ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ccs_hits),
+                                   ctypes.POINTER(ctypes.POINTER(ccs_trace_opts)), ctypes.c_void_p],
     "ccs_scene_sync_status": [ctypes.c_void_p, ctypes.c_void_p],
     "ccs_gen_diffuse": [ctypes.c_void_p, ctypes.POINTER(ccs_rays), ctypes.POINTER(ccs_hits), ctypes.c_uint32,
                         ctypes.c_uint64, ctypes.c_uint32, ctypes.c_float, ctypes.POINTER(ccs_rays), ctypes.c_void_p],
@@ -280,6 +283,19 @@ def ccs_intersect_host(scene: int, rays, n: int, hits, opts: ccs_trace_opts | No
     h = hits if isinstance(hits, ccs_hits) else hits_struct(hits)
     _check(lib().ccs_intersect_host(scene, ctypes.byref(r), n, ctypes.byref(h),
                                     ctypes.byref(opts) if opts else None, _stream(stream)))
+
+
+def ccs_intersect_host_batches(scene: int, rays_list, n_list, hits_list, opts_list=None, stream=None):
+    """Several host batches through one copy/trace pipeline; opts_list entries may be None (defaults)."""
+    nb = len(rays_list)
+    R = (ccs_rays * nb)(*[r if isinstance(r, ccs_rays) else rays_struct(r) for r in rays_list])
+    H = (ccs_hits * nb)(*[h if isinstance(h, ccs_hits) else hits_struct(h) for h in hits_list])
+    N = (ctypes.c_uint32 * nb)(*[int(x) for x in n_list])
+    O = None
+    if opts_list is not None:
+        O = (ctypes.POINTER(ccs_trace_opts) * nb)(*[ctypes.pointer(o) if o is not None else None
+                                                     for o in opts_list])
+    _check(lib().ccs_intersect_host_batches(scene, nb, R, N, H, O, _stream(stream)))
 
 
 def ccs_gen_diffuse(scene: int, in_rays, hits, n: int, seed: int, leaf_depth: int, offset_abs: float, out_rays,

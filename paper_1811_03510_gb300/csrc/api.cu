@@ -140,6 +140,134 @@ ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRa
     return CCS_OK;
 }
 
+// One batch of host rays for the staged pipeline.
+struct HostBatch {
+    const ccs_rays *hr;
+    uint32_t n;
+    ccs_hits *hh;
+    LaunchCfg cfg;
+};
+
+// The staged copy/trace pipeline of the host-buffer entry points, over the chunks of one or more batches
+// in order: chunk k's rays are copied in while chunk k-1 is traced and chunk k-2's hits are copied out.
+// Consecutive chunks alternate between the caller's stream and a second compute stream, each with its own
+// queue head, so that one chunk's launch fills the SMs that the previous one frees while its last rays
+// finish; across batches the same holds, so one batch's copies and launch overlap the end of the last.
+// Chunks stay large: every launch ends on its slowest rays, and many small chunks pay that drain more
+// often than they save in exposed copy time.  An image's chunk boundaries fall on rows of 8-pixel tiles,
+// so that each chunk is an image too.  Batch j stages its twelve planes (eight of rays, four of hits) at
+// 12 * (rays of the batches before it) floats into the scene's staging buffer.
+ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaStream_t s)
+{
+    size_t total = 0;
+    std::vector<size_t> base(nb);
+    for (uint32_t j = 0; j < nb; ++j) {
+        base[j] = 12 * total;
+        total += bt[j].n;
+    }
+    if (total == 0) return CCS_OK;
+    const size_t need = total * 12 * sizeof(float);
+    if (need > sc->stage_bytes) {
+        CCS_CUDA(cudaStreamSynchronize(s));
+        cudaFree(sc->d_stage);
+        sc->d_stage = nullptr;
+        sc->stage_bytes = 0;
+        CCS_CUDA(cudaMalloc(&sc->d_stage, need));
+        sc->stage_bytes = need;
+    }
+    if (!sc->pipe_h2d) {
+        for (cudaStream_t *q : {&sc->pipe_h2d, &sc->pipe_d2h, &sc->pipe_comp})
+            CCS_CUDA(cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : sc->pipe_ev) CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    struct Chunk {
+        uint32_t j;
+        size_t a, m;
+    };
+    std::vector<Chunk> chunks;
+    for (uint32_t j = 0; j < nb; ++j) {
+        const LaunchCfg &c = bt[j].cfg;
+        const size_t align = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8 : 1;
+        size_t cut[kHostMaxChunks + 1];
+        const uint32_t k_n = bt[j].n ? host_chunk_plan(bt[j].n, c.host_chunk, align, cut) : 0;
+        for (uint32_t k = 0; k < k_n; ++k)
+            if (cut[k + 1] > cut[k]) chunks.push_back(Chunk{j, cut[k], cut[k + 1] - cut[k]});
+    }
+    // events: [0] start, [1] end of the copies out, then pairs (input copied, hits written) that chunks
+    // take in turn: every record is waited on before the pair comes round again, and a wait holds the
+    // work the event captured when it was issued
+    constexpr size_t kPairs = (sizeof(sc->pipe_ev) / sizeof(sc->pipe_ev[0]) - 2) / 2;
+    const cudaEvent_t ev_start = sc->pipe_ev[0], ev_out = sc->pipe_ev[1];
+    CCS_CUDA(cudaEventRecord(ev_start, s));
+    for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));
+    // planes at one constant stride (rows of one host block) move as one 2D copy per chunk
+    auto stride_of = [](const void *const *pl, int k, size_t n) -> size_t {
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(pl[0]);
+        const uintptr_t a1 = reinterpret_cast<uintptr_t>(pl[1]);
+        if (a1 <= a0 || (a1 - a0) % 4 != 0 || a1 - a0 < n * 4) return 0;
+        for (int c = 2; c < k; ++c)
+            if (reinterpret_cast<uintptr_t>(pl[c]) != a0 + (uintptr_t)c * (a1 - a0)) return 0;
+        return a1 - a0;
+    };
+    std::vector<size_t> in_pitch(nb), out_pitch(nb);
+    for (uint32_t j = 0; j < nb; ++j) {
+        const ccs_rays *r = bt[j].hr;
+        const ccs_hits *h = bt[j].hh;
+        const void *srcv[8] = {r->ox, r->oy, r->oz, r->dx, r->dy, r->dz, r->tmin, r->tmax};
+        const void *dstv[4] = {h->t, h->u, h->v, h->patch_id};
+        in_pitch[j] = stride_of(srcv, 8, bt[j].n);
+        out_pitch[j] = stride_of(dstv, 4, bt[j].n);
+    }
+    float *stage = static_cast<float *>(sc->d_stage);
+    for (size_t k = 0; k < chunks.size(); ++k) {
+        const Chunk &ck = chunks[k];
+        const HostBatch &B = bt[ck.j];
+        const size_t n = B.n, a = ck.a, m = ck.m;
+        float *b = stage + base[ck.j];
+        const float *src[8] = {B.hr->ox, B.hr->oy, B.hr->oz, B.hr->dx, B.hr->dy, B.hr->dz, B.hr->tmin, B.hr->tmax};
+        void *dst[4] = {B.hh->t, B.hh->u, B.hh->v, B.hh->patch_id};
+        const cudaEvent_t ev_in = sc->pipe_ev[2 + 2 * (k % kPairs)], ev_hit = sc->pipe_ev[3 + 2 * (k % kPairs)];
+        // (equally spaced planes of separate allocations are refused by the runtime at the call, with
+        // nothing enqueued; the copies then go plane by plane)
+        if (in_pitch[ck.j] && cudaMemcpy2DAsync(b + a, n * 4, src[0] + a, in_pitch[ck.j], m * 4, 8,
+                                                cudaMemcpyHostToDevice, sc->pipe_h2d) != cudaSuccess) {
+            (void)cudaGetLastError();
+            in_pitch[ck.j] = 0;
+        }
+        if (!in_pitch[ck.j]) {
+            for (int c = 0; c < 8; ++c)
+                CCS_CUDA(cudaMemcpyAsync(b + c * n + a, src[c] + a, m * 4, cudaMemcpyHostToDevice, sc->pipe_h2d));
+        }
+        CCS_CUDA(cudaEventRecord(ev_in, sc->pipe_h2d));
+        cudaStream_t cs = (k & 1) ? sc->pipe_comp : s;
+        CCS_CUDA(cudaStreamWaitEvent(cs, ev_in, 0));
+        const DevRays dr{b + a, b + n + a, b + 2 * n + a, b + 3 * n + a, b + 4 * n + a, b + 5 * n + a,
+                         b + 6 * n + a, b + 7 * n + a};
+        const DevHits dh{b + 8 * n + a, b + 9 * n + a, b + 10 * n + a, reinterpret_cast<uint32_t *>(b + 11 * n + a)};
+        const uint32_t *perm;
+        ccs_status st = work_order(sc, (int)(k & 1), B.cfg, dr, (uint32_t)m, cs, &perm);
+        if (st != CCS_OK) return st;
+        CCS_CUDA(launch_intersect(dev_scene(sc, B.cfg.bvh_width), dr, dh, (uint32_t)m, B.cfg, take_queue(sc),
+                                  sc->d_work + 1, sc->num_sms, cs, perm));
+        CCS_CUDA(cudaEventRecord(ev_hit, cs));
+        CCS_CUDA(cudaStreamWaitEvent(sc->pipe_d2h, ev_hit, 0));
+        if (out_pitch[ck.j] && cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + a * 4, out_pitch[ck.j], b + 8 * n + a,
+                                                 n * 4, m * 4, 4, cudaMemcpyDeviceToHost, sc->pipe_d2h) != cudaSuccess) {
+            (void)cudaGetLastError();
+            out_pitch[ck.j] = 0;
+        }
+        if (!out_pitch[ck.j]) {
+            for (int c = 0; c < 4; ++c)
+                CCS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst[c]) + a * 4, b + (8 + c) * n + a, m * 4,
+                                         cudaMemcpyDeviceToHost, sc->pipe_d2h));
+        }
+    }
+    CCS_CUDA(cudaEventRecord(ev_out, sc->pipe_d2h));
+    CCS_CUDA(cudaStreamWaitEvent(s, ev_out, 0));
+    CCS_CUDA(cudaStreamSynchronize(s));
+    return CCS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -460,92 +588,31 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
             return CCS_OK;
         }
     }
-    const size_t need = (size_t)n * 12 * sizeof(float);
-    if (need > sc->stage_bytes) {
-        CCS_CUDA(cudaStreamSynchronize(s));
-        cudaFree(sc->d_stage);
-        sc->d_stage = nullptr;
-        sc->stage_bytes = 0;
-        CCS_CUDA(cudaMalloc(&sc->d_stage, need));
-        sc->stage_bytes = need;
+    const HostBatch one{hr, n, hh, cfg};
+    return host_pipeline(sc, &one, 1, s);
+}
+
+ccs_status ccs_intersect_host_batches(ccs_scene *sc, uint32_t n_batches, const ccs_rays *hr, const uint32_t *n,
+                                      ccs_hits *hh, const ccs_trace_opts *const *opts, void *stream)
+{
+    CCS_ARG(sc, "scene is NULL");
+    CCS_ARG(n_batches == 0 || (hr && n && hh), "rays, n and hits must be given when n_batches > 0");
+    if (!sc->built) {
+        set_error("ccs_intersect_host_batches before ccs_bvh_build");
+        return CCS_ERR_NOT_BUILT;
     }
-    if (!sc->pipe_h2d) {
-        for (cudaStream_t *q : {&sc->pipe_h2d, &sc->pipe_d2h, &sc->pipe_comp})
-            CCS_CUDA(cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
-        for (cudaEvent_t &e : sc->pipe_ev) CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    // every batch is checked before any work is queued
+    std::vector<HostBatch> bt(n_batches);
+    for (uint32_t j = 0; j < n_batches; ++j) {
+        ccs_status st = check_rays(&hr[j], &hh[j]);
+        if (st != CCS_OK) return st;
+        LaunchCfg cfg;
+        if ((st = fill_launch_cfg(opts ? opts[j] : nullptr, cfg)) != CCS_OK) return st;
+        CCS_ARG(has_width(sc, cfg.bvh_width), "the scene has no BVH of the width opts->bvh_width asks for");
+        if (cfg.pixel_spread > 0.0f) cfg.mode = 4;
+        bt[j] = HostBatch{&hr[j], n[j], &hh[j], cfg};
     }
-    // Pipeline over chunks: chunk k's rays are copied in while chunk k-1 is traced and chunk k-2's hits
-    // are copied out.  Consecutive chunks alternate between the caller's stream and a second compute
-    // stream, each with its own queue head, so that one chunk's launch fills the SMs that the previous
-    // one frees while its last rays finish.  Chunks stay large: every launch ends on its slowest rays,
-    // and many small chunks pay that drain more often than they save in exposed copy time.  An image's
-    // chunk boundaries fall on rows of 8-pixel tiles, so that each chunk is an image too.
-    const size_t align = (cfg.flags & CCS_TRACE_ORDER) && cfg.image_width ? (size_t)cfg.image_width * 8 : 1;
-    size_t cut[kHostMaxChunks + 1];
-    const uint32_t chunks = host_chunk_plan(n, cfg.host_chunk, align, cut);
-    auto bound = [&](uint32_t k) -> size_t { return cut[k]; };
-    cudaEvent_t *ev_in = sc->pipe_ev, *ev_hit = sc->pipe_ev + 8, ev_start = sc->pipe_ev[16], ev_out = sc->pipe_ev[17];
-    CCS_CUDA(cudaEventRecord(ev_start, s));
-    for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));
-    float *b = static_cast<float *>(sc->d_stage);
-    const float *src[8] = {hr->ox, hr->oy, hr->oz, hr->dx, hr->dy, hr->dz, hr->tmin, hr->tmax};
-    void *dst[4] = {hh->t, hh->u, hh->v, hh->patch_id};
-    // planes at one constant stride (rows of one host block) move as one 2D copy per chunk
-    auto stride_of = [n](const void *const *pl, int k) -> size_t {
-        const uintptr_t a0 = reinterpret_cast<uintptr_t>(pl[0]);
-        const uintptr_t a1 = reinterpret_cast<uintptr_t>(pl[1]);
-        if (a1 <= a0 || (a1 - a0) % 4 != 0 || a1 - a0 < (size_t)n * 4) return 0;
-        for (int c = 2; c < k; ++c)
-            if (reinterpret_cast<uintptr_t>(pl[c]) != a0 + (uintptr_t)c * (a1 - a0)) return 0;
-        return a1 - a0;
-    };
-    const void *srcv[8];
-    for (int c = 0; c < 8; ++c) srcv[c] = src[c];
-    // (equally spaced planes of separate allocations are refused by the runtime at the call, with nothing
-    // enqueued; the copies then go plane by plane)
-    size_t in_pitch = stride_of(srcv, 8), out_pitch = stride_of(dst, 4);
-    const DevScene ds = dev_scene(sc, cfg.bvh_width);
-    for (uint32_t k = 0; k < chunks; ++k) {
-        const size_t a = bound(k), m = bound(k + 1) - a;
-        if (m == 0) continue;
-        if (in_pitch && cudaMemcpy2DAsync(b + a, (size_t)n * 4, src[0] + a, in_pitch, m * 4, 8, cudaMemcpyHostToDevice,
-                                          sc->pipe_h2d) != cudaSuccess) {
-            (void)cudaGetLastError();
-            in_pitch = 0;
-        }
-        if (!in_pitch) {
-            for (int c = 0; c < 8; ++c)
-                CCS_CUDA(cudaMemcpyAsync(b + (size_t)c * n + a, src[c] + a, m * 4, cudaMemcpyHostToDevice,
-                                         sc->pipe_h2d));
-        }
-        CCS_CUDA(cudaEventRecord(ev_in[k], sc->pipe_h2d));
-        cudaStream_t cs = (k & 1) ? sc->pipe_comp : s;
-        CCS_CUDA(cudaStreamWaitEvent(cs, ev_in[k], 0));
-        const DevRays dr{b + a, b + n + a, b + 2 * (size_t)n + a, b + 3 * (size_t)n + a, b + 4 * (size_t)n + a,
-                         b + 5 * (size_t)n + a, b + 6 * (size_t)n + a, b + 7 * (size_t)n + a};
-        const DevHits dh{b + 8 * (size_t)n + a, b + 9 * (size_t)n + a, b + 10 * (size_t)n + a,
-                         reinterpret_cast<uint32_t *>(b + 11 * (size_t)n + a)};
-        const uint32_t *perm;
-        if ((st = work_order(sc, (int)(k & 1), cfg, dr, (uint32_t)m, cs, &perm)) != CCS_OK) return st;
-        CCS_CUDA(launch_intersect(ds, dr, dh, (uint32_t)m, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, cs,
-                                  perm));
-        CCS_CUDA(cudaEventRecord(ev_hit[k], cs));
-        CCS_CUDA(cudaStreamWaitEvent(sc->pipe_d2h, ev_hit[k], 0));
-        if (out_pitch && cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + a * 4, out_pitch, b + (size_t)8 * n + a,
-                                           (size_t)n * 4, m * 4, 4, cudaMemcpyDeviceToHost, sc->pipe_d2h) != cudaSuccess) {
-            (void)cudaGetLastError();
-            out_pitch = 0;
-        }
-        if (!out_pitch) {
-            for (int c = 0; c < 4; ++c)
-                CCS_CUDA(cudaMemcpyAsync(static_cast<char *>(dst[c]) + a * 4, b + (size_t)(8 + c) * n + a, m * 4,
-                                         cudaMemcpyDeviceToHost, sc->pipe_d2h));
-        }
-    }
-    CCS_CUDA(cudaEventRecord(ev_out, sc->pipe_d2h));
-    CCS_CUDA(cudaStreamWaitEvent(s, ev_out, 0));
-    CCS_CUDA(cudaStreamSynchronize(s));
-    return CCS_OK;
+    return host_pipeline(sc, bt.data(), n_batches, (cudaStream_t)stream);
 }
 
 static ccs_status gen_secondary(const ccs_scene *sc, const ccs_rays *in, const ccs_hits *hits, uint32_t n, uint64_t seed,

@@ -372,3 +372,47 @@ def test_concurrent_launches_on_one_scene_use_separate_queues():
                 assert np.array_equal(got[k], ref[k]), k
     assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
     sc.close()
+
+
+def test_host_batches_match_the_device_path_batch_by_batch():
+    """ccs_intersect_host_batches: host batches with options of their own go through one copy/trace
+    pipeline (a batch's copies and launches overlap the end of the one before) and each gets its device
+    path's hits.  Page-locked and pageable planes, an empty batch, a batch of 17 rays, and more chunks
+    than the scene has event pairs; an invalid batch is refused before anything runs."""
+    s = sg.config_scene(2)
+    sc = ccs.Scene(s.P, s.types, local=True, bvh_width="both")
+    prim = sg.pinhole_rays(1920, 1080).subset(np.arange(1920 * 700 + 13))
+    diff = sg.random_rays(333918, seed=93)
+    tiny = sg.random_rays(17, seed=94)
+    rays = [prim, tiny, diff, tiny]
+    n_list = [prim.n, 0, diff.n, tiny.n]
+    opts = [ccs.make_opts(order=True, image_width=1920), None,
+            ccs.make_opts(bvh_width=4, host_chunk=40000), ccs.make_opts(lanes_per_ray=3)]
+    refs = []
+    for r, n, o in zip(rays, n_list, opts):
+        refs.append(ccs.hits_to_numpy(ccs.intersect(sc, ccs.rays_to_device(r.soa()), o or ccs.make_opts()))
+                    if n else None)
+    torch.cuda.synchronize()
+    # the first batch in page-locked memory, the others pageable
+    planes = [[torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in prim.soa()]]
+    planes += [[np.ascontiguousarray(a) for a in r.soa()] for r in rays[1:]]
+    ray_ptrs = [[a.data_ptr() if torch.is_tensor(a) else a.ctypes.data for a in p] for p in planes]
+    for rep in range(2):    # the second call reuses the staging buffer, streams and events
+        outs = [[torch.full((max(n, 1),), -7.0).pin_memory() for _ in range(4)] if j == 0 else
+                [np.full(max(n, 1), -7, np.float32) for _ in range(4)] for j, n in enumerate(n_list)]
+        hit_ptrs = [[h.data_ptr() if torch.is_tensor(h) else h.ctypes.data for h in o] for o in outs]
+        ccs.ccs_intersect_host_batches(sc.handle, ray_ptrs, n_list, hit_ptrs, opts)
+        for j, (o, ref) in enumerate(zip(outs, refs)):
+            got = [h.numpy() if torch.is_tensor(h) else h for h in o]
+            if ref is None:
+                assert (got[0] == -7).all()
+                continue
+            assert np.array_equal(got[3].view(np.uint32), ref["pid"]), (rep, j)
+            for k, c in (("t", 0), ("u", 1), ("v", 2)):
+                assert np.array_equal(got[c], ref[k]), (rep, j, k)
+    with pytest.raises(ccs.CcsError):      # an invalid BVH width in the third batch
+        ccs.ccs_intersect_host_batches(sc.handle, ray_ptrs[:3], n_list[:3], hit_ptrs[:3],
+                                       [None, None, ccs.make_opts(bvh_width=8)])
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    assert (refs[0]["pid"] != MISS).sum() > 1000 and (refs[2]["pid"] != MISS).sum() > 1000
+    sc.close()
