@@ -494,7 +494,7 @@ ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t 
     CCS_ARG(cfg.leaf_depth >= 3, "trace export needs leaf_depth >= 3 (labels are depth-3 cells)");
     cfg.flags &= ~CCS_TRACE_COUNT;
     cfg.mode = 1;
-    cfg.mc = ModeCtx{features, labels, count, capacity};
+    cfg.mc = ModeCtx{features, labels, count, capacity, nullptr, 0.0f};
     CCS_CUDA(cudaMemsetAsync(count, 0, sizeof(uint32_t), (cudaStream_t)stream));
     DevScene ds = dev_scene(sc, cfg.bvh_width);
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
