@@ -180,19 +180,15 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
             CCS_CUDA(cudaStreamCreateWithFlags(q, cudaStreamNonBlocking));
         for (cudaEvent_t &e : sc->pipe_ev) CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
-    struct Chunk {
-        uint32_t j;
-        size_t a, m;
-    };
-    std::vector<Chunk> chunks;
+    std::vector<uint32_t> ns(nb), hc(nb);
+    std::vector<size_t> align(nb);
     for (uint32_t j = 0; j < nb; ++j) {
         const LaunchCfg &c = bt[j].cfg;
-        const size_t align = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8 : 1;
-        size_t cut[kHostMaxChunks + 1];
-        const uint32_t k_n = bt[j].n ? host_chunk_plan(bt[j].n, c.host_chunk, align, cut) : 0;
-        for (uint32_t k = 0; k < k_n; ++k)
-            if (cut[k + 1] > cut[k]) chunks.push_back(Chunk{j, cut[k], cut[k + 1] - cut[k]});
+        ns[j] = bt[j].n;
+        hc[j] = c.host_chunk;
+        align[j] = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8 : 1;
     }
+    const std::vector<HostChunk> chunks = host_batch_chunks(nb, ns.data(), hc.data(), align.data());
     // events: [0] start, [1] end of the copies out, then pairs (input copied, hits written) that chunks
     // take in turn: every record is waited on before the pair comes round again, and a wait holds the
     // work the event captured when it was issued
@@ -220,7 +216,7 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
     }
     float *stage = static_cast<float *>(sc->d_stage);
     for (size_t k = 0; k < chunks.size(); ++k) {
-        const Chunk &ck = chunks[k];
+        const HostChunk &ck = chunks[k];
         const HostBatch &B = bt[ck.j];
         const size_t n = B.n, a = ck.a, m = ck.m;
         float *b = stage + base[ck.j];

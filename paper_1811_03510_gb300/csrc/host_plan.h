@@ -1,10 +1,12 @@
-// Chunk plan of the host-buffer path (ccs_intersect_host), plain host C++ so that it can be tested on
-// its own: boundaries cut[0..chunks] of at most 8 chunks over n rays.
+// Chunk plan of the host-buffer paths (ccs_intersect_host, ccs_intersect_host_batches), plain host C++ so
+// that it can be tested on its own: boundaries cut[0..chunks] of at most 8 chunks over n rays, and the
+// chunk list of several batches in a row.
 #pragma once
 #include <stddef.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 namespace ccs {
 
@@ -34,6 +36,28 @@ inline uint32_t host_chunk_plan(uint32_t n, uint32_t host_chunk, size_t align, s
     if (align > 1)
         for (uint32_t k = 1; k < chunks; ++k) cut[k] = cut[k] / align * align;
     return chunks;
+}
+
+// One chunk of a pipeline over several batches: rays [a, a + m) of batch j.
+struct HostChunk {
+    uint32_t j;
+    size_t a, m;
+};
+
+// The chunks of batches 0..nb-1 in order, each batch planned by host_chunk_plan with its own chunk size
+// and alignment; empty chunks (and so empty batches) are left out.
+inline std::vector<HostChunk> host_batch_chunks(uint32_t nb, const uint32_t *n, const uint32_t *host_chunk,
+                                                const size_t *align)
+{
+    std::vector<HostChunk> out;
+    for (uint32_t j = 0; j < nb; ++j) {
+        if (n[j] == 0) continue;
+        size_t cut[kHostMaxChunks + 1];
+        const uint32_t c = host_chunk_plan(n[j], host_chunk[j], align[j], cut);
+        for (uint32_t k = 0; k < c; ++k)
+            if (cut[k + 1] > cut[k]) out.push_back(HostChunk{j, cut[k], cut[k + 1] - cut[k]});
+    }
+    return out;
 }
 
 }  // namespace ccs
