@@ -10,8 +10,8 @@
  *    asynchronously on it unless the entry point says otherwise; caller-owned device buffers must stay
  *    valid until that work completes.  Launches on one scene may run at the same time on different
  *    streams (each takes its own work-queue head from a ring of 48), except launches with
- *    CCS_TRACE_ORDER, which share the scene's work-order scratch, and ccs_intersect_host calls, which
- *    share its staging buffer.
+ *    CCS_TRACE_ORDER, which share the scene's work-order scratch, and ccs_intersect_host and
+ *    ccs_intersect_host_batches calls, which share its staging buffer.
  *  - Every call returns a ccs_status.  On failure, ccs_last_error() returns a message for the calling
  *    thread.  Errors detected on the device (traversal iteration cap reached) are latched in a status
  *    word of the scene and returned by ccs_scene_sync_status().
