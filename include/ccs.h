@@ -76,7 +76,8 @@ typedef struct {
     uint32_t bvh_burst;       /* BVH steps a traversing lane takes per subdivision step of the others,
                                  1..16 [8] */
     uint32_t cache_slots;     /* grids of pending Bezier siblings kept in shared memory per thread,
-                                 0 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root */
+                                 0, 1 or 2 [2]; 0 re-derives every sibling by de Casteljau from the root
+                                 (the ray-persistent kernel takes 1 as 2) */
     uint32_t min_blocks;      /* 0: kernel compiled for 3 blocks of 128 threads per SM (168 registers);
                                  4: compiled for 4 blocks (128 registers, spills to L1) [0] */
     uint32_t vote;            /* 0: every lane steps every iteration; v > 0: per iteration a warp steps
@@ -124,6 +125,20 @@ typedef struct {
                                        the scene (allocated on first use and on growth, which synchronises
                                        the stream).  Used by ccs_intersect, ccs_intersect_host and
                                        ccs_occluded; the other entry points ignore it. */
+#define CCS_TRACE_PAIRS 8u          /* pair engine, for the plain closest hit and the any-hit query with one
+                                       lane per ray (other modes ignore it): (1) one thread per ray walks
+                                       the BVH and keeps the ray's 16 nearest candidate patches (by entry
+                                       distance of the patch box); (2) persistent warps run Algorithm 3 on
+                                       one (ray, patch) pair per lane, taking each ray's Bezier candidates
+                                       in entry order until one enters beyond its best hit, so that every
+                                       warp iteration is one subdivision step of up to 32 pairs; (3) the
+                                       same over the Gregory candidates, from the Bezier answer; (4) rays
+                                       whose dropped candidates could still hold the answer are traced
+                                       again by the ray-persistent kernel.  Hits are bit-identical.  Uses
+                                       about 100 bytes of scratch per ray from a stream-ordered memory
+                                       pool of the library (kept for reuse), on the launch's stream; the
+                                       work order, bvh_burst, vote, chunk and min_blocks do not apply, and
+                                       blocks_per_sm is what fits. */
 #define CCS_NUM_COUNTERS 23         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
                                        splits, leaves, backtracks, re-descent levels, pruned siblings, pairs;
                                        schedule of the warps, summed over warp iterations (8..19): warp
@@ -280,8 +295,10 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
 ccs_status ccs_batch_set_points(ccs_batch *b, uint32_t scene_index, const float *x, const float *y, const float *z);
 
 /* Enqueue the selected stages (CCS_BATCH_* bits) on `stream`: the table copy, one repack launch,
- * one refit launch and one intersect launch.  Allocates nothing and does not synchronise.  Answers
- * are bit-identical to ccs_intersect on each scene alone. */
+ * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's five
+ * launches over the rays of all scenes, whose scratch of about 100 bytes per ray the batch allocates
+ * with cudaMalloc on its first such run and keeps).  Otherwise allocates nothing; does not synchronise.
+ * Answers are bit-identical to ccs_intersect on each scene alone. */
 ccs_status ccs_batch_run(ccs_batch *b, uint32_t stages, const ccs_trace_opts *opts, void *stream);
 
 /* Run once, then capture ccs_batch_run(stages, opts) into a CUDA graph owned by the batch (on an

@@ -20,6 +20,7 @@ CCS_GREGORY = 1
 CCS_TRACE_COUNT = 1
 CCS_TRACE_ORDER = 2
 CCS_TRACE_HOST_MAPPED = 4
+CCS_TRACE_PAIRS = 8
 CCS_BVH_BOTH = 6
 CCS_NUM_COUNTERS = 23
 COUNTER_NAMES = ("bvh_nodes", "bezier_splits", "gregory_splits", "leaves", "backtracks", "redescent_levels",
@@ -206,10 +207,11 @@ CCS_CACHE_DEFAULT = 0xFFFFFFFF
 def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0, bvh_burst=0,
               cache_slots=CCS_CACHE_DEFAULT, min_blocks=0, vote=0, lanes_per_ray=0, iter_cap=0,
               counters=None, pixel_spread=0.0, order=False, image_width=0, host_chunk=0,
-              host_mapped=False, bvh_width=0) -> ccs_trace_opts:
+              host_mapped=False, bvh_width=0, pairs=False) -> ccs_trace_opts:
     """ccs_trace_opts with the fields of include/ccs.h (0: the library's default).  counters: a device
     int64 tensor of CCS_NUM_COUNTERS entries (sets CCS_TRACE_COUNT); order: CCS_TRACE_ORDER over tiles of
-    an image of width image_width (0: runs of 32 rays); host_mapped: CCS_TRACE_HOST_MAPPED."""
+    an image of width image_width (0: runs of 32 rays); host_mapped: CCS_TRACE_HOST_MAPPED; pairs:
+    CCS_TRACE_PAIRS (the pair engine)."""
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth
     o.block_threads = block_threads
@@ -224,7 +226,7 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
     o.iter_cap = iter_cap
     o.pixel_spread = pixel_spread
     o.flags = ((CCS_TRACE_COUNT if counters is not None else 0) | (CCS_TRACE_ORDER if order else 0)
-               | (CCS_TRACE_HOST_MAPPED if host_mapped else 0))
+               | (CCS_TRACE_HOST_MAPPED if host_mapped else 0) | (CCS_TRACE_PAIRS if pairs else 0))
     o.counters = _ptr(counters) if counters is not None else None
     o.image_width = image_width
     o.host_chunk = host_chunk

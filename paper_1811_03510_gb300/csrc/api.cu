@@ -94,14 +94,15 @@ ccs_status ccs::fill_launch_cfg(const ccs_trace_opts *o, LaunchCfg &c)
     CCS_ARG(c.refill >= 1 && c.refill <= 32, "refill must be in 1..32");
     CCS_ARG(c.chunk % 32 == 0 && c.chunk >= 32 && c.chunk <= 4096, "chunk must be a multiple of 32 in 32..4096");
     CCS_ARG(c.bvh_burst >= 1 && c.bvh_burst <= 16, "bvh_burst must be in 1..16");
-    CCS_ARG(c.cache_slots == 0 || c.cache_slots == 2, "cache_slots must be 0 or 2");
+    CCS_ARG(c.cache_slots <= 2, "cache_slots must be 0, 1 or 2");
     CCS_ARG(c.min_blocks == 0 || c.min_blocks == 4, "min_blocks must be 0 or 4");
     CCS_ARG(c.vote <= 32, "vote must be in 0..32");
     CCS_ARG(c.lanes_per_ray == 1 || c.lanes_per_ray == 3, "lanes_per_ray must be 1 or 3");
     CCS_ARG(c.pixel_spread >= 0.0f && c.pixel_spread < 1.0f, "pixel_spread must be in [0, 1) radians per pixel");
     CCS_ARG(c.bvh_width == 0 || c.bvh_width == 2 || c.bvh_width == 4, "bvh_width must be 0, 2 or 4");
     CCS_ARG(!(c.flags & CCS_TRACE_COUNT) || c.counters, "CCS_TRACE_COUNT needs opts->counters");
-    CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER | CCS_TRACE_HOST_MAPPED)) == 0, "unknown trace flags");
+    CCS_ARG((c.flags & ~(CCS_TRACE_COUNT | CCS_TRACE_ORDER | CCS_TRACE_HOST_MAPPED | CCS_TRACE_PAIRS)) == 0,
+            "unknown trace flags");
     return CCS_OK;
 }
 
@@ -122,7 +123,7 @@ ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRa
                       const uint32_t **perm)
 {
     *perm = nullptr;
-    if (!(cfg.flags & CCS_TRACE_ORDER) || n == 0) return CCS_OK;
+    if (!(cfg.flags & CCS_TRACE_ORDER) || n == 0 || use_pairs(cfg)) return CCS_OK;
     const size_t words = order_scratch_words(n, cfg.image_width);
     if (words > sc->order_words[slot]) {
         CCS_CUDA(cudaStreamSynchronize(s));
@@ -305,7 +306,10 @@ ccs_status ccs_scene_create(ccs_scene **out, const float *x, const float *y, con
             if ((e = cudaMemcpy(sc->hy.data(), y, np * 4, k)) != cudaSuccess) break;
             if ((e = cudaMemcpy(sc->hz.data(), z, np * 4, k)) != cudaSuccess) break;
             if ((e = cudaMemcpy(sc->htypes.data(), types, n_patches, k)) != cudaSuccess) break;
-            for (uint32_t i = 0; i < n_patches; ++i) sc->htypes[i] = sc->htypes[i] ? 1 : 0;
+            for (uint32_t i = 0; i < n_patches; ++i) {
+                sc->htypes[i] = sc->htypes[i] ? 1 : 0;
+                sc->n_greg += sc->htypes[i];
+            }
             if ((e = cudaMalloc(&sc->d_rec, (size_t)n_patches * kRecF4 * sizeof(float4))) != cudaSuccess) break;
             if ((e = cudaMalloc(&sc->d_leaf_box, (size_t)n_patches * 2 * sizeof(float4))) != cudaSuccess) break;
             if ((e = cudaMalloc(&sc->d_types, n_patches)) != cudaSuccess) break;

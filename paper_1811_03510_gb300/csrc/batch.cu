@@ -76,6 +76,7 @@ struct ccs_batch {
     uint32_t *d_ray_prefix = nullptr, *d_patch_prefix = nullptr;
     uint32_t *d_flags = nullptr;          // refit arrival counters of every scene's nodes
     uint32_t *d_work = nullptr;           // [0] queue head, [1] status word
+    void *d_pairs = nullptr;              // the pair engine's scratch (CCS_TRACE_PAIRS), made on first use
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -93,6 +94,7 @@ static void batch_free(ccs_batch *b)
     cudaFree(b->d_patch_prefix);
     cudaFree(b->d_flags);
     cudaFree(b->d_work);
+    cudaFree(b->d_pairs);
     delete b;
 }
 
@@ -229,9 +231,14 @@ ccs_status ccs_batch_run(ccs_batch *b, uint32_t stages, const ccs_trace_opts *op
     if (stages & CCS_BATCH_UPDATE) BCK(launch_batch_repack(b->d_table, b->d_patch_prefix, b->n, b->n_patches, s));
     if (stages & CCS_BATCH_REFIT)
         BCK(launch_batch_refit(b->d_table, b->d_patch_prefix, b->n, b->n_patches, b->d_flags, b->n_nodes, s));
-    if (stages & CCS_BATCH_INTERSECT)
+    if ((stages & CCS_BATCH_INTERSECT) && use_pairs(cfg)) {
+        if (!b->d_pairs) BCK(cudaMalloc(&b->d_pairs, pairs_scratch_bytes(b->n_rays ? b->n_rays : 1)));
+        BCK(launch_pairs_batch(b->d_table, b->d_ray_prefix, b->n, b->n_rays, cfg, b->d_pairs, b->d_work + 1,
+                               b->num_sms, s, b->width));
+    } else if (stages & CCS_BATCH_INTERSECT) {
         BCK(launch_intersect_batch(b->d_table, b->d_ray_prefix, b->n, b->n_rays, cfg, b->d_work, b->d_work + 1,
                                    b->num_sms, s, b->width));
+    }
     return CCS_OK;
 }
 

@@ -61,6 +61,7 @@ struct LaunchCfg {
     ModeCtx mc{};
     const MlpWeights *mlp = nullptr;
     float min_conf = 0.0f;
+    const uint32_t *count_dev = nullptr;  // device word: the launch traces only its first *count_dev rays
 };
 
 struct DevScene {
@@ -70,6 +71,8 @@ struct DevScene {
     uint32_t n_patches, n_nodes;
     uint32_t local;          // records hold points in local frames (Sec. 3.4)
     uint32_t width;          // BVH node width: 2 or 4
+    const uint8_t *types;    // n_patches bytes: 0 Bezier, 1 Gregory
+    uint32_t n_greg;         // Gregory patches in the scene
 };
 
 struct DevRays {
@@ -108,7 +111,16 @@ cudaError_t launch_order(const DevScene &sc, const DevRays &r, uint32_t n, uint3
                          cudaStream_t s);
 cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
                                    uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
-                                   int num_sms, cudaStream_t s, uint32_t width);
+                                   int num_sms, cudaStream_t s, uint32_t width, const uint32_t *perm = nullptr);
+// pair engine (pairs.cu): whether a launch with these options runs it, its scratch for n rays, and the
+// launches (single scene: scratch from the library's stream-ordered pool; batch: the caller's scratch)
+bool use_pairs(const LaunchCfg &cfg);
+size_t pairs_scratch_bytes(uint32_t n);
+cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
+                                const LaunchCfg &cfg, uint32_t *status, int num_sms, cudaStream_t s);
+cudaError_t launch_pairs_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
+                               uint32_t n_total, const LaunchCfg &cfg, void *scratch,
+                               uint32_t *status, int num_sms, cudaStream_t s, uint32_t width);
 cudaError_t launch_batch_repack(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
                                 uint32_t n_patches, cudaStream_t s);
 cudaError_t launch_batch_refit(const BatchEntry *entries, const uint32_t *patch_prefix, uint32_t n_scenes,
@@ -133,6 +145,7 @@ struct ccs_scene {
     float4 *d_rec = nullptr;           // patch records
     float4 *d_leaf_box = nullptr;      // 2 float4 per patch: (lo.xyz, 0), (hi.xyz, 0)
     uint8_t *d_types = nullptr;
+    uint32_t n_greg = 0;               // Gregory patches
     float4 *d_nodes = nullptr;
     int *d_leaf_parent = nullptr;      // per patch: (node << 1) | slot
     uint32_t *d_refit_flags = nullptr; // per node arrival counters of the refit
@@ -170,7 +183,8 @@ inline uint32_t *take_queue(ccs_scene *sc)
 
 inline DevScene dev_scene(const ccs_scene *sc)
 {
-    return DevScene{sc->d_rec, sc->d_nodes, sc->d_leaf_box, sc->n, sc->n_nodes, sc->local ? 1u : 0u, sc->bvh_width};
+    return DevScene{sc->d_rec,        sc->d_nodes, sc->d_leaf_box, sc->n, sc->n_nodes, sc->local ? 1u : 0u,
+                    sc->bvh_width,    sc->d_types, sc->n_greg};
 }
 
 // The scene seen through its BVH of the given width (0: the default one); the caller has checked that
@@ -182,7 +196,7 @@ inline bool has_width(const ccs_scene *sc, uint32_t width)
 inline DevScene dev_scene(const ccs_scene *sc, uint32_t width)
 {
     if (width == 0 || width == sc->bvh_width) return dev_scene(sc);
-    return DevScene{sc->d_rec, sc->d_nodes_alt, sc->d_leaf_box, sc->n, sc->n_nodes_alt, sc->local ? 1u : 0u,
-                    sc->alt_width};
+    return DevScene{sc->d_rec,     sc->d_nodes_alt, sc->d_leaf_box, sc->n,       sc->n_nodes_alt,
+                    sc->local ? 1u : 0u, sc->alt_width, sc->d_types, sc->n_greg};
 }
 }  // namespace ccs

@@ -1,0 +1,685 @@
+// Closest hit in passes that each keep a warp on one kind of work (the pair engine, CCS_TRACE_PAIRS).
+//
+//  1. k_cand: one thread per ray walks the BVH (Sec. 4) and keeps the ray's kPairCands nearest candidate
+//     patches, ordered by (entry distance of the patch box, patch id).  Before the list is full nothing
+//     is pruned but [tmin, tmax]; once it is full, subtrees that enter beyond its last entry are skipped
+//     and the smallest entry distance dropped that way is kept (t_evict).  A ray with candidates becomes a
+//     task with a cost class (its candidates, Gregory patches counted three times); rays with no
+//     candidate are written as misses here.
+//  2. k_task_place: a counting sort of the tasks by cost class, costliest first, so that the long rays
+//     start early and the launch does not end on a few of them.
+//  3. k_pairs: persistent warps take tasks in that order.  A lane runs Algorithm 3 on one (ray, patch) pair
+//     at a time, taking the ray's candidates in entry order and stopping at the first one that enters
+//     beyond the ray's best hit.  Every warp iteration is one subdivision step (Algorithm 3's loop body)
+//     of up to 32 pairs: the BVH walk, whose step count differs from ray to ray, is not in the loop.
+//  4. Rays whose dropped candidates could still hold the answer (best hit not before t_evict), or whose
+//     candidates did not fit the buffer, go to a fallback list, traced again by the ray-persistent kernel
+//     (k_intersect) from scratch.
+//
+// The answer is the smallest leaf key over all nested intervals (readings A14/A15), which does not depend
+// on the order in which pairs are searched, so every pass reuses the arithmetic of traverse.cuh and the
+// hits are bit-identical to k_intersect's.
+#pragma once
+
+#include "intersect_impl.cuh"
+
+namespace ccs {
+
+constexpr int kPairCands = 16;           // candidates kept per ray (nearest entries)
+constexpr uint32_t kCandPerRay = 8;      // candidate buffer per ray of the launch, on average
+constexpr int kCostClasses = 16;
+// counter words of a launch: tasks, candidates written, fallback rays, queue heads (tasks, fallback), the
+// tasks of each cost class and the places handed out in each
+constexpr int kCtrTasks = 0, kCtrCand = 1, kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16,
+              kCtrFill = 32, kPairCtrWords = 64;
+// A task is 4 uint4 (64 bytes), everything a lane needs to start the ray:
+//   (ray, first candidate, z, t_evict bits), (first candidate's patch id, its entry distance, tmin, tmax),
+//   (ox, oy, oz, dx), (dy, dz, 0, 0) as float bits;
+// z = candidates (bits 0..7) | cost class (bits 8..11) | candidates were dropped (bit 30).
+constexpr uint32_t kTaskEvicted = 0x40000000u;
+
+struct PairBufs {
+    uint32_t *ctr;            // kPairCtrWords words, zeroed before the candidate pass
+    uint4 *task;              // tasks in the order the candidate pass made them, up to one per ray
+    uint4 *sorted;            // the same, in the order the queue hands them out
+    uint2 *cand;              // (patch id, entry distance bits)
+    uint32_t *fallback;       // rays traced again by k_intersect, up to n
+    uint32_t cap_cand;        // entries of cand
+};
+
+// Bytes of the pair engine's scratch for n rays, and its layout (every part 256-byte aligned).
+__host__ __device__ inline size_t pair_align(size_t b) { return (b + 255) & ~(size_t)255; }
+inline size_t pair_scratch_bytes(uint32_t n)
+{
+    return pair_align(kPairCtrWords * 4) + 2 * pair_align((size_t)n * 64) + pair_align((size_t)n * kCandPerRay * 8) +
+           pair_align((size_t)n * 4);
+}
+inline PairBufs pair_bufs_at(void *base, uint32_t n)
+{
+    char *p = static_cast<char *>(base);
+    PairBufs b;
+    b.ctr = reinterpret_cast<uint32_t *>(p);
+    p += pair_align(kPairCtrWords * 4);
+    b.task = reinterpret_cast<uint4 *>(p);
+    p += pair_align((size_t)n * 64);
+    b.sorted = reinterpret_cast<uint4 *>(p);
+    p += pair_align((size_t)n * 64);
+    b.cand = reinterpret_cast<uint2 *>(p);
+    p += pair_align((size_t)n * kCandPerRay * 8);
+    b.fallback = reinterpret_cast<uint32_t *>(p);
+    const uint64_t cap = (uint64_t)n * kCandPerRay;
+    b.cap_cand = cap > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap;
+    return b;
+}
+
+// Shared memory of a k_pairs thread after its traversal scratch: the world ray of its task (origin,
+// 1 / direction, tmin, tmax) and t_evict, read when a pair starts and when the ray ends.
+constexpr int kRaySlotFloats = 9;
+
+CCS_DEV bool cand_less(float ta, uint32_t pa, float tb, uint32_t pb) { return ta < tb || (ta == tb && pa < pb); }
+
+// The ray as k_intersect's begin_ray reads it (false: a ray that is a miss by definition).
+CCS_DEV bool load_world_ray(const DevRays &rr, uint32_t j, float (&o)[3], float (&d)[3], float (&inv)[3], float &tmin,
+                            float &tmax)
+{
+    o[0] = __ldg(rr.ox + j);
+    o[1] = __ldg(rr.oy + j);
+    o[2] = __ldg(rr.oz + j);
+    d[0] = __ldg(rr.dx + j);
+    d[1] = __ldg(rr.dy + j);
+    d[2] = __ldg(rr.dz + j);
+    tmin = __ldg(rr.tmin + j);
+    tmax = __ldg(rr.tmax + j);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) inv[k] = safe_inv(d[k]);
+    return !(!(tmin <= tmax) || isnan(o[0]) || isnan(o[1]) || isnan(o[2]) || isnan(d[0]) || isnan(d[1]) ||
+             isnan(d[2]));
+}
+
+template <int MODE, class Src>
+CCS_DEV void write_miss(const Src &src, uint32_t scene, uint32_t j, uint8_t *occluded)
+{
+    if (MODE == kModeAnyHit) {
+        occluded[j] = 0;
+    } else {
+        const DevHits &hh = src.hits_of(scene);
+        hh.t[j] = __int_as_float(0x7f800000);
+        hh.u[j] = 0.0f;
+        hh.v[j] = 0.0f;
+        hh.pid[j] = kMissId;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pass 1: BVH walk with the sorted candidate list.
+// ------------------------------------------------------------------------------------------------
+template <bool STATS, int MODE, class Src, int BW>
+__global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t iter_cap, uint32_t *status,
+                                              unsigned long long *counters, uint8_t *occluded)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const uint32_t n = src.total();
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    constexpr int C = kPairCands;
+    const float kInf = __int_as_float(0x7f800000);
+    float kt[C];
+    uint32_t kp[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        kt[j] = kInf;
+        kp[j] = kMissId;
+    }
+    int cnt = 0;
+    float t_evict = kInf;
+    bool evicted = false, live = false, capped = false;
+    uint32_t ray_scene = 0, ray_local = 0;
+    typename Src::LaneScene lsc;
+    unsigned long long nodes = 0;
+    Grp G;
+    G.c = 0;
+    G.mask = FULL;
+    G.l0 = G.l1 = G.l2 = lane;
+    float ro[3] = {0.0f, 0.0f, 0.0f}, rd[3] = {0.0f, 0.0f, 0.0f}, tmin = 0.0f, tmax = 0.0f;
+    if (i < n) {
+        live = true;
+        src.locate(i, lsc, ray_scene, ray_local);
+        const DevScene &sc = src.scene(lsc);
+        RayG<3> r;
+        const bool ok = load_world_ray(src.rays_of(ray_scene), ray_local, r.org, rd, r.inv, tmin, tmax);
+        ro[0] = r.org[0];
+        ro[1] = r.org[1];
+        ro[2] = r.org[2];
+        if (ok && sc.n_nodes != 0) {
+            int2 stk[kBvhStack];
+            int sp = 0, node = 0;
+            float n0 = tmin;
+            uint32_t it = iter_cap;
+            for (;;) {
+                if (node == kDone) break;
+                if (it == 0) {
+                    capped = true;
+                    break;
+                }
+                --it;
+                if (node < 0) {   // a patch: into the list (the leaf's box is the patch box)
+                    const uint32_t p = (uint32_t)(~node);
+                    bool ins = true;
+                    if (cnt == C) {
+                        evicted = true;
+                        if (!cand_less(n0, p, kt[C - 1], kp[C - 1])) {
+                            t_evict = fminf(t_evict, n0);
+                            ins = false;
+                        } else {
+                            t_evict = fminf(t_evict, kt[C - 1]);
+                        }
+                    } else {
+                        ++cnt;
+                    }
+                    if (ins) {
+                        int m = 0;
+#pragma unroll
+                        for (int j = 0; j < C; ++j) m += cand_less(kt[j], kp[j], n0, p) ? 1 : 0;
+#pragma unroll
+                        for (int j = C - 1; j >= 1; --j) {
+                            kt[j] = j > m ? kt[j - 1] : (j == m ? n0 : kt[j]);
+                            kp[j] = j > m ? kp[j - 1] : (j == m ? p : kp[j]);
+                        }
+                        kt[0] = m == 0 ? n0 : kt[0];
+                        kp[0] = m == 0 ? p : kp[0];
+                    }
+                } else {
+                    ++nodes;
+                    // once the list is full, a subtree entered beyond its last entry only holds dropped patches
+                    const float bound = cnt == C ? kt[C - 1] : tmax;
+                    if constexpr (BW == 4) {
+                        const float4 *nd = sc.nodes + (size_t)node * kNode4F4;
+                        float4 lo4[3], hi4[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) {
+                            lo4[k] = __ldg(nd + 2 * k);
+                            hi4[k] = __ldg(nd + 2 * k + 1);
+                        }
+                        const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+                        int c[4] = {ch.x, ch.y, ch.z, ch.w};
+                        float key[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            float lo[3], hi[3];
+#pragma unroll
+                            for (int k = 0; k < 3; ++k) {
+                                lo[k] = j == 0 ? lo4[k].x : j == 1 ? lo4[k].y : j == 2 ? lo4[k].z : lo4[k].w;
+                                hi[k] = j == 0 ? hi4[k].x : j == 1 ? hi4[k].y : j == 2 ? hi4[k].z : hi4[k].w;
+                            }
+                            float t0, t1;
+                            slab<3>(r, lo, hi, tmin, tmax, G, t0, t1);
+                            bool h = t0 <= t1 && c[j] != kEmptyChild;
+                            if (h && t0 > bound) {
+                                h = false;
+                                evicted = true;
+                                t_evict = fminf(t_evict, t0);
+                            }
+                            key[j] = h ? t0 : kInf;
+                        }
+                        cx4(key, c, 0, 1);
+                        cx4(key, c, 2, 3);
+                        cx4(key, c, 0, 2);
+                        cx4(key, c, 1, 3);
+                        cx4(key, c, 1, 2);
+                        if (key[0] < kInf) {
+#pragma unroll
+                            for (int j = 3; j >= 1; --j) {
+                                if (key[j] < kInf && sp < kBvhStack) {
+                                    stk[sp] = make_int2(c[j], __float_as_int(key[j]));
+                                    ++sp;
+                                }
+                            }
+                            node = c[0];
+                            n0 = key[0];
+                            continue;
+                        }
+                    } else {
+                        const float4 *nd = sc.nodes + (size_t)node * kNodeF4;
+                        float4 q[3];
+#pragma unroll
+                        for (int k = 0; k < 3; ++k) q[k] = __ldg(nd + k);
+                        const int2 ch = __ldg(reinterpret_cast<const int2 *>(nd + 3));
+                        float a0, a1, b0, b1;
+                        node_child_boxes<3>(q, r, tmin, tmax, G, a0, a1, b0, b1);
+                        bool ha = a0 <= a1 && ch.x != kEmptyChild;
+                        bool hb = b0 <= b1 && ch.y != kEmptyChild;
+                        if (ha && a0 > bound) {
+                            ha = false;
+                            evicted = true;
+                            t_evict = fminf(t_evict, a0);
+                        }
+                        if (hb && b0 > bound) {
+                            hb = false;
+                            evicted = true;
+                            t_evict = fminf(t_evict, b0);
+                        }
+                        if (ha && hb) {
+                            const bool bfirst = b0 < a0;
+                            if (sp < kBvhStack) {
+                                stk[sp] = make_int2(bfirst ? ch.x : ch.y, __float_as_int(bfirst ? a0 : b0));
+                                ++sp;
+                            }
+                            node = bfirst ? ch.y : ch.x;
+                            n0 = bfirst ? b0 : a0;
+                            continue;
+                        }
+                        if (ha || hb) {
+                            node = ha ? ch.x : ch.y;
+                            n0 = ha ? a0 : b0;
+                            continue;
+                        }
+                    }
+                }
+                // pop the nearest pending subtree that can still add to the list
+                node = kDone;
+                while (sp > 0) {
+                    --sp;
+                    const int2 e = stk[sp];
+                    const float t0 = __int_as_float(e.y);
+                    if (cnt == C && t0 > kt[C - 1]) {
+                        evicted = true;
+                        t_evict = fminf(t_evict, t0);
+                        continue;
+                    }
+                    node = e.x;
+                    n0 = t0;
+                    break;
+                }
+            }
+        }
+    }
+    // the task: the candidates in list order in one run of the buffer; its cost class
+    const bool has = live && !capped && cnt > 0;
+    int key = -1;
+    if (has) {
+        const DevScene &sc = src.scene(lsc);
+        int ng = 0;
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < cnt && __ldg(sc.types + kp[j]) != 0) ++ng;
+        key = min(kCostClasses - 1, cnt + 2 * ng);
+    }
+    const uint32_t want = has ? (uint32_t)cnt : 0u;
+    uint32_t incl = want;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t total = __shfl_sync(FULL, incl, 31);
+    uint32_t base = 0;
+    if (lane == 0 && total) base = atomicAdd(pb.ctr + kCtrCand, total);
+    base = __shfl_sync(FULL, base, 0);
+    const uint64_t off = (uint64_t)base + incl - want;
+    const bool ok = has && off + want <= pb.cap_cand;
+    const bool fb = has && !ok;
+    const unsigned mt = __ballot_sync(FULL, ok), mf = __ballot_sync(FULL, fb);
+    uint32_t bt = 0, bf = 0;
+    if (lane == 0) {
+        if (mt) bt = atomicAdd(pb.ctr + kCtrTasks, (uint32_t)__popc(mt));
+        if (mf) bf = atomicAdd(pb.ctr + kCtrFallback, (uint32_t)__popc(mf));
+    }
+    bt = __shfl_sync(FULL, bt, 0);
+    bf = __shfl_sync(FULL, bf, 0);
+    const unsigned lt = (1u << lane) - 1u;
+    if (ok) {
+        uint2 *dst = pb.cand + off;
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < cnt) dst[j] = make_uint2(kp[j], __float_as_uint(kt[j]));
+        uint4 *tk = pb.task + 4 * (size_t)(bt + __popc(mt & lt));
+        tk[0] = make_uint4(i, (uint32_t)off, (uint32_t)cnt | ((uint32_t)key << 8) | (evicted ? kTaskEvicted : 0u),
+                           __float_as_uint(t_evict));
+        tk[1] = make_uint4(kp[0], __float_as_uint(kt[0]), __float_as_uint(tmin), __float_as_uint(tmax));
+        tk[2] = make_uint4(__float_as_uint(ro[0]), __float_as_uint(ro[1]), __float_as_uint(ro[2]), __float_as_uint(rd[0]));
+        tk[3] = make_uint4(__float_as_uint(rd[1]), __float_as_uint(rd[2]), 0u, 0u);
+    }
+    const int hkey = ok ? key : -1;
+    const unsigned same = __match_any_sync(FULL, hkey);
+    if (ok && lane == __ffs(same) - 1) atomicAdd(pb.ctr + kCtrHist + key, (uint32_t)__popc(same));
+    if (fb) pb.fallback[bf + __popc(mf & lt)] = i;
+    if (live && !has) {
+        if (capped) atomicOr(status, 1u);
+        write_miss<MODE>(src, ray_scene, ray_local, occluded);
+    }
+    if (STATS) {   // BVH nodes; diagnostics in the schedule slots: candidates listed, rays that dropped some
+        unsigned long long v[3] = {nodes, want, (unsigned long long)(has && evicted)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
+        if (lane == 0) {
+            if (v[0]) atomicAdd(counters + 0, v[0]);
+            if (v[1]) atomicAdd(counters + 8, v[1]);
+            if (v[2]) atomicAdd(counters + 9, v[2]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Pass 3: Algorithm 3 over (ray, patch) pairs, one pair per lane.
+// ------------------------------------------------------------------------------------------------
+template <bool STATS, int K, int MODE, class Src>
+__global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, uint32_t refill, uint32_t iter_cap,
+                                                  uint32_t *status, unsigned long long *counters, uint8_t *occluded)
+{
+    extern __shared__ __align__(16) float smem[];
+    const int stride = blockDim.x;
+    Scratch scr;
+    scr.stride = stride;
+    scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
+    scr.cache = smem + 4 * L * stride + threadIdx.x;
+    scr.tag = reinterpret_cast<int *>(smem + (4 * L + 16 * 3 * K) * stride) + threadIdx.x;
+    scr.node = nullptr;
+    float *rs = smem + scratch_floats(L, K, 3) * stride + threadIdx.x;   // [k * stride], k < kRaySlotFloats
+    Counters cnt;
+#pragma unroll
+    for (int k = 0; k < kNumSumCounters; ++k) cnt.v[k] = 0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    Grp G;
+    G.c = 0;
+    G.mask = FULL;
+    G.l0 = G.l1 = G.l2 = lane;
+    const float kInf = __int_as_float(0x7f800000);
+    const float cellw = __int_as_float((127 - L) << 23);
+    const uint32_t n_tasks = pb.ctr[kCtrTasks];
+    uint32_t *queue = pb.ctr + kCtrQueue;
+    if (STATS && lane == 0) atomicMax(counters + 20, ~global_ns());   // first warp start
+
+    // the lane's ray (task)
+    bool has_task = false, exhausted = false, evicted = false;
+    uint32_t ray = 0, cur = 0, end = 0, ray_scene = 0, ray_local = 0, iters = 0;
+    uint2 nxt = make_uint2(0u, 0u);   // the ray's candidate at cur, loaded ahead
+    typename Src::LaneScene lsc;
+    Best best;
+    best.t = 0.0f;
+    best.pid = best.cell = kMissId;
+    best.lvl = 0;
+    // the lane's pair
+    bool in_pair = false, want_root = false, start = false, gpend = false, greg = false;
+    uint32_t pid = 0, start_pid = 0, path = 0, trail = 0;
+    RayG<3> pr;
+    float tau = 0.0f, c0 = 0.0f, c1 = 0.0f;
+    float d[3] = {0.0f, 0.0f, 0.0f};
+    int level = 0, rd_target = -1, ctop = 0, cvalid = 0;
+    float g[48];
+
+    for (;;) {
+        // (1) a lane whose pair has ended takes its ray's next candidate, or finishes the ray (its answer,
+        //     or the fallback when dropped candidates may still hold it); idle lanes take new rays from the
+        //     queue, then their first candidate
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            if (has_task && !in_pair && !start) {
+                if (cur < end && __uint_as_float(nxt.y) <= best.t) {
+                    start = true;
+                    start_pid = nxt.x;
+                    ++cur;
+                } else {   // entries are sorted: the rest enter later still
+                    has_task = false;
+                    if (MODE == kModeAnyHit) {
+                        const bool occ = best.pid != kMissId;
+                        if (!occ && evicted)
+                            pb.fallback[atomicAdd(pb.ctr + kCtrFallback, 1u)] = ray;
+                        else
+                            occluded[ray_local] = occ ? 1 : 0;
+                    } else if (evicted && !(best.t < rs[8 * stride])) {
+                        pb.fallback[atomicAdd(pb.ctr + kCtrFallback, 1u)] = ray;
+                        if (STATS) cnt.v[10]++;
+                    } else {
+                        const DevHits &hh = src.hits_of(ray_scene);
+                        const uint32_t j = ray_local;
+                        if (best.pid != kMissId) {
+                            const uint32_t cu = best.cell & ((1u << L) - 1u), cv = best.cell >> L;
+                            hh.t[j] = best.t;
+                            hh.u[j] = ((float)cu + 0.5f) * cellw;
+                            hh.v[j] = ((float)cv + 0.5f) * cellw;
+                            hh.pid[j] = best.pid;
+                        } else {
+                            hh.t[j] = kInf;
+                            hh.u[j] = 0.0f;
+                            hh.v[j] = 0.0f;
+                            hh.pid[j] = kMissId;
+                        }
+                    }
+                }
+            }
+            if (pass == 1 || exhausted) break;
+            const unsigned idle = __ballot_sync(FULL, !has_task);
+            if (idle == 0u || ((uint32_t)__popc(idle) < refill && idle != FULL)) break;
+            uint32_t qb = 0;
+            if (lane == 0) qb = atomicAdd(queue, (uint32_t)__popc(idle));
+            qb = __shfl_sync(FULL, qb, 0);
+            if (qb + (uint32_t)__popc(idle) >= n_tasks) {
+                exhausted = true;
+                if (STATS && lane == 0) atomicMax(counters + 21, ~global_ns());   // queue found empty
+            }
+            const uint32_t k = qb + (uint32_t)__popc(idle & lt);
+            if (!has_task && k < n_tasks) {
+                const uint4 *tp = pb.sorted + 4 * (size_t)k;
+                const uint4 w0 = tp[0], w1 = tp[1], w2 = tp[2], w3 = tp[3];
+                has_task = true;
+                ray = w0.x;
+                cur = w0.y;
+                end = w0.y + (w0.z & 255u);
+                evicted = (w0.z & kTaskEvicted) != 0u;
+                nxt = make_uint2(w1.x, w1.y);
+                rs[0 * stride] = __uint_as_float(w2.x);
+                rs[1 * stride] = __uint_as_float(w2.y);
+                rs[2 * stride] = __uint_as_float(w2.z);
+                rs[3 * stride] = safe_inv(__uint_as_float(w2.w));
+                rs[4 * stride] = safe_inv(__uint_as_float(w3.x));
+                rs[5 * stride] = safe_inv(__uint_as_float(w3.y));
+                rs[6 * stride] = __uint_as_float(w1.z);
+                rs[7 * stride] = __uint_as_float(w1.w);
+                rs[8 * stride] = __uint_as_float(w0.w);
+                src.locate(ray, lsc, ray_scene, ray_local);
+                iters = iter_cap;
+                best.t = __uint_as_float(w1.w);
+                best.pid = best.cell = kMissId;
+            }
+        }
+        // (2) the lanes that start a pair: the next candidate ahead, root interval, the ray in the patch
+        //     frame, and (Bezier) the root grid
+        if (start) {
+            start = false;
+            if (cur < end) nxt = pb.cand[cur];
+            const DevScene &sc = src.scene(lsc);
+            pid = start_pid;
+            const float4 *rec = rec_of(sc, pid);
+            const float4 an = __ldg(rec + 15);
+            in_pair = true;
+            greg = an.w != 0.0f;
+            if (STATS) cnt.v[7]++;
+            RayG<3> wr;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                wr.org[k] = rs[k * stride];
+                wr.inv[k] = rs[(3 + k) * stride];
+            }
+            const float tmin = rs[6 * stride], tmax = rs[7 * stride];
+            {   // the root interval: the slab of the patch box (as k_intersect computes it)
+                const float4 blo = __ldg(sc.leaf_box + 2 * (size_t)pid), bhi = __ldg(sc.leaf_box + 2 * (size_t)pid + 1);
+                const float lo[3] = {blo.x, blo.y, blo.z}, hi[3] = {bhi.x, bhi.y, bhi.z};
+                slab<3>(wr, lo, hi, tmin, tmax, G, c0, c1);
+            }
+            pr = wr;
+            tau = 0.0f;
+            if (!sc.local) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) pr.org[k] = wr.org[k] - pick(k, an.x, an.y, an.z);
+            } else {   // the ray in the patch's frame (Sec. 3.4): R (o - anchor), R d
+                float o3[3], d3[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o3[c] = wr.org[c] - pick(c, an.x, an.y, an.z);
+                    d3[c] = 1.0f / wr.inv[c];
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float4 Rk = __ldg(rec + 16 + k);
+                    pr.org[k] = fmaf(Rk.x, o3[0], fmaf(Rk.y, o3[1], Rk.z * o3[2]));
+                    pr.inv[k] = safe_inv(fmaf(Rk.x, d3[0], fmaf(Rk.y, d3[1], Rk.z * d3[2])));
+                }
+                tau = __fmul_rn(__int_as_float((127 - 19) << 23),
+                                __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) d[k] = 0.0f;
+            level = 0;
+            rd_target = -1;
+            path = trail = 0u;
+            ctop = cvalid = 0;
+            gpend = greg;
+            want_root = !greg;
+        }
+        if (want_root) {   // a Bezier pair's start or a re-descent: the root grid
+            want_root = false;
+            load_grid<3>(rec_of(src.scene(lsc), pid), G, g);
+        }
+        // (3) one subdivision step of every lane's pair
+        if (in_pair) {
+            if (iters == 0) {   // iteration cap: a miss, status latched
+                has_task = false;
+                in_pair = false;
+                atomicOr(status, 1u);
+                if (MODE == kModeAnyHit) {
+                    occluded[ray_local] = 0;
+                } else {
+                    const DevHits &hh = src.hits_of(ray_scene);
+                    hh.t[ray_local] = kInf;
+                    hh.u[ray_local] = 0.0f;
+                    hh.v[ray_local] = 0.0f;
+                    hh.pid[ray_local] = kMissId;
+                }
+            } else {
+                --iters;
+                if (gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level)
+                    float u0, u1, v0, v1;
+                    node_domain(path, level, L, u0, u1, v0, v1);
+                    gregory_node<3>(rec_of(src.scene(lsc), pid), u0, u1, v0, v1, level, G, g, d);
+                    gpend = false;
+                }
+                const bool redesc = rd_target >= 0;
+                const bool leafkids = !redesc && level + 1 == 2 * L;
+                const int force = redesc ? (int)((path >> level) & 1u) : -1;
+                const int slot = (!redesc && !leafkids && K > 0 && !greg) ? (ctop % (K > 0 ? K : 1)) : -1;
+                if (STATS && !redesc) cnt.v[greg ? 2 : 1]++;
+                const StepOut so = split_step<K, 3>(g, pr, d, c0, c1, best.t, redesc || (!greg && !leafkids), scr, slot,
+                                                    true, true, force, G, tau);
+                bool back = false;
+                if (redesc) {
+                    if (++level == rd_target) rd_target = -1;
+                } else if (so.hitL || so.hitR) {
+                    const uint32_t bit = 1u << level;
+                    if (leafkids) {   // both children are leaves: record them here (key order, A14/A15)
+                        uint32_t cu, cv;
+                        if (so.hitL) {
+                            path_cells(path, L, cu, cv);
+                            const uint32_t cell = (cv << L) | cu;
+                            if (key_less(so.l0, pid, cell, best)) {
+                                best.t = so.l0;
+                                best.pid = pid;
+                                best.cell = cell;
+                            }
+                        }
+                        if (so.hitR) {
+                            path_cells(path | bit, L, cu, cv);
+                            const uint32_t cell = (cv << L) | cu;
+                            if (key_less(so.r0, pid, cell, best)) {
+                                best.t = so.r0;
+                                best.pid = pid;
+                                best.cell = cell;
+                            }
+                        }
+                        if (STATS) cnt.v[3] += (so.hitL ? 1 : 0) + (so.hitR ? 1 : 0);
+                        back = true;
+                    } else {
+                        if (so.hitL && so.hitR) {
+                            trail |= bit;
+                            scr.sib[level * stride] = so.goR ? make_float2(so.l0, so.l1) : make_float2(so.r0, so.r1);
+                            if (K > 0 && !greg) {
+                                scr.tag[slot * stride] = level;
+                                ++ctop;
+                                cvalid = cvalid < K ? cvalid + 1 : K;
+                            }
+                        }
+                        path = so.goR ? (path | bit) : path;
+                        c0 = so.goR ? so.r0 : so.l0;
+                        c1 = so.goR ? so.r1 : so.l1;
+                        ++level;
+                        gpend = greg;
+                    }
+                } else {
+                    back = true;
+                }
+                if (back) {   // the deepest pending sibling that may still hold a closer leaf, or the pair ends
+                    bool found = false;
+                    if (!(MODE == kModeAnyHit && best.pid != kMissId)) {
+                        while (trail != 0u) {
+                            const int l = 31 - __clz(trail);
+                            const uint32_t bit = 1u << l;
+                            trail ^= bit;
+                            bool cached = false;
+                            int cslot = 0;
+                            if (K > 0 && !greg && cvalid > 0) {
+                                cslot = (ctop - 1) % (K > 0 ? K : 1);
+                                if (scr.tag[cslot * stride] == l) {
+                                    cached = true;
+                                    --ctop;
+                                    --cvalid;
+                                }
+                            }
+                            const float2 sb = scr.sib[l * stride];
+                            if (sb.x > best.t) {
+                                if (STATS) cnt.v[6]++;
+                                continue;
+                            }
+                            path = (path & (bit - 1u)) | (~path & bit);
+                            c0 = sb.x;
+                            c1 = sb.y;
+                            if (STATS) cnt.v[4]++;
+                            if (greg) {
+                                level = l + 1;
+                                gpend = true;
+                            } else if (cached) {
+                                level = l + 1;
+                                const float *src_g = scr.cache + (size_t)(cslot * 48) * stride;
+#pragma unroll
+                                for (int k = 0; k < 48; ++k) g[k] = src_g[k * stride];
+                            } else {
+                                if (STATS) cnt.v[5] += l + 1;
+                                level = 0;
+                                rd_target = l + 1;
+                                want_root = true;
+                            }
+                            found = true;
+                            break;
+                        }
+                    } else {
+                        cur = end;   // any hit: the ray is answered
+                    }
+                    if (!found) in_pair = false;
+                }
+            }
+        }
+        if (exhausted && !__any_sync(FULL, has_task)) break;
+    }
+    if (STATS) {
+#pragma unroll
+        for (int k = 0; k < kNumSumCounters; ++k) {
+            unsigned long long v = cnt.v[k];
+            for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(FULL, v, o2);
+            if (lane == 0 && v) atomicAdd(counters + k, v);
+        }
+        if (lane == 0) atomicMax(counters + 22, global_ns());   // last warp exit
+    }
+}
+
+}  // namespace ccs

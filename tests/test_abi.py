@@ -56,7 +56,8 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
            'printf("trial %zu\\n", sizeof(ccs_autotune_trial));',
            'printf("NUM_COUNTERS %d\\n", CCS_NUM_COUNTERS);', 'printf("TRACE_COUNT %u\\n", CCS_TRACE_COUNT);',
            'printf("TRACE_ORDER %u\\n", CCS_TRACE_ORDER);', 'printf("CACHE_DEFAULT %u\\n", CCS_CACHE_DEFAULT);',
-           'printf("TRACE_HOST_MAPPED %u\\n", CCS_TRACE_HOST_MAPPED);']
+           'printf("TRACE_HOST_MAPPED %u\\n", CCS_TRACE_HOST_MAPPED);',
+           'printf("TRACE_PAIRS %u\\n", CCS_TRACE_PAIRS);']
     src += [f'printf("off_{f} %zu\\n", offsetof(ccs_trace_opts, {f}));' for f in fields]
     src += ["return 0; }"]
     c = tmp_path / "layout.c"
@@ -75,4 +76,5 @@ def test_binding_structs_and_constants_match_the_header(tmp_path):
     assert int(got["TRACE_COUNT"]) == ccs.CCS_TRACE_COUNT
     assert int(got["TRACE_ORDER"]) == ccs.CCS_TRACE_ORDER
     assert int(got["TRACE_HOST_MAPPED"]) == ccs.CCS_TRACE_HOST_MAPPED
+    assert int(got["TRACE_PAIRS"]) == ccs.CCS_TRACE_PAIRS
     assert int(got["CACHE_DEFAULT"]) == ccs.CCS_CACHE_DEFAULT
