@@ -9,9 +9,9 @@
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is enqueued
  *    asynchronously on it unless the entry point says otherwise; caller-owned device buffers must stay
  *    valid until that work completes.  Launches on one scene may run at the same time on different
- *    streams (each takes its own work-queue head from a ring of 48), except launches with
- *    CCS_TRACE_ORDER, which share the scene's work-order scratch, and ccs_intersect_host and
- *    ccs_intersect_host_batches calls, which share its staging buffer.
+ *    streams (each takes its own work-queue head from a ring of 48, and the scratch of the work order
+ *    and of the pair engine from a stream-ordered memory pool of the library), except
+ *    ccs_intersect_host and ccs_intersect_host_batches calls, which share the scene's staging buffer.
  *  - Every call returns a ccs_status.  On failure, ccs_last_error() returns a message for the calling
  *    thread.  Errors detected on the device (traversal iteration cap reached) are latched in a status
  *    word of the scene and returned by ccs_scene_sync_status().
@@ -121,10 +121,11 @@ typedef struct {
                                        count (stable within a count, counts clamped to 15), so that the
                                        rays that subdivide most start first and the launch does not end
                                        on a few late, long rays.  Never changes an answer.  Three small
-                                       kernels and a permutation of 4 bytes per ray in scratch owned by
-                                       the scene (allocated on first use and on growth, which synchronises
-                                       the stream).  Used by ccs_intersect, ccs_intersect_host and
-                                       ccs_occluded; the other entry points ignore it. */
+                                       kernels and a permutation of 4 bytes per ray in scratch of the
+                                       launch, from a stream-ordered memory pool of the library (kept for
+                                       reuse).  Used by ccs_intersect, ccs_intersect_host and
+                                       ccs_occluded; the other entry points ignore it, and so does the
+                                       pair engine. */
 #define CCS_TRACE_PAIRS 8u          /* pair engine, for the plain closest hit and the any-hit query with one
                                        lane per ray (other modes ignore it): (1) one thread per ray walks
                                        the BVH and keeps the ray's 16 nearest candidate patches (by entry

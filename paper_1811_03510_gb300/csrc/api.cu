@@ -61,7 +61,6 @@ void free_scene(ccs_scene *s)
         if (e) cudaEventDestroy(e);
     for (cudaStream_t q : {s->pipe_h2d, s->pipe_d2h, s->pipe_comp})
         if (q) cudaStreamDestroy(q);
-    for (uint32_t *o : s->d_order) cudaFree(o);
     delete s;
 }
 
@@ -117,27 +116,32 @@ ccs_status check_rays(const ccs_rays *r, const ccs_hits *h)
 }
 
 // With CCS_TRACE_ORDER: the permutation of the launch's rays in estimated-cost order, computed on
-// `stream` into the scene's order scratch `slot` (grown on demand, which synchronises the stream);
+// `stream` into scratch of its own from the library's stream-ordered pool (so that launches on different
+// streams never share it); the caller releases it on the same stream after the launch (release_order).
 // *perm stays null without the flag.
-ccs_status work_order(ccs_scene *sc, int slot, const LaunchCfg &cfg, const DevRays &dr, uint32_t n, cudaStream_t s,
+ccs_status work_order(const ccs_scene *sc, const LaunchCfg &cfg, const DevRays &dr, uint32_t n, cudaStream_t s,
                       const uint32_t **perm)
 {
     *perm = nullptr;
     if (!(cfg.flags & CCS_TRACE_ORDER) || n == 0 || use_pairs(cfg)) return CCS_OK;
     const size_t words = order_scratch_words(n, cfg.image_width);
-    if (words > sc->order_words[slot]) {
-        CCS_CUDA(cudaStreamSynchronize(s));
-        cudaFree(sc->d_order[slot]);
-        sc->d_order[slot] = nullptr;
-        sc->order_words[slot] = 0;
-        CCS_CUDA(cudaMalloc(&sc->d_order[slot], words * sizeof(uint32_t)));
-        sc->order_words[slot] = words;
-    }
+    void *p = nullptr;
+    CCS_CUDA(pool_alloc(&p, words * sizeof(uint32_t), s));
     // the estimate counts the patch boxes a ray enters, the same in either tree: it walks the 4-wide one
     // when the scene has it (fewer dependent node loads)
     const uint32_t est_width = (sc->bvh_width == 4 || sc->alt_width == 4) ? 4u : 0u;
-    CCS_CUDA(launch_order(dev_scene(sc, est_width), dr, n, cfg.image_width, sc->d_order[slot], s));
-    *perm = sc->d_order[slot];
+    const cudaError_t e = launch_order(dev_scene(sc, est_width), dr, n, cfg.image_width, static_cast<uint32_t *>(p), s);
+    if (e != cudaSuccess) {
+        pool_free(p, s);
+        CCS_CUDA(e);
+    }
+    *perm = static_cast<const uint32_t *>(p);
+    return CCS_OK;
+}
+
+ccs_status release_order(const uint32_t *perm, cudaStream_t s)
+{
+    if (perm) CCS_CUDA(pool_free(const_cast<uint32_t *>(perm), s));
     return CCS_OK;
 }
 
@@ -242,10 +246,11 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
                          b + 6 * n + a, b + 7 * n + a};
         const DevHits dh{b + 8 * n + a, b + 9 * n + a, b + 10 * n + a, reinterpret_cast<uint32_t *>(b + 11 * n + a)};
         const uint32_t *perm;
-        ccs_status st = work_order(sc, (int)(k & 1), B.cfg, dr, (uint32_t)m, cs, &perm);
+        ccs_status st = work_order(sc, B.cfg, dr, (uint32_t)m, cs, &perm);
         if (st != CCS_OK) return st;
         CCS_CUDA(launch_intersect(dev_scene(sc, B.cfg.bvh_width), dr, dh, (uint32_t)m, B.cfg, take_queue(sc),
                                   sc->d_work + 1, sc->num_sms, cs, perm));
+        if ((st = release_order(perm, cs)) != CCS_OK) return st;
         CCS_CUDA(cudaEventRecord(ev_hit, cs));
         CCS_CUDA(cudaStreamWaitEvent(sc->pipe_d2h, ev_hit, 0));
         if (out_pitch[ck.j] && cudaMemcpy2DAsync(static_cast<char *>(dst[0]) + a * 4, out_pitch[ck.j], b + 8 * n + a,
@@ -470,10 +475,10 @@ ccs_status ccs_intersect(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, 
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{hits->t, hits->u, hits->v, hits->patch_id};
     const uint32_t *perm;
-    if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
+    if ((st = work_order(sc, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
                               (cudaStream_t)stream, perm));
-    return CCS_OK;
+    return release_order(perm, (cudaStream_t)stream);
 }
 
 ccs_status ccs_trace_export(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, ccs_hits *hits,
@@ -581,9 +586,10 @@ ccs_status ccs_intersect_host(ccs_scene *sc, const ccs_rays *hr, uint32_t n, ccs
             const DevHits dh{static_cast<float *>(dout[0]), static_cast<float *>(dout[1]),
                              static_cast<float *>(dout[2]), static_cast<uint32_t *>(dout[3])};
             const uint32_t *perm;
-            if ((st = work_order(sc, 0, cfg, dr, n, s, &perm)) != CCS_OK) return st;
+            if ((st = work_order(sc, cfg, dr, n, s, &perm)) != CCS_OK) return st;
             CCS_CUDA(launch_intersect(dev_scene(sc, cfg.bvh_width), dr, dh, n, cfg, take_queue(sc), sc->d_work + 1, sc->num_sms, s,
                                       perm));
+            if ((st = release_order(perm, s)) != CCS_OK) return st;
             CCS_CUDA(cudaStreamSynchronize(s));
             return CCS_OK;
         }
@@ -678,10 +684,10 @@ ccs_status ccs_occluded(const ccs_scene *sc, const ccs_rays *rays, uint32_t n, u
     DevRays dr{rays->ox, rays->oy, rays->oz, rays->dx, rays->dy, rays->dz, rays->tmin, rays->tmax};
     DevHits dh{nullptr, nullptr, nullptr, nullptr};
     const uint32_t *perm;
-    if ((st = work_order(const_cast<ccs_scene *>(sc), 0, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
+    if ((st = work_order(sc, cfg, dr, n, (cudaStream_t)stream, &perm)) != CCS_OK) return st;
     CCS_CUDA(launch_intersect(ds, dr, dh, n, cfg, take_queue(const_cast<ccs_scene *>(sc)), sc->d_work + 1, sc->num_sms,
                               (cudaStream_t)stream, perm));
-    return CCS_OK;
+    return release_order(perm, (cudaStream_t)stream);
 }
 
 ccs_status ccs_scene_sync_status(ccs_scene *sc, void *stream)

@@ -116,6 +116,10 @@ cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ra
 // launches (single scene: scratch from the library's stream-ordered pool; batch: the caller's scratch)
 bool use_pairs(const LaunchCfg &cfg);
 size_t pairs_scratch_bytes(uint32_t n);
+// scratch of one launch from the library's stream-ordered memory pool of the current device (pairs.cu):
+// allocated and freed in the order of `s`; freed memory stays in the pool for reuse
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t pool_free(void *p, cudaStream_t s);
 cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
                                 const LaunchCfg &cfg, uint32_t *status, int num_sms, cudaStream_t s);
 cudaError_t launch_pairs_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
@@ -166,10 +170,6 @@ struct ccs_scene {
     size_t stage_bytes = 0;
     cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr, pipe_comp = nullptr;
     cudaEvent_t pipe_ev[2 * 8 + 2] = {};   // per chunk: input copied, hits written; start; end of the copies out
-    // work-order scratch (CCS_TRACE_ORDER): [0] for launches on the caller's stream, [1] for the host
-    // path's second compute stream
-    uint32_t *d_order[2] = {};
-    size_t order_words[2] = {};
 };
 
 namespace ccs {

@@ -52,7 +52,7 @@ size_t pairs_scratch_bytes(uint32_t n) { return pair_scratch_bytes(n); }
 
 namespace {
 
-// The memory pool of the current device (created on first use; freed memory stays in the pool).
+// The library's memory pool of the current device (created on first use; freed memory stays in the pool).
 cudaError_t pair_pool(cudaMemPool_t *out)
 {
     constexpr int kMaxDevices = 64;
@@ -123,15 +123,23 @@ LaunchCfg fallback_cfg(const LaunchCfg &cfg, const PairBufs &pb)
 
 }  // namespace
 
+cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    cudaMemPool_t pool = nullptr;
+    const cudaError_t e = pair_pool(&pool);
+    if (e != cudaSuccess) return e;
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t pool_free(void *p, cudaStream_t s) { return cudaFreeAsync(p, s); }
+
 cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n,
                                 const LaunchCfg &cfg, uint32_t *status, int num_sms, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    cudaMemPool_t pool = nullptr;
-    cudaError_t e = pair_pool(&pool);
-    if (e != cudaSuccess) return e;
     void *base = nullptr;
-    if ((e = cudaMallocFromPoolAsync(&base, pair_scratch_bytes(n), pool, s)) != cudaSuccess) return e;
+    cudaError_t e = pool_alloc(&base, pair_scratch_bytes(n), s);
+    if (e != cudaSuccess) return e;
     const PairBufs pb = pair_bufs_at(base, n);
     const SingleSource src{sc, r, h, n, nullptr, nullptr};
     e = cudaMemsetAsync(pb.ctr, 0, kPairCtrWords * sizeof(uint32_t), s);
@@ -148,7 +156,7 @@ cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevH
     }
     if (e == cudaSuccess)
         e = launch_intersect(sc, r, h, n, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF, status, num_sms, s, pb.fallback);
-    const cudaError_t e2 = cudaFreeAsync(base, s);
+    const cudaError_t e2 = pool_free(base, s);
     return e != cudaSuccess ? e : e2;
 }
 

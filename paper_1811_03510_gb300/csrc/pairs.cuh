@@ -73,8 +73,34 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
 }
 
 // Shared memory of a k_pairs thread after its traversal scratch: the world ray of its task (origin,
-// 1 / direction, tmin, tmax) and t_evict, read when a pair starts and when the ray ends.
-constexpr int kRaySlotFloats = 9;
+// 1 / direction, tmin, tmax), t_evict and the direction rebuilt from 1 / direction (the one that the local
+// frames rotate), read when a pair starts and when the ray ends; then the
+// thread's mailbox for the subtrees it handed to other lanes (the smallest (t, cell) key they found,
+// 64 bits), the number of them still running, and a flag for one that reached the iteration cap.
+constexpr int kRaySlotFloats = 12, kHelpFloats = 4;
+// A subtree is handed to an idle lane when it has at least this many levels below its root.
+constexpr int kMinDonateLevels = 4;
+
+// Order-preserving map of a float's bits to an unsigned integer, and back (the mailbox key).
+CCS_DEV uint32_t ord_bits(float t)
+{
+    const uint32_t u = __float_as_uint(t);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+CCS_DEV float unord_bits(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k); }
+
+// The scene of a lane's pair, handed from lane `from` to the lanes that take one of its subtrees (a batch
+// lane carries its scene; one scene is the launch's).
+template <class Src>
+CCS_DEV void share_scene(typename Src::LaneScene &l, int from)
+{
+    if constexpr (std::is_same<Src, BatchSource>::value) {
+        const unsigned long long r = reinterpret_cast<unsigned long long>(l.sc.rec);
+        const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)r, from);
+        const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(r >> 32), from);
+        l.sc.rec = reinterpret_cast<const float4 *>(((unsigned long long)hi << 32) | lo);
+    }
+}
 
 CCS_DEV bool cand_less(float ta, uint32_t pa, float tb, uint32_t pb) { return ta < tb || (ta == tb && pa < pb); }
 
@@ -376,6 +402,16 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     scr.tag = reinterpret_cast<int *>(smem + (4 * L + 16 * 3 * K) * stride) + threadIdx.x;
     scr.node = nullptr;
     float *rs = smem + scratch_floats(L, K, 3) * stride + threadIdx.x;   // [k * stride], k < kRaySlotFloats
+    // mailboxes, helper counts and cap flags of the block's threads (indexed by thread)
+    unsigned long long *mbox =
+        reinterpret_cast<unsigned long long *>(smem + (scratch_floats(L, K, 3) + kRaySlotFloats) * stride);
+    int *hcount = reinterpret_cast<int *>(mbox + stride);
+    int *hcap = hcount + stride;
+    const int wbase = threadIdx.x & ~31;
+    mbox[threadIdx.x] = ~0ull;
+    hcount[threadIdx.x] = 0;
+    hcap[threadIdx.x] = 0;
+    __syncwarp();
     Counters cnt;
 #pragma unroll
     for (int k = 0; k < kNumSumCounters; ++k) cnt.v[k] = 0;
@@ -403,6 +439,8 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     best.lvl = 0;
     // the lane's pair
     bool in_pair = false, want_root = false, start = false, gpend = false, greg = false;
+    bool helper = false, waiting = false;   // a subtree of lane `owner`'s pair; waiting for helpers
+    int owner = lane;
     uint32_t pid = 0, start_pid = 0, path = 0, trail = 0;
     RayG<3> pr;
     float tau = 0.0f, c0 = 0.0f, c1 = 0.0f;
@@ -479,6 +517,8 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 rs[6 * stride] = __uint_as_float(w1.z);
                 rs[7 * stride] = __uint_as_float(w1.w);
                 rs[8 * stride] = __uint_as_float(w0.w);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) rs[(9 + c) * stride] = 1.0f / rs[(3 + c) * stride];
                 src.locate(ray, lsc, ray_scene, ray_local);
                 iters = iter_cap;
                 best.t = __uint_as_float(w1.w);
@@ -519,7 +559,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     o3[c] = wr.org[c] - pick(c, an.x, an.y, an.z);
-                    d3[c] = 1.0f / wr.inv[c];
+                    d3[c] = rs[(9 + c) * stride];
                 }
 #pragma unroll
                 for (int k = 0; k < 3; ++k) {
@@ -543,9 +583,30 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
             want_root = false;
             load_grid<3>(rec_of(src.scene(lsc), pid), G, g);
         }
+        if (STATS) {   // schedule of this warp iteration, in lanes (slots 12..16)
+            const unsigned ks = __ballot_sync(FULL, in_pair && !waiting), kh = __ballot_sync(FULL, helper);
+            const unsigned kw = __ballot_sync(FULL, waiting), ki = __ballot_sync(FULL, !in_pair && !has_task);
+            if (lane == 0) {
+                cnt.v[12] += 1;
+                cnt.v[13] += __popc(ks);
+                cnt.v[14] += __popc(kh);
+                cnt.v[15] += __popc(kw);
+                cnt.v[16] += __popc(ki);
+            }
+        }
         // (3) one subdivision step of every lane's pair
-        if (in_pair) {
-            if (iters == 0) {   // iteration cap: a miss, status latched
+        if (in_pair && !waiting) {
+            if (iters == 0 && helper) {   // iteration cap in a subtree: the owner's ray becomes a capped miss
+                atomicOr(status, 1u);
+                hcap[wbase + owner] = 1;
+                __threadfence_block();
+                atomicSub(hcount + wbase + owner, 1);
+                helper = false;
+                in_pair = false;
+            } else if (iters == 0 && hcount[threadIdx.x] > 0) {   // wait for the subtrees, then the cap
+                hcap[threadIdx.x] = 1;
+                waiting = true;
+            } else if (iters == 0) {   // iteration cap: a miss, status latched
                 has_task = false;
                 in_pair = false;
                 atomicOr(status, 1u);
@@ -665,9 +726,147 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     } else {
                         cur = end;   // any hit: the ray is answered
                     }
-                    if (!found) in_pair = false;
+                    if (!found) {
+                        if (helper) {   // the subtree is searched: its best leaf to the owner's mailbox
+                            if (best.pid == pid)
+                                atomicMin(mbox + wbase + owner, ((unsigned long long)ord_bits(best.t) << 32) | best.cell);
+                            __threadfence_block();
+                            atomicSub(hcount + wbase + owner, 1);
+                            helper = false;
+                            in_pair = false;
+                        } else {
+                            waiting = true;   // merged when every subtree handed out is searched
+                        }
+                    }
                 }
             }
+        }
+        // a lane whose search has ended takes the best leaf of the subtrees it handed out, once every one of
+        // them is searched (until then it waits)
+        __syncwarp();
+        if (waiting && hcount[threadIdx.x] == 0) {
+            __threadfence_block();
+            const unsigned long long mk = mbox[threadIdx.x];
+            if (mk != ~0ull) {
+                const float mt = unord_bits((uint32_t)(mk >> 32));
+                const uint32_t mc = (uint32_t)mk;
+                if (key_less(mt, pid, mc, best)) {
+                    best.t = mt;
+                    best.pid = pid;
+                    best.cell = mc;
+                }
+                mbox[threadIdx.x] = ~0ull;
+            }
+            waiting = false;
+            in_pair = false;
+            if (hcap[threadIdx.x]) {   // a subtree reached the iteration cap: answered as a capped ray
+                hcap[threadIdx.x] = 0;
+                iters = 0;
+                in_pair = true;
+            }
+        }
+        // (4) once the queue is empty, idle lanes take a pending subtree of a busy lane of the warp
+        //     (closest-hit mode): the deepest one when its grid is in the busy lane's sibling cache or the
+        //     patch is a Gregory patch (no re-descent), else the shallowest one of at least
+        //     kMinDonateLevels levels (re-descended); the key of a pair's best leaf is the minimum over its
+        //     subtrees
+        if (MODE == kModePlain && exhausted) {
+            const bool idle_l = !has_task && !in_pair;
+            const int lmin = trail != 0u ? __ffs(trail) - 1 : 2 * L;
+            const int ldeep = trail != 0u ? 31 - __clz(trail) : 2 * L;
+            int cslot = -1;
+            if (K > 0 && !greg && cvalid > 0 && trail != 0u) {
+                const int c = (ctop - 1) % (K > 0 ? K : 1);
+                if (scr.tag[c * stride] == ldeep) cslot = c;
+            }
+            const bool deep = trail != 0u && (greg || cslot >= 0);
+            const int lgive = deep ? ldeep : lmin;
+            const bool can_give = in_pair && !waiting && (deep || 2 * L - (lmin + 1) >= kMinDonateLevels);
+            const unsigned T = __ballot_sync(FULL, idle_l), D = __ballot_sync(FULL, can_give);
+            if (T != 0u && D != 0u) {
+                const int m = min(__popc(T), __popc(D));
+                int from = lane;
+                if (idle_l && __popc(T & lt) < m) from = (int)__fns(D, 0, __popc(T & lt) + 1);
+                const bool gives = can_give && __popc(D & lt) < m;
+                uint32_t sp = 0u;
+                float sx = 0.0f, sy = 0.0f;
+                int gslot = -1;   // the donor's cache slot holding the subtree root's grid
+                if (gives) {   // the sibling's path and interval, as a backtrack to it would set them
+                    const uint32_t bit = 1u << lgive;
+                    sp = (path & (bit - 1u)) | (~path & bit);
+                    const float2 sb = scr.sib[lgive * stride];
+                    sx = sb.x;
+                    sy = sb.y;
+                    trail ^= bit;
+                    if (deep && cslot >= 0) {
+                        gslot = cslot;
+                        --ctop;
+                        --cvalid;
+                    }
+                }
+                const int x_gslot = __shfl_sync(FULL, gslot, from);
+                const uint32_t x_pid = __shfl_sync(FULL, pid, from);
+                const int x_greg = __shfl_sync(FULL, greg ? 1 : 0, from);
+                float x_pr[6];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    x_pr[k] = __shfl_sync(FULL, pr.org[k], from);
+                    x_pr[3 + k] = __shfl_sync(FULL, pr.inv[k], from);
+                }
+                const float x_tau = __shfl_sync(FULL, tau, from);
+                const float x_bt = __shfl_sync(FULL, best.t, from);
+                const uint32_t x_bp = __shfl_sync(FULL, best.pid, from);
+                const uint32_t x_bc = __shfl_sync(FULL, best.cell, from);
+                const uint32_t x_sp = __shfl_sync(FULL, sp, from);
+                const int x_sl = __shfl_sync(FULL, lgive, from);
+                const float x_sx = __shfl_sync(FULL, sx, from);
+                const float x_sy = __shfl_sync(FULL, sy, from);
+                const int x_owner = __shfl_sync(FULL, helper ? owner : lane, from);
+                share_scene<Src>(lsc, from);
+                if (idle_l && from != lane) {   // a helper on the subtree below the sibling
+                    helper = true;
+                    in_pair = true;
+                    owner = x_owner;
+                    pid = x_pid;
+                    greg = x_greg != 0;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        pr.org[k] = x_pr[k];
+                        pr.inv[k] = x_pr[3 + k];
+                        d[k] = 0.0f;
+                    }
+                    tau = x_tau;
+                    best.t = x_bt;
+                    best.pid = x_bp;
+                    best.cell = x_bc;
+                    path = x_sp;
+                    trail = 0u;
+                    c0 = x_sx;
+                    c1 = x_sy;
+                    ctop = cvalid = 0;
+                    iters = iter_cap;
+                    if (greg) {
+                        level = x_sl + 1;
+                        rd_target = -1;
+                        gpend = true;
+                    } else if (x_gslot >= 0) {   // the grid from the donor's cache slot
+                        level = x_sl + 1;
+                        rd_target = -1;
+                        gpend = false;
+                        const float *src_g = scr.cache + (size_t)(x_gslot * 48) * stride + (from - lane);
+#pragma unroll
+                        for (int k = 0; k < 48; ++k) g[k] = src_g[k * stride];
+                    } else {
+                        level = 0;
+                        rd_target = x_sl + 1;
+                        gpend = false;
+                        want_root = true;
+                    }
+                    atomicAdd(hcount + wbase + owner, 1);
+                    if (STATS) cnt.v[11]++;
+                }
+            }
+            __syncwarp();
         }
         if (exhausted && !__any_sync(FULL, has_task)) break;
     }

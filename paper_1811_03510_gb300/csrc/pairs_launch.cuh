@@ -13,7 +13,8 @@ cudaError_t launch_pair_pass(const Src &src, const PairBufs &pb, const LaunchCfg
 {
     auto kern = k_pairs<STATS, K, MODE, Src>;
     constexpr uint32_t threads = 128;
-    const size_t smem = (size_t)threads * (scratch_floats((int)cfg.leaf_depth, K, 3) + kRaySlotFloats) * sizeof(float);
+    const size_t smem =
+        (size_t)threads * (scratch_floats((int)cfg.leaf_depth, K, 3) + kRaySlotFloats + kHelpFloats) * sizeof(float);
     static size_t configured = 0;   // largest dynamic shared memory size set on this instantiation
     static size_t occ_smem = 0;
     static int occ_active = 0;

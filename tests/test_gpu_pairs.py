@@ -227,3 +227,21 @@ def test_pairs_batched_and_graph_replay_equal_single_scenes():
     ccs.ccs_batch_destroy(b)
     for h in handles:
         h.close()
+
+
+@pytest.mark.parametrize("local", [False, True])
+def test_pairs_subtrees_handed_to_idle_lanes(local):
+    """A batch much smaller than the GPU: the queue empties at once and idle lanes search subtrees of the
+    busy lanes' pairs (counter 11 counts the hand-overs); the hits stay bit-identical."""
+    s = sg.make_scene(8, 0.05, 3, 1, gregory_ring=True)
+    r = sg.random_rays(3000, seed=75, target=1.05)
+    sc = ccs.Scene(s.P, s.types, local=local)
+    ref = run(sc, r)
+    cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    for K in (0, 1, 2):
+        same(run(sc, r, pairs=True, cache_slots=K), ref, K)
+    got = run(sc, r, counters=cnt, pairs=True)
+    same(got, ref, "counting")
+    assert int(cnt[11]) > 100
+    compare(got, oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True, local=local), 8, max_flagged_frac=0.05)
+    sc.close()

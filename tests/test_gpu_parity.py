@@ -350,9 +350,10 @@ def test_host_path_on_page_locked_memory(layout):
     sc.close()
 
 
-def test_concurrent_launches_on_one_scene_use_separate_queues():
-    """Two launches on one scene at the same time on two streams (each takes its own work-queue head)
-    give the hits each gives alone."""
+@pytest.mark.parametrize("kw", [{}, dict(order=True, image_width=960), dict(pairs=True)])
+def test_concurrent_launches_on_one_scene_use_separate_queues(kw):
+    """Two launches on one scene at the same time on two streams (each takes its own work-queue head, and
+    its own work-order or pair-engine scratch from the library's pool) give the hits each gives alone."""
     s = sg.config_scene(2)
     sc = ccs.Scene(s.P, s.types, local=True)
     ra, rb = sg.pinhole_rays(960, 540), sg.random_rays(200000, seed=91)
@@ -364,8 +365,8 @@ def test_concurrent_launches_on_one_scene_use_separate_queues():
     for _ in range(3):
         ha, hb = ccs.alloc_hits(ra.n), ccs.alloc_hits(rb.n)
         torch.cuda.synchronize()
-        ccs.ccs_intersect(sc.handle, da, ra.n, ha, ccs.make_opts(), s1)
-        ccs.ccs_intersect(sc.handle, db, rb.n, hb, ccs.make_opts(), s2)
+        ccs.ccs_intersect(sc.handle, da, ra.n, ha, ccs.make_opts(**kw), s1)
+        ccs.ccs_intersect(sc.handle, db, rb.n, hb, ccs.make_opts(**kw), s2)
         torch.cuda.synchronize()
         for got, ref in ((ccs.hits_to_numpy(ha), ref_a), (ccs.hits_to_numpy(hb), ref_b)):
             for k in ("t", "u", "v", "pid"):
