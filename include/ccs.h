@@ -402,9 +402,10 @@ typedef struct {
 } ccs_autotune_trial;
 
 /* Autotuner: coordinate descent (two passes) over the BVH width (when the scene was built with
- * CCS_BVH_BOTH), the work order (CCS_TRACE_ORDER off / on, with the base's image_width), lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
+ * CCS_BVH_BOTH), the engine (the ray-persistent kernel without or with CCS_TRACE_ORDER, with the base's
+ * image_width, or the pair engine CCS_TRACE_PAIRS), lanes_per_ray {1, 3}, vote {0, 4, 8, 12, 16, 20, 24},
  * threads per block {64, 96, 128}, blocks per SM {1..6}, refill {1, 2, 4, 8, 16, 24}, chunk {32..1024},
- * bvh_burst {1..16}, cache_slots {0, 2} and min_blocks {0, 4}, starting from
+ * bvh_burst {1..16}, cache_slots {0, 1, 2} and min_blocks {0, 4}, starting from
  * `base` (NULL: defaults).  These options never change the answer (leaf_depth is kept as given), so
  * tuning is safe.  Each candidate is timed with CUDA events over `reps` launches (after one warm-up)
  * of ccs_intersect on the caller's device rays/hits on `stream`, which is synchronised.  The fastest

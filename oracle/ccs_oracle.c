@@ -536,13 +536,16 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
     if (!slab(r, lo, hi, r->tmin, r->tmax, &a, &b)) return;
     b *= ORC_FAR_SCALE;
     if (a > bound || a > b) return;
-    /* below the root the boxes are compared with the ray in the patch frame; its FP32 transform (origin,
-     * direction recovered from the inverse, the new inverse) adds an error that grows with the distance
-     * of the origin from the patch: 6e-7 per unit of distance bounds it */
+    /* below the root the FP32 path compares the boxes with the ray anchored at its entry into the patch box
+     * (its origin formed in FP64 and rounded once, rotated into the patch frame with local frames; the
+     * direction in FP32) and measures distances from there: the error of that ray grows with the size of
+     * the anchored origin and of the patch, not with the distance from the ray's own origin; 3e-7 per unit
+     * of |entry point - box centre| + the box's diagonal bounds it */
     const ray_t rl = local_ray(P, r);
     const v3 cen = scl(add(P->lo, P->hi), 0.5);
-    const v3 oc = sub(r->o, cen);
-    const double eps_in = P->local ? eps + 6e-7 * sqrt(dot3(oc, oc)) : eps;
+    const v3 ec = sub(add(r->o, scl(r->d, a)), cen);
+    const v3 dg = sub(P->hi, P->lo);
+    const double eps_in = eps + 3e-7 * (sqrt(dot3(ec, ec)) + sqrt(dot3(dg, dg)));
     const double tau = box_tau(P, r);
     enode_t *root = &stack[sp++];
     memcpy(root->q, P->gl, sizeof(root->q));

@@ -535,6 +535,7 @@ def opts_dict(o: ccs_trace_opts) -> dict:
                                           "bvh_burst", "cache_slots", "min_blocks", "vote", "lanes_per_ray",
                                           "image_width", "host_chunk", "bvh_width")}
     d["order"] = bool(o.flags & CCS_TRACE_ORDER)
+    d["pairs"] = bool(o.flags & CCS_TRACE_PAIRS)
     return d
 
 

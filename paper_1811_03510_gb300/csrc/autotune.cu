@@ -1,6 +1,7 @@
 // Autotuner of the closest-hit launch: coordinate descent over options that cannot change the answer
-// (BVH width when the scene holds two, work order, lanes per ray, phase vote, threads per block, blocks
-// per SM, warp refill threshold, queue chunk, BVH burst, sibling cache, register budget),
+// (BVH width when the scene holds two, the engine: ray-persistent kernel with or without the work order,
+// or the pair engine; lanes per ray, phase vote, threads per block, blocks per SM, warp refill threshold,
+// queue chunk, BVH burst, sibling cache, register budget),
 // each candidate timed with CUDA events over `reps` launches on the caller's rays.
 #include <cuda_runtime.h>
 
@@ -26,7 +27,7 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     cudaStream_t s = (cudaStream_t)stream;
     ccs_trace_opts cur{};
     if (base) cur = *base;
-    cur.flags &= CCS_TRACE_ORDER;
+    cur.flags &= CCS_TRACE_ORDER | CCS_TRACE_PAIRS;
     cur.counters = nullptr;
     if (!cur.leaf_depth) cur.leaf_depth = 8;
     if (!cur.block_threads) cur.block_threads = 128;
@@ -70,10 +71,10 @@ ccs_status ccs_autotune(const ccs_scene *scene, const ccs_rays *rays, uint32_t n
     const std::vector<uint32_t> refill_c = {1, 2, 4, 8, 16, 24};
     const std::vector<uint32_t> chunk_c = {32, 64, 128, 256, 512, 1024};
     const std::vector<uint32_t> burst_c = {1, 2, 4, 8, 16};
-    const std::vector<uint32_t> cache_c = {0, 2};
+    const std::vector<uint32_t> cache_c = {0, 1, 2};
     const std::vector<uint32_t> minb_c = {0, 4};
     const std::vector<uint32_t> vote_c = {0, 4, 8, 12, 16, 20, 24};
-    const std::vector<uint32_t> order_c = {0, CCS_TRACE_ORDER};
+    const std::vector<uint32_t> order_c = {0, CCS_TRACE_ORDER, CCS_TRACE_PAIRS};
     std::vector<uint32_t> width_c = {0};   // the scene's default BVH, and its second one if it has one
     if (scene->alt_width) width_c.push_back(scene->alt_width);
     const std::vector<uint32_t> *cands[11] = {&width_c, &order_c, &lanes_c, &vote_c, &threads_c, &bps_c, &refill_c,

@@ -73,8 +73,8 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
 }
 
 // Shared memory of a k_pairs thread after its traversal scratch: the world ray of its task (origin,
-// 1 / direction, tmin, tmax), t_evict and the direction rebuilt from 1 / direction (the one that the local
-// frames rotate), read when a pair starts and when the ray ends; then the
+// 1 / direction, tmin, tmax), t_evict and the direction, read when a pair starts and when the ray ends; then
+// the
 // thread's mailbox for the subtrees it handed to other lanes (the smallest (t, cell) key they found,
 // 64 bits), the number of them still running, and a flag for one that reached the iteration cap.
 constexpr int kRaySlotFloats = 12, kHelpFloats = 4;
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     int owner = lane;
     uint32_t pid = 0, start_pid = 0, path = 0, trail = 0;
     RayG<3> pr;
-    float tau = 0.0f, c0 = 0.0f, c1 = 0.0f;
+    float tau = 0.0f, c0 = 0.0f, c1 = 0.0f, te = 0.0f;   // intervals are distances from the anchored origin
     float d[3] = {0.0f, 0.0f, 0.0f};
     int level = 0, rd_target = -1, ctop = 0, cvalid = 0;
     float g[48];
@@ -517,8 +517,9 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 rs[6 * stride] = __uint_as_float(w1.z);
                 rs[7 * stride] = __uint_as_float(w1.w);
                 rs[8 * stride] = __uint_as_float(w0.w);
-#pragma unroll
-                for (int c = 0; c < 3; ++c) rs[(9 + c) * stride] = 1.0f / rs[(3 + c) * stride];
+                rs[9 * stride] = __uint_as_float(w2.w);
+                rs[10 * stride] = __uint_as_float(w3.x);
+                rs[11 * stride] = __uint_as_float(w3.y);
                 src.locate(ray, lsc, ray_scene, ray_local);
                 iters = iter_cap;
                 best.t = __uint_as_float(w1.w);
@@ -543,32 +544,25 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 wr.org[k] = rs[k * stride];
                 wr.inv[k] = rs[(3 + k) * stride];
             }
-            const float tmin = rs[6 * stride], tmax = rs[7 * stride];
-            {   // the root interval: the slab of the patch box (as k_intersect computes it)
+            const float tmin = rs[6 * stride];
+            {   // the root interval: the slab of the patch box from tmin (as k_intersect computes it)
                 const float4 blo = __ldg(sc.leaf_box + 2 * (size_t)pid), bhi = __ldg(sc.leaf_box + 2 * (size_t)pid + 1);
                 const float lo[3] = {blo.x, blo.y, blo.z}, hi[3] = {bhi.x, bhi.y, bhi.z};
-                slab<3>(wr, lo, hi, tmin, tmax, G, c0, c1);
+                slab<3>(wr, lo, hi, tmin, kInf, G, c0, c1);
             }
-            pr = wr;
+            {
+                const float dw[3] = {rs[9 * stride], rs[10 * stride], rs[11 * stride]};
+                te = c0;
+                anchored_ray<3>(rec, an, sc.local != 0, wr.org, dw, wr.inv, c0, G, pr);
+                c1 = __fsub_rn(c1, c0);
+                c0 = 0.0f;
+            }
             tau = 0.0f;
-            if (!sc.local) {
+            if (sc.local) {   // box extension (Sec. 3.4)
+                float o3[3];
 #pragma unroll
-                for (int k = 0; k < 3; ++k) pr.org[k] = wr.org[k] - pick(k, an.x, an.y, an.z);
-            } else {   // the ray in the patch's frame (Sec. 3.4): R (o - anchor), R d
-                float o3[3], d3[3];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    o3[c] = wr.org[c] - pick(c, an.x, an.y, an.z);
-                    d3[c] = rs[(9 + c) * stride];
-                }
-#pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const float4 Rk = __ldg(rec + 16 + k);
-                    pr.org[k] = fmaf(Rk.x, o3[0], fmaf(Rk.y, o3[1], Rk.z * o3[2]));
-                    pr.inv[k] = safe_inv(fmaf(Rk.x, d3[0], fmaf(Rk.y, d3[1], Rk.z * d3[2])));
-                }
-                tau = __fmul_rn(__int_as_float((127 - 19) << 23),
-                                __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
+                for (int c = 0; c < 3; ++c) o3[c] = wr.org[c] - pick(c, an.x, an.y, an.z);
+                tau = pair_tau(o3);
             }
 #pragma unroll
             for (int k = 0; k < 3; ++k) d[k] = 0.0f;
@@ -632,8 +626,8 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 const int force = redesc ? (int)((path >> level) & 1u) : -1;
                 const int slot = (!redesc && !leafkids && K > 0 && !greg) ? (ctop % (K > 0 ? K : 1)) : -1;
                 if (STATS && !redesc) cnt.v[greg ? 2 : 1]++;
-                const StepOut so = split_step<K, 3>(g, pr, d, c0, c1, best.t, redesc || (!greg && !leafkids), scr, slot,
-                                                    true, true, force, G, tau);
+                const StepOut so = split_step<K, 3>(g, pr, d, c0, c1, te, best.t, redesc || (!greg && !leafkids), scr,
+                                                    slot, true, true, force, G, tau);
                 bool back = false;
                 if (redesc) {
                     if (++level == rd_target) rd_target = -1;
@@ -644,8 +638,9 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                         if (so.hitL) {
                             path_cells(path, L, cu, cv);
                             const uint32_t cell = (cv << L) | cu;
-                            if (key_less(so.l0, pid, cell, best)) {
-                                best.t = so.l0;
+                            const float tk = __fadd_rn(te, so.l0);
+                            if (key_less(tk, pid, cell, best)) {
+                                best.t = tk;
                                 best.pid = pid;
                                 best.cell = cell;
                             }
@@ -653,8 +648,9 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                         if (so.hitR) {
                             path_cells(path | bit, L, cu, cv);
                             const uint32_t cell = (cv << L) | cu;
-                            if (key_less(so.r0, pid, cell, best)) {
-                                best.t = so.r0;
+                            const float tk = __fadd_rn(te, so.r0);
+                            if (key_less(tk, pid, cell, best)) {
+                                best.t = tk;
                                 best.pid = pid;
                                 best.cell = cell;
                             }
@@ -698,7 +694,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                                 }
                             }
                             const float2 sb = scr.sib[l * stride];
-                            if (sb.x > best.t) {
+                            if (__fadd_rn(te, sb.x) > best.t) {
                                 if (STATS) cnt.v[6]++;
                                 continue;
                             }
@@ -814,6 +810,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     x_pr[3 + k] = __shfl_sync(FULL, pr.inv[k], from);
                 }
                 const float x_tau = __shfl_sync(FULL, tau, from);
+                const float x_te = __shfl_sync(FULL, te, from);
                 const float x_bt = __shfl_sync(FULL, best.t, from);
                 const uint32_t x_bp = __shfl_sync(FULL, best.pid, from);
                 const uint32_t x_bc = __shfl_sync(FULL, best.cell, from);
@@ -836,6 +833,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                         d[k] = 0.0f;
                     }
                     tau = x_tau;
+                    te = x_te;
                     best.t = x_bt;
                     best.pid = x_bp;
                     best.cell = x_bc;

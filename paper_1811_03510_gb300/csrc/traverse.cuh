@@ -384,7 +384,9 @@ CCS_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "me
 
 // One subdivision step of a Bezier/Gregory node (Algorithm 3, the body of the while loop): de Casteljau
 // split of the node grid along its fixed axis, the two child boxes (Gregory: upper corner + d), both
-// slab tests clipped to the node's interval, closer-first choice (ties: lower half).  On return g holds
+// slab tests clipped to the node's interval, closer-first choice (ties: lower half).  Intervals are
+// distances from the pair's anchored origin; a child is pruned when te + its entry exceeds the best
+// distance tb.  On return g holds
 // the chosen child (transposed for its own split) unless neither child is hit; if both are hit the
 // other child's grid goes to the cache slot when one is given.
 struct StepOut {
@@ -405,9 +407,9 @@ CCS_DEV void extend(float &lo, float &hi, float tau)
 }
 
 template <int K, int NC>
-CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (&d)[NC], float c0, float c1, float tb,
-                           bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR, int force,
-                           const Grp &G, float tau)
+CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (&d)[NC], float c0, float c1, float te,
+                           float tb, bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR,
+                           int force, const Grp &G, float tau)
 {
     float e0[4 * NC], e3[4 * NC], m01[4 * NC], m012[4 * NC], mm[4 * NC], m123[4 * NC], m23[4 * NC];
     float lmin[NC], lmax[NC], rmin[NC], rmax[NC];
@@ -454,8 +456,8 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
     }
     slab<NC>(r, lmin, lmax, c0, c1, G, o.l0, o.l1);
     slab<NC>(r, rmin, rmax, c0, c1, G, o.r0, o.r1);
-    o.hitL = allowL && o.l0 <= o.l1 && o.l0 <= tb;
-    o.hitR = allowR && o.r0 <= o.r1 && o.r0 <= tb;
+    o.hitL = allowL && o.l0 <= o.l1 && __fadd_rn(te, o.l0) <= tb;
+    o.hitR = allowR && o.r0 <= o.r1 && __fadd_rn(te, o.r0) <= tb;
     o.goR = force >= 0 ? force == 1 : (o.hitR && (!o.hitL || o.r0 < o.l0));
     if ((force >= 0 || o.hitL || o.hitR) && keep_grid) {
         const bool up = o.goR;
@@ -513,6 +515,56 @@ struct BvhStack {
     int2 e[kBvhStack];
 };
 
+// Box extension of the local frames (Sec. 3.4; reading B4): tau = 2^-19 (1 + |o - anchor|_1) from the
+// FP32 origin relative to the patch anchor.
+CCS_DEV float pair_tau(const float (&o3)[3])
+{
+    return __fmul_rn(__int_as_float((127 - 19) << 23),
+                     __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
+}
+
+// The ray of a pair.  Sec. 3.4 anchors the patches (points relative to their box centre) to keep the
+// magnitudes of the subdivision small; the ray is anchored the same way, at its entry into the patch box:
+// its origin e = (o - anchor) + te d, with te the entry distance of the pair's root interval, is formed in
+// FP64 from the FP32 inputs, rotated into the patch frame (local frames) and rounded once.  Distances inside
+// the pair are measured from e, so the slab tests subtract numbers of the size of the patch instead of the
+// distance to the camera; a leaf's key distance is te + its entry.  The direction is R d in FP32 (the world
+// direction without local frames), and pr.inv its inverse.  NC = 1: the group exchanges its components.
+template <int NC>
+CCS_DEV void anchored_ray(const float4 *__restrict__ rec, const float4 &an, bool local, const float (&o)[NC],
+                          const float (&dw)[NC], const float (&winv)[NC], float te, const Grp &G, RayG<NC> &pr)
+{
+    double e[3];
+    float dd[3];
+    if constexpr (NC == 3) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e[c] = __fma_rn((double)te, (double)dw[c], (double)o[c] - (double)pick(c, an.x, an.y, an.z));
+            dd[c] = dw[c];
+        }
+    } else {
+        const double ec = __fma_rn((double)te, (double)dw[0], (double)o[0] - (double)pick(G.c, an.x, an.y, an.z));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e[c] = __shfl_sync(G.mask, ec, G.l0 + c);
+            dd[c] = __shfl_sync(G.mask, dw[0], G.l0 + c);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        const int c = comp<NC>(G, k);
+        if (!local) {
+            pr.org[k] = __double2float_rn(e[c]);
+            pr.inv[k] = winv[k];
+        } else {
+            const float4 Rk = __ldg(rec + 16 + c);
+            pr.org[k] = __double2float_rn(
+                __fma_rn((double)Rk.x, e[0], __fma_rn((double)Rk.y, e[1], (double)Rk.z * e[2])));
+            pr.inv[k] = safe_inv(fmaf(Rk.x, dd[0], fmaf(Rk.y, dd[1], Rk.z * dd[2])));
+        }
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // Per-ray state machine.  A lane (NC = 3) or a group of three lanes (NC = 1) owns one ray; every call
 // of lane_step() does one unit of work: one BVH node, the start of a patch, one subdivision step of
@@ -533,6 +585,8 @@ struct BvhStack {
 template <int NC>
 struct Lane {
     float o[NC], tmin, tmax;        // ray origin (the lane's components, world frame) and interval
+    float dw[NC];                   // ray direction (the lane's components, world frame)
+    float te;                       // distance of the current pair's anchored origin along the ray
     RayG<NC> r;
     Best best;
     uint32_t iters;
@@ -542,11 +596,11 @@ struct Lane {
     bool in_pair, greg;             // Algorithm 3 on patch `pid`
     bool gpend;                     // Gregory node (path, level) still needs its (q, d): next step computes it
     uint32_t pid;
-    RayG<NC> pr;                    // ray in the patch's anchored frame
+    RayG<NC> pr;                    // ray in the patch's frame, anchored at its entry into the patch box
     float d[NC];                    // Gregory displacement of the current node
     int level, rd_target;           // tree level; re-descent target level (-1: none)
     uint32_t path, trail;
-    float c0, c1;                   // interval of the current node
+    float c0, c1;                   // interval of the current node (distances from the anchored origin)
     int ctop, cvalid;               // sibling cache: pushes (slot = ctop % K) and valid entries
     uint32_t skip_path;             // subtree (skip_path, skip_level) not to enter again
     int skip_level;
@@ -597,6 +651,7 @@ CCS_DEV void begin_ray(Lane<NC> &s, const DevScene &sc, float ox, float oy, floa
     for (int k = 0; k < NC; ++k) {
         const int c = comp<NC>(G, k);
         s.o[k] = pick(c, ox, oy, oz);
+        s.dw[k] = pick(c, dx, dy, dz);
         s.r.org[k] = s.o[k];
         s.r.inv[k] = safe_inv(pick(c, dx, dy, dz));
     }
@@ -625,7 +680,8 @@ CCS_DEV void pop_next(Lane<NC> &s, BvhStack &stk)
 
 CCS_DEV const float4 *rec_of(const DevScene &sc, uint32_t pid) { return sc.rec + (size_t)pid * kRecF4; }
 
-// Begin Algorithm 3 on patch pid with root interval [c0, c1].
+// Begin Algorithm 3 on patch pid with root interval [c0, c1] (the patch box's slab from tmin; the ray's
+// tmax is the best distance the search starts from).
 template <int MODE, int NC>
 CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, uint32_t pid, float c0, float c1,
                         const Grp &G)
@@ -635,52 +691,36 @@ CCS_DEV void start_pair(Lane<NC> &s, float (&g)[16 * NC], const DevScene &sc, ui
     s.in_pair = true;
     s.greg = an.w != 0.0f;
     s.pid = pid;
-    s.pr = s.r;
+    s.te = c0;
+    anchored_ray<NC>(rec, an, sc.local != 0, s.o, s.dw, s.r.inv, c0, G, s.pr);
     s.tau = 0.0f;
-    if (!sc.local) {
-#pragma unroll
-        for (int k = 0; k < NC; ++k) s.pr.org[k] = s.o[k] - pick(comp<NC>(G, k), an.x, an.y, an.z);
-    } else {   // the ray in the patch's frame (Sec. 3.4): R (o - anchor), R d
-        float o3[3], d3[3];
+    if (sc.local) {   // box extension (Sec. 3.4): boxes below the root at least tau wide along every axis
+        float o3[3];
         if constexpr (NC == 3) {
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                o3[c] = s.o[c] - pick(c, an.x, an.y, an.z);
-                d3[c] = 1.0f / s.r.inv[c];
-            }
+            for (int c = 0; c < 3; ++c) o3[c] = s.o[c] - pick(c, an.x, an.y, an.z);
         } else {   // gather the three components from the group
-            const float oc = s.o[0] - pick(G.c, an.x, an.y, an.z), dc = 1.0f / s.r.inv[0];
+            const float oc = s.o[0] - pick(G.c, an.x, an.y, an.z);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                o3[c] = __shfl_sync(G.mask, oc, G.l0 + c);
-                d3[c] = __shfl_sync(G.mask, dc, G.l0 + c);
-            }
+            for (int c = 0; c < 3; ++c) o3[c] = __shfl_sync(G.mask, oc, G.l0 + c);
         }
-#pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            const float4 Rk = __ldg(rec + 16 + comp<NC>(G, k));
-            s.pr.org[k] = fmaf(Rk.x, o3[0], fmaf(Rk.y, o3[1], Rk.z * o3[2]));
-            s.pr.inv[k] = safe_inv(fmaf(Rk.x, d3[0], fmaf(Rk.y, d3[1], Rk.z * d3[2])));
-        }
-        // box extension (Sec. 3.4): boxes below the root at least tau wide along every axis of the frame
-        s.tau = __fmul_rn(__int_as_float((127 - 19) << 23),
-                          __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
+        s.tau = pair_tau(o3);
     }
 #pragma unroll
     for (int k = 0; k < NC; ++k) s.d[k] = 0.0f;
     s.level = 0;
     s.rd_target = -1;
     s.path = s.trail = 0u;
-    s.c0 = c0;
-    s.c1 = c1;
+    s.c0 = 0.0f;   // the root interval from the anchored origin (te = c0)
+    s.c1 = __fsub_rn(c1, c0);
     s.ctop = s.cvalid = 0;
     if (MODE == kModeScreen) {
         s.sleaf = false;
         s.sleaf_trail = 0u;
     }
     if (MODE != kModePlain && MODE != kModeScreen) {
-        s.rc0 = c0;
-        s.rc1 = c1;
+        s.rc0 = s.c0;
+        s.rc1 = s.c1;
     }
     if (MODE == kModeLearned) {
         s.phase = kPhasePropose;
@@ -753,7 +793,7 @@ CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const De
             }
         }
         const float2 sb = scr.sib[l * scr.stride];
-        if (sb.x > s.best.t) {
+        if (__fadd_rn(s.te, sb.x) > s.best.t) {
             if (STATS) cnt.v[6]++;
             if (MODE == kModeScreen) s.sleaf_trail &= ~bit;
             continue;
@@ -819,8 +859,9 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         path_cells(s.path, L, cu, cv);   // lowest leaf cell of the node (path bits below its level are 0)
         const uint32_t cell = (cv << L) | cu;
         if (STATS) cnt.v[3]++;
-        if (key_less(s.c0, s.pid, cell, s.best)) {
-            s.best.t = s.c0;
+        const float tk = __fadd_rn(s.te, s.c0);   // the leaf's key distance along the ray
+        if (key_less(tk, s.pid, cell, s.best)) {
+            s.best.t = tk;
             s.best.pid = s.pid;
             s.best.cell = cell;
             if (MODE == kModeScreen) s.best.lvl = s.level;
@@ -836,8 +877,8 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         if ((s.skip_path >> s.level) & 1u) allowR = false; else allowL = false;
     }
     if (STATS && !redesc) cnt.v[s.greg ? 2 : 1]++;
-    const StepOut o = split_step<K, NC>(g, s.pr, s.d, s.c0, s.c1, s.best.t, redesc || !s.greg, scr, slot, allowL,
-                                        allowR, force, G, s.tau);
+    const StepOut o = split_step<K, NC>(g, s.pr, s.d, s.c0, s.c1, s.te, s.best.t, redesc || !s.greg, scr, slot,
+                                        allowL, allowR, force, G, s.tau);
     if (redesc) {
         if (++s.level == s.rd_target) s.rd_target = -1;
         return kStepSplit;
@@ -860,8 +901,9 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         const uint32_t bit = 1u << s.level;
         if (MODE == kModeScreen) {   // Sec. 3.3: a box under half a pixel at its entry distance is a leaf
             const float h = 0.5f * mc.spread;
-            s.sleaf = (o.goR ? o.dR : o.dL) < h * (o.goR ? o.r0 : o.l0);
-            if (o.hitL && o.hitR && (o.goR ? o.dL : o.dR) < h * (o.goR ? o.l0 : o.r0)) s.sleaf_trail |= bit;
+            s.sleaf = (o.goR ? o.dR : o.dL) < h * __fadd_rn(s.te, o.goR ? o.r0 : o.l0);
+            if (o.hitL && o.hitR && (o.goR ? o.dL : o.dR) < h * __fadd_rn(s.te, o.goR ? o.l0 : o.r0))
+                s.sleaf_trail |= bit;
         }
         if (o.hitL && o.hitR) {
             s.trail |= bit;
@@ -911,7 +953,8 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
         const uint32_t pid = (uint32_t)(~s.node);
         if (s.n0 <= s.best.t) {
             if (STATS) cnt.v[7]++;
-            // the root interval: the slab of the patch box, as its parent's step computed it
+            // the root interval: the slab of the patch box from tmin (tmax bounds the leaves' key distances,
+            // through the best distance it starts from)
             float lo[NC], hi[NC], c0, c1;
             const float4 blo = __ldg(sc.leaf_box + 2 * (size_t)pid), bhi = __ldg(sc.leaf_box + 2 * (size_t)pid + 1);
 #pragma unroll
@@ -920,7 +963,7 @@ CCS_DEV void bvh_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
                 lo[k] = pick(c, blo.x, blo.y, blo.z);
                 hi[k] = pick(c, bhi.x, bhi.y, bhi.z);
             }
-            slab<NC>(s.r, lo, hi, s.tmin, s.tmax, G, c0, c1);
+            slab<NC>(s.r, lo, hi, s.tmin, __int_as_float(0x7f800000), G, c0, c1);
             start_pair<MODE, NC>(s, g, sc, pid, c0, c1, G);
         } else {
             pop_next<NC>(s, stk);

@@ -110,7 +110,8 @@ def test_local_frames_keep_shared_boundaries_watertight():
 
 def test_local_frames_agree_with_world_frames_away_from_edges():
     """Both frames bound the same surface with boxes around each leaf cell, so away from patch edges they
-    report the same patch, at distances a few leaf-box sizes apart at most."""
+    report the same patch, at distances a few leaf-box sizes apart (divided by the sine of the angle
+    between ray and surface, which lets the rare grazing ray differ by more)."""
     s = sg.config_scene(2)
     r = sg.pinhole_rays(160, 90)
     w = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
@@ -120,7 +121,7 @@ def test_local_frames_agree_with_world_frames_away_from_edges():
     same = both & (w["pid"] == l["pid"])
     assert same.mean() / both.mean() > 0.97
     dt = np.abs(l["t"][same] - w["t"][same])
-    assert dt.max() < 1e-2 and np.median(dt) < 1e-3
+    assert np.percentile(dt, 99.5) < 1e-2 and dt.max() < 3e-2 and np.median(dt) < 1e-3
 
 
 def test_frame_of_a_curved_patch_is_a_rotation():
@@ -136,3 +137,51 @@ def test_frame_of_a_curved_patch_is_a_rotation():
         np.testing.assert_allclose(R[2], n / np.linalg.norm(n), atol=1e-12)
         e = g[3] - g[0]
         assert abs(R[1] @ e) <= 1e-12 * np.linalg.norm(e) and R[0] @ e > 0
+
+
+def _f32_fma(a, b, c):
+    """FP32 fused multiply-add: a*b is exact in FP64 for FP32 inputs, one rounding of the sum to FP32."""
+    return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
+
+
+def test_anchored_ray_error_is_within_the_flag_model():
+    """The FP32 path intersects a pair with the ray anchored at its entry into the patch box: origin
+    e = (o - anchor) + te d formed in FP64, rotated into the patch frame and rounded once, direction R d in
+    FP32.  Over the patch box that ray stays within 3e-7 (|e| + box diagonal) of the exact ray in the same
+    frame, whatever the distance from the ray's own origin (here 3 and 300 scene units): the term the
+    oracle's parity flags add to eps.  The FP32 transform without the anchor misses that bound by far."""
+    s = sg.config_scene(2)
+    P = s.P.astype(np.float32)
+    worst, worst_plain = 0.0, 0.0
+    for k, p in enumerate(RNG.choice(s.n, 300, replace=False)):
+        g = P[p]
+        pts = g[:20] if s.types[p] else g[:16]
+        lo, hi = pts.min(0), pts.max(0)
+        an = ((lo + hi).astype(np.float32) * np.float32(0.5)).astype(np.float32)
+        R = oracle.local_frame(g.astype(np.float64)).astype(np.float32)
+        target = (lo + (hi - lo) * RNG.uniform(0.2, 0.8, 3)).astype(np.float64)
+        for dist in (3.0, 300.0):
+            u = RNG.normal(size=3)
+            u /= np.linalg.norm(u)
+            o = (target + dist * u).astype(np.float32)
+            d = (-u).astype(np.float32)
+            te = np.float32(dist - np.linalg.norm(hi - lo))
+            e = np.float64(te) * d.astype(np.float64) + (o.astype(np.float64) - an.astype(np.float64))
+            org = np.array([np.float32(R[i].astype(np.float64) @ e) for i in range(3)], np.float32)
+            dl = np.array([_f32_fma(R[i, 0], d[0], _f32_fma(R[i, 1], d[1], np.float32(R[i, 2] * d[2])))
+                           for i in range(3)], np.float32)
+            # the exact ray in the same (rounded) frame, and the unanchored FP32 transform for comparison
+            ex_o = R.astype(np.float64) @ (o.astype(np.float64) - an.astype(np.float64))
+            ex_d = R.astype(np.float64) @ d.astype(np.float64)
+            o3 = (o - an).astype(np.float32)
+            plain = np.array([_f32_fma(R[i, 0], o3[0], _f32_fma(R[i, 1], o3[1], np.float32(R[i, 2] * o3[2])))
+                              for i in range(3)], np.float32)
+            diag = float(np.linalg.norm((hi - lo).astype(np.float64)))
+            bound = 3e-7 * (float(np.linalg.norm(e)) + diag)
+            for tp in (0.0, diag, 2.0 * diag):
+                exact = ex_o + (float(te) + tp) * ex_d
+                worst = max(worst, float(np.linalg.norm(org + tp * dl.astype(np.float64) - exact)) / bound)
+                worst_plain = max(worst_plain, float(np.linalg.norm(plain + (float(te) + tp) * dl.astype(np.float64)
+                                                                    - exact)) / bound)
+    assert worst < 1.0, worst
+    assert worst_plain > 10.0, worst_plain
