@@ -145,9 +145,33 @@ def whole_job_rate(rays_per_step: int, steps: int, t_slowest: float, world: int)
     return rays_per_step * world * steps / t_slowest / 1e6
 
 
-def schedule_summary(c: dict, lanes_per_ray: int) -> dict:
-    """Warp schedule from the kernel's schedule counters: rays resident per warp iteration, and for each step
-    kind the share of iterations that run it and the rays taking part when it runs."""
+def engine_of(o) -> str:
+    from paper_1811_03510_gb300 import ccs
+    d = ccs.opts_dict(o)
+    return "pairs" if d["pairs"] and d["lanes_per_ray"] != 3 else ("ray+order" if d["order"] else "ray")
+
+
+def kernels_per_launch(o) -> int:
+    """Kernels of this library one ccs_intersect launches: the pair engine's candidate pass, task order,
+    subdivision pass and fallback; the work order's three kernels and k_intersect; or k_intersect alone."""
+    return {"pairs": 4, "ray+order": 4, "ray": 1}[engine_of(o)]
+
+
+def schedule_summary(c: dict, lanes_per_ray: int, engine: str = "ray") -> dict:
+    """Warp schedule from the kernel's schedule counters.  Ray-persistent kernel: rays resident per warp
+    iteration, and for each step kind the share of iterations that run it and the rays taking part when it
+    runs.  Pair engine: lanes per warp iteration in a subdivision step, helping with a handed-over subtree,
+    waiting for helpers or idle; the candidate lists and the fallback."""
+    from paper_1811_03510_gb300 import ccs
+    if engine == "pairs":   # slots 8..16 of the pair engine's counting launch
+        v = [c[ccs.COUNTER_NAMES[k]] for k in range(ccs.CCS_NUM_COUNTERS)]
+        it = max(1, v[12])
+        out = {"engine": "pairs", "warp_iters": v[12], "split_lanes_per_iter": v[13] / it,
+               "helper_lanes_per_iter": v[14] / it, "waiting_lanes_per_iter": v[15] / it,
+               "idle_lanes_per_iter": v[16] / it, "subtrees_handed_over": v[11], "candidates": v[8],
+               "rays_with_dropped_candidates": v[9], "fallback_rays": v[10]}
+        out.update(ccs.timeline(c))
+        return out
     it = max(1, c["warp_iters"])
     rpw = 10 if lanes_per_ray == 3 else 32
     out = {"warp_iters": c["warp_iters"], "rays_per_warp": rpw, "resident_per_iter": c["resident_rays"] / it}
@@ -165,16 +189,17 @@ def kernel_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     for f in ("traverse.cuh", "intersect_impl.cuh", "intersect.cu", "intersect4.cu", "order.cu", "order_plan.h",
-              "learned.cuh", "ccs_internal.h"):
+              "learned.cuh", "ccs_internal.h", "pairs.cuh", "pairs.cu", "pairs_launch.cuh", "pairs_plain.cu"):
         with open(os.path.join(ROOT, "paper_1811_03510_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic() -> tuple:
-    """DRAM bytes per primary and diffuse launch from the committed ncu summary, if it was taken on the current
-    kernel sources (else None: the counters describe another kernel)."""
-    path = os.path.join(ROOT, "profiles", "k_intersect_cfg2_dram.md")
+    """DRAM bytes per primary and diffuse launch of the dominant kernel (the pair engine's subdivision pass)
+    from the committed ncu summary, if it was taken on the current kernel sources (else None: the counters
+    describe another kernel)."""
+    path = os.path.join(ROOT, "profiles", "k_pairs_cfg2_dram.md")
     try:
         text = open(path).read()
     except OSError:
@@ -191,7 +216,7 @@ def measured_traffic() -> tuple:
 def measured_issue() -> tuple:
     """Thread-instruction issue of the primary launch over the FP32 lane peak (all instructions, and FADD/FMUL/FFMA
     alone) from the committed full ncu capture, if it was taken on the current kernel sources (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_intersect_cfg2_960x540_ncu.md")
+    path = os.path.join(ROOT, "profiles", "k_pairs_cfg2_960x540_ncu.md")
     try:
         text = open(path).read()
     except OSError:
@@ -432,29 +457,36 @@ def run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p):
     return out
 
 
-def run_large(args, dev, stream, flush):
+def run_large(args, dev, stream, flush, n_sm):
     """The 393,216-patch cube-sphere (128 x 128 quads per face, noise 0.1, 5 octaves) with 3840 x 2160
-    primary rays and their diffuse rays, tuned, on binary and on 4-wide BVHs: MRays/s and BVH nodes per
-    ray (Sec. 4: larger models are dominated by the traversal of the hierarchy)."""
+    primary rays and the diffuse and mirror generations from their hits (active slots), each tuned, on binary
+    and on 4-wide BVHs: MRays/s, the fraction of the FP32 issue peak and BVH nodes per ray (Sec. 4: larger
+    models are dominated by the traversal of the hierarchy)."""
     import torch
     from paper_1811_03510_gb300 import ccs, scenegen as sg
     s = sg.config_scene(3)
     cam = sg.pinhole_rays(3840, 2160)
     prim = ccs.rays_to_device(cam.soa(), dev)
     out = {"patches": int(s.n), "primary_rays": cam.n}
+    reps = max(3, args.steps // 4)
     for width in (2, 4):
         sc = ccs.Scene(s.P, s.types, local=args.boxes == "local", bvh_width=width)
         hp = ccs.intersect(sc, prim, ccs.make_opts(), stream)
-        d = ccs.gen_diffuse(sc, prim, hp, seed=1, leaf_depth=8, offset_abs=1e-4, stream=stream)
-        torch.cuda.synchronize()
-        act = (d[7] >= d[6]).nonzero().squeeze(1)
-        diff = [p.index_select(0, act).contiguous() for p in d]
+        gens = {"primary": (prim, cam.n, 3840)}
+        for name, planes in (("diffuse", ccs.gen_diffuse(sc, prim, hp, seed=1, leaf_depth=8, offset_abs=1e-4,
+                                                         stream=stream)),
+                             ("mirror", ccs.gen_mirror(sc, prim, hp, leaf_depth=8, offset_abs=1e-4, stream=stream))):
+            torch.cuda.synchronize()
+            act = (planes[7] >= planes[6]).nonzero().squeeze(1)
+            gens[name] = ([p.index_select(0, act).contiguous() for p in planes], int(act.numel()), 0)
         res = {}
-        for name, rays, n, iw in (("primary", prim, cam.n, 3840), ("diffuse", diff, int(act.numel()), 0)):
+        for name, (rays, n, iw) in gens.items():
             h = ccs.alloc_hits(n, dev)
             best, _, _ = ccs.ccs_autotune(sc.handle, rays, n, h, ccs.make_opts(image_width=iw), reps=1, stream=stream)
+            for _ in range(2):
+                ccs.ccs_intersect(sc.handle, rays, n, h, best, stream)
             tot = 0.0
-            for k in range(max(3, args.steps // 4)):
+            for k in range(reps):
                 flush.fill_(float(k))
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -462,15 +494,63 @@ def run_large(args, dev, stream, flush):
                 e1.record(stream)
                 torch.cuda.synchronize()
                 tot += e0.elapsed_time(e1) / 1e3
-            c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
-            ccs.ccs_intersect(sc.handle, rays, n, h, ccs.make_opts(counters=c), stream)
-            torch.cuda.synchronize()
-            cc = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
-            res[name + "_mrays_s"] = n * max(3, args.steps // 4) / tot / 1e6
+            ops, cc = alg_ops_of(sc, rays, n, h, stream, dev)
+            res[name + "_rays"] = n
+            res[name + "_mrays_s"] = n * reps / tot / 1e6
+            res[name + "_roofline_frac"] = ops * reps / tot / fp32_peak_ops(n_sm, 2070.0)
             res[name + "_bvh_nodes_per_ray"] = cc["bvh_nodes"] / n
-        res["diffuse_rays"] = int(act.numel())
+            res[name + "_engine"] = engine_of(best)
         out[f"bvh{width}"] = res
         sc.close()
+    return out
+
+
+def alg_ops_of(scene, rays, n, hits, stream, dev) -> tuple:
+    """Algorithmic FP32 ops of one launch, from a counting launch of the ray-persistent kernel (binary BVH,
+    default options): BVH nodes, Bezier and Gregory splits, the local-frame ray per pair."""
+    import torch
+    from paper_1811_03510_gb300 import ccs
+    c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+    ccs.ccs_intersect(scene.handle, rays, n, hits, ccs.make_opts(leaf_depth=8, counters=c), stream)
+    torch.cuda.synchronize()
+    v = dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist()))
+    ops = (v["bvh_nodes"] * OPS_BVH_NODE + v["bezier_splits"] * OPS_SPLIT_BEZIER + v["gregory_splits"] * OPS_SPLIT_GREGORY
+           + (v["pairs"] * OPS_PAIR_FRAME if scene.local else 0))
+    return ops, v
+
+
+def run_world_step(args, dev, stream, s, prim, n_prim, diff, n_diff, flush, n_sm):
+    """The benchmark step (the same primary and diffuse rays) on a scene whose sub-domain boxes are in world
+    axes, launch options tuned per batch: MRays/s and the fraction of the FP32 issue peak."""
+    import torch
+    from paper_1811_03510_gb300 import ccs
+    sc = ccs.Scene(s.P, s.types, local=False, bvh_width=bvh_arg(args))
+    out, ops, t_tot = {}, 0.0, 0.0
+    for name, rays, n, width in (("primary", prim, n_prim, args.width), ("diffuse", diff, n_diff, 0)):
+        h = ccs.alloc_hits(n, dev)
+        best = ccs.make_opts(leaf_depth=8)
+        if not args.no_autotune:
+            best, _, _ = ccs.ccs_autotune(sc.handle, rays, n, h, ccs.make_opts(leaf_depth=8, image_width=width),
+                                          reps=2, stream=stream)
+        for _ in range(max(3, args.warmup)):
+            ccs.ccs_intersect(sc.handle, rays, n, h, best, stream)
+        tot = 0.0
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ccs.ccs_intersect(sc.handle, rays, n, h, best, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+        o, _ = alg_ops_of(sc, rays, n, h, stream, dev)
+        ops += o * args.steps
+        t_tot += tot
+        out[name + "_mrays_s"] = n * args.steps / tot / 1e6
+        out[name + "_engine"] = engine_of(best)
+    sc.close()
+    out["step_mrays_s"] = (n_prim + n_diff) * args.steps / t_tot / 1e6
+    out["roofline_frac"] = ops / t_tot / fp32_peak_ops(n_sm, 2070.0)
     return out
 
 
@@ -603,6 +683,29 @@ def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
         out["splits_learned"] = cl["bezier_splits"] + cl["gregory_splits"]
         out["backtracks_plain"], out["backtracks_learned"] = cp["backtracks"], cl["backtracks"]
         out["speedup"] = out["learned_mrays_s"] / out["plain_mrays_s"]
+        # the most any proposal can gain: the same search started with the final best distance (tmax set to
+        # the plain answer's distance, inclusive, so the hits stay the same), plain launch options
+        seeded = list(rays)
+        seeded[7] = torch.where(hp[3] != -1, hp[0], rays[7]).contiguous()
+        hs = ccs.alloc_hits(n, dev)
+        ts = []
+        for k in range(args.warmup + args.steps):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ccs.ccs_intersect(scene.handle, seeded, n, hs, op, stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        c_s = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
+        ccs.ccs_intersect(scene.handle, seeded, n, hs, ccs.make_opts(leaf_depth=8, cache_slots=0, counters=c_s), stream)
+        torch.cuda.synchronize()
+        cs = dict(zip(ccs.COUNTER_NAMES, c_s.tolist()))
+        out["bound_seeded_best"] = {"mrays_s": n * args.steps / sum(ts) / 1e6,
+                                    "splits": cs["bezier_splits"] + cs["gregory_splits"],
+                                    "identical_hits": bool(all(torch.equal(a, b) for a, b in zip(hp, hs))),
+                                    "time_speedup_bound": (n * args.steps / sum(ts) / 1e6) / out["plain_mrays_s"]}
         res[name] = out
     ccs.ccs_proposal_destroy(prop)
     return res
@@ -696,7 +799,7 @@ def main():
         c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device=dev)
         ccs.ccs_intersect(scene.handle, rays, n, h, ccs.make_opts(**ccs.opts_dict(o), counters=c), stream)
         torch.cuda.synchronize()
-        sched[name] = schedule_summary(dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist())), o.lanes_per_ray)
+        sched[name] = schedule_summary(dict(zip(ccs.COUNTER_NAMES, c.cpu().tolist())), o.lanes_per_ray, engine_of(o))
 
     for _ in range(args.warmup):
         step()
@@ -786,6 +889,12 @@ def main():
         e2e[name] = whole_job_rate(rays_per_step, args.steps, max_over_ranks(sum(te), dev), world)
     e2e_value = e2e["one_pipeline"]
 
+    # the same step with the sub-domain boxes in world axes (Algorithm 3 as printed, without Sec. 3.4's local
+    # frames), tuned the same way: the plain method's own rate and roofline fraction beside the headline
+    world_step = None
+    if scene.local and args.variant == "all":
+        world_step = run_world_step(args, dev, stream, s, prim, n_prim, diff, n_diff, flush, n_sm)
+
     traffic, traffic_src = measured_traffic()
     issue, issue_src = measured_issue()
     peak_max = fp32_peak_ops(n_sm, 2070.0)
@@ -809,19 +918,25 @@ def main():
         "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_max / 1e12, "unit": "Top/s (FP32)",
                      "frac": achieved / peak_max,
                      "traffic": (traffic[0] + traffic[1]) / 2 if traffic else None,
-                     "per": "launch (mean of the step's primary and diffuse k_intersect launches)",
-                     "note": "algorithmic FP32 ops (BVH node 34, Bezier split 360, Gregory split 1490) from the "
-                             "kernel's traversal counters / event-timed launch time (with the work-order kernels "
-                             "where the launch uses them); peak = SMs x 128 lanes x 2070 MHz "
-                             "(nominal FP32 issue; no FP32 figure in the measured peaks); traffic = DRAM bytes per "
-                             "launch from " + (os.path.relpath(traffic_src, ROOT) if traffic_src else "no capture") +
-                             ("" if traffic else " (null: no capture of the current kernel sources)"),
+                     "per": "step (both batches, every kernel of the chosen engines, event-timed)",
+                     "note": "algorithmic FP32 ops (BVH node 34, Bezier split 360, Gregory split 1490, local-frame "
+                             "ray 24 per pair) / event-timed step time; peak = SMs x 128 lanes x 2070 MHz "
+                             "(nominal FP32 issue; no FP32 figure in the measured peaks)",
+                     "op_counts": "work counters of a counting launch of the ray-persistent kernel on the binary "
+                                  "BVH with default options: the method's work with best-distance pruning (the "
+                                  "pair engine's candidate pass visits more BVH nodes, not credited)",
+                     "traffic_per": "launch of the dominant kernel (the pair engine's subdivision pass), mean of "
+                                    "the primary and diffuse batches",
+                     "traffic_source": ({"file": os.path.relpath(traffic_src, ROOT), "kernel_sources_sha16":
+                                         kernel_source_hash(), "matches": bool(traffic)} if traffic_src else None),
                      "algorithmic_bytes_per_launch": 48 * rays_per_step / 2,
                      "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None,
                      "issue_frac_ncu": ({"all_instructions": issue[0], "fadd_fmul_ffma": issue[1],
                                          "source": os.path.relpath(issue_src, ROOT),
-                                         "per": "thread instructions per cycle / (SMs x 128 lanes), one 960x540 "
-                                                "primary launch under ncu"} if issue else None)},
+                                         "kernel_sources_sha16": kernel_source_hash(),
+                                         "per": "thread instructions per cycle / (SMs x 128 lanes), the dominant "
+                                                "kernel of one 960x540 primary launch under ncu"} if issue else None)},
+        "world_axes": world_step,
         "counters": counts,
         "schedule": sched,
         "clocks": {"sm_mhz": ck["sm_mhz"], "sm_max_mhz": ck["sm_max_mhz"], "reasons": ck["reasons"],
@@ -832,8 +947,10 @@ def main():
                             "of copies staged through device buffers in chunks that overlap the traversal; wall "
                             "clock per step including the call's synchronisation",
                 "separate_calls_value": e2e["staged_copies"], "mapped_value": e2e["mapped"]},
-        # k_intersect per batch, plus the three kernels of the work order where the tuner chose it
-        "gpu_launches": args.steps * sum(1 + 3 * ccs.opts_dict(o)["order"] for o in (opts_p, opts_d)),
+        # this library's kernels per step: the pair engine's four, the work order's three and k_intersect, or
+        # k_intersect alone, per batch as the tuner chose
+        "gpu_launches": args.steps * sum(kernels_per_launch(o) for o in (opts_p, opts_d)),
+        "engine": {"primary": engine_of(opts_p), "diffuse": engine_of(opts_d)},
     }
     if args.variant in ("all", "learned"):
         res["learned"] = run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d)
@@ -843,7 +960,7 @@ def main():
         res["shadow"] = run_shadow(args, dev, stream, flush)
         res["screen_space"] = run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p)
         res["frames"] = run_frames(args, dev, stream, s, prim, n_prim, diff, n_diff, flush)
-        res["large_scene"] = run_large(args, dev, stream, flush)
+        res["large_scene"] = run_large(args, dev, stream, flush, n_sm)
     if rank == 0 and not args.no_cpu_baseline:
         # the FP64 oracle on all host cores over the same step, repeated until about 10 s of CPU work
         import oracle

@@ -4,8 +4,8 @@
 //     patches, ordered by (entry distance of the patch box, patch id).  Before the list is full nothing
 //     is pruned but [tmin, tmax]; once it is full, subtrees that enter beyond its last entry are skipped
 //     and the smallest entry distance dropped that way is kept (t_evict).  A ray with candidates becomes a
-//     task with a cost class (its candidates, Gregory patches counted three times); rays with no
-//     candidate are written as misses here.
+//     task with a cost class (the highest when a candidate is a Gregory patch, else its number of
+//     candidates); rays with no candidate are written as misses here.
 //  2. k_task_place: a counting sort of the tasks by cost class, costliest first, so that the long rays
 //     start early and the launch does not end on a few of them.
 //  3. k_pairs: persistent warps take tasks in that order.  A lane runs Algorithm 3 on one (ray, patch) pair
@@ -328,7 +328,9 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
 #pragma unroll
         for (int j = 0; j < C; ++j)
             if (j < cnt && __ldg(sc.types + kp[j]) != 0) ++ng;
-        key = min(kCostClasses - 1, cnt + 2 * ng);
+        // rays with a Gregory candidate first: their pairs then share warps, so fewer warp iterations pay
+        // for the bound of Algorithm 2 with a single Gregory lane; the others by their number of candidates
+        key = ng > 0 ? kCostClasses - 1 : min(kCostClasses - 2, cnt);
     }
     const uint32_t want = has ? (uint32_t)cnt : 0u;
     uint32_t incl = want;

@@ -10,7 +10,7 @@ import pytest
 import oracle
 from oracle import mlp
 from paper_1811_03510_gb300 import ccs, scenegen as sg
-from parity import MISS
+from parity import MISS, compare
 
 pytestmark = pytest.mark.gpu
 
@@ -198,6 +198,7 @@ def test_learned_hits_identical_to_plain(which):
     ref = ccs.alloc_hits(r.n)
     ccs.ccs_intersect(sc.handle, rays, r.n, ref, ccs.make_opts())
     p = ccs.ccs_proposal_create(seed=9)   # an untrained network proposes arbitrary cells: a hard case
+    orc = oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True)
     for conf in (0.0, 0.05):
         out = ccs.alloc_hits(r.n)
         ccs.ccs_intersect_learned(sc.handle, p, rays, r.n, out, ccs.make_opts(), conf)
@@ -205,5 +206,57 @@ def test_learned_hits_identical_to_plain(which):
         assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
         for a, b in zip(ref, out):
             assert torch.equal(a, b)
+        compare(ccs.hits_to_numpy(out), orc, 8)   # the learned traversal against the oracle itself
     ccs.ccs_proposal_destroy(p)
+    sc.close()
+
+
+def _splits(sc, planes, learned=None):
+    n = len(planes[0])
+    rays = ccs.rays_to_device(planes)
+    hits = ccs.alloc_hits(n)
+    c = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    if learned is None:
+        ccs.ccs_intersect(sc.handle, rays, n, hits, ccs.make_opts(counters=c))
+    else:
+        ccs.ccs_intersect_learned(sc.handle, learned, rays, n, hits, ccs.make_opts(counters=c), 0.0)
+    torch.cuda.synchronize()
+    assert ccs.ccs_scene_sync_status(sc.handle) == ccs.CCS_OK
+    return int(c[1] + c[2]), ccs.hits_to_numpy(hits)
+
+
+@pytest.mark.parametrize("local", [False, True])
+def test_seeded_best_distance_bounds_what_any_proposal_can_save(local):
+    """The most a proposal can save: the search started with the final best distance already known (tmax
+    set to the oracle's hit distance, which the inclusive tmax keeps).  Nodes entered before that distance
+    must be searched whatever the order, so the seeded run does the least subdivision work any traversal
+    can.  On the 1536-patch scene it saves under 3% of the plain traversal's splits on primary rays and
+    none on diffuse rays: the closer-first order with sibling pruning already finds the best leaf first.
+    The learned traversal, whose proposal is only a depth-3 cell, does more work than the seeded run."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(480, 270)
+    sc = ccs.Scene(s.P, s.types, local=local)
+    o = oracle.intersect(s.P, s.types, r.soa(), L=8, local=local)
+    hit = o["pid"] != MISS
+    seeded = r.soa()
+    seeded[7] = np.where(hit, o["t"] * (1 + 1e-6), np.inf).astype(np.float32)
+    plain, hp = _splits(sc, r.soa())
+    best, hs = _splits(sc, seeded)
+    assert np.array_equal(hs["pid"], hp["pid"]) and np.array_equal(hs["t"], hp["t"])
+    assert best <= plain < 1.03 * best, (plain, best)
+    p = ccs.ccs_proposal_create(seed=9)
+    learned, _ = _splits(sc, r.soa(), learned=p)
+    assert learned >= best
+    ccs.ccs_proposal_destroy(p)
+    # diffuse rays leave the (near-convex) sphere: nothing to save
+    from oracle.raygen import diffuse_rays
+    d = diffuse_rays(s.P, s.types, r.soa(), o, seed=1)
+    act = d[7] >= d[6]
+    dr = [np.ascontiguousarray(a[act]) for a in d]
+    od = oracle.intersect(s.P, s.types, dr, L=8, local=local)
+    ds = list(dr)
+    ds[7] = np.where(od["pid"] != MISS, od["t"] * (1 + 1e-6), dr[7]).astype(np.float32)
+    plain_d, _ = _splits(sc, dr)
+    best_d, _ = _splits(sc, ds)
+    assert best_d <= plain_d <= 1.03 * best_d + 10, (plain_d, best_d)
     sc.close()
