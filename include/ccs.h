@@ -383,10 +383,15 @@ ccs_status ccs_intersect_learned(const ccs_scene *scene, const ccs_proposal *pro
  * scratch that ccs_intersect_batched allocates (scene table, ray prefix, work-queue head, status word)
  * lives instead in one fixed file-scope device array sized for CCS_NOALLOC_MAX_SCENES scenes (about
  * 50 KB), which every GPU that loads the library holds until the process exits.
- *  - The first call on a device looks up that array's device address (once per device, with the
- *    device current); make that first call before any stream capture.
+ *  - Every call looks up that array's device address in the current device's context
+ *    (cudaGetSymbolAddress), so a device reset between calls does not leave a stale address; the first
+ *    call on a device also loads the module there.
+ *  - The call copies the scene table and synchronises `stream`, and reads the status word back with a
+ *    blocking copy: it can never be called while `stream` (or the legacy stream) is being captured into
+ *    a CUDA graph.
  *  - More than CCS_NOALLOC_MAX_SCENES scenes: CCS_ERR_INVALID_ARG with a message; nothing runs.
  *  - Calls no cudaMalloc / cudaFree; the queue head and status word are reset at every call.
+ *    CCS_TRACE_PAIRS is ignored (the pair engine's scratch grows with the number of rays).
  *  - All calls share the one array: calls whose work overlaps on the GPU (other threads or streams)
  *    race on it.  The call synchronises `stream` before it returns, so calls from one thread do not.
  * Answers are bit-identical to ccs_intersect_batched and ccs_intersect. */

@@ -4,7 +4,6 @@
 #include <cuda_runtime.h>
 
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "ccs_internal.h"
@@ -24,24 +23,15 @@ struct NoAllocScratch {
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
 
-constexpr int kMaxDevices = 64;
-static NoAllocScratch *g_scratch_addr[kMaxDevices];
-static std::mutex g_scratch_mu;
-
-// Device address of the scratch array on the current device (set up once per device).
-static cudaError_t scratch_on_current_device(NoAllocScratch **out, int *device)
+// Device address of the scratch array in the current device's context.  Looked up at every call: a
+// lookup is cheap next to the call's own synchronisation, and an address kept from an earlier context
+// would be stale after cudaDeviceReset.
+static cudaError_t scratch_on_current_device(NoAllocScratch **out)
 {
-    cudaError_t e = cudaGetDevice(device);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (*device < 0 || *device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_addr[*device]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[*device] = static_cast<NoAllocScratch *>(p);
-    }
-    *out = g_scratch_addr[*device];
+    *out = static_cast<NoAllocScratch *>(p);
     return cudaSuccess;
 }
 
@@ -65,6 +55,7 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
     LaunchCfg cfg;
     ccs_status st = fill_launch_cfg(opts, cfg);
     if (st != CCS_OK) return st;
+    cfg.flags &= ~CCS_TRACE_PAIRS;   // the pair engine's scratch grows with the rays: not here
     uint64_t total = 0;
     for (uint32_t s = 0; s < n_scenes; ++s) {
         const ccs_scene *sc = scenes[s];
@@ -90,8 +81,7 @@ extern "C" ccs_status ccs_intersect_batched_noalloc(ccs_scene *const *scenes, co
         return CCS_ERR_INVALID_ARG;
     }
     NoAllocScratch *scr = nullptr;
-    int device = 0;
-    cudaError_t e = scratch_on_current_device(&scr, &device);
+    cudaError_t e = scratch_on_current_device(&scr);
     if (e != cudaSuccess) {
         set_error(std::string("ccs_intersect_batched_noalloc: scratch set-up: ") + cudaGetErrorString(e));
         return CCS_ERR_CUDA;
