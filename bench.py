@@ -163,13 +163,14 @@ def schedule_summary(c: dict, lanes_per_ray: int, engine: str = "ray") -> dict:
     runs.  Pair engine: lanes per warp iteration in a subdivision step, helping with a handed-over subtree,
     waiting for helpers or idle; the candidate lists and the fallback."""
     from paper_1811_03510_gb300 import ccs
-    if engine == "pairs":   # slots 8..16 of the pair engine's counting launch
+    if engine == "pairs":   # slots 8..17 of the pair engine's counting launch
         v = [c[ccs.COUNTER_NAMES[k]] for k in range(ccs.CCS_NUM_COUNTERS)]
         it = max(1, v[12])
         out = {"engine": "pairs", "warp_iters": v[12], "split_lanes_per_iter": v[13] / it,
                "helper_lanes_per_iter": v[14] / it, "waiting_lanes_per_iter": v[15] / it,
                "idle_lanes_per_iter": v[16] / it, "subtrees_handed_over": v[11], "candidates": v[8],
-               "rays_with_dropped_candidates": v[9], "fallback_rays": v[10]}
+               "candidates_culled_by_root_box": v[17], "rays_with_dropped_candidates": v[9],
+               "fallback_rays": v[10]}
         out.update(ccs.timeline(c))
         return out
     it = max(1, c["warp_iters"])
@@ -427,12 +428,14 @@ def run_shadow(args, dev, stream, flush):
 
 def run_screen(args, dev, stream, scene, prim, n_prim, flush, opts_p):
     """Primary rays with screen-space termination (Sec. 3.3) at the camera's pixel size, against the fixed
-    leaf depth of the benchmark, on the same rays and launch options."""
+    leaf depth of the benchmark, on the same rays and launch options.  Both arms run the ray-persistent
+    kernel: the pair engine has no screen-space mode, so its flag is cleared for both."""
     import torch
     from paper_1811_03510_gb300 import ccs
     spread = 2.0 * np.tan(np.radians(30.0)) / args.height   # 60 degree vertical field of view
     base = ccs.opts_dict(opts_p)
-    out = {"pixel_spread": spread}
+    base["pairs"] = False
+    out = {"pixel_spread": spread, "engine": "ray-persistent (both arms)"}
     hits = ccs.alloc_hits(n_prim, dev)
     for name, sp in (("fixed_depth", 0.0), ("screen_space", spread)):
         opts = ccs.make_opts(**base, pixel_spread=sp)

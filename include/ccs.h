@@ -128,18 +128,26 @@ typedef struct {
                                        pair engine. */
 #define CCS_TRACE_PAIRS 8u          /* pair engine, for the plain closest hit and the any-hit query with one
                                        lane per ray (other modes ignore it): (1) one thread per ray walks
-                                       the BVH and keeps the ray's 16 nearest candidate patches (by entry
-                                       distance of the patch box); (2) persistent warps run Algorithm 3 on
-                                       one (ray, patch) pair per lane, taking each ray's Bezier candidates
-                                       in entry order until one enters beyond its best hit, so that every
-                                       warp iteration is one subdivision step of up to 32 pairs; (3) the
-                                       same over the Gregory candidates, from the Bezier answer; (4) rays
+                                       the BVH and keeps the ray's 8 nearest candidate patches (by entry
+                                       distance of the patch box); with local frames a Bezier patch whose
+                                       root box in its own frame the ray does not come near is no
+                                       candidate; (2) the rays with candidates are ordered by a cost
+                                       class (a Gregory candidate first, then more candidates first);
+                                       (3) persistent warps run Algorithm 3 on one (ray, patch) pair per
+                                       lane, taking each ray's candidates in entry order until one enters
+                                       beyond its best hit, so that every warp iteration is one
+                                       subdivision step of up to 32 pairs; once the queue is empty, idle
+                                       lanes take pending subtrees of busy lanes of their warp; (4) rays
                                        whose dropped candidates could still hold the answer are traced
                                        again by the ray-persistent kernel.  Hits are bit-identical.  Uses
                                        about 100 bytes of scratch per ray from a stream-ordered memory
                                        pool of the library (kept for reuse), on the launch's stream; the
                                        work order, bvh_burst, vote, chunk and min_blocks do not apply, and
-                                       blocks_per_sm is what fits. */
+                                       blocks_per_sm is what fits.  Counters: slots 8..17 hold candidates
+                                       listed, rays that dropped some, fallback rays, subtrees handed
+                                       over, warp iterations of the subdivision pass and, per iteration,
+                                       lanes splitting, helping, waiting and idle, then candidates culled
+                                       by their root box. */
 #define CCS_NUM_COUNTERS 23         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
                                        splits, leaves, backtracks, re-descent levels, pruned siblings, pairs;
                                        schedule of the warps, summed over warp iterations (8..19): warp

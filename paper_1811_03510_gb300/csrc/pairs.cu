@@ -111,14 +111,31 @@ cudaError_t place_tasks(const PairBufs &pb, uint32_t n, int num_sms, cudaStream_
     return cudaGetLastError();
 }
 
-// The fallback's options: the ray-persistent kernel over the list the passes filled.
+// The fallback's options: the ray-persistent kernel over the list the passes filled.  A counting launch
+// counts into the scratch's own words: its schedule counts would mix with the pair engine's.
 LaunchCfg fallback_cfg(const LaunchCfg &cfg, const PairBufs &pb)
 {
     LaunchCfg fc = cfg;
     fc.flags &= ~(CCS_TRACE_PAIRS | CCS_TRACE_ORDER);
     fc.count_dev = pb.ctr + kCtrFallback;
     if (fc.cache_slots == 1) fc.cache_slots = 2;
+    if (fc.counters) fc.counters = reinterpret_cast<unsigned long long *>(pb.ctr + kCtrFallbackCounts);
     return fc;
+}
+
+static __global__ void k_add_work_counts(const unsigned long long *__restrict__ from, unsigned long long *to)
+{
+    constexpr unsigned kWork = 8;   // counters 0..7: the work of the method
+    if (threadIdx.x < kWork && from[threadIdx.x]) atomicAdd(to + threadIdx.x, from[threadIdx.x]);
+}
+
+// The fallback launch's work counts (slots 0..7) into the caller's counters.
+cudaError_t add_fallback_counts(const LaunchCfg &cfg, const PairBufs &pb, cudaStream_t s)
+{
+    if (!cfg.counters) return cudaSuccess;
+    k_add_work_counts<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned long long *>(pb.ctr + kCtrFallbackCounts),
+                                       cfg.counters);
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -156,6 +173,7 @@ cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevH
     }
     if (e == cudaSuccess)
         e = launch_intersect(sc, r, h, n, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF, status, num_sms, s, pb.fallback);
+    if (e == cudaSuccess) e = add_fallback_counts(cfg, pb, s);
     const cudaError_t e2 = pool_free(base, s);
     return e != cudaSuccess ? e : e2;
 }
@@ -172,8 +190,10 @@ cudaError_t launch_pairs_batch(const BatchEntry *entries, const uint32_t *ray_pr
     if ((e = cand_pass<kModePlain>(src, pb, cfg, n_total, width, status, s)) != cudaSuccess) return e;
     if ((e = place_tasks(pb, n_total, num_sms, s)) != cudaSuccess) return e;
     if ((e = pair_passes_batch(src, pb, cfg, n_total, status, num_sms, s)) != cudaSuccess) return e;
-    return launch_intersect_batch(entries, ray_prefix, n_scenes, n_total, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF,
-                                  status, num_sms, s, width, pb.fallback);
+    if ((e = launch_intersect_batch(entries, ray_prefix, n_scenes, n_total, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF,
+                                    status, num_sms, s, width, pb.fallback)) != cudaSuccess)
+        return e;
+    return add_fallback_counts(cfg, pb, s);
 }
 
 }  // namespace ccs

@@ -3,8 +3,9 @@
 //  1. k_cand: one thread per ray walks the BVH (Sec. 4) and keeps the ray's kPairCands nearest candidate
 //     patches, ordered by (entry distance of the patch box, patch id).  Before the list is full nothing
 //     is pruned but [tmin, tmax]; once it is full, subtrees that enter beyond its last entry are skipped
-//     and the smallest entry distance dropped that way is kept (t_evict).  A ray with candidates becomes a
-//     task with a cost class (the highest when a candidate is a Gregory patch, else its number of
+//     and the smallest entry distance dropped that way is kept (t_evict).  With local frames a Bezier patch
+//     whose root box in its own frame the ray does not come near is no candidate (root_box_near: its pair
+//     would end at the first split).  A ray with candidates becomes a task with a cost class (the highest when a candidate is a Gregory patch, else its number of
 //     candidates); rays with no candidate are written as misses here.
 //  2. k_task_place: a counting sort of the tasks by cost class, costliest first, so that the long rays
 //     start early and the launch does not end on a few of them.
@@ -25,13 +26,14 @@
 
 namespace ccs {
 
-constexpr int kPairCands = 16;           // candidates kept per ray (nearest entries)
+constexpr int kPairCands = 8;            // candidates kept per ray (nearest entries)
 constexpr uint32_t kCandPerRay = 8;      // candidate buffer per ray of the launch, on average
 constexpr int kCostClasses = 16;
 // counter words of a launch: tasks, candidates written, fallback rays, queue heads (tasks, fallback), the
-// tasks of each cost class and the places handed out in each
+// tasks of each cost class and the places handed out in each; from word 64, the counters of a counting
+// fallback launch (CCS_NUM_COUNTERS 64-bit words), of which the work counts are then added to the caller's
 constexpr int kCtrTasks = 0, kCtrCand = 1, kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16,
-              kCtrFill = 32, kPairCtrWords = 64;
+              kCtrFill = 32, kCtrFallbackCounts = 64, kPairCtrWords = 64 + 2 * 32;
 // A task is 4 uint4 (64 bytes), everything a lane needs to start the ray:
 //   (ray, first candidate, z, t_evict bits), (first candidate's patch id, its entry distance, tmin, tmax),
 //   (ox, oy, oz, dx), (dy, dz, 0, 0) as float bits;
@@ -136,6 +138,37 @@ CCS_DEV void write_miss(const Src &src, uint32_t scene, uint32_t j, uint8_t *occ
     }
 }
 
+// Cull test of a candidate with local frames (Sec. 3.4): does the ray pass near the patch's root box in
+// the patch frame?  Every box of a Bezier pair's subdivision lies in that box (de Casteljau midpoints stay
+// between their operands), widened by the box extension by at most tau / 2; a pair's FP32 slab tests
+// report a hit only within about 1e-6 (|o - anchor| + box diagonal) of a box.  The test pads the box by
+// 2^-16 (1 + |o - anchor|_1 + |hi - lo|_1), far more than both and far less than a patch, so a culled
+// pair holds no leaf that its subdivision would record.  Gregory patches are kept (their boxes come from
+// the bounds of Algorithm 2, not from the control points).
+CCS_DEV bool root_box_near(const float4 *__restrict__ rec, const float (&o)[3], const float (&d)[3], float tmin,
+                           const Grp &G)
+{
+    const float4 an = __ldg(rec + 15);
+    if (an.w != 0.0f) return true;
+    const float4 R[3] = {__ldg(rec + 16), __ldg(rec + 17), __ldg(rec + 18)};
+    const float4 hb = __ldg(rec + 19);
+    const float o3[3] = {__fsub_rn(o[0], an.x), __fsub_rn(o[1], an.y), __fsub_rn(o[2], an.z)};
+    const float pad = __fmul_rn(__int_as_float((127 - 16) << 23),
+                                __fadd_rn(hb.w, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
+    RayG<3> r;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        r.org[k] = fmaf(R[k].x, o3[0], fmaf(R[k].y, o3[1], R[k].z * o3[2]));
+        r.inv[k] = safe_inv(fmaf(R[k].x, d[0], fmaf(R[k].y, d[1], R[k].z * d[2])));
+        lo[k] = __fsub_rn(R[k].w, pad);
+        hi[k] = __fadd_rn(pick(k, hb.x, hb.y, hb.z), pad);
+    }
+    float t0, t1;
+    slab<3>(r, lo, hi, tmin, __int_as_float(0x7f800000), G, t0, t1);
+    return t0 <= t1;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Pass 1: BVH walk with the sorted candidate list.
 // ------------------------------------------------------------------------------------------------
@@ -161,7 +194,7 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
     bool evicted = false, live = false, capped = false;
     uint32_t ray_scene = 0, ray_local = 0;
     typename Src::LaneScene lsc;
-    unsigned long long nodes = 0;
+    unsigned long long nodes = 0, culled = 0;
     Grp G;
     G.c = 0;
     G.mask = FULL;
@@ -190,8 +223,10 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
                 --it;
                 if (node < 0) {   // a patch: into the list (the leaf's box is the patch box)
                     const uint32_t p = (uint32_t)(~node);
-                    bool ins = true;
-                    if (cnt == C) {
+                    bool ins = !sc.local || root_box_near(rec_of(sc, p), ro, rd, tmin, G);
+                    if (!ins) {
+                        if (STATS) ++culled;
+                    } else if (cnt == C) {
                         evicted = true;
                         if (!cand_less(n0, p, kt[C - 1], kp[C - 1])) {
                             t_evict = fminf(t_evict, n0);
@@ -375,15 +410,17 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
         if (capped) atomicOr(status, 1u);
         write_miss<MODE>(src, ray_scene, ray_local, occluded);
     }
-    if (STATS) {   // BVH nodes; diagnostics in the schedule slots: candidates listed, rays that dropped some
-        unsigned long long v[3] = {nodes, want, (unsigned long long)(has && evicted)};
+    if (STATS) {   // BVH nodes; diagnostics in the schedule slots: candidates listed, rays that dropped some,
+                   // candidates culled by their root box
+        unsigned long long v[4] = {nodes, want, (unsigned long long)(has && evicted), culled};
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
             for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(FULL, v[k], o);
         if (lane == 0) {
             if (v[0]) atomicAdd(counters + 0, v[0]);
             if (v[1]) atomicAdd(counters + 8, v[1]);
             if (v[2]) atomicAdd(counters + 9, v[2]);
+            if (v[3]) atomicAdd(counters + 17, v[3]);
         }
     }
 }

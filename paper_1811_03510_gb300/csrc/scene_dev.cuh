@@ -76,7 +76,26 @@ __device__ __forceinline__ void repack_one(const float *__restrict__ x, const fl
                           : make_float4(c == 0 ? 1.0f : 0.0f, c == 1 ? 1.0f : 0.0f, c == 2 ? 1.0f : 0.0f, 0.0f);
     }
     r[15] = make_float4(an[0], an[1], an[2], greg ? 1.0f : 0.0f);
-    r[19] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    // the root box of a Bezier patch in its own frame: the AABB of the 16 stored grid components, which
+    // holds every box of its subdivision (de Casteljau midpoints stay between their operands); lo in
+    // the w of the frame rows, hi and 1 + |hi - lo|_1 in slot 19 (Gregory patches: unused, zero)
+    float blo[3] = {0.0f, 0.0f, 0.0f}, bhi[3] = {0.0f, 0.0f, 0.0f};
+    if (!greg) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float a = r[c * 4].x, b = a;
+            for (int q = 0; q < 4; ++q) {
+                const float4 v = r[c * 4 + q];
+                a = fminf(fminf(a, v.x), fminf(fminf(v.y, v.z), v.w));
+                b = fmaxf(fmaxf(b, v.x), fmaxf(fmaxf(v.y, v.z), v.w));
+            }
+            blo[c] = a;
+            bhi[c] = b;
+            r[16 + c].w = a;
+        }
+    }
+    r[19] = make_float4(bhi[0], bhi[1], bhi[2],
+                        greg ? 0.0f : 1.0f + ((bhi[0] - blo[0]) + (bhi[1] - blo[1])) + (bhi[2] - blo[2]));
     leaf_box[2 * (size_t)p] = make_float4(lo[0], lo[1], lo[2], 0.0f);
     leaf_box[2 * (size_t)p + 1] = make_float4(hi[0], hi[1], hi[2], 0.0f);
 }

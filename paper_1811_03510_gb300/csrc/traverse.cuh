@@ -523,30 +523,73 @@ CCS_DEV float pair_tau(const float (&o3)[3])
                      __fadd_rn(1.0f, __fadd_rn(__fadd_rn(fabsf(o3[0]), fabsf(o3[1])), fabsf(o3[2]))));
 }
 
+// Error-free transformations in FP32: a + b = s + err exactly (Knuth's TwoSum, six operations) and
+// a b = p + err exactly (TwoProduct with one FMA), s and p the rounded results.
+struct F2 {
+    float h, l;
+};
+CCS_DEV F2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+CCS_DEV F2 two_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+
+// One coordinate of the anchored origin (o - a) + t d as an unevaluated sum h + l: both differences and
+// the product are split exactly, the large parts (which cancel near the patch) are added exactly, and the
+// small parts once rounded.
+CCS_DEV F2 anchored_coord(float o, float a, float t, float d)
+{
+    const F2 s = two_sum(o, -a);
+    const F2 p = two_prod(t, d);
+    const F2 h = two_sum(s.h, p.h);
+    return {h.h, __fadd_rn(h.l, __fadd_rn(s.l, p.l))};
+}
+
+// R . e for e = h + l: the compensated dot product (Ogita, Rump and Oishi 2005, Dot2), as accurate as the
+// same sum in twice the working precision and then rounded once.
+CCS_DEV float rotate_coord(const float4 &R, const F2 (&e)[3])
+{
+    const F2 p0 = two_prod(R.x, e[0].h), p1 = two_prod(R.y, e[1].h), p2 = two_prod(R.z, e[2].h);
+    const F2 s1 = two_sum(p0.h, p1.h);
+    const F2 s2 = two_sum(s1.h, p2.h);
+    float c = __fadd_rn(__fadd_rn(p0.l, p1.l), __fadd_rn(s1.l, __fadd_rn(s2.l, p2.l)));
+    c = __fmaf_rn(R.x, e[0].l, __fmaf_rn(R.y, e[1].l, __fmaf_rn(R.z, e[2].l, c)));
+    return __fadd_rn(s2.h, c);
+}
+
 // The ray of a pair.  Sec. 3.4 anchors the patches (points relative to their box centre) to keep the
 // magnitudes of the subdivision small; the ray is anchored the same way, at its entry into the patch box:
-// its origin e = (o - anchor) + te d, with te the entry distance of the pair's root interval, is formed in
-// FP64 from the FP32 inputs, rotated into the patch frame (local frames) and rounded once.  Distances inside
-// the pair are measured from e, so the slab tests subtract numbers of the size of the patch instead of the
-// distance to the camera; a leaf's key distance is te + its entry.  The direction is R d in FP32 (the world
-// direction without local frames), and pr.inv its inverse.  NC = 1: the group exchanges its components.
+// its origin e = (o - anchor) + te d, with te the entry distance of the pair's root interval, is formed
+// from the FP32 inputs without losing the cancellation to rounding (error-free transformations: about
+// twice FP32's precision, as FP64 would give, but on the FP32 pipes), rotated into the patch frame (local
+// frames) by a compensated dot product and rounded once.  Distances inside the pair are measured from e,
+// so the slab tests subtract numbers of the size of the patch instead of the distance to the camera; a
+// leaf's key distance is te + its entry.  The direction is R d in FP32 (the world direction without local
+// frames), and pr.inv its inverse.  NC = 1: the group exchanges its components.
 template <int NC>
 CCS_DEV void anchored_ray(const float4 *__restrict__ rec, const float4 &an, bool local, const float (&o)[NC],
                           const float (&dw)[NC], const float (&winv)[NC], float te, const Grp &G, RayG<NC> &pr)
 {
-    double e[3];
+    F2 e[3];
     float dd[3];
     if constexpr (NC == 3) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            e[c] = __fma_rn((double)te, (double)dw[c], (double)o[c] - (double)pick(c, an.x, an.y, an.z));
+            e[c] = anchored_coord(o[c], pick(c, an.x, an.y, an.z), te, dw[c]);
             dd[c] = dw[c];
         }
     } else {
-        const double ec = __fma_rn((double)te, (double)dw[0], (double)o[0] - (double)pick(G.c, an.x, an.y, an.z));
+        const F2 ec = anchored_coord(o[0], pick(G.c, an.x, an.y, an.z), te, dw[0]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            e[c] = __shfl_sync(G.mask, ec, G.l0 + c);
+            e[c].h = __shfl_sync(G.mask, ec.h, G.l0 + c);
+            e[c].l = __shfl_sync(G.mask, ec.l, G.l0 + c);
             dd[c] = __shfl_sync(G.mask, dw[0], G.l0 + c);
         }
     }
@@ -554,12 +597,11 @@ CCS_DEV void anchored_ray(const float4 *__restrict__ rec, const float4 &an, bool
     for (int k = 0; k < NC; ++k) {
         const int c = comp<NC>(G, k);
         if (!local) {
-            pr.org[k] = __double2float_rn(e[c]);
+            pr.org[k] = __fadd_rn(e[c].h, e[c].l);
             pr.inv[k] = winv[k];
         } else {
             const float4 Rk = __ldg(rec + 16 + c);
-            pr.org[k] = __double2float_rn(
-                __fma_rn((double)Rk.x, e[0], __fma_rn((double)Rk.y, e[1], (double)Rk.z * e[2])));
+            pr.org[k] = rotate_coord(Rk, e);
             pr.inv[k] = safe_inv(fmaf(Rk.x, dd[0], fmaf(Rk.y, dd[1], Rk.z * dd[2])));
         }
     }

@@ -1,9 +1,9 @@
-"""The pair engine (CCS_TRACE_PAIRS): a BVH pass that keeps each ray's 16 nearest candidate patches, then
-subdivision passes that run Algorithm 3 on one (ray, patch) pair per lane (Bezier, then Gregory), then the
-ray-persistent kernel over the rays whose dropped candidates could still hold the answer.  The answer is
-the smallest leaf key over all nested intervals (readings A14/A15), so every hit must be bit-identical to
-the ray-persistent kernel's, which the FP64 oracle pins; scenes with more than 16 candidate boxes along a
-ray drive the fallback."""
+"""The pair engine (CCS_TRACE_PAIRS): a BVH pass that keeps each ray's 8 nearest candidate patches (with
+local frames, only those whose root box in the patch frame the ray comes near), then a subdivision pass
+that runs Algorithm 3 on one (ray, patch) pair per lane, then the ray-persistent kernel over the rays whose
+dropped candidates could still hold the answer.  The answer is the smallest leaf key over all nested
+intervals (readings A14/A15), so every hit must be bit-identical to the ray-persistent kernel's, which the
+FP64 oracle pins; scenes with more than 8 candidate boxes along a ray drive the fallback."""
 import numpy as np
 import pytest
 
@@ -245,3 +245,43 @@ def test_pairs_subtrees_handed_to_idle_lanes(local):
     assert int(cnt[11]) > 100
     compare(got, oracle.intersect(s.P, s.types, r.soa(), L=8, flags=True, local=local), 8, max_flagged_frac=0.05)
     sc.close()
+
+
+@pytest.mark.parametrize("width", [2, 4])
+def test_pairs_root_box_cull_keeps_every_hit(width):
+    """With local frames the candidate pass drops Bezier patches whose root box (in the patch frame) the
+    ray does not come near (counter 17).  Rays that graze the surface, just above it and nearly tangent,
+    are the ones a too-tight test would lose: their hits stay bit-identical to the ray-persistent kernel's,
+    which never culls.  Without local frames nothing is culled."""
+    s = sg.config_scene(2)
+    cam = sg.pinhole_rays(160, 90)
+    sc = ccs.Scene(s.P, s.types, local=True, bvh_width=width)
+    h = run(sc, cam)
+    hit = h["pid"] != MISS
+    p = cam.o[hit].astype(np.float64) + cam.d[hit].astype(np.float64) * h["t"][hit][:, None]
+    rng = np.random.default_rng(17)
+    nrm = p / np.linalg.norm(p, axis=1, keepdims=True)
+    tan = np.cross(nrm, rng.normal(size=p.shape))
+    tan /= np.linalg.norm(tan, axis=1, keepdims=True)
+    oo, dd = [], []
+    for lift in (1e-5, 1e-4, 1e-3, 1e-2):
+        tilt = rng.uniform(-2.0, 2.0, (len(p), 1)) * lift
+        dv = tan - tilt * nrm
+        dv /= np.linalg.norm(dv, axis=1, keepdims=True)
+        oo.append(p * (1.0 + lift) - 2.0 * dv)
+        dd.append(dv)
+    oo, dd = np.concatenate(oo).astype(np.float32), np.concatenate(dd).astype(np.float32)
+    n = len(oo)
+    r = sg.Rays(oo, dd, np.zeros(n, np.float32), np.full(n, np.inf, np.float32))
+    ref = run(sc, r)
+    assert 0.2 * n < (ref["pid"] != MISS).sum() < n
+    cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
+    same(run(sc, r, counters=cnt, pairs=True), ref, "grazing")
+    assert int(cnt[17]) > n // 4
+    same(run(sc, cam, pairs=True), h, "primary")
+    sc.close()
+    sw = ccs.Scene(s.P, s.types, local=False, bvh_width=width)
+    cnt.zero_()
+    same(run(sw, r, counters=cnt, pairs=True), run(sw, r), "world axes")
+    assert int(cnt[17]) == 0
+    sw.close()

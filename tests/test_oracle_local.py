@@ -144,10 +144,45 @@ def _f32_fma(a, b, c):
     return np.float32(np.float64(a) * np.float64(b) + np.float64(c))
 
 
+def _two_sum(a, b):
+    """Knuth's TwoSum in FP32: a + b = s + err exactly."""
+    a, b = np.float32(a), np.float32(b)
+    s = np.float32(a + b)
+    bb = np.float32(s - a)
+    return s, np.float32(np.float32(a - np.float32(s - bb)) + np.float32(b - bb))
+
+
+def _two_prod(a, b):
+    """TwoProduct in FP32: a b = p + err exactly (the error of a product of two floats is a float)."""
+    a, b = np.float32(a), np.float32(b)
+    p = np.float32(a * b)
+    return p, np.float32(np.float64(a) * np.float64(b) - np.float64(p))
+
+
+def _anchored_coord(o, a, t, d):
+    """(o - a) + t d as an unevaluated FP32 sum h + l, as the kernels form it."""
+    sh, sl = _two_sum(o, -np.float32(a))
+    ph, pl = _two_prod(t, d)
+    hh, hl = _two_sum(sh, ph)
+    return hh, np.float32(hl + np.float32(sl + pl))
+
+
+def _rotate_coord(Rk, e):
+    """Compensated dot product (Ogita, Rump and Oishi 2005, Dot2) of a frame row with e = h + l, one
+    final rounding, as the kernels form it."""
+    p = [_two_prod(Rk[j], e[j][0]) for j in range(3)]
+    s1 = _two_sum(p[0][0], p[1][0])
+    s2 = _two_sum(s1[0], p[2][0])
+    c = np.float32(np.float32(p[0][1] + p[1][1]) + np.float32(s1[1] + np.float32(s2[1] + p[2][1])))
+    c = _f32_fma(Rk[0], e[0][1], _f32_fma(Rk[1], e[1][1], _f32_fma(Rk[2], e[2][1], c)))
+    return np.float32(s2[0] + c)
+
+
 def test_anchored_ray_error_is_within_the_flag_model():
     """The FP32 path intersects a pair with the ray anchored at its entry into the patch box: origin
-    e = (o - anchor) + te d formed in FP64, rotated into the patch frame and rounded once, direction R d in
-    FP32.  Over the patch box that ray stays within 3e-7 (|e| + box diagonal) of the exact ray in the same
+    e = (o - anchor) + te d formed by error-free FP32 transformations (TwoSum, TwoProduct), rotated into the
+    patch frame by a compensated dot product (Dot2) and rounded once, direction R d in FP32; emulated here
+    operation by operation.  Over the patch box that ray stays within 3e-7 (|e| + box diagonal) of the exact ray in the same
     frame, whatever the distance from the ray's own origin (here 3 and 300 scene units): the term the
     oracle's parity flags add to eps.  The FP32 transform without the anchor misses that bound by far."""
     s = sg.config_scene(2)
@@ -167,7 +202,8 @@ def test_anchored_ray_error_is_within_the_flag_model():
             d = (-u).astype(np.float32)
             te = np.float32(dist - np.linalg.norm(hi - lo))
             e = np.float64(te) * d.astype(np.float64) + (o.astype(np.float64) - an.astype(np.float64))
-            org = np.array([np.float32(R[i].astype(np.float64) @ e) for i in range(3)], np.float32)
+            ef = [_anchored_coord(o[c], an[c], te, d[c]) for c in range(3)]
+            org = np.array([_rotate_coord(R[i], ef) for i in range(3)], np.float32)
             dl = np.array([_f32_fma(R[i, 0], d[0], _f32_fma(R[i, 1], d[1], np.float32(R[i, 2] * d[2])))
                            for i in range(3)], np.float32)
             # the exact ray in the same (rounded) frame, and the unanchored FP32 transform for comparison
