@@ -140,7 +140,7 @@ typedef struct {
                                        lanes take pending subtrees of busy lanes of their warp; (4) rays
                                        whose dropped candidates could still hold the answer are traced
                                        again by the ray-persistent kernel.  Hits are bit-identical.  Uses
-                                       about 100 bytes of scratch per ray from a stream-ordered memory
+                                       about 200 bytes of scratch per ray from a stream-ordered memory
                                        pool of the library (kept for reuse), on the launch's stream; the
                                        work order, bvh_burst, vote, chunk and min_blocks do not apply, and
                                        blocks_per_sm is what fits.  Counters: slots 8..17 hold candidates
@@ -305,7 +305,7 @@ ccs_status ccs_batch_set_points(ccs_batch *b, uint32_t scene_index, const float 
 
 /* Enqueue the selected stages (CCS_BATCH_* bits) on `stream`: the table copy, one repack launch,
  * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's five
- * launches over the rays of all scenes, whose scratch of about 100 bytes per ray the batch allocates
+ * launches over the rays of all scenes, whose scratch of about 200 bytes per ray the batch allocates
  * with cudaMalloc on its first such run and keeps).  Otherwise allocates nothing; does not synchronise.
  * Answers are bit-identical to ccs_intersect on each scene alone. */
 ccs_status ccs_batch_run(ccs_batch *b, uint32_t stages, const ccs_trace_opts *opts, void *stream);

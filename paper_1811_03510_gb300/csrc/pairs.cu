@@ -1,46 +1,13 @@
-// The pair engine's launch sequence (CCS_TRACE_PAIRS): counters zeroed, the candidate pass, the order of
-// the tasks, the subdivision pass, then the ray-persistent kernel over the fallback list.  One scene takes
-// its scratch from the library's stream-ordered memory pool on the launch's stream; a batch brings its
-// own, allocated with the batch, so that its run stays capturable in a CUDA graph.
+// The pair engine's launch sequence (CCS_TRACE_PAIRS): counters zeroed, the candidate pass (which also
+// lists each task under its cost class), the subdivision pass, then the ray-persistent kernel over the
+// fallback list.  One scene takes its scratch from the library's stream-ordered memory pool on the
+// launch's stream; a batch brings its own, allocated with the batch, so that its run stays capturable in
+// a CUDA graph.
 #include <mutex>
 
 #include "pairs_launch.cuh"
 
 namespace ccs {
-
-// ------------------------------------------------------------------------------------------------
-// Pass 2: the tasks in queue order, costliest class first (a counting sort; within a class, warps of
-// neighbouring tasks stay together).
-// ------------------------------------------------------------------------------------------------
-static __global__ void __launch_bounds__(256) k_task_place(PairBufs pb)
-{
-    __shared__ uint32_t start[kCostClasses];
-    if (threadIdx.x < kCostClasses) {
-        uint32_t s = 0;
-        for (int k = kCostClasses - 1; k > (int)threadIdx.x; --k) s += pb.ctr[kCtrHist + k];
-        start[threadIdx.x] = s;
-    }
-    __syncthreads();
-    const uint32_t n_tasks = pb.ctr[kCtrTasks];
-    const int lane = threadIdx.x & 31;
-    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tasks; t += gridDim.x * blockDim.x) {
-        const uint4 *tp = pb.task + 4 * (size_t)t;
-        const uint4 w0 = tp[0], w1 = tp[1], w2 = tp[2], w3 = tp[3];
-        const int key = (int)((w0.z >> 8) & 15u);
-        const unsigned act = __activemask();
-        const unsigned same = __match_any_sync(act, key);
-        const int leader = __ffs(same) - 1;
-        uint32_t b = 0;
-        if (lane == leader) b = atomicAdd(pb.ctr + kCtrFill + key, (uint32_t)__popc(same));
-        b = __shfl_sync(same, b, leader);
-        uint4 *dst = pb.sorted + 4 * (size_t)(start[key] + b + __popc(same & ((1u << lane) - 1u)));
-        dst[0] = w0;
-        dst[1] = w1;
-        dst[2] = w2;
-        dst[3] = w3;
-    }
-}
-
 
 bool use_pairs(const LaunchCfg &cfg)
 {
@@ -102,15 +69,6 @@ cudaError_t cand_pass(const Src &src, const PairBufs &pb, const LaunchCfg &cfg, 
                  : launch_cand<false, MODE, Src, 2>(src, pb, cfg, n, status, s);
 }
 
-// The queue order of the tasks (one thread per task; the count is on the device, the grid covers n).
-cudaError_t place_tasks(const PairBufs &pb, uint32_t n, int num_sms, cudaStream_t s)
-{
-    uint32_t blocks = (n + 255) / 256;
-    if (blocks > (uint32_t)num_sms * 8) blocks = (uint32_t)num_sms * 8;
-    k_task_place<<<blocks, 256, 0, s>>>(pb);
-    return cudaGetLastError();
-}
-
 // The fallback's options: the ray-persistent kernel over the list the passes filled.  A counting launch
 // counts into the scratch's own words: its schedule counts would mix with the pair engine's.
 LaunchCfg fallback_cfg(const LaunchCfg &cfg, const PairBufs &pb)
@@ -163,11 +121,9 @@ cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevH
     if (e == cudaSuccess) {
         if (cfg.mode == kModeAnyHit) {
             e = cand_pass<kModeAnyHit>(src, pb, cfg, n, sc.width, status, s);
-            if (e == cudaSuccess) e = place_tasks(pb, n, num_sms, s);
             if (e == cudaSuccess) e = pair_passes_single_anyhit(src, pb, cfg, n, status, num_sms, s);
         } else {
             e = cand_pass<kModePlain>(src, pb, cfg, n, sc.width, status, s);
-            if (e == cudaSuccess) e = place_tasks(pb, n, num_sms, s);
             if (e == cudaSuccess) e = pair_passes_single_plain(src, pb, cfg, n, status, num_sms, s);
         }
     }
@@ -188,7 +144,6 @@ cudaError_t launch_pairs_batch(const BatchEntry *entries, const uint32_t *ray_pr
     cudaError_t e = cudaMemsetAsync(pb.ctr, 0, kPairCtrWords * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = cand_pass<kModePlain>(src, pb, cfg, n_total, width, status, s)) != cudaSuccess) return e;
-    if ((e = place_tasks(pb, n_total, num_sms, s)) != cudaSuccess) return e;
     if ((e = pair_passes_batch(src, pb, cfg, n_total, status, num_sms, s)) != cudaSuccess) return e;
     if ((e = launch_intersect_batch(entries, ray_prefix, n_scenes, n_total, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF,
                                     status, num_sms, s, width, pb.fallback)) != cudaSuccess)

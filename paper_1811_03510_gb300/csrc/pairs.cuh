@@ -7,8 +7,9 @@
 //     whose root box in its own frame the ray does not come near is no candidate (root_box_near: its pair
 //     would end at the first split).  A ray with candidates becomes a task with a cost class (the highest when a candidate is a Gregory patch, else its number of
 //     candidates); rays with no candidate are written as misses here.
-//  2. k_task_place: a counting sort of the tasks by cost class, costliest first, so that the long rays
-//     start early and the launch does not end on a few of them.
+//  2. Each task's index goes to the list of its cost class (the candidate pass counts the classes' places),
+//     and the subdivision pass's queue takes the classes costliest first, so that the long rays start
+//     early and the launch does not end on a few of them.
 //  3. k_pairs: persistent warps take tasks in that order.  A lane runs Algorithm 3 on one (ray, patch) pair
 //     at a time, taking the ray's candidates in entry order and stopping at the first one that enters
 //     beyond the ray's best hit.  Every warp iteration is one subdivision step (Algorithm 3's loop body)
@@ -30,10 +31,10 @@ constexpr int kPairCands = 8;            // candidates kept per ray (nearest ent
 constexpr uint32_t kCandPerRay = 8;      // candidate buffer per ray of the launch, on average
 constexpr int kCostClasses = 16;
 // counter words of a launch: tasks, candidates written, fallback rays, queue heads (tasks, fallback), the
-// tasks of each cost class and the places handed out in each; from word 64, the counters of a counting
-// fallback launch (CCS_NUM_COUNTERS 64-bit words), of which the work counts are then added to the caller's
+// tasks of each cost class; from word 64, the counters of a counting fallback launch (CCS_NUM_COUNTERS
+// 64-bit words), of which the work counts are then added to the caller's
 constexpr int kCtrTasks = 0, kCtrCand = 1, kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16,
-              kCtrFill = 32, kCtrFallbackCounts = 64, kPairCtrWords = 64 + 2 * 32;
+              kCtrFallbackCounts = 64, kPairCtrWords = 64 + 2 * 32;
 // A task is 4 uint4 (64 bytes), everything a lane needs to start the ray:
 //   (ray, first candidate, z, t_evict bits), (first candidate's patch id, its entry distance, tmin, tmax),
 //   (ox, oy, oz, dx), (dy, dz, 0, 0) as float bits;
@@ -43,18 +44,19 @@ constexpr uint32_t kTaskEvicted = 0x40000000u;
 struct PairBufs {
     uint32_t *ctr;            // kPairCtrWords words, zeroed before the candidate pass
     uint4 *task;              // tasks in the order the candidate pass made them, up to one per ray
-    uint4 *sorted;            // the same, in the order the queue hands them out
+    uint32_t *cls;            // per cost class c, from c * n: the indices of its tasks in task
     uint2 *cand;              // (patch id, entry distance bits)
     uint32_t *fallback;       // rays traced again by k_intersect, up to n
     uint32_t cap_cand;        // entries of cand
+    uint32_t n;               // rays of the launch (the stride of cls)
 };
 
 // Bytes of the pair engine's scratch for n rays, and its layout (every part 256-byte aligned).
 __host__ __device__ inline size_t pair_align(size_t b) { return (b + 255) & ~(size_t)255; }
 inline size_t pair_scratch_bytes(uint32_t n)
 {
-    return pair_align(kPairCtrWords * 4) + 2 * pair_align((size_t)n * 64) + pair_align((size_t)n * kCandPerRay * 8) +
-           pair_align((size_t)n * 4);
+    return pair_align(kPairCtrWords * 4) + pair_align((size_t)n * 64) + pair_align((size_t)n * 4 * kCostClasses) +
+           pair_align((size_t)n * kCandPerRay * 8) + pair_align((size_t)n * 4);
 }
 inline PairBufs pair_bufs_at(void *base, uint32_t n)
 {
@@ -64,13 +66,14 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
     p += pair_align(kPairCtrWords * 4);
     b.task = reinterpret_cast<uint4 *>(p);
     p += pair_align((size_t)n * 64);
-    b.sorted = reinterpret_cast<uint4 *>(p);
-    p += pair_align((size_t)n * 64);
+    b.cls = reinterpret_cast<uint32_t *>(p);
+    p += pair_align((size_t)n * 4 * kCostClasses);
     b.cand = reinterpret_cast<uint2 *>(p);
     p += pair_align((size_t)n * kCandPerRay * 8);
     b.fallback = reinterpret_cast<uint32_t *>(p);
     const uint64_t cap = (uint64_t)n * kCandPerRay;
     b.cap_cand = cap > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap;
+    b.n = n;
     return b;
 }
 
@@ -402,9 +405,14 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
         tk[2] = make_uint4(__float_as_uint(ro[0]), __float_as_uint(ro[1]), __float_as_uint(ro[2]), __float_as_uint(rd[0]));
         tk[3] = make_uint4(__float_as_uint(rd[1]), __float_as_uint(rd[2]), 0u, 0u);
     }
+    // the task's place in the list of its class
     const int hkey = ok ? key : -1;
     const unsigned same = __match_any_sync(FULL, hkey);
-    if (ok && lane == __ffs(same) - 1) atomicAdd(pb.ctr + kCtrHist + key, (uint32_t)__popc(same));
+    const int leader = __ffs(same) - 1;
+    uint32_t cb = 0;
+    if (ok && lane == leader) cb = atomicAdd(pb.ctr + kCtrHist + key, (uint32_t)__popc(same));
+    cb = __shfl_sync(FULL, cb, leader);
+    if (ok) pb.cls[(size_t)key * pb.n + cb + __popc(same & lt)] = bt + __popc(mt & lt);
     if (fb) pb.fallback[bf + __popc(mf & lt)] = i;
     if (live && !has) {
         if (capped) atomicOr(status, 1u);
@@ -450,7 +458,14 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     mbox[threadIdx.x] = ~0ull;
     hcount[threadIdx.x] = 0;
     hcap[threadIdx.x] = 0;
-    __syncwarp();
+    // the queue hands out the tasks class by class, costliest first: cstart[c] = first place of class c
+    __shared__ uint32_t cstart[kCostClasses];
+    if (threadIdx.x < kCostClasses) {
+        uint32_t a = 0;
+        for (int c = kCostClasses - 1; c > (int)threadIdx.x; --c) a += pb.ctr[kCtrHist + c];
+        cstart[threadIdx.x] = a;
+    }
+    __syncthreads();
     Counters cnt;
 #pragma unroll
     for (int k = 0; k < kNumSumCounters; ++k) cnt.v[k] = 0;
@@ -539,7 +554,9 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
             }
             const uint32_t k = qb + (uint32_t)__popc(idle & lt);
             if (!has_task && k < n_tasks) {
-                const uint4 *tp = pb.sorted + 4 * (size_t)k;
+                int c = kCostClasses - 1;
+                while (c > 0 && k >= cstart[c - 1]) --c;
+                const uint4 *tp = pb.task + 4 * (size_t)__ldg(pb.cls + (size_t)c * pb.n + (k - cstart[c]));
                 const uint4 w0 = tp[0], w1 = tp[1], w2 = tp[2], w3 = tp[3];
                 has_task = true;
                 ray = w0.x;
