@@ -152,9 +152,9 @@ def engine_of(o) -> str:
 
 
 def kernels_per_launch(o) -> int:
-    """Kernels of this library one ccs_intersect launches: the pair engine's candidate pass, task order,
-    subdivision pass and fallback; the work order's three kernels and k_intersect; or k_intersect alone."""
-    return {"pairs": 4, "ray+order": 4, "ray": 1}[engine_of(o)]
+    """Kernels of this library one ccs_intersect launches: the pair engine's candidate pass, subdivision pass
+    and fallback; the work order's three kernels and k_intersect; or k_intersect alone."""
+    return {"pairs": 3, "ray+order": 4, "ray": 1}[engine_of(o)]
 
 
 def schedule_summary(c: dict, lanes_per_ray: int, engine: str = "ray") -> dict:

@@ -304,7 +304,7 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
 ccs_status ccs_batch_set_points(ccs_batch *b, uint32_t scene_index, const float *x, const float *y, const float *z);
 
 /* Enqueue the selected stages (CCS_BATCH_* bits) on `stream`: the table copy, one repack launch,
- * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's five
+ * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's four
  * launches over the rays of all scenes, whose scratch of about 200 bytes per ray the batch allocates
  * with cudaMalloc on its first such run and keeps).  Otherwise allocates nothing; does not synchronise.
  * Answers are bit-identical to ccs_intersect on each scene alone. */
