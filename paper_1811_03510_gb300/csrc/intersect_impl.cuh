@@ -71,7 +71,7 @@ struct BatchSource {
 
 // Shared memory per thread, in floats: sibling intervals (2L float2), the sibling grid cache (K slots of
 // 16 * NC floats), the K cache tags, padded to 16 bytes; then the float4s of the BVH prefetch slot.
-__host__ __device__ constexpr int scratch_floats(int L, int K, int NC) { return (4 * L + 16 * NC * K + K + 3) / 4 * 4; }
+__host__ __device__ constexpr int scratch_floats(int L, int K, int NC) { return cache_floats(K, NC) + 4 * L; }
 __host__ __device__ constexpr int scratch_total_floats(int L, int K, int NC, int BW)
 {
     return scratch_floats(L, K, NC) + 4 * (BW == 2 ? NC + 1 : 2 * NC + 1);   // node_f4<BW, NC>()
@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(128, MINB) k_intersect(Src src, int L, uint32_
     }
     Scratch scr;
     scr.stride = stride;
-    scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
-    scr.cache = smem + 4 * L * stride + threadIdx.x;
-    scr.tag = reinterpret_cast<int *>(smem + (4 * L + 16 * NC * K) * stride) + threadIdx.x;
+    scr.cstride = cache_floats(K, NC);
+    scr.cache = smem + threadIdx.x * scr.cstride;
+    scr.tag = reinterpret_cast<int *>(scr.cache + 16 * NC * K);
+    scr.sib = reinterpret_cast<float2 *>(smem + cache_floats(K, NC) * stride) + threadIdx.x;
     scr.node = reinterpret_cast<float4 *>(smem + sf * stride) + threadIdx.x;
     Counters cnt;
 #pragma unroll

@@ -444,9 +444,10 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     const int stride = blockDim.x;
     Scratch scr;
     scr.stride = stride;
-    scr.sib = reinterpret_cast<float2 *>(smem) + threadIdx.x;
-    scr.cache = smem + 4 * L * stride + threadIdx.x;
-    scr.tag = reinterpret_cast<int *>(smem + (4 * L + 16 * 3 * K) * stride) + threadIdx.x;
+    scr.cstride = cache_floats(K, 3);
+    scr.cache = smem + threadIdx.x * scr.cstride;
+    scr.tag = reinterpret_cast<int *>(scr.cache + 48 * K);
+    scr.sib = reinterpret_cast<float2 *>(smem + cache_floats(K, 3) * stride) + threadIdx.x;
     scr.node = nullptr;
     float *rs = smem + scratch_floats(L, K, 3) * stride + threadIdx.x;   // [k * stride], k < kRaySlotFloats
     // mailboxes, helper counts and cap flags of the block's threads (indexed by thread)
@@ -718,7 +719,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                             trail |= bit;
                             scr.sib[level * stride] = so.goR ? make_float2(so.l0, so.l1) : make_float2(so.r0, so.r1);
                             if (K > 0 && !greg) {
-                                scr.tag[slot * stride] = level;
+                                scr.tag[slot] = level;
                                 ++ctop;
                                 cvalid = cvalid < K ? cvalid + 1 : K;
                             }
@@ -743,7 +744,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                             int cslot = 0;
                             if (K > 0 && !greg && cvalid > 0) {
                                 cslot = (ctop - 1) % (K > 0 ? K : 1);
-                                if (scr.tag[cslot * stride] == l) {
+                                if (scr.tag[cslot] == l) {
                                     cached = true;
                                     --ctop;
                                     --cvalid;
@@ -763,9 +764,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                                 gpend = true;
                             } else if (cached) {
                                 level = l + 1;
-                                const float *src_g = scr.cache + (size_t)(cslot * 48) * stride;
-#pragma unroll
-                                for (int k = 0; k < 48; ++k) g[k] = src_g[k * stride];
+                                load_cached<3>(scr.cache + cslot * 48, g);
                             } else {
                                 if (STATS) cnt.v[5] += l + 1;
                                 level = 0;
@@ -829,7 +828,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
             int cslot = -1;
             if (K > 0 && !greg && cvalid > 0 && trail != 0u) {
                 const int c = (ctop - 1) % (K > 0 ? K : 1);
-                if (scr.tag[c * stride] == ldeep) cslot = c;
+                if (scr.tag[c] == ldeep) cslot = c;
             }
             const bool deep = trail != 0u && (greg || cslot >= 0);
             const int lgive = deep ? ldeep : lmin;
@@ -907,9 +906,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                         level = x_sl + 1;
                         rd_target = -1;
                         gpend = false;
-                        const float *src_g = scr.cache + (size_t)(x_gslot * 48) * stride + (from - lane);
-#pragma unroll
-                        for (int k = 0; k < 48; ++k) g[k] = src_g[k * stride];
+                        load_cached<3>(scr.cache + (from - lane) * scr.cstride + x_gslot * 48, g);
                     } else {
                         level = 0;
                         rd_target = x_sl + 1;

@@ -360,18 +360,39 @@ struct Counters {
 };
 
 // ------------------------------------------------------------------------------------------------
-// Shared-memory scratch of one thread (addresses strided by the block size, so a warp's accesses hit
-// 32 consecutive words): the entry/exit interval of every pending sibling (one per tree level), a
-// K-slot cache of the lane's components of the most recently pushed Bezier siblings' grids, and the
-// prefetch slot of the next BVH node.
+// Shared-memory scratch of one thread: a K-slot cache of the lane's components of the most recently
+// pushed Bezier siblings' grids (the thread's own rows of 16-byte words: a grid moves in 4 NC 16-byte
+// accesses), the entry/exit interval of every pending sibling (one per tree level) and the prefetch slot
+// of the next BVH node (both strided by the block size, so a warp's accesses hit 32 consecutive words).
 // ------------------------------------------------------------------------------------------------
+// Floats of a thread's cache: K slots of 16 NC floats, then the K tags in a 4-float pad.  The stride
+// 16 NC K + 4 is 4 or 20 modulo 32, so the 16-byte accesses of 8 consecutive threads hit 8 distinct groups
+// of 4 banks: no bank conflicts.
+__host__ __device__ constexpr int cache_floats(int K, int NC) { return K > 0 ? 16 * NC * K + 4 : 0; }
+
 struct Scratch {
     float2 *sib;     // [level * stride]
-    float *cache;    // [(slot * 16 * NC + k) * stride]
-    int *tag;        // [slot * stride]
+    float *cache;    // this thread's cache: slot s at cache + 16 NC s
+    int *tag;        // this thread's tags: [slot]
     float4 *node;    // [k * stride], k < node_f4<BW, NC>(): prefetched float4s of a BVH node
     int stride;
+    int cstride;     // floats from one thread's cache to the next thread's
 };
+
+// Copy of a cached grid (16 NC floats, 16-byte aligned) into registers.
+template <int NC>
+CCS_DEV void load_cached(const float *src, float (&g)[16 * NC])
+{
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+    for (int q = 0; q < 4 * NC; ++q) {
+        const float4 v = s4[q];
+        g[4 * q + 0] = v.x;
+        g[4 * q + 1] = v.y;
+        g[4 * q + 2] = v.z;
+        g[4 * q + 3] = v.w;
+    }
+}
 
 // Asynchronous 16-byte global -> shared copy (cached in L1 and L2), per thread.
 CCS_DEV void cp_async16(void *smem_dst, const void *gsrc)
@@ -472,11 +493,9 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
                 const float k2 = up ? m23[q] : m012[q], k3 = up ? b3 : mm[q];
                 if (K > 0 && store) {
                     // the other child, in the same transposed layout
-                    float *dst = sc.cache + (size_t)(cache_slot * 16 * NC) * sc.stride;
-                    dst[(c * 16 + b * 4 + 0) * sc.stride] = up ? b0 : mm[q];
-                    dst[(c * 16 + b * 4 + 1) * sc.stride] = up ? m01[q] : m123[q];
-                    dst[(c * 16 + b * 4 + 2) * sc.stride] = up ? m012[q] : m23[q];
-                    dst[(c * 16 + b * 4 + 3) * sc.stride] = up ? mm[q] : b3;
+                    float4 *dst = reinterpret_cast<float4 *>(sc.cache + cache_slot * 16 * NC);
+                    dst[c * 4 + b] = make_float4(up ? b0 : mm[q], up ? m01[q] : m123[q], up ? m012[q] : m23[q],
+                                                 up ? mm[q] : b3);
                 }
                 g[c * 16 + b * 4 + 0] = k0;
                 g[c * 16 + b * 4 + 1] = k1;
@@ -828,7 +847,7 @@ CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const De
         int cslot = 0;
         if (K > 0 && !s.greg && s.cvalid > 0) {
             cslot = (s.ctop - 1) % (K > 0 ? K : 1);
-            if (scr.tag[cslot * scr.stride] == l) {
+            if (scr.tag[cslot] == l) {
                 cached = true;
                 --s.ctop;
                 --s.cvalid;
@@ -858,9 +877,7 @@ CCS_DEV void backtrack(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const De
             s.gpend = s.level < 2 * L;   // a leaf needs no bound
         } else if (cached) {
             s.level = l + 1;
-            const float *src = scr.cache + (size_t)(cslot * 16 * NC) * scr.stride;
-#pragma unroll
-            for (int k = 0; k < 16 * NC; ++k) g[k] = src[k * scr.stride];
+            load_cached<NC>(scr.cache + cslot * 16 * NC, g);
         } else {
             if (STATS) cnt.v[5] += l + 1;
             load_grid<NC>(rec_of(sc, s.pid), G, g);
@@ -951,7 +968,7 @@ CCS_DEV int pair_step(Lane<NC> &s, float (&g)[16 * NC], BvhStack &stk, const Dev
             s.trail |= bit;
             scr.sib[s.level * scr.stride] = o.goR ? make_float2(o.l0, o.l1) : make_float2(o.r0, o.r1);
             if (K > 0 && !s.greg) {
-                scr.tag[slot * scr.stride] = s.level;
+                scr.tag[slot] = s.level;
                 ++s.ctop;
                 s.cvalid = s.cvalid < K ? s.cvalid + 1 : K;
             }
