@@ -52,8 +52,8 @@ template <bool STATS, int MODE, class Src, int BW>
 cudaError_t launch_cand(const Src &src, const PairBufs &pb, const LaunchCfg &cfg, uint32_t n, uint32_t *status,
                         cudaStream_t s)
 {
-    k_cand<STATS, MODE, Src, BW><<<(n + 127) / 128, 128, 0, s>>>(src, pb, cfg.iter_cap, status, cfg.counters,
-                                                                  cfg.mc.occluded);
+    k_cand<STATS, MODE, Src, BW><<<(n + kCandBlock - 1) / kCandBlock, kCandBlock, 0, s>>>(
+        src, pb, cfg.iter_cap, status, cfg.counters, cfg.mc.occluded);
     return cudaGetLastError();
 }
 

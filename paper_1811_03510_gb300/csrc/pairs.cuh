@@ -14,9 +14,8 @@
 //     at a time, taking the ray's candidates in entry order and stopping at the first one that enters
 //     beyond the ray's best hit.  Every warp iteration is one subdivision step (Algorithm 3's loop body)
 //     of up to 32 pairs: the BVH walk, whose step count differs from ray to ray, is not in the loop.
-//  4. Rays whose dropped candidates could still hold the answer (best hit not before t_evict), or whose
-//     candidates did not fit the buffer, go to a fallback list, traced again by the ray-persistent kernel
-//     (k_intersect) from scratch.
+//  4. Rays whose dropped candidates could still hold the answer (best hit not before t_evict) go to a
+//     fallback list, traced again by the ray-persistent kernel (k_intersect) from scratch.
 //
 // The answer is the smallest leaf key over all nested intervals (readings A14/A15), which does not depend
 // on the order in which pairs are searched, so every pass reuses the arithmetic of traverse.cuh and the
@@ -28,14 +27,16 @@
 namespace ccs {
 
 constexpr int kPairCands = 8;            // candidates kept per ray (nearest entries)
-constexpr uint32_t kCandPerRay = 8;      // candidate buffer per ray of the launch, on average
+constexpr int kCandBlock = 128;          // threads of a candidate-pass block (its warps work independently)
 constexpr int kCostClasses = 16;
-// counter words of a launch: tasks, candidates written, fallback rays, queue heads (tasks, fallback), the
-// tasks of each cost class; from word 64, the counters of a counting fallback launch (CCS_NUM_COUNTERS
-// 64-bit words), of which the work counts are then added to the caller's
-constexpr int kCtrTasks = 0, kCtrCand = 1, kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16,
-              kCtrFallbackCounts = 64, kPairCtrWords = 64 + 2 * 32;
-// A task is 4 uint4 (64 bytes), everything a lane needs to start the ray:
+// counter words of a launch: fallback rays, queue heads (tasks, fallback), the tasks of each cost class;
+// from word 64, the counters of a counting fallback launch (CCS_NUM_COUNTERS 64-bit words), of which the
+// work counts are then added to the caller's
+constexpr int kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16, kCtrFallbackCounts = 64,
+              kPairCtrWords = 64 + 2 * 32;
+// Ray i's task and candidates have fixed places (task i, candidates from i kPairCands), so the candidate
+// pass needs no atomic counter for them.  A task is 4 uint4 (64 bytes), everything a lane needs to start
+// the ray:
 //   (ray, first candidate, z, t_evict bits), (first candidate's patch id, its entry distance, tmin, tmax),
 //   (ox, oy, oz, dx), (dy, dz, 0, 0) as float bits;
 // z = candidates (bits 0..7) | cost class (bits 8..11) | candidates were dropped (bit 30).
@@ -43,11 +44,10 @@ constexpr uint32_t kTaskEvicted = 0x40000000u;
 
 struct PairBufs {
     uint32_t *ctr;            // kPairCtrWords words, zeroed before the candidate pass
-    uint4 *task;              // tasks in the order the candidate pass made them, up to one per ray
-    uint32_t *cls;            // per cost class c, from c * n: the indices of its tasks in task
-    uint2 *cand;              // (patch id, entry distance bits)
+    uint4 *task;              // task of ray i at 4 i (rays with candidates only)
+    uint32_t *cls;            // per cost class c, from c * n: the rays of its tasks
+    uint2 *cand;              // (patch id, entry distance bits), ray i's from i kPairCands
     uint32_t *fallback;       // rays traced again by k_intersect, up to n
-    uint32_t cap_cand;        // entries of cand
     uint32_t n;               // rays of the launch (the stride of cls)
 };
 
@@ -56,7 +56,7 @@ __host__ __device__ inline size_t pair_align(size_t b) { return (b + 255) & ~(si
 inline size_t pair_scratch_bytes(uint32_t n)
 {
     return pair_align(kPairCtrWords * 4) + pair_align((size_t)n * 64) + pair_align((size_t)n * 4 * kCostClasses) +
-           pair_align((size_t)n * kCandPerRay * 8) + pair_align((size_t)n * 4);
+           pair_align((size_t)n * kPairCands * 8) + pair_align((size_t)n * 4);
 }
 inline PairBufs pair_bufs_at(void *base, uint32_t n)
 {
@@ -69,10 +69,8 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
     b.cls = reinterpret_cast<uint32_t *>(p);
     p += pair_align((size_t)n * 4 * kCostClasses);
     b.cand = reinterpret_cast<uint2 *>(p);
-    p += pair_align((size_t)n * kCandPerRay * 8);
+    p += pair_align((size_t)n * kPairCands * 8);
     b.fallback = reinterpret_cast<uint32_t *>(p);
-    const uint64_t cap = (uint64_t)n * kCandPerRay;
-    b.cap_cand = cap > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)cap;
     b.n = n;
     return b;
 }
@@ -176,7 +174,7 @@ CCS_DEV bool root_box_near(const float4 *__restrict__ rec, const float (&o)[3], 
 // Pass 1: BVH walk with the sorted candidate list.
 // ------------------------------------------------------------------------------------------------
 template <bool STATS, int MODE, class Src, int BW>
-__global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t iter_cap, uint32_t *status,
+__global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint32_t iter_cap, uint32_t *status,
                                               unsigned long long *counters, uint8_t *occluded)
 {
     const unsigned FULL = 0xffffffffu;
@@ -371,34 +369,14 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
         key = ng > 0 ? kCostClasses - 1 : min(kCostClasses - 2, cnt);
     }
     const uint32_t want = has ? (uint32_t)cnt : 0u;
-    uint32_t incl = want;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t v = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const uint32_t total = __shfl_sync(FULL, incl, 31);
-    uint32_t base = 0;
-    if (lane == 0 && total) base = atomicAdd(pb.ctr + kCtrCand, total);
-    base = __shfl_sync(FULL, base, 0);
-    const uint64_t off = (uint64_t)base + incl - want;
-    const bool ok = has && off + want <= pb.cap_cand;
-    const bool fb = has && !ok;
-    const unsigned mt = __ballot_sync(FULL, ok), mf = __ballot_sync(FULL, fb);
-    uint32_t bt = 0, bf = 0;
-    if (lane == 0) {
-        if (mt) bt = atomicAdd(pb.ctr + kCtrTasks, (uint32_t)__popc(mt));
-        if (mf) bf = atomicAdd(pb.ctr + kCtrFallback, (uint32_t)__popc(mf));
-    }
-    bt = __shfl_sync(FULL, bt, 0);
-    bf = __shfl_sync(FULL, bf, 0);
     const unsigned lt = (1u << lane) - 1u;
-    if (ok) {
+    if (has) {
+        const size_t off = (size_t)i * C;
         uint2 *dst = pb.cand + off;
 #pragma unroll
         for (int j = 0; j < C; ++j)
             if (j < cnt) dst[j] = make_uint2(kp[j], __float_as_uint(kt[j]));
-        uint4 *tk = pb.task + 4 * (size_t)(bt + __popc(mt & lt));
+        uint4 *tk = pb.task + 4 * (size_t)i;
         tk[0] = make_uint4(i, (uint32_t)off, (uint32_t)cnt | ((uint32_t)key << 8) | (evicted ? kTaskEvicted : 0u),
                            __float_as_uint(t_evict));
         tk[1] = make_uint4(kp[0], __float_as_uint(kt[0]), __float_as_uint(tmin), __float_as_uint(tmax));
@@ -406,14 +384,13 @@ __global__ void __launch_bounds__(128) k_cand(Src src, PairBufs pb, uint32_t ite
         tk[3] = make_uint4(__float_as_uint(rd[1]), __float_as_uint(rd[2]), 0u, 0u);
     }
     // the task's place in the list of its class
-    const int hkey = ok ? key : -1;
+    const int hkey = has ? key : -1;
     const unsigned same = __match_any_sync(FULL, hkey);
     const int leader = __ffs(same) - 1;
     uint32_t cb = 0;
-    if (ok && lane == leader) cb = atomicAdd(pb.ctr + kCtrHist + key, (uint32_t)__popc(same));
+    if (has && lane == leader) cb = atomicAdd(pb.ctr + kCtrHist + key, (uint32_t)__popc(same));
     cb = __shfl_sync(FULL, cb, leader);
-    if (ok) pb.cls[(size_t)key * pb.n + cb + __popc(same & lt)] = bt + __popc(mt & lt);
-    if (fb) pb.fallback[bf + __popc(mf & lt)] = i;
+    if (has) pb.cls[(size_t)key * pb.n + cb + __popc(same & lt)] = i;
     if (live && !has) {
         if (capped) atomicOr(status, 1u);
         write_miss<MODE>(src, ray_scene, ray_local, occluded);
@@ -460,11 +437,12 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     hcount[threadIdx.x] = 0;
     hcap[threadIdx.x] = 0;
     // the queue hands out the tasks class by class, costliest first: cstart[c] = first place of class c
-    __shared__ uint32_t cstart[kCostClasses];
+    __shared__ uint32_t cstart[kCostClasses + 1];
     if (threadIdx.x < kCostClasses) {
         uint32_t a = 0;
         for (int c = kCostClasses - 1; c > (int)threadIdx.x; --c) a += pb.ctr[kCtrHist + c];
         cstart[threadIdx.x] = a;
+        if (threadIdx.x == 0) cstart[kCostClasses] = a + pb.ctr[kCtrHist];   // all tasks
     }
     __syncthreads();
     Counters cnt;
@@ -479,7 +457,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     G.l0 = G.l1 = G.l2 = lane;
     const float kInf = __int_as_float(0x7f800000);
     const float cellw = __int_as_float((127 - L) << 23);
-    const uint32_t n_tasks = pb.ctr[kCtrTasks];
+    const uint32_t n_tasks = cstart[kCostClasses];
     uint32_t *queue = pb.ctr + kCtrQueue;
     if (STATS && lane == 0) atomicMax(counters + 20, ~global_ns());   // first warp start
 
