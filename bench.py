@@ -197,9 +197,9 @@ def kernel_source_hash() -> str:
 
 
 def measured_traffic() -> tuple:
-    """DRAM bytes per primary and diffuse launch of the dominant kernel (the pair engine's subdivision pass)
-    from the committed ncu summary, if it was taken on the current kernel sources (else None: the counters
-    describe another kernel)."""
+    """DRAM bytes per primary and diffuse launch of the dominant kernel (the pair engine's subdivision pass,
+    under ncu's cold cache) from the committed ncu summary, if it was taken on the current kernel sources
+    (else None: the counters describe another kernel)."""
     path = os.path.join(ROOT, "profiles", "k_pairs_cfg2_dram.md")
     try:
         text = open(path).read()
@@ -212,6 +212,22 @@ def measured_traffic() -> tuple:
     if not (m_hash and m_p and m_d) or m_hash.group(1) != kernel_source_hash():
         return None, path
     return (int(m_p.group(1)), int(m_d.group(1))), path
+
+
+def measured_share() -> tuple:
+    """Share of the subdivision pass (both batches) in the step's kernel time, from the committed ncu launch
+    list, if it was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "k_pairs_cfg2_launches.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None, None
+    import re
+    m_hash = re.search(r"kernel sources sha256\[:16\]: ([0-9a-f]{16})", text)
+    m = re.search(r"k_pairs share of the step: ([0-9.]+)", text)
+    if not (m_hash and m) or m_hash.group(1) != kernel_source_hash():
+        return None, path
+    return float(m.group(1)), path
 
 
 def measured_issue() -> tuple:
@@ -900,6 +916,18 @@ def main():
 
     traffic, traffic_src = measured_traffic()
     issue, issue_src = measured_issue()
+    share, share_src = measured_share()
+    # the dominant kernel alone: the subdivision steps (Bezier and Gregory splits, the local-frame ray per
+    # pair) over its share of the event-timed step, when the pair engine runs both batches
+    kernel_roof = None
+    if share and engine_of(opts_p) == "pairs" and engine_of(opts_d) == "pairs":
+        ops_k = sum(v["bezier_splits"] * OPS_SPLIT_BEZIER + v["gregory_splits"] * OPS_SPLIT_GREGORY
+                    + (v["pairs"] * OPS_PAIR_FRAME if scene.local else 0) for v in counts.values())
+        t_k = share * T / args.steps
+        kernel_roof = {"kernel": "k_pairs (subdivision pass, primary + diffuse)", "achieved": ops_k / t_k / 1e12,
+                       "frac": ops_k / t_k / fp32_peak_ops(n_sm, 2070.0), "unit": "Top/s (FP32)",
+                       "time_share": share, "share_source": os.path.relpath(share_src, ROOT),
+                       "per": "its algorithmic ops over its share (ncu launch list) of the event-timed step"}
     peak_max = fp32_peak_ops(n_sm, 2070.0)
     ops_step = alg_ops["primary"] + alg_ops["diffuse"]
     achieved = ops_step * args.steps / T
@@ -934,6 +962,7 @@ def main():
                                          kernel_source_hash(), "matches": bool(traffic)} if traffic_src else None),
                      "algorithmic_bytes_per_launch": 48 * rays_per_step / 2,
                      "frac_at_measured_clock": (achieved / fp32_peak_ops(n_sm, ck["sm_mhz"])) if ck["sm_mhz"] else None,
+                     "dominant_kernel": kernel_roof,
                      "issue_frac_ncu": ({"all_instructions": issue[0], "fadd_fmul_ffma": issue[1],
                                          "source": os.path.relpath(issue_src, ROOT),
                                          "kernel_sources_sha16": kernel_source_hash(),
