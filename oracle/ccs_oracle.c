@@ -537,8 +537,8 @@ static void enumerate_patch(const patch_t *P, const ray_t *r, int L, double spre
     b *= ORC_FAR_SCALE;
     if (a > bound || a > b) return;
     /* below the root the FP32 path compares the boxes with the ray anchored at its entry into the patch box
-     * (its origin formed in FP64 and rounded once, rotated into the patch frame with local frames; the
-     * direction in FP32) and measures distances from there: the error of that ray grows with the size of
+     * (its origin formed without losing the cancellation, as accurately as in FP64, rotated into the patch
+     * frame with local frames and rounded once; the direction in FP32) and measures distances from there: the error of that ray grows with the size of
      * the anchored origin and of the patch, not with the distance from the ray's own origin; 3e-7 per unit
      * of |entry point - box centre| + the box's diagonal bounds it */
     const ray_t rl = local_ray(P, r);
