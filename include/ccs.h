@@ -105,9 +105,9 @@ typedef struct {
     uint32_t bvh_width;       /* the scene's BVH to traverse: 0 its default, 2 or 4 (INVALID_ARG when the
                                  scene was not built with that width) [0] */
     uint32_t host_chunk;      /* ccs_intersect_host: rays per chunk of its copy/trace pipeline, at most 8
-                                 chunks (larger chunks then); 0: below 2^17 rays one chunk, else a short
-                                 first and last chunk (n/8 rays, at most 2^18) around middle chunks of
-                                 about 2^20 rays [0] */
+                                 chunks (larger chunks then); 0: below 2^17 rays (2^19 with the pair
+                                 engine) one chunk, else a short first and last chunk (n/8 rays, at most
+                                 2^18) around middle chunks of about 2^20 rays [0] */
 } ccs_trace_opts;
 
 #define CCS_CACHE_DEFAULT 0xFFFFFFFFu

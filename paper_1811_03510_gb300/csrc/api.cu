@@ -191,6 +191,8 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
         const LaunchCfg &c = bt[j].cfg;
         ns[j] = bt[j].n;
         hc[j] = c.host_chunk;
+        // the pair engine pays a launch's drain once per chunk: a batch under 2^19 rays goes in one chunk
+        if (!hc[j] && use_pairs(c) && ns[j] < (1u << 19)) hc[j] = ns[j];
         align[j] = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8 : 1;
     }
     const std::vector<HostChunk> chunks = host_batch_chunks(nb, ns.data(), hc.data(), align.data());
