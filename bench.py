@@ -152,9 +152,9 @@ def engine_of(o) -> str:
 
 
 def kernels_per_launch(o) -> int:
-    """Kernels of this library one ccs_intersect launches: the pair engine's candidate pass, subdivision pass
-    and fallback; the work order's three kernels and k_intersect; or k_intersect alone."""
-    return {"pairs": 3, "ray+order": 4, "ray": 1}[engine_of(o)]
+    """Kernels of this library one ccs_intersect launches: the pair engine's candidate and subdivision passes;
+    the work order's three kernels and k_intersect; or k_intersect alone."""
+    return {"pairs": 2, "ray+order": 4, "ray": 1}[engine_of(o)]
 
 
 def schedule_summary(c: dict, lanes_per_ray: int, engine: str = "ray") -> dict:
@@ -170,7 +170,7 @@ def schedule_summary(c: dict, lanes_per_ray: int, engine: str = "ray") -> dict:
                "helper_lanes_per_iter": v[14] / it, "waiting_lanes_per_iter": v[15] / it,
                "idle_lanes_per_iter": v[16] / it, "subtrees_handed_over": v[11], "candidates": v[8],
                "candidates_culled_by_root_box": v[17], "rays_with_dropped_candidates": v[9],
-               "fallback_rays": v[10]}
+               "walks_for_dropped_candidates": v[10]}
         out.update(ccs.timeline(c))
         return out
     it = max(1, c["warp_iters"])

@@ -137,17 +137,17 @@ typedef struct {
                                        lane, taking each ray's candidates in entry order until one enters
                                        beyond its best hit, so that every warp iteration is one
                                        subdivision step of up to 32 pairs; once the queue is empty, idle
-                                       lanes take pending subtrees of busy lanes of their warp; (4) rays
-                                       whose dropped candidates could still hold the answer are traced
-                                       again by the ray-persistent kernel.  Hits are bit-identical.  Uses
+                                       lanes take pending subtrees of busy lanes of their warp; (4) a ray
+                                       whose dropped candidates could still hold the answer has its lane
+                                       walk the BVH again for the next ones.  Hits are bit-identical.  Uses
                                        about 200 bytes of scratch per ray from a stream-ordered memory
                                        pool of the library (kept for reuse), on the launch's stream; the
                                        work order, bvh_burst, vote, chunk and min_blocks do not apply, and
                                        blocks_per_sm is what fits.  Counters: slots 8..17 hold candidates
-                                       listed, rays that dropped some, fallback rays, subtrees handed
-                                       over, warp iterations of the subdivision pass and, per iteration,
-                                       lanes splitting, helping, waiting and idle, then candidates culled
-                                       by their root box. */
+                                       listed, rays that dropped some, walks for dropped candidates,
+                                       subtrees handed over, warp iterations of the subdivision pass and,
+                                       per iteration, lanes splitting, helping, waiting and idle, then
+                                       candidates culled by their root box. */
 #define CCS_NUM_COUNTERS 23         /* work per ray, summed (0..7): bvh nodes, bezier splits, gregory
                                        splits, leaves, backtracks, re-descent levels, pruned siblings, pairs;
                                        schedule of the warps, summed over warp iterations (8..19): warp
@@ -304,7 +304,7 @@ ccs_status ccs_batch_create(ccs_batch **out, ccs_scene *const *scenes, uint32_t 
 ccs_status ccs_batch_set_points(ccs_batch *b, uint32_t scene_index, const float *x, const float *y, const float *z);
 
 /* Enqueue the selected stages (CCS_BATCH_* bits) on `stream`: the table copy, one repack launch,
- * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's four
+ * one refit launch and one intersect launch (with CCS_TRACE_PAIRS in opts: the pair engine's three
  * launches over the rays of all scenes, whose scratch of about 200 bytes per ray the batch allocates
  * with cudaMalloc on its first such run and keeps).  Otherwise allocates nothing; does not synchronise.
  * Answers are bit-identical to ccs_intersect on each scene alone. */

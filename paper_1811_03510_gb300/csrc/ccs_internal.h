@@ -61,7 +61,6 @@ struct LaunchCfg {
     ModeCtx mc{};
     const MlpWeights *mlp = nullptr;
     float min_conf = 0.0f;
-    const uint32_t *count_dev = nullptr;  // device word: the launch traces only its first *count_dev rays
 };
 
 struct DevScene {
@@ -111,7 +110,7 @@ cudaError_t launch_order(const DevScene &sc, const DevRays &r, uint32_t n, uint3
                          cudaStream_t s);
 cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
                                    uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
-                                   int num_sms, cudaStream_t s, uint32_t width, const uint32_t *perm = nullptr);
+                                   int num_sms, cudaStream_t s, uint32_t width);
 // pair engine (pairs.cu): whether a launch with these options runs it, its scratch for n rays, and the
 // launches (single scene: scratch from the library's stream-ordered pool; batch: the caller's scratch)
 bool use_pairs(const LaunchCfg &cfg);

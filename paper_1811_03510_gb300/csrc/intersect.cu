@@ -8,13 +8,12 @@ template cudaError_t launch_single_w<2>(const DevScene &, const DevRays &, const
                                         const LaunchCfg &, uint32_t *, uint32_t *, int, cudaStream_t,
                                         const uint32_t *);
 template cudaError_t launch_batch_w<2>(const BatchEntry *, const uint32_t *, uint32_t, uint32_t, const LaunchCfg &,
-                                       uint32_t *, uint32_t *, int, cudaStream_t, const uint32_t *);
+                                       uint32_t *, uint32_t *, int, cudaStream_t);
 extern template cudaError_t launch_single_w<4>(const DevScene &, const DevRays &, const DevHits &, uint32_t,
                                                const LaunchCfg &, uint32_t *, uint32_t *, int, cudaStream_t,
                                                const uint32_t *);
 extern template cudaError_t launch_batch_w<4>(const BatchEntry *, const uint32_t *, uint32_t, uint32_t,
-                                              const LaunchCfg &, uint32_t *, uint32_t *, int, cudaStream_t,
-                                              const uint32_t *);
+                                              const LaunchCfg &, uint32_t *, uint32_t *, int, cudaStream_t);
 
 cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
                              uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s, const uint32_t *perm)
@@ -26,10 +25,10 @@ cudaError_t launch_intersect(const DevScene &sc, const DevRays &r, const DevHits
 
 cudaError_t launch_intersect_batch(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes,
                                    uint32_t n_total, const LaunchCfg &cfg, uint32_t *queue, uint32_t *status,
-                                   int num_sms, cudaStream_t s, uint32_t width, const uint32_t *perm)
+                                   int num_sms, cudaStream_t s, uint32_t width)
 {
-    return width == 4 ? launch_batch_w<4>(entries, ray_prefix, n_scenes, n_total, cfg, queue, status, num_sms, s, perm)
-                      : launch_batch_w<2>(entries, ray_prefix, n_scenes, n_total, cfg, queue, status, num_sms, s, perm);
+    return width == 4 ? launch_batch_w<4>(entries, ray_prefix, n_scenes, n_total, cfg, queue, status, num_sms, s)
+                      : launch_batch_w<2>(entries, ray_prefix, n_scenes, n_total, cfg, queue, status, num_sms, s);
 }
 
 }  // namespace ccs

@@ -7,6 +7,6 @@ template cudaError_t launch_single_w<4>(const DevScene &, const DevRays &, const
                                         const LaunchCfg &, uint32_t *, uint32_t *, int, cudaStream_t,
                                         const uint32_t *);
 template cudaError_t launch_batch_w<4>(const BatchEntry *, const uint32_t *, uint32_t, uint32_t, const LaunchCfg &,
-                                       uint32_t *, uint32_t *, int, cudaStream_t, const uint32_t *);
+                                       uint32_t *, uint32_t *, int, cudaStream_t);
 
 }  // namespace ccs

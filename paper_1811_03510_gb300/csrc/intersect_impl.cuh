@@ -28,9 +28,8 @@ struct SingleSource {
     DevHits hits;
     uint32_t n;
     const uint32_t *perm;   // queue position -> ray index (work order), or null for the identity
-    const uint32_t *count_dev;   // device word bounding the rays traced (a fallback list), or null
     struct LaneScene {};
-    CCS_DEV uint32_t total() const { return count_dev ? min(*count_dev, n) : n; }
+    CCS_DEV uint32_t total() const { return n; }
     CCS_DEV const DevScene &scene(const LaneScene &) const { return sc; }
     CCS_DEV void locate(uint32_t i, LaneScene &, uint32_t &scene, uint32_t &local) const
     {
@@ -46,16 +45,13 @@ struct BatchSource {
     const BatchEntry *entries;
     const uint32_t *ray_prefix;   // n_scenes + 1
     uint32_t n_scenes, n;
-    const uint32_t *perm;        // queue position -> global ray index (a fallback list), or null
-    const uint32_t *count_dev;   // device word bounding the rays traced, or null
     struct LaneScene {
         DevScene sc;
     };
-    CCS_DEV uint32_t total() const { return count_dev ? min(*count_dev, n) : n; }
+    CCS_DEV uint32_t total() const { return n; }
     CCS_DEV const DevScene &scene(const LaneScene &l) const { return l.sc; }
     CCS_DEV void locate(uint32_t i, LaneScene &lsc, uint32_t &scene, uint32_t &local) const
     {
-        if (perm) i = __ldg(perm + i);
         uint32_t lo = 0, hi = n_scenes;   // largest s with ray_prefix[s] <= i
         while (hi - lo > 1) {
             const uint32_t m = (lo + hi) >> 1;
@@ -378,16 +374,15 @@ template <int BW>
 cudaError_t launch_single_w(const DevScene &sc, const DevRays &r, const DevHits &h, uint32_t n, const LaunchCfg &cfg,
                             uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s, const uint32_t *perm)
 {
-    SingleSource src{sc, r, h, n, perm, cfg.count_dev};
+    SingleSource src{sc, r, h, n, perm};
     return dispatch<BW>(src, cfg, queue, status, num_sms, s);
 }
 
 template <int BW>
 cudaError_t launch_batch_w(const BatchEntry *entries, const uint32_t *ray_prefix, uint32_t n_scenes, uint32_t n_total,
-                           const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s,
-                           const uint32_t *perm)
+                           const LaunchCfg &cfg, uint32_t *queue, uint32_t *status, int num_sms, cudaStream_t s)
 {
-    BatchSource src{entries, ray_prefix, n_scenes, n_total, perm, cfg.count_dev};
+    BatchSource src{entries, ray_prefix, n_scenes, n_total};
     LaunchCfg c = cfg;
     c.mode = kModePlain;
     return dispatch<BW>(src, c, queue, status, num_sms, s);

@@ -1,8 +1,7 @@
 // The pair engine's launch sequence (CCS_TRACE_PAIRS): counters zeroed, the candidate pass (which also
-// lists each task under its cost class), the subdivision pass, then the ray-persistent kernel over the
-// fallback list.  One scene takes its scratch from the library's stream-ordered memory pool on the
-// launch's stream; a batch brings its own, allocated with the batch, so that its run stays capturable in
-// a CUDA graph.
+// lists each task under its cost class), then the subdivision pass.  One scene takes its scratch from the
+// library's stream-ordered memory pool on the launch's stream; a batch brings its own, allocated with the
+// batch, so that its run stays capturable in a CUDA graph.
 #include <mutex>
 
 #include "pairs_launch.cuh"
@@ -69,33 +68,6 @@ cudaError_t cand_pass(const Src &src, const PairBufs &pb, const LaunchCfg &cfg, 
                  : launch_cand<false, MODE, Src, 2>(src, pb, cfg, n, status, s);
 }
 
-// The fallback's options: the ray-persistent kernel over the list the passes filled.  A counting launch
-// counts into the scratch's own words: its schedule counts would mix with the pair engine's.
-LaunchCfg fallback_cfg(const LaunchCfg &cfg, const PairBufs &pb)
-{
-    LaunchCfg fc = cfg;
-    fc.flags &= ~(CCS_TRACE_PAIRS | CCS_TRACE_ORDER);
-    fc.count_dev = pb.ctr + kCtrFallback;
-    if (fc.cache_slots == 1) fc.cache_slots = 2;
-    if (fc.counters) fc.counters = reinterpret_cast<unsigned long long *>(pb.ctr + kCtrFallbackCounts);
-    return fc;
-}
-
-static __global__ void k_add_work_counts(const unsigned long long *__restrict__ from, unsigned long long *to)
-{
-    constexpr unsigned kWork = 8;   // counters 0..7: the work of the method
-    if (threadIdx.x < kWork && from[threadIdx.x]) atomicAdd(to + threadIdx.x, from[threadIdx.x]);
-}
-
-// The fallback launch's work counts (slots 0..7) into the caller's counters.
-cudaError_t add_fallback_counts(const LaunchCfg &cfg, const PairBufs &pb, cudaStream_t s)
-{
-    if (!cfg.counters) return cudaSuccess;
-    k_add_work_counts<<<1, 32, 0, s>>>(reinterpret_cast<const unsigned long long *>(pb.ctr + kCtrFallbackCounts),
-                                       cfg.counters);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t pool_alloc(void **p, size_t bytes, cudaStream_t s)
@@ -116,7 +88,7 @@ cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevH
     cudaError_t e = pool_alloc(&base, pair_scratch_bytes(n), s);
     if (e != cudaSuccess) return e;
     const PairBufs pb = pair_bufs_at(base, n);
-    const SingleSource src{sc, r, h, n, nullptr, nullptr};
+    const SingleSource src{sc, r, h, n, nullptr};
     e = cudaMemsetAsync(pb.ctr, 0, kPairCtrWords * sizeof(uint32_t), s);
     if (e == cudaSuccess) {
         if (cfg.mode == kModeAnyHit) {
@@ -127,9 +99,6 @@ cudaError_t launch_pairs_single(const DevScene &sc, const DevRays &r, const DevH
             if (e == cudaSuccess) e = pair_passes_single_plain(src, pb, cfg, n, status, num_sms, s);
         }
     }
-    if (e == cudaSuccess)
-        e = launch_intersect(sc, r, h, n, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF, status, num_sms, s, pb.fallback);
-    if (e == cudaSuccess) e = add_fallback_counts(cfg, pb, s);
     const cudaError_t e2 = pool_free(base, s);
     return e != cudaSuccess ? e : e2;
 }
@@ -140,15 +109,11 @@ cudaError_t launch_pairs_batch(const BatchEntry *entries, const uint32_t *ray_pr
 {
     if (n_total == 0) return cudaSuccess;
     const PairBufs pb = pair_bufs_at(scratch, n_total);
-    const BatchSource src{entries, ray_prefix, n_scenes, n_total, nullptr, nullptr};
+    const BatchSource src{entries, ray_prefix, n_scenes, n_total};
     cudaError_t e = cudaMemsetAsync(pb.ctr, 0, kPairCtrWords * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if ((e = cand_pass<kModePlain>(src, pb, cfg, n_total, width, status, s)) != cudaSuccess) return e;
-    if ((e = pair_passes_batch(src, pb, cfg, n_total, status, num_sms, s)) != cudaSuccess) return e;
-    if ((e = launch_intersect_batch(entries, ray_prefix, n_scenes, n_total, fallback_cfg(cfg, pb), pb.ctr + kCtrQueueF,
-                                    status, num_sms, s, width, pb.fallback)) != cudaSuccess)
-        return e;
-    return add_fallback_counts(cfg, pb, s);
+    return pair_passes_batch(src, pb, cfg, n_total, status, num_sms, s);
 }
 
 }  // namespace ccs

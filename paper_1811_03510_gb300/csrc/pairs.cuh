@@ -14,8 +14,9 @@
 //     at a time, taking the ray's candidates in entry order and stopping at the first one that enters
 //     beyond the ray's best hit.  Every warp iteration is one subdivision step (Algorithm 3's loop body)
 //     of up to 32 pairs: the BVH walk, whose step count differs from ray to ray, is not in the loop.
-//  4. Rays whose dropped candidates could still hold the answer (best hit not before t_evict) go to a
-//     fallback list, traced again by the ray-persistent kernel (k_intersect) from scratch.
+//  4. A ray whose dropped candidates could still hold the answer (best hit not before t_evict) has its lane
+//     collect the next ones, those after the last listed, by a BVH walk of its own (collect_more), and goes
+//     on with them.
 //
 // The answer is the smallest leaf key over all nested intervals (readings A14/A15), which does not depend
 // on the order in which pairs are searched, so every pass reuses the arithmetic of traverse.cuh and the
@@ -29,11 +30,8 @@ namespace ccs {
 constexpr int kPairCands = 8;            // candidates kept per ray (nearest entries)
 constexpr int kCandBlock = 128;          // threads of a candidate-pass block (its warps work independently)
 constexpr int kCostClasses = 16;
-// counter words of a launch: fallback rays, queue heads (tasks, fallback), the tasks of each cost class;
-// from word 64, the counters of a counting fallback launch (CCS_NUM_COUNTERS 64-bit words), of which the
-// work counts are then added to the caller's
-constexpr int kCtrFallback = 2, kCtrQueue = 3, kCtrQueueF = 4, kCtrHist = 16, kCtrFallbackCounts = 64,
-              kPairCtrWords = 64 + 2 * 32;
+// counter words of a launch: the queue head, the tasks of each cost class
+constexpr int kCtrQueue = 3, kCtrHist = 16, kPairCtrWords = 64;
 // Ray i's task and candidates have fixed places (task i, candidates from i kPairCands), so the candidate
 // pass needs no atomic counter for them.  A task is 4 uint4 (64 bytes), everything a lane needs to start
 // the ray:
@@ -47,7 +45,6 @@ struct PairBufs {
     uint4 *task;              // task of ray i at 4 i (rays with candidates only)
     uint32_t *cls;            // per cost class c, from c * n: the rays of its tasks
     uint2 *cand;              // (patch id, entry distance bits), ray i's from i kPairCands
-    uint32_t *fallback;       // rays traced again by k_intersect, up to n
     uint32_t n;               // rays of the launch (the stride of cls)
 };
 
@@ -56,7 +53,7 @@ __host__ __device__ inline size_t pair_align(size_t b) { return (b + 255) & ~(si
 inline size_t pair_scratch_bytes(uint32_t n)
 {
     return pair_align(kPairCtrWords * 4) + pair_align((size_t)n * 64) + pair_align((size_t)n * 4 * kCostClasses) +
-           pair_align((size_t)n * kPairCands * 8) + pair_align((size_t)n * 4);
+           pair_align((size_t)n * kPairCands * 8);
 }
 inline PairBufs pair_bufs_at(void *base, uint32_t n)
 {
@@ -69,8 +66,6 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
     b.cls = reinterpret_cast<uint32_t *>(p);
     p += pair_align((size_t)n * 4 * kCostClasses);
     b.cand = reinterpret_cast<uint2 *>(p);
-    p += pair_align((size_t)n * kPairCands * 8);
-    b.fallback = reinterpret_cast<uint32_t *>(p);
     b.n = n;
     return b;
 }
@@ -173,6 +168,165 @@ CCS_DEV bool root_box_near(const float4 *__restrict__ rec, const float (&o)[3], 
 // ------------------------------------------------------------------------------------------------
 // Pass 1: BVH walk with the sorted candidate list.
 // ------------------------------------------------------------------------------------------------
+// The BVH walk of the candidate pass (Sec. 4): the C candidates of the ray with the smallest keys (entry
+// distance of the patch box, patch id), sorted in kt / kp, counting only keys above (lb_t, lb_p) when has_lb
+// (the candidates an earlier walk did not list: all its dropped keys are above its last listed one).  Before
+// the list is full nothing is pruned but [tmin, tmax]; once it is full, subtrees entered beyond its last
+// entry are skipped and the smallest entry distance dropped that way is kept (t_evict).  With local frames,
+// Bezier patches whose root box the ray does not come near are no candidates (root_box_near).  Returns false
+// when the iteration budget it ran out.
+template <bool STATS, int BW>
+CCS_DEV bool walk_candidates(const DevScene &sc, const RayG<3> &r, const float (&ro)[3], const float (&rd)[3],
+                             float tmin, float tmax, bool has_lb, float lb_t, uint32_t lb_p, uint32_t &it,
+                             float (&kt)[kPairCands], uint32_t (&kp)[kPairCands], int &cnt, float &t_evict,
+                             bool &evicted, unsigned long long &nodes, unsigned long long &culled, const Grp &G)
+{
+    constexpr int C = kPairCands;
+    const float kInf = __int_as_float(0x7f800000);
+    int2 stk[kBvhStack];
+    int sp = 0, node = 0;
+    float n0 = tmin;
+    for (;;) {
+        if (node == kDone) break;
+        if (it == 0) return false;
+        --it;
+        if (node < 0) {   // a patch: into the list (the leaf's box is the patch box)
+            const uint32_t p = (uint32_t)(~node);
+            bool ins = true;
+            if (has_lb && !cand_less(lb_t, lb_p, n0, p)) {
+                ins = false;   // listed by an earlier walk
+            } else if (sc.local && !root_box_near(rec_of(sc, p), ro, rd, tmin, G)) {
+                ins = false;
+                if (STATS) ++culled;
+            } else if (cnt == C) {
+                evicted = true;
+                if (!cand_less(n0, p, kt[C - 1], kp[C - 1])) {
+                    t_evict = fminf(t_evict, n0);
+                    ins = false;
+                } else {
+                    t_evict = fminf(t_evict, kt[C - 1]);
+                }
+            } else {
+                ++cnt;
+            }
+            if (ins) {
+                int m = 0;
+#pragma unroll
+                for (int j = 0; j < C; ++j) m += cand_less(kt[j], kp[j], n0, p) ? 1 : 0;
+#pragma unroll
+                for (int j = C - 1; j >= 1; --j) {
+                    kt[j] = j > m ? kt[j - 1] : (j == m ? n0 : kt[j]);
+                    kp[j] = j > m ? kp[j - 1] : (j == m ? p : kp[j]);
+                }
+                kt[0] = m == 0 ? n0 : kt[0];
+                kp[0] = m == 0 ? p : kp[0];
+            }
+        } else {
+            ++nodes;
+            // once the list is full, a subtree entered beyond its last entry only holds dropped patches
+            const float bound = cnt == C ? kt[C - 1] : tmax;
+            if constexpr (BW == 4) {
+                const float4 *nd = sc.nodes + (size_t)node * kNode4F4;
+                float4 lo4[3], hi4[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    lo4[k] = __ldg(nd + 2 * k);
+                    hi4[k] = __ldg(nd + 2 * k + 1);
+                }
+                const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 6));
+                int c[4] = {ch.x, ch.y, ch.z, ch.w};
+                float key[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    float lo[3], hi[3];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        lo[k] = j == 0 ? lo4[k].x : j == 1 ? lo4[k].y : j == 2 ? lo4[k].z : lo4[k].w;
+                        hi[k] = j == 0 ? hi4[k].x : j == 1 ? hi4[k].y : j == 2 ? hi4[k].z : hi4[k].w;
+                    }
+                    float t0, t1;
+                    slab<3>(r, lo, hi, tmin, tmax, G, t0, t1);
+                    bool h = t0 <= t1 && c[j] != kEmptyChild;
+                    if (h && t0 > bound) {
+                        h = false;
+                        evicted = true;
+                        t_evict = fminf(t_evict, t0);
+                    }
+                    key[j] = h ? t0 : kInf;
+                }
+                cx4(key, c, 0, 1);
+                cx4(key, c, 2, 3);
+                cx4(key, c, 0, 2);
+                cx4(key, c, 1, 3);
+                cx4(key, c, 1, 2);
+                if (key[0] < kInf) {
+#pragma unroll
+                    for (int j = 3; j >= 1; --j) {
+                        if (key[j] < kInf && sp < kBvhStack) {
+                            stk[sp] = make_int2(c[j], __float_as_int(key[j]));
+                            ++sp;
+                        }
+                    }
+                    node = c[0];
+                    n0 = key[0];
+                    continue;
+                }
+            } else {
+                const float4 *nd = sc.nodes + (size_t)node * kNodeF4;
+                float4 q[3];
+#pragma unroll
+                for (int k = 0; k < 3; ++k) q[k] = __ldg(nd + k);
+                const int2 ch = __ldg(reinterpret_cast<const int2 *>(nd + 3));
+                float a0, a1, b0, b1;
+                node_child_boxes<3>(q, r, tmin, tmax, G, a0, a1, b0, b1);
+                bool ha = a0 <= a1 && ch.x != kEmptyChild;
+                bool hb = b0 <= b1 && ch.y != kEmptyChild;
+                if (ha && a0 > bound) {
+                    ha = false;
+                    evicted = true;
+                    t_evict = fminf(t_evict, a0);
+                }
+                if (hb && b0 > bound) {
+                    hb = false;
+                    evicted = true;
+                    t_evict = fminf(t_evict, b0);
+                }
+                if (ha && hb) {
+                    const bool bfirst = b0 < a0;
+                    if (sp < kBvhStack) {
+                        stk[sp] = make_int2(bfirst ? ch.x : ch.y, __float_as_int(bfirst ? a0 : b0));
+                        ++sp;
+                    }
+                    node = bfirst ? ch.y : ch.x;
+                    n0 = bfirst ? b0 : a0;
+                    continue;
+                }
+                if (ha || hb) {
+                    node = ha ? ch.x : ch.y;
+                    n0 = ha ? a0 : b0;
+                    continue;
+                }
+            }
+        }
+        // pop the nearest pending subtree that can still add to the list
+        node = kDone;
+        while (sp > 0) {
+            --sp;
+            const int2 e = stk[sp];
+            const float t0 = __int_as_float(e.y);
+            if (cnt == C && t0 > kt[C - 1]) {
+                evicted = true;
+                t_evict = fminf(t_evict, t0);
+                continue;
+            }
+            node = e.x;
+            n0 = t0;
+            break;
+        }
+    }
+    return true;
+}
+
 template <bool STATS, int MODE, class Src, int BW>
 __global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint32_t iter_cap, uint32_t *status,
                                               unsigned long long *counters, uint8_t *occluded)
@@ -211,148 +365,9 @@ __global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint3
         ro[1] = r.org[1];
         ro[2] = r.org[2];
         if (ok && sc.n_nodes != 0) {
-            int2 stk[kBvhStack];
-            int sp = 0, node = 0;
-            float n0 = tmin;
             uint32_t it = iter_cap;
-            for (;;) {
-                if (node == kDone) break;
-                if (it == 0) {
-                    capped = true;
-                    break;
-                }
-                --it;
-                if (node < 0) {   // a patch: into the list (the leaf's box is the patch box)
-                    const uint32_t p = (uint32_t)(~node);
-                    bool ins = !sc.local || root_box_near(rec_of(sc, p), ro, rd, tmin, G);
-                    if (!ins) {
-                        if (STATS) ++culled;
-                    } else if (cnt == C) {
-                        evicted = true;
-                        if (!cand_less(n0, p, kt[C - 1], kp[C - 1])) {
-                            t_evict = fminf(t_evict, n0);
-                            ins = false;
-                        } else {
-                            t_evict = fminf(t_evict, kt[C - 1]);
-                        }
-                    } else {
-                        ++cnt;
-                    }
-                    if (ins) {
-                        int m = 0;
-#pragma unroll
-                        for (int j = 0; j < C; ++j) m += cand_less(kt[j], kp[j], n0, p) ? 1 : 0;
-#pragma unroll
-                        for (int j = C - 1; j >= 1; --j) {
-                            kt[j] = j > m ? kt[j - 1] : (j == m ? n0 : kt[j]);
-                            kp[j] = j > m ? kp[j - 1] : (j == m ? p : kp[j]);
-                        }
-                        kt[0] = m == 0 ? n0 : kt[0];
-                        kp[0] = m == 0 ? p : kp[0];
-                    }
-                } else {
-                    ++nodes;
-                    // once the list is full, a subtree entered beyond its last entry only holds dropped patches
-                    const float bound = cnt == C ? kt[C - 1] : tmax;
-                    if constexpr (BW == 4) {
-                        const float4 *nd = sc.nodes + (size_t)node * kNode4F4;
-                        float4 lo4[3], hi4[3];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) {
-                            lo4[k] = __ldg(nd + 2 * k);
-                            hi4[k] = __ldg(nd + 2 * k + 1);
-                        }
-                        const int4 ch = __ldg(reinterpret_cast<const int4 *>(nd + 6));
-                        int c[4] = {ch.x, ch.y, ch.z, ch.w};
-                        float key[4];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            float lo[3], hi[3];
-#pragma unroll
-                            for (int k = 0; k < 3; ++k) {
-                                lo[k] = j == 0 ? lo4[k].x : j == 1 ? lo4[k].y : j == 2 ? lo4[k].z : lo4[k].w;
-                                hi[k] = j == 0 ? hi4[k].x : j == 1 ? hi4[k].y : j == 2 ? hi4[k].z : hi4[k].w;
-                            }
-                            float t0, t1;
-                            slab<3>(r, lo, hi, tmin, tmax, G, t0, t1);
-                            bool h = t0 <= t1 && c[j] != kEmptyChild;
-                            if (h && t0 > bound) {
-                                h = false;
-                                evicted = true;
-                                t_evict = fminf(t_evict, t0);
-                            }
-                            key[j] = h ? t0 : kInf;
-                        }
-                        cx4(key, c, 0, 1);
-                        cx4(key, c, 2, 3);
-                        cx4(key, c, 0, 2);
-                        cx4(key, c, 1, 3);
-                        cx4(key, c, 1, 2);
-                        if (key[0] < kInf) {
-#pragma unroll
-                            for (int j = 3; j >= 1; --j) {
-                                if (key[j] < kInf && sp < kBvhStack) {
-                                    stk[sp] = make_int2(c[j], __float_as_int(key[j]));
-                                    ++sp;
-                                }
-                            }
-                            node = c[0];
-                            n0 = key[0];
-                            continue;
-                        }
-                    } else {
-                        const float4 *nd = sc.nodes + (size_t)node * kNodeF4;
-                        float4 q[3];
-#pragma unroll
-                        for (int k = 0; k < 3; ++k) q[k] = __ldg(nd + k);
-                        const int2 ch = __ldg(reinterpret_cast<const int2 *>(nd + 3));
-                        float a0, a1, b0, b1;
-                        node_child_boxes<3>(q, r, tmin, tmax, G, a0, a1, b0, b1);
-                        bool ha = a0 <= a1 && ch.x != kEmptyChild;
-                        bool hb = b0 <= b1 && ch.y != kEmptyChild;
-                        if (ha && a0 > bound) {
-                            ha = false;
-                            evicted = true;
-                            t_evict = fminf(t_evict, a0);
-                        }
-                        if (hb && b0 > bound) {
-                            hb = false;
-                            evicted = true;
-                            t_evict = fminf(t_evict, b0);
-                        }
-                        if (ha && hb) {
-                            const bool bfirst = b0 < a0;
-                            if (sp < kBvhStack) {
-                                stk[sp] = make_int2(bfirst ? ch.x : ch.y, __float_as_int(bfirst ? a0 : b0));
-                                ++sp;
-                            }
-                            node = bfirst ? ch.y : ch.x;
-                            n0 = bfirst ? b0 : a0;
-                            continue;
-                        }
-                        if (ha || hb) {
-                            node = ha ? ch.x : ch.y;
-                            n0 = ha ? a0 : b0;
-                            continue;
-                        }
-                    }
-                }
-                // pop the nearest pending subtree that can still add to the list
-                node = kDone;
-                while (sp > 0) {
-                    --sp;
-                    const int2 e = stk[sp];
-                    const float t0 = __int_as_float(e.y);
-                    if (cnt == C && t0 > kt[C - 1]) {
-                        evicted = true;
-                        t_evict = fminf(t_evict, t0);
-                        continue;
-                    }
-                    node = e.x;
-                    n0 = t0;
-                    break;
-                }
-            }
+            capped = !walk_candidates<STATS, BW>(sc, r, ro, rd, tmin, tmax, false, 0.0f, 0u, it, kt, kp, cnt, t_evict,
+                                                 evicted, nodes, culled, G);
         }
     }
     // the task: the candidates in list order in one run of the buffer; its cost class
@@ -410,6 +425,52 @@ __global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint3
     }
 }
 
+// The next candidates of a ray whose best hit may lie among those the candidate pass dropped: a walk of the
+// BVH by one lane for the kPairCands smallest keys above (lb_t, lb_p), the last listed, written to the ray's
+// candidate places.  The ray comes from the lane's task slot in shared memory (rs, strided).  Rare: rays
+// with more candidates than the list holds, whose best hit is not before the first dropped one.
+struct MoreCands {
+    int cnt;          // candidates written (0: none left)
+    float t_evict;    // smallest entry distance this walk dropped
+    bool evicted, capped;
+};
+template <int BW>
+__device__ __forceinline__ MoreCands collect_more(const DevScene sc, const float *rs, int stride, float lb_t,
+                                               uint32_t lb_p, uint32_t iter_cap, uint2 *dst)
+{
+    constexpr int C = kPairCands;
+    RayG<3> r;
+    float ro[3], rd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        ro[k] = r.org[k] = rs[k * stride];
+        r.inv[k] = rs[(3 + k) * stride];
+        rd[k] = rs[(9 + k) * stride];
+    }
+    float kt[C];
+    uint32_t kp[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        kt[j] = __int_as_float(0x7f800000);
+        kp[j] = kMissId;
+    }
+    MoreCands out;
+    out.cnt = 0;
+    out.t_evict = __int_as_float(0x7f800000);
+    out.evicted = false;
+    unsigned long long nodes = 0, culled = 0;
+    Grp G;
+    G.c = 0;
+    G.mask = 0xffffffffu;
+    G.l0 = G.l1 = G.l2 = threadIdx.x & 31;
+    uint32_t it = iter_cap;
+    out.capped = !walk_candidates<false, BW>(sc, r, ro, rd, rs[6 * stride], rs[7 * stride], true, lb_t, lb_p, it, kt, kp,
+                                             out.cnt, out.t_evict, out.evicted, nodes, culled, G);
+    if (!out.capped)
+        for (int j = 0; j < out.cnt; ++j) dst[j] = make_uint2(kp[j], __float_as_uint(kt[j]));
+    return out;
+}
+
 // ------------------------------------------------------------------------------------------------
 // Pass 3: Algorithm 3 over (ray, patch) pairs, one pair per lane.
 // ------------------------------------------------------------------------------------------------
@@ -463,7 +524,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
 
     // the lane's ray (task)
     bool has_task = false, exhausted = false, evicted = false;
-    uint32_t ray = 0, cur = 0, end = 0, ray_scene = 0, ray_local = 0, iters = 0;
+    uint32_t ray = 0, cur = 0, end = 0, cbase = 0, ray_scene = 0, ray_local = 0, iters = 0;
     uint2 nxt = make_uint2(0u, 0u);   // the ray's candidate at cur, loaded ahead
     typename Src::LaneScene lsc;
     Best best;
@@ -482,9 +543,9 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
     float g[48];
 
     for (;;) {
-        // (1) a lane whose pair has ended takes its ray's next candidate, or finishes the ray (its answer,
-        //     or the fallback when dropped candidates may still hold it); idle lanes take new rays from the
-        //     queue, then their first candidate
+        // (1) a lane whose pair has ended takes its ray's next candidate (collecting more when dropped
+        //     candidates may still hold the answer), or writes the ray's answer; idle lanes take new rays
+        //     from the queue, then their first candidate
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             if (has_task && !in_pair && !start) {
@@ -493,30 +554,50 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     start_pid = nxt.x;
                     ++cur;
                 } else {   // entries are sorted: the rest enter later still
-                    has_task = false;
-                    if (MODE == kModeAnyHit) {
-                        const bool occ = best.pid != kMissId;
-                        if (!occ && evicted)
-                            pb.fallback[atomicAdd(pb.ctr + kCtrFallback, 1u)] = ray;
-                        else
-                            occluded[ray_local] = occ ? 1 : 0;
-                    } else if (evicted && !(best.t < rs[8 * stride])) {
-                        pb.fallback[atomicAdd(pb.ctr + kCtrFallback, 1u)] = ray;
+                    // the answer may lie among the candidates the walk dropped (entries from t_evict on): this
+                    // lane collects the next ones, after the last listed, by a walk of its own
+                    bool finish = true;
+                    if (evicted && (MODE == kModeAnyHit ? best.pid == kMissId : !(best.t < rs[8 * stride]))) {
+                        const uint2 last = pb.cand[end - 1];
+                        const DevScene &sc = src.scene(lsc);
+                        const MoreCands mc =
+                            sc.width == 4
+                                ? collect_more<4>(sc, rs, stride, __uint_as_float(last.y), last.x, iter_cap, pb.cand + cbase)
+                                : collect_more<2>(sc, rs, stride, __uint_as_float(last.y), last.x, iter_cap, pb.cand + cbase);
                         if (STATS) cnt.v[10]++;
-                    } else {
-                        const DevHits &hh = src.hits_of(ray_scene);
-                        const uint32_t j = ray_local;
-                        if (best.pid != kMissId) {
-                            const uint32_t cu = best.cell & ((1u << L) - 1u), cv = best.cell >> L;
-                            hh.t[j] = best.t;
-                            hh.u[j] = ((float)cu + 0.5f) * cellw;
-                            hh.v[j] = ((float)cv + 0.5f) * cellw;
-                            hh.pid[j] = best.pid;
+                        evicted = mc.evicted;
+                        if (mc.capped) {   // iteration cap of the walk: a miss, status latched
+                            finish = false;
+                            has_task = false;
+                            atomicOr(status, 1u);
+                            write_miss<MODE>(src, ray_scene, ray_local, occluded);
+                        } else if (mc.cnt > 0) {
+                            finish = false;
+                            cur = cbase;
+                            end = cbase + (uint32_t)mc.cnt;
+                            nxt = pb.cand[cbase];
+                            rs[8 * stride] = mc.t_evict;
+                        }
+                    }
+                    if (finish) {   // the ray's answer
+                        has_task = false;
+                        if (MODE == kModeAnyHit) {
+                            occluded[ray_local] = best.pid != kMissId ? 1 : 0;
                         } else {
-                            hh.t[j] = kInf;
-                            hh.u[j] = 0.0f;
-                            hh.v[j] = 0.0f;
-                            hh.pid[j] = kMissId;
+                            const DevHits &hh = src.hits_of(ray_scene);
+                            const uint32_t j = ray_local;
+                            if (best.pid != kMissId) {
+                                const uint32_t cu = best.cell & ((1u << L) - 1u), cv = best.cell >> L;
+                                hh.t[j] = best.t;
+                                hh.u[j] = ((float)cu + 0.5f) * cellw;
+                                hh.v[j] = ((float)cv + 0.5f) * cellw;
+                                hh.pid[j] = best.pid;
+                            } else {
+                                hh.t[j] = kInf;
+                                hh.u[j] = 0.0f;
+                                hh.v[j] = 0.0f;
+                                hh.pid[j] = kMissId;
+                            }
                         }
                     }
                 }
@@ -540,6 +621,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 has_task = true;
                 ray = w0.x;
                 cur = w0.y;
+                cbase = w0.y;
                 end = w0.y + (w0.z & 255u);
                 evicted = (w0.z & kTaskEvicted) != 0u;
                 nxt = make_uint2(w1.x, w1.y);

@@ -1,9 +1,9 @@
 """The pair engine (CCS_TRACE_PAIRS): a BVH pass that keeps each ray's 8 nearest candidate patches (with
 local frames, only those whose root box in the patch frame the ray comes near), then a subdivision pass
-that runs Algorithm 3 on one (ray, patch) pair per lane, then the ray-persistent kernel over the rays whose
-dropped candidates could still hold the answer.  The answer is the smallest leaf key over all nested
-intervals (readings A14/A15), so every hit must be bit-identical to the ray-persistent kernel's, which the
-FP64 oracle pins; scenes with more than 8 candidate boxes along a ray drive the fallback."""
+that runs Algorithm 3 on one (ray, patch) pair per lane; a ray whose dropped candidates could still hold
+the answer has its lane walk the BVH again for the next ones.  The answer is the smallest leaf key over all
+nested intervals (readings A14/A15), so every hit must be bit-identical to the ray-persistent kernel's,
+which the FP64 oracle pins; scenes with more than 8 candidate boxes along a ray drive the second walks."""
 import numpy as np
 import pytest
 
@@ -65,8 +65,8 @@ def tunnel_scene(n_u=40, gregory_every=0):
 
 
 def tunnel_rays(n_u=40):
-    """Rays along the tunnel (reach the wall through the fallback), rays sloping down onto a U within its
-    first 16 patches (answered by the passes although candidates were dropped), rays straight down into
+    """Rays along the tunnel (they reach the wall after several walks for dropped candidates), rays sloping
+    down onto a U within the first 16 patches (answered within one or two lists), rays straight down into
     single U patches, and rays that leave the tunnel sideways."""
     o, d = [], []
     for z in np.linspace(0.05, 0.6, 12):
@@ -117,7 +117,7 @@ def test_pairs_match_oracle_on_primary_image_with_local_frames():
 
 @pytest.mark.parametrize("gregory_every", [0, 3])
 @pytest.mark.parametrize("width", [2, 4])
-def test_pairs_fallback_when_candidates_are_dropped(gregory_every, width):
+def test_pairs_walk_again_when_candidates_are_dropped(gregory_every, width):
     P, types = tunnel_scene(40, gregory_every)
     r = tunnel_rays(40)
     sc = ccs.Scene(P, types, bvh_width=width)
@@ -131,6 +131,7 @@ def test_pairs_fallback_when_candidates_are_dropped(gregory_every, width):
     cnt = torch.zeros(ccs.CCS_NUM_COUNTERS, dtype=torch.int64, device="cuda")
     run(sc, r, counters=cnt, pairs=True)
     assert int(cnt[7]) > 0 and int(cnt[1]) > 0
+    assert int(cnt[10]) >= 84   # the rays along the tunnel walked again for their dropped candidates
     sc.close()
 
 
