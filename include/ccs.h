@@ -135,8 +135,8 @@ typedef struct {
                                        class (a Gregory candidate first, then more candidates first);
                                        (3) persistent warps run Algorithm 3 on one (ray, patch) pair per
                                        lane, taking each ray's candidates in entry order until one enters
-                                       beyond its best hit, so that every warp iteration is one
-                                       subdivision step of up to 32 pairs; once the queue is empty, idle
+                                       beyond its best hit, so that every warp iteration is one or two
+                                       subdivision steps of up to 32 pairs; once the queue is empty, idle
                                        lanes take pending subtrees of busy lanes of their warp; (4) a ray
                                        whose dropped candidates could still hold the answer has its lane
                                        walk the BVH again for the next ones.  Hits are bit-identical.  Uses

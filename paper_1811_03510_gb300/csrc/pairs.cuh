@@ -12,8 +12,8 @@
 //     early and the launch does not end on a few of them.
 //  3. k_pairs: persistent warps take tasks in that order.  A lane runs Algorithm 3 on one (ray, patch) pair
 //     at a time, taking the ray's candidates in entry order and stopping at the first one that enters
-//     beyond the ray's best hit.  Every warp iteration is one subdivision step (Algorithm 3's loop body)
-//     of up to 32 pairs: the BVH walk, whose step count differs from ray to ray, is not in the loop.
+//     beyond the ray's best hit.  Every warp iteration is one or two subdivision steps (Algorithm 3's loop
+//     body) of up to 32 pairs: the BVH walk, whose step count differs from ray to ray, is not in the loop.
 //  4. A ray whose dropped candidates could still hold the answer (best hit not before t_evict) has its lane
 //     collect the next ones, those after the last listed, by a BVH walk of its own (collect_more), and goes
 //     on with them.
@@ -29,6 +29,7 @@ namespace ccs {
 
 constexpr int kPairCands = 8;            // candidates kept per ray (nearest entries)
 constexpr int kCandBlock = 128;          // threads of a candidate-pass block (its warps work independently)
+constexpr int kStepsPerIter = 2;         // subdivision steps per warp iteration of the subdivision pass
 constexpr int kCostClasses = 16;
 // counter words of a launch: the queue head, the tasks of each cost class
 constexpr int kCtrQueue = 3, kCtrHist = 16, kPairCtrWords = 64;
@@ -705,19 +706,19 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 cnt.v[16] += __popc(ki);
             }
         }
-        // (3) one subdivision step of every lane's pair
-        if (in_pair && !waiting) {
-            if (iters == 0 && helper) {   // iteration cap in a subtree: the owner's ray becomes a capped miss
+        // (3) subdivision steps of every lane's pair: the iteration cap first
+        if (in_pair && !waiting && iters == 0) {
+            if (helper) {   // iteration cap in a subtree: the owner's ray becomes a capped miss
                 atomicOr(status, 1u);
                 hcap[wbase + owner] = 1;
                 __threadfence_block();
                 atomicSub(hcount + wbase + owner, 1);
                 helper = false;
                 in_pair = false;
-            } else if (iters == 0 && hcount[threadIdx.x] > 0) {   // wait for the subtrees, then the cap
+            } else if (hcount[threadIdx.x] > 0) {   // wait for the subtrees, then the cap
                 hcap[threadIdx.x] = 1;
                 waiting = true;
-            } else if (iters == 0) {   // iteration cap: a miss, status latched
+            } else {   // iteration cap: a miss, status latched
                 has_task = false;
                 in_pair = false;
                 atomicOr(status, 1u);
@@ -730,7 +731,16 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     hh.v[ray_local] = 0.0f;
                     hh.pid[ray_local] = kMissId;
                 }
-            } else {
+            }
+        }
+        // up to kStepsPerIter steps (Algorithm 3's loop body) per warp iteration: after the first, the lanes
+        // whose pair keeps descending (no leaf, no backtrack, no Gregory bound due) step again, so that the
+        // divergent rest of the iteration is paid once for more steps
+        bool stepping = in_pair && !waiting && iters > 0, back = false;
+#pragma unroll 1
+        for (int pass = 0; pass < kStepsPerIter; ++pass) {
+            if (pass > 0 && !__any_sync(FULL, stepping)) break;
+            if (stepping) {
                 --iters;
                 if (gpend) {   // Algorithm 2 with the crop of Algorithm 1 for the Gregory node (path, level)
                     float u0, u1, v0, v1;
@@ -745,7 +755,6 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 if (STATS && !redesc) cnt.v[greg ? 2 : 1]++;
                 const StepOut so = split_step<K, 3>(g, pr, d, c0, c1, te, best.t, redesc || (!greg && !leafkids), scr,
                                                     slot, true, true, force, G, tau);
-                bool back = false;
                 if (redesc) {
                     if (++level == rd_target) rd_target = -1;
                 } else if (so.hitL || so.hitR) {
@@ -793,62 +802,63 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 } else {
                     back = true;
                 }
-                if (back) {   // the deepest pending sibling that may still hold a closer leaf, or the pair ends
-                    bool found = false;
-                    if (!(MODE == kModeAnyHit && best.pid != kMissId)) {
-                        while (trail != 0u) {
-                            const int l = 31 - __clz(trail);
-                            const uint32_t bit = 1u << l;
-                            trail ^= bit;
-                            bool cached = false;
-                            int cslot = 0;
-                            if (K > 0 && !greg && cvalid > 0) {
-                                cslot = (ctop - 1) % (K > 0 ? K : 1);
-                                if (scr.tag[cslot] == l) {
-                                    cached = true;
-                                    --ctop;
-                                    --cvalid;
-                                }
-                            }
-                            const float2 sb = scr.sib[l * stride];
-                            if (__fadd_rn(te, sb.x) > best.t) {
-                                if (STATS) cnt.v[6]++;
-                                continue;
-                            }
-                            path = (path & (bit - 1u)) | (~path & bit);
-                            c0 = sb.x;
-                            c1 = sb.y;
-                            if (STATS) cnt.v[4]++;
-                            if (greg) {
-                                level = l + 1;
-                                gpend = true;
-                            } else if (cached) {
-                                level = l + 1;
-                                load_cached<3>(scr.cache + cslot * 48, g);
-                            } else {
-                                if (STATS) cnt.v[5] += l + 1;
-                                level = 0;
-                                rd_target = l + 1;
-                                want_root = true;
-                            }
-                            found = true;
-                            break;
+                stepping = !back && !gpend && iters > 0;
+            }
+        }
+        if (back) {   // the deepest pending sibling that may still hold a closer leaf, or the pair ends
+            bool found = false;
+            if (!(MODE == kModeAnyHit && best.pid != kMissId)) {
+                while (trail != 0u) {
+                    const int l = 31 - __clz(trail);
+                    const uint32_t bit = 1u << l;
+                    trail ^= bit;
+                    bool cached = false;
+                    int cslot = 0;
+                    if (K > 0 && !greg && cvalid > 0) {
+                        cslot = (ctop - 1) % (K > 0 ? K : 1);
+                        if (scr.tag[cslot] == l) {
+                            cached = true;
+                            --ctop;
+                            --cvalid;
                         }
+                    }
+                    const float2 sb = scr.sib[l * stride];
+                    if (__fadd_rn(te, sb.x) > best.t) {
+                        if (STATS) cnt.v[6]++;
+                        continue;
+                    }
+                    path = (path & (bit - 1u)) | (~path & bit);
+                    c0 = sb.x;
+                    c1 = sb.y;
+                    if (STATS) cnt.v[4]++;
+                    if (greg) {
+                        level = l + 1;
+                        gpend = true;
+                    } else if (cached) {
+                        level = l + 1;
+                        load_cached<3>(scr.cache + cslot * 48, g);
                     } else {
-                        cur = end;   // any hit: the ray is answered
+                        if (STATS) cnt.v[5] += l + 1;
+                        level = 0;
+                        rd_target = l + 1;
+                        want_root = true;
                     }
-                    if (!found) {
-                        if (helper) {   // the subtree is searched: its best leaf to the owner's mailbox
-                            if (best.pid == pid)
-                                atomicMin(mbox + wbase + owner, ((unsigned long long)ord_bits(best.t) << 32) | best.cell);
-                            __threadfence_block();
-                            atomicSub(hcount + wbase + owner, 1);
-                            helper = false;
-                            in_pair = false;
-                        } else {
-                            waiting = true;   // merged when every subtree handed out is searched
-                        }
-                    }
+                    found = true;
+                    break;
+                }
+            } else {
+                cur = end;   // any hit: the ray is answered
+            }
+            if (!found) {
+                if (helper) {   // the subtree is searched: its best leaf to the owner's mailbox
+                    if (best.pid == pid)
+                        atomicMin(mbox + wbase + owner, ((unsigned long long)ord_bits(best.t) << 32) | best.cell);
+                    __threadfence_block();
+                    atomicSub(hcount + wbase + owner, 1);
+                    helper = false;
+                    in_pair = false;
+                } else {
+                    waiting = true;   // merged when every subtree handed out is searched
                 }
             }
         }

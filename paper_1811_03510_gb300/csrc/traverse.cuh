@@ -427,6 +427,21 @@ CCS_DEV void extend(float &lo, float &hi, float tau)
     }
 }
 
+// Minimum and maximum of 16 values in 8 operations (three-input min/max; exact, so the grouping does not
+// change the result).
+CCS_DEV float min16(float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7, float a8,
+                    float a9, float a10, float a11, float a12, float a13, float a14, float a15)
+{
+    return fminf(min3f(min3f(a0, a1, a2), min3f(a3, a4, a5), min3f(a6, a7, a8)),
+                 min3f(min3f(a9, a10, a11), min3f(a12, a13, a14), a15));
+}
+CCS_DEV float max16(float a0, float a1, float a2, float a3, float a4, float a5, float a6, float a7, float a8,
+                    float a9, float a10, float a11, float a12, float a13, float a14, float a15)
+{
+    return fmaxf(max3f(max3f(a0, a1, a2), max3f(a3, a4, a5), max3f(a6, a7, a8)),
+                 max3f(max3f(a9, a10, a11), max3f(a12, a13, a14), a15));
+}
+
 template <int K, int NC>
 CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (&d)[NC], float c0, float c1, float te,
                            float tb, bool keep_grid, const Scratch &sc, int cache_slot, bool allowL, bool allowR,
@@ -436,7 +451,6 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
     float lmin[NC], lmax[NC], rmin[NC], rmax[NC];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
-        float cl[4], cL[4], cr[4], cR[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int q = c * 4 + b;
@@ -450,15 +464,21 @@ CCS_DEV StepOut split_step(float (&g)[16 * NC], const RayG<NC> &r, const float (
             m012[q] = mid(m01[q], m12);
             m123[q] = mid(m12, m23[q]);
             mm[q] = mid(m012[q], m123[q]);
-            cl[b] = min3f(b0, m01[q], fminf(m012[q], mm[q]));   // per column, then a tree over columns
-            cL[b] = max3f(b0, m01[q], fmaxf(m012[q], mm[q]));
-            cr[b] = min3f(mm[q], m123[q], fminf(m23[q], b3));
-            cR[b] = max3f(mm[q], m123[q], fmaxf(m23[q], b3));
         }
-        lmin[c] = fminf(min3f(cl[0], cl[1], cl[2]), cl[3]);
-        lmax[c] = __fadd_rn(fmaxf(max3f(cL[0], cL[1], cL[2]), cL[3]), d[c]);
-        rmin[c] = fminf(min3f(cr[0], cr[1], cr[2]), cr[3]);
-        rmax[c] = __fadd_rn(fmaxf(max3f(cR[0], cR[1], cR[2]), cR[3]), d[c]);
+        // the lower half's 16 points (b0, m01, m012, mm of each column) and the upper half's (mm, m123, m23, b3)
+        const int q = c * 4;
+        lmin[c] = min16(e0[q], m01[q], m012[q], mm[q], e0[q + 1], m01[q + 1], m012[q + 1], mm[q + 1], e0[q + 2],
+                        m01[q + 2], m012[q + 2], mm[q + 2], e0[q + 3], m01[q + 3], m012[q + 3], mm[q + 3]);
+        lmax[c] = __fadd_rn(max16(e0[q], m01[q], m012[q], mm[q], e0[q + 1], m01[q + 1], m012[q + 1], mm[q + 1],
+                                  e0[q + 2], m01[q + 2], m012[q + 2], mm[q + 2], e0[q + 3], m01[q + 3], m012[q + 3],
+                                  mm[q + 3]),
+                            d[c]);
+        rmin[c] = min16(mm[q], m123[q], m23[q], e3[q], mm[q + 1], m123[q + 1], m23[q + 1], e3[q + 1], mm[q + 2],
+                        m123[q + 2], m23[q + 2], e3[q + 2], mm[q + 3], m123[q + 3], m23[q + 3], e3[q + 3]);
+        rmax[c] = __fadd_rn(max16(mm[q], m123[q], m23[q], e3[q], mm[q + 1], m123[q + 1], m23[q + 1], e3[q + 1],
+                                  mm[q + 2], m123[q + 2], m23[q + 2], e3[q + 2], mm[q + 3], m123[q + 3], m23[q + 3],
+                                  e3[q + 3]),
+                            d[c]);
     }
     if (tau > 0.0f) {
 #pragma unroll
