@@ -98,10 +98,13 @@ typedef struct {
                                  method parameter, not a launch option); one lane per ray.  [0] */
     uint32_t flags;           /* CCS_TRACE_* bits */
     uint64_t *counters;       /* optional device array of CCS_NUM_COUNTERS uint64 (CCS_TRACE_COUNT) */
-    uint32_t image_width;     /* CCS_TRACE_ORDER: the rays are an image of this width, ray y * width + x
-                                 (the last row may be partial), ordered in tiles of 8 x 8 pixels with
+    uint32_t image_width;     /* the rays are an image of this width, ray y * width + x (the last row may
+                                 be partial).  CCS_TRACE_ORDER: ordered in tiles of 8 x 8 pixels with
                                  every 4th pixel in x and y sampled; 0: tiles of 32 consecutive rays,
-                                 every 4th ray sampled [0] */
+                                 every 4th ray sampled.  CCS_TRACE_PAIRS, a multiple of 8: each warp of
+                                 the candidate pass takes a tile of 8 x 4 pixels (a host chunk is tiled
+                                 from its own first ray); else 32 consecutive rays.  Never changes the
+                                 answer [0] */
     uint32_t bvh_width;       /* the scene's BVH to traverse: 0 its default, 2 or 4 (INVALID_ARG when the
                                  scene was not built with that width) [0] */
     uint32_t host_chunk;      /* ccs_intersect_host: rays per chunk of its copy/trace pipeline, at most 8

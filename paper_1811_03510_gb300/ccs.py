@@ -210,7 +210,8 @@ def make_opts(leaf_depth=8, block_threads=0, blocks_per_sm=0, refill=0, chunk=0,
               host_mapped=False, bvh_width=0, pairs=False) -> ccs_trace_opts:
     """ccs_trace_opts with the fields of include/ccs.h (0: the library's default).  counters: a device
     int64 tensor of CCS_NUM_COUNTERS entries (sets CCS_TRACE_COUNT); order: CCS_TRACE_ORDER over tiles of
-    an image of width image_width (0: runs of 32 rays); host_mapped: CCS_TRACE_HOST_MAPPED; pairs:
+    an image of width image_width (0: runs of 32 rays; the pair engine's candidate pass also takes 8 x 4
+    pixel tiles of it when the width is a multiple of 8); host_mapped: CCS_TRACE_HOST_MAPPED; pairs:
     CCS_TRACE_PAIRS (the pair engine)."""
     o = ccs_trace_opts()
     o.leaf_depth = leaf_depth

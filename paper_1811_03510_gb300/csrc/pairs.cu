@@ -51,8 +51,11 @@ template <bool STATS, int MODE, class Src, int BW>
 cudaError_t launch_cand(const Src &src, const PairBufs &pb, const LaunchCfg &cfg, uint32_t n, uint32_t *status,
                         cudaStream_t s)
 {
-    k_cand<STATS, MODE, Src, BW><<<(n + kCandBlock - 1) / kCandBlock, kCandBlock, 0, s>>>(
-        src, pb, cfg.iter_cap, status, cfg.counters, cfg.mc.occluded);
+    // 8 x 4 pixel tiles per warp when the rays are an image whose width is a multiple of 8
+    const uint32_t img_w = (cfg.image_width & 7u) == 0u ? cfg.image_width : 0u;
+    const uint32_t t = cand_threads(n, img_w);
+    k_cand<STATS, MODE, Src, BW><<<(t + kCandBlock - 1) / kCandBlock, kCandBlock, 0, s>>>(
+        src, pb, img_w, cfg.iter_cap, status, cfg.counters, cfg.mc.occluded);
     return cudaGetLastError();
 }
 

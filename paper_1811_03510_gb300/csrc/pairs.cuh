@@ -328,14 +328,32 @@ CCS_DEV bool walk_candidates(const DevScene &sc, const RayG<3> &r, const float (
     return true;
 }
 
+// The ray of candidate-pass thread t.  With img_w > 0 (a multiple of 8) the rays are an image of that width,
+// ray y * img_w + x, and each warp takes a tile of 8 x 4 pixels, whose rays walk more of the same BVH nodes
+// than a row of 32; the threads then cover whole bands of 4 rows (cand_threads), and those past the last ray
+// have none.  A bijection of [0, cand_threads) onto the same range either way.
+CCS_DEV uint32_t cand_ray(uint32_t t, uint32_t img_w)
+{
+    if (img_w == 0u) return t;
+    const uint32_t w = t >> 5, l = t & 31u, tiles_x = img_w >> 3;
+    const uint32_t ty = w / tiles_x, tx = w - ty * tiles_x;
+    return (ty * 4u + (l >> 3)) * img_w + tx * 8u + (l & 7u);
+}
+inline uint32_t cand_threads(uint32_t n, uint32_t img_w)
+{
+    if (img_w == 0u) return n;
+    const uint64_t band = 4ull * img_w;
+    return (uint32_t)((n + band - 1) / band * band);
+}
+
 template <bool STATS, int MODE, class Src, int BW>
-__global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint32_t iter_cap, uint32_t *status,
-                                              unsigned long long *counters, uint8_t *occluded)
+__global__ void __launch_bounds__(kCandBlock) k_cand(Src src, PairBufs pb, uint32_t img_w, uint32_t iter_cap,
+                                              uint32_t *status, unsigned long long *counters, uint8_t *occluded)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const uint32_t n = src.total();
-    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t i = cand_ray(blockIdx.x * blockDim.x + threadIdx.x, img_w);
     constexpr int C = kPairCands;
     const float kInf = __int_as_float(0x7f800000);
     float kt[C];

@@ -115,6 +115,36 @@ def test_pairs_match_oracle_on_primary_image_with_local_frames():
     sc.close()
 
 
+def test_pairs_candidate_pass_in_image_tiles():
+    """With image_width a multiple of 8 the candidate pass gives each warp an 8 x 4 pixel tile: the threads
+    cover whole bands of 4 rows, those past the last ray (a ragged band, a partial last row, a host chunk
+    that starts mid-row) have none, and every ray is traced once with the same answer."""
+    s = sg.config_scene(2)
+    r = sg.pinhole_rays(336, 211)   # 211 rows: the last band holds 3
+    sc = ccs.Scene(s.P, s.types, local=True)
+    ref = run(sc, r)
+    assert (ref["pid"] != MISS).sum() > 10000
+    for w in (336, 8, 333, 0):   # 333 is not a multiple of 8: rays in their own order
+        same(run(sc, r, pairs=True, cache_slots=1, image_width=w), ref, w)
+    # a partial last row: the first n - 5 rays, the rest of the hit planes untouched
+    m = r.n - 5
+    rays = ccs.rays_to_device(r.soa())
+    hits = [torch.full((r.n,), -7.0, device="cuda") for _ in range(3)] + \
+        [torch.full((r.n,), 0x5A5A5A5A, dtype=torch.int32, device="cuda")]
+    ccs.ccs_intersect(sc.handle, rays, m, hits, ccs.make_opts(pairs=True, image_width=336))
+    torch.cuda.synchronize()
+    got = ccs.hits_to_numpy(hits)
+    same({k: v[:m] for k, v in got.items()}, {k: v[:m] for k, v in ref.items()}, "partial row")
+    assert (got["t"][m:] == -7.0).all() and (got["pid"][m:] == 0x5A5A5A5A).all()
+    # host chunks of 20,000 rays: each chunk is tiled from its own first ray
+    planes = [np.ascontiguousarray(a) for a in r.soa()]
+    out = [np.empty(r.n, np.float32) for _ in range(3)] + [np.empty(r.n, np.uint32)]
+    ccs.ccs_intersect_host(sc.handle, [a.ctypes.data for a in planes], r.n, [a.ctypes.data for a in out],
+                           ccs.make_opts(pairs=True, image_width=336, host_chunk=20000))
+    same(dict(t=out[0], u=out[1], v=out[2], pid=out[3]), ref, "host chunks")
+    sc.close()
+
+
 @pytest.mark.parametrize("gregory_every", [0, 3])
 @pytest.mark.parametrize("width", [2, 4])
 def test_pairs_walk_again_when_candidates_are_dropped(gregory_every, width):
