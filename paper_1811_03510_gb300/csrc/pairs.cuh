@@ -72,11 +72,11 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
 }
 
 // Shared memory of a k_pairs thread after its traversal scratch: the world ray of its task (origin,
-// 1 / direction, tmin, tmax), t_evict and the direction, read when a pair starts and when the ray ends; then
-// the
-// thread's mailbox for the subtrees it handed to other lanes (the smallest (t, cell) key they found,
+// 1 / direction, tmin, tmax), t_evict and the direction, read when a pair starts and when the ray ends, and
+// the first and end places of the task's candidates (kept here, not in registers, so that the 1-slot sibling
+// cache variant does not spill); then the thread's mailbox for the subtrees it handed to other lanes (the smallest (t, cell) key they found,
 // 64 bits), the number of them still running, and a flag for one that reached the iteration cap.
-constexpr int kRaySlotFloats = 12, kHelpFloats = 4;
+constexpr int kRaySlotFloats = 14, kHelpFloats = 4;
 // A subtree is handed to an idle lane when it has at least this many levels below its root.
 constexpr int kMinDonateLevels = 4;
 
@@ -543,7 +543,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
 
     // the lane's ray (task)
     bool has_task = false, exhausted = false, evicted = false;
-    uint32_t ray = 0, cur = 0, end = 0, cbase = 0, ray_scene = 0, ray_local = 0, iters = 0;
+    uint32_t ray = 0, cur = 0, ray_scene = 0, ray_local = 0, iters = 0;
     uint2 nxt = make_uint2(0u, 0u);   // the ray's candidate at cur, loaded ahead
     typename Src::LaneScene lsc;
     Best best;
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
 #pragma unroll 1
         for (int pass = 0; pass < 2; ++pass) {
             if (has_task && !in_pair && !start) {
-                if (cur < end && __uint_as_float(nxt.y) <= best.t) {
+                if (cur < __float_as_uint(rs[13 * stride]) && __uint_as_float(nxt.y) <= best.t) {
                     start = true;
                     start_pid = nxt.x;
                     ++cur;
@@ -577,7 +577,8 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     // lane collects the next ones, after the last listed, by a walk of its own
                     bool finish = true;
                     if (evicted && (MODE == kModeAnyHit ? best.pid == kMissId : !(best.t < rs[8 * stride]))) {
-                        const uint2 last = pb.cand[end - 1];
+                        const uint2 last = pb.cand[__float_as_uint(rs[13 * stride]) - 1];
+                        const uint32_t cbase = __float_as_uint(rs[12 * stride]);
                         const DevScene &sc = src.scene(lsc);
                         const MoreCands mc =
                             sc.width == 4
@@ -593,7 +594,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                         } else if (mc.cnt > 0) {
                             finish = false;
                             cur = cbase;
-                            end = cbase + (uint32_t)mc.cnt;
+                            rs[13 * stride] = __uint_as_float(cbase + (uint32_t)mc.cnt);
                             nxt = pb.cand[cbase];
                             rs[8 * stride] = mc.t_evict;
                         }
@@ -640,8 +641,8 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                 has_task = true;
                 ray = w0.x;
                 cur = w0.y;
-                cbase = w0.y;
-                end = w0.y + (w0.z & 255u);
+                rs[12 * stride] = __uint_as_float(w0.y);
+                rs[13 * stride] = __uint_as_float(w0.y + (w0.z & 255u));
                 evicted = (w0.z & kTaskEvicted) != 0u;
                 nxt = make_uint2(w1.x, w1.y);
                 rs[0 * stride] = __uint_as_float(w2.x);
@@ -666,7 +667,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
         //     frame, and (Bezier) the root grid
         if (start) {
             start = false;
-            if (cur < end) nxt = pb.cand[cur];
+            if (cur < __float_as_uint(rs[13 * stride])) nxt = pb.cand[cur];
             const DevScene &sc = src.scene(lsc);
             pid = start_pid;
             const float4 *rec = rec_of(sc, pid);
@@ -865,7 +866,7 @@ __global__ void __launch_bounds__(128, 3) k_pairs(Src src, PairBufs pb, int L, u
                     break;
                 }
             } else {
-                cur = end;   // any hit: the ray is answered
+                cur = __float_as_uint(rs[13 * stride]);   // any hit: the ray is answered
             }
             if (!found) {
                 if (helper) {   // the subtree is searched: its best leaf to the owner's mailbox
