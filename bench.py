@@ -884,6 +884,10 @@ def main():
     # launches overlapping the end of the primary one; staged: one ccs_intersect_host call per batch, copies
     # through device buffers in chunks overlapping the traversal; mapped: one call per batch, the launch
     # reads rays and writes hits through the page-locked memory's device mapping)
+    # (the plane pointers go into the C structs once, as a caller that traces the same buffers every frame
+    # would keep them)
+    rs_p, rs_d = ccs.rays_struct(host_p), ccs.rays_struct(host_d)
+    hs_p, hs_d = ccs.hits_struct(out_p), ccs.hits_struct(out_d)
     e2e = {}
     for name, mapped, one in (("one_pipeline", False, True), ("staged_copies", False, False), ("mapped", True, False)):
         op = ccs.make_opts(**ccs.opts_dict(opts_p), host_mapped=mapped)
@@ -891,11 +895,11 @@ def main():
 
         def step():
             if one:
-                ccs.ccs_intersect_host_batches(scene.handle, [host_p, host_d], [n_prim, n_diff], [out_p, out_d],
+                ccs.ccs_intersect_host_batches(scene.handle, [rs_p, rs_d], [n_prim, n_diff], [hs_p, hs_d],
                                                [op, od], stream)
             else:
-                ccs.ccs_intersect_host(scene.handle, host_p, n_prim, out_p, op, stream)
-                ccs.ccs_intersect_host(scene.handle, host_d, n_diff, out_d, od, stream)
+                ccs.ccs_intersect_host(scene.handle, rs_p, n_prim, hs_p, op, stream)
+                ccs.ccs_intersect_host(scene.handle, rs_d, n_diff, hs_d, od, stream)
         for _ in range(2):
             step()
         te = []
@@ -906,6 +910,10 @@ def main():
             step()
             te.append(time.perf_counter() - t0)
         e2e[name] = whole_job_rate(rays_per_step, args.steps, max_over_ranks(sum(te), dev), world)
+        # the host path gives the device-resident step's hits, bit for bit
+        for outs, dev_h in ((out_p, hits_p), (out_d, hits_d)):
+            for a, b in zip(outs, dev_h):
+                assert torch.equal(a.view(torch.int32), b.cpu().view(torch.int32)), f"{name}: hits differ"
     e2e_value = e2e["one_pipeline"]
 
     # the same step with the sub-domain boxes in world axes (Algorithm 3 as printed, without Sec. 3.4's local

@@ -59,6 +59,7 @@ void free_scene(ccs_scene *s)
     cudaFree(s->d_stage);
     for (cudaEvent_t e : s->pipe_ev)
         if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : s->pipe_chunk_ev) cudaEventDestroy(e);
     for (cudaStream_t q : {s->pipe_h2d, s->pipe_d2h, s->pipe_comp})
         if (q) cudaStreamDestroy(q);
     delete s;
@@ -155,12 +156,15 @@ struct HostBatch {
 
 // The staged copy/trace pipeline of the host-buffer entry points, over the chunks of one or more batches
 // in order: chunk k's rays are copied in while chunk k-1 is traced and chunk k-2's hits are copied out.
-// Consecutive chunks alternate between the caller's stream and a second compute stream, each with its own
-// queue head, so that one chunk's launch fills the SMs that the previous one frees while its last rays
-// finish; across batches the same holds, so one batch's copies and launch overlap the end of the last.
+// Every chunk's copy in is queued first, so that the copy engine never waits for the host to queue a
+// launch.  Consecutive chunks alternate between the caller's stream and a second compute stream, each
+// launch with its own queue head, so that one chunk's launch fills the SMs that the previous one frees
+// while its last rays finish; across batches the same holds, so one batch's copies and launch overlap the
+// end of the last.  (A third compute stream measured the same.)
 // Chunks stay large: every launch ends on its slowest rays, and many small chunks pay that drain more
-// often than they save in exposed copy time.  An image's chunk boundaries fall on rows of 8-pixel tiles,
-// so that each chunk is an image too.  Batch j stages its twelve planes (eight of rays, four of hits) at
+// often than they save in exposed copy time.  An image's chunk boundaries fall on rows of 8-pixel tiles
+// of the work order, or on the bands of 4 rows of the pair engine's candidate pass, so that each chunk is
+// an image too.  Batch j stages its twelve planes (eight of rays, four of hits) at
 // 12 * (rays of the batches before it) floats into the scene's staging buffer.
 ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaStream_t s)
 {
@@ -191,15 +195,21 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
         const LaunchCfg &c = bt[j].cfg;
         ns[j] = bt[j].n;
         hc[j] = c.host_chunk;
-        // the pair engine pays a launch's drain once per chunk: a batch under 2^19 rays goes in one chunk
-        if (!hc[j] && use_pairs(c) && ns[j] < (1u << 19)) hc[j] = ns[j];
-        align[j] = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8 : 1;
+        // the pair engine pays a launch's drain once per chunk: a batch under 2^19 rays goes in one chunk;
+        // chunk boundaries fall on its candidate pass's bands of 4 image rows
+        const bool pairs = use_pairs(c);
+        if (!hc[j] && pairs && ns[j] < (1u << 19)) hc[j] = ns[j];
+        align[j] = (c.flags & CCS_TRACE_ORDER) && c.image_width ? (size_t)c.image_width * 8
+                   : pairs && c.image_width && (c.image_width & 7u) == 0 ? (size_t)c.image_width * 4
+                                                                        : 1;
     }
     const std::vector<HostChunk> chunks = host_batch_chunks(nb, ns.data(), hc.data(), align.data());
-    // events: [0] start, [1] end of the copies out, then pairs (input copied, hits written) that chunks
-    // take in turn: every record is waited on before the pair comes round again, and a wait holds the
-    // work the event captured when it was issued
-    constexpr size_t kPairs = (sizeof(sc->pipe_ev) / sizeof(sc->pipe_ev[0]) - 2) / 2;
+    // events: start, end of the copies out, and a pair per chunk (input copied, hits written)
+    while (sc->pipe_chunk_ev.size() < 2 * chunks.size()) {
+        cudaEvent_t e;
+        CCS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        sc->pipe_chunk_ev.push_back(e);
+    }
     const cudaEvent_t ev_start = sc->pipe_ev[0], ev_out = sc->pipe_ev[1];
     CCS_CUDA(cudaEventRecord(ev_start, s));
     for (cudaStream_t q : {sc->pipe_h2d, sc->pipe_d2h, sc->pipe_comp}) CCS_CUDA(cudaStreamWaitEvent(q, ev_start, 0));
@@ -222,14 +232,13 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
         out_pitch[j] = stride_of(dstv, 4, bt[j].n);
     }
     float *stage = static_cast<float *>(sc->d_stage);
+    // (1) every chunk's rays in, in order
     for (size_t k = 0; k < chunks.size(); ++k) {
         const HostChunk &ck = chunks[k];
         const HostBatch &B = bt[ck.j];
         const size_t n = B.n, a = ck.a, m = ck.m;
         float *b = stage + base[ck.j];
         const float *src[8] = {B.hr->ox, B.hr->oy, B.hr->oz, B.hr->dx, B.hr->dy, B.hr->dz, B.hr->tmin, B.hr->tmax};
-        void *dst[4] = {B.hh->t, B.hh->u, B.hh->v, B.hh->patch_id};
-        const cudaEvent_t ev_in = sc->pipe_ev[2 + 2 * (k % kPairs)], ev_hit = sc->pipe_ev[3 + 2 * (k % kPairs)];
         // (equally spaced planes of separate allocations are refused by the runtime at the call, with
         // nothing enqueued; the copies then go plane by plane)
         if (in_pitch[ck.j] && cudaMemcpy2DAsync(b + a, n * 4, src[0] + a, in_pitch[ck.j], m * 4, 8,
@@ -241,9 +250,18 @@ ccs_status host_pipeline(ccs_scene *sc, const HostBatch *bt, uint32_t nb, cudaSt
             for (int c = 0; c < 8; ++c)
                 CCS_CUDA(cudaMemcpyAsync(b + c * n + a, src[c] + a, m * 4, cudaMemcpyHostToDevice, sc->pipe_h2d));
         }
-        CCS_CUDA(cudaEventRecord(ev_in, sc->pipe_h2d));
+        CCS_CUDA(cudaEventRecord(sc->pipe_chunk_ev[2 * k], sc->pipe_h2d));
+    }
+    // (2) the launches, each chunk's hits out after its launch
+    for (size_t k = 0; k < chunks.size(); ++k) {
+        const HostChunk &ck = chunks[k];
+        const HostBatch &B = bt[ck.j];
+        const size_t n = B.n, a = ck.a, m = ck.m;
+        float *b = stage + base[ck.j];
+        void *dst[4] = {B.hh->t, B.hh->u, B.hh->v, B.hh->patch_id};
+        const cudaEvent_t ev_hit = sc->pipe_chunk_ev[2 * k + 1];
         cudaStream_t cs = (k & 1) ? sc->pipe_comp : s;
-        CCS_CUDA(cudaStreamWaitEvent(cs, ev_in, 0));
+        CCS_CUDA(cudaStreamWaitEvent(cs, sc->pipe_chunk_ev[2 * k], 0));
         const DevRays dr{b + a, b + n + a, b + 2 * n + a, b + 3 * n + a, b + 4 * n + a, b + 5 * n + a,
                          b + 6 * n + a, b + 7 * n + a};
         const DevHits dh{b + 8 * n + a, b + 9 * n + a, b + 10 * n + a, reinterpret_cast<uint32_t *>(b + 11 * n + a)};

@@ -168,7 +168,8 @@ struct ccs_scene {
     void *d_stage = nullptr;
     size_t stage_bytes = 0;
     cudaStream_t pipe_h2d = nullptr, pipe_d2h = nullptr, pipe_comp = nullptr;
-    cudaEvent_t pipe_ev[2 * 8 + 2] = {};   // per chunk: input copied, hits written; start; end of the copies out
+    cudaEvent_t pipe_ev[2] = {};             // start; end of the copies out
+    std::vector<cudaEvent_t> pipe_chunk_ev;  // per chunk of a call: input copied, hits written (grown on use)
 };
 
 namespace ccs {
