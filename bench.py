@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ccs", choices=["ccs", "reference"])
     ap.add_argument("--variant", default="all", choices=["all", "plain", "batched", "learned"])
-    ap.add_argument("--train-seeds", type=int, default=3, help="scenes (seeds 2..) whose traces train the proposal")
+    ap.add_argument("--train-seeds", type=int, default=15,
+                    help="scenes (seeds 2..) whose traces train the proposal (until 4.5 M traces: 4 M to train on, "
+                         "the rest held out)")
     ap.add_argument("--frames", type=int, default=8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="default launch options (profiling runs)")
@@ -616,7 +618,7 @@ def run_learned(args, dev, stream, scene, s, prim, diff, opts_p, opts_d):
     import torch
     from paper_1811_03510_gb300 import ccs, scenegen as sg
     t_setup = time.perf_counter()
-    cap = 4_000_000
+    cap = 4_500_000   # 4 M (ray, patch, hit cell) traces to train on, one tenth more held out
     feat = torch.empty(cap, 24, device=dev)
     lab = torch.empty(cap, dtype=torch.uint8, device=dev)
     cnt = torch.zeros(1, dtype=torch.int32, device=dev)

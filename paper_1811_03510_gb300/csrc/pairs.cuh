@@ -77,6 +77,9 @@ inline PairBufs pair_bufs_at(void *base, uint32_t n)
 // cache variant does not spill); then the thread's mailbox for the subtrees it handed to other lanes (the smallest (t, cell) key they found,
 // 64 bits), the number of them still running, and a flag for one that reached the iteration cap.
 constexpr int kRaySlotFloats = 14, kHelpFloats = 4;
+// the per-thread helper area must hold the mailbox and the two counters k_pairs places there
+static_assert(kHelpFloats * sizeof(float) >= sizeof(unsigned long long) + 2 * sizeof(int),
+              "the helper area of a k_pairs thread is smaller than its mailbox and counters");
 // A subtree is handed to an idle lane when it has at least this many levels below its root.
 constexpr int kMinDonateLevels = 4;
 
