@@ -46,10 +46,11 @@ struct BatchSource {
     const uint32_t *ray_prefix;   // n_scenes + 1
     uint32_t n_scenes, n;
     struct LaneScene {
-        DevScene sc;
+        uint32_t s = 0;   // the scene of the lane's ray: its descriptor is read from the table where used, so
+                          // that a lane does not hold a copy of it in registers
     };
     CCS_DEV uint32_t total() const { return n; }
-    CCS_DEV const DevScene &scene(const LaneScene &l) const { return l.sc; }
+    CCS_DEV const DevScene &scene(const LaneScene &l) const { return entries[l.s].sc; }
     CCS_DEV void locate(uint32_t i, LaneScene &lsc, uint32_t &scene, uint32_t &local) const
     {
         uint32_t lo = 0, hi = n_scenes;   // largest s with ray_prefix[s] <= i
@@ -59,7 +60,7 @@ struct BatchSource {
         }
         scene = lo;
         local = i - __ldg(ray_prefix + lo);
-        lsc.sc = entries[lo].sc;
+        lsc.s = lo;
     }
     CCS_DEV const DevRays &rays_of(uint32_t s) const { return entries[s].rays; }
     CCS_DEV const DevHits &hits_of(uint32_t s) const { return entries[s].hits; }

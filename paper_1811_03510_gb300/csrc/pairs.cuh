@@ -92,16 +92,11 @@ CCS_DEV uint32_t ord_bits(float t)
 CCS_DEV float unord_bits(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k); }
 
 // The scene of a lane's pair, handed from lane `from` to the lanes that take one of its subtrees (a batch
-// lane carries its scene; one scene is the launch's).
+// lane carries its scene's index; one scene is the launch's).
 template <class Src>
 CCS_DEV void share_scene(typename Src::LaneScene &l, int from)
 {
-    if constexpr (std::is_same<Src, BatchSource>::value) {
-        const unsigned long long r = reinterpret_cast<unsigned long long>(l.sc.rec);
-        const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)r, from);
-        const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(r >> 32), from);
-        l.sc.rec = reinterpret_cast<const float4 *>(((unsigned long long)hi << 32) | lo);
-    }
+    if constexpr (std::is_same<Src, BatchSource>::value) l.s = __shfl_sync(0xffffffffu, l.s, from);
 }
 
 CCS_DEV bool cand_less(float ta, uint32_t pa, float tb, uint32_t pb) { return ta < tb || (ta == tb && pa < pb); }
