@@ -136,6 +136,10 @@ def test_pairs_candidate_pass_in_image_tiles():
     got = ccs.hits_to_numpy(hits)
     same({k: v[:m] for k, v in got.items()}, {k: v[:m] for k, v in ref.items()}, "partial row")
     assert (got["t"][m:] == -7.0).all() and (got["pid"][m:] == 0x5A5A5A5A).all()
+    # the any-hit query takes the same tiles: occlusion equals the closest hit's answer
+    occ = ccs.occluded(sc, rays, ccs.make_opts(pairs=True, image_width=336))
+    torch.cuda.synchronize()
+    assert np.array_equal(occ.cpu().numpy().astype(bool), ref["pid"] != MISS)
     # host chunks of 20,000 rays: each chunk is tiled from its own first ray
     planes = [np.ascontiguousarray(a) for a in r.soa()]
     out = [np.empty(r.n, np.float32) for _ in range(3)] + [np.empty(r.n, np.uint32)]
@@ -244,6 +248,12 @@ def test_pairs_batched_and_graph_replay_equal_single_scenes():
     for h, rf, r in zip(hits, ref, rays):
         if r.n:
             same({k: v[:r.n] for k, v in ccs.hits_to_numpy(h).items()}, rf, "batched")
+    # an image width over a batch tiles the concatenated rays, which are no image: the same answers
+    ccs.ccs_intersect_batched(handles, dev_rays, hits, ccs.make_opts(pairs=True, image_width=64))
+    torch.cuda.synchronize()
+    for h, rf, r in zip(hits, ref, rays):
+        if r.n:
+            same({k: v[:r.n] for k, v in ccs.hits_to_numpy(h).items()}, rf, "batched, tiled")
     b = ccs.ccs_batch_create(handles, dev_rays, hits, n_rays=[r.n for r in rays])
     ccs.ccs_batch_capture(b, ccs.CCS_BATCH_INTERSECT, ccs.make_opts(pairs=True, cache_slots=1))
     for _ in range(2):
